@@ -1,0 +1,261 @@
+"""FP64 CPU oracle for one IMEX-SSP2(2,2,2) step of resistive GRMHD.
+
+TEST INFRASTRUCTURE ONLY.  This package restates, in plain C called through
+ctypes, what arXiv:2510.18968 (Sec. II-III) computes: primitive->conserved map
+(Eqs. conserved_dens/tau/S), fluxes and sources (Eq. GRRMHD_flux_form), Ohm's
+law (Eq. Ohm_law), HLLE with light-speed bounds (Sec. III), TVD/WENO5
+reconstruction, the IMEX-SSP2(2,2,2) stages (Table imex, Eq. IMEX3) and the
+implicit-E + 1D recovery (Sec. III.B).  It shares no code with the CUDA
+library and never imports it.  Only tests/, __graft_entry__.smoke() and
+bench.py's CPU-baseline / reference legs may use it.
+
+Array conventions: grid fields are interior-only, float64, shape
+(nfields, nz, ny, nx) (x fastest).  Primitive order: rho, p, vx, vy, vz,
+Ex, Ey, Ez, Bx, By, Bz, psi, phi, q.  Conserved order: D, Sx, Sy, Sz, tau,
+Bx, By, Bz, Ex, Ey, Ez, Phi, Psi, Q (densitised).
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+
+_DP = ctypes.POINTER(ctypes.c_double)
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_int * 3),
+        ("dx", ctypes.c_double * 3),
+        ("bc", ctypes.c_int * 3),
+        ("recon", ctypes.c_int),
+        ("gamma_eos", ctypes.c_double),
+        ("kappa", ctypes.c_double),
+        ("sigma_model", ctypes.c_int),
+        ("sigma0", ctypes.c_double),
+        ("sigma_exp", ctypes.c_double),
+        ("D_atmo", ctypes.c_double),
+        ("rho_atmo", ctypes.c_double),
+        ("K_atmo", ctypes.c_double),
+        ("atmo_tol", ctypes.c_double),
+        ("c2p_tol", ctypes.c_double),
+        ("c2p_maxit", ctypes.c_int),
+        ("c2p_wmax", ctypes.c_double),
+        ("qflux_mode", ctypes.c_int),
+    ]
+
+
+DEFAULTS = dict(n=(1, 1, 1), dx=(1.0, 1.0, 1.0), bc=(0, 0, 0), recon=0,
+                gamma_eos=2.0, kappa=1.0, sigma_model=0, sigma0=0.0,
+                sigma_exp=0.0, D_atmo=0.0, rho_atmo=1e-10, K_atmo=100.0,
+                atmo_tol=1e-2, c2p_tol=1e-14, c2p_maxit=100, c2p_wmax=100.0,
+                qflux_mode=0)
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = ctypes.CDLL(path)
+        P = ctypes.POINTER(_Params)
+        i, d = ctypes.c_int, ctypes.c_double
+        L.orc_metric_inverse.argtypes = [_DP, _DP, _DP]
+        L.orc_prim2con.argtypes = [_DP, d, _DP, _DP, d, _DP]
+        L.orc_flux.argtypes = [i, _DP, d, _DP, _DP, d, d, _DP, _DP]
+        L.orc_hlle.argtypes = [i, _DP, _DP, d, _DP, _DP, d, d, _DP]
+        L.orc_recon_line.argtypes = [i, i, _DP, _DP, _DP]
+        L.orc_implicit_E.argtypes = [_DP, _DP, _DP, d, _DP, d, d, _DP]
+        L.orc_implicit_E.restype = i
+        L.orc_con2prim.argtypes = [P, _DP, i, d, d, d, _DP, _DP, _DP, _DP,
+                                   ctypes.POINTER(i)]
+        L.orc_con2prim.restype = i
+        L.orc_rhs.argtypes = [P, _DP, _DP, _DP, _DP, _DP, _DP, _DP, _DP]
+        L.orc_prim2con_grid.argtypes = [P, _DP, _DP, _DP, _DP, _DP]
+        L.orc_step.argtypes = [P, _DP, _DP, _DP, _DP, _DP, _DP, _DP, d, i,
+                               ctypes.POINTER(ctypes.c_longlong)]
+        L.orc_step.restype = i
+        L.orc_set_status_buffer.argtypes = [ctypes.c_void_p]
+        _lib = L
+    return _lib
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(_DP)
+
+
+def _arr(x, n=None):
+    a = np.ascontiguousarray(np.asarray(x, dtype=np.float64))
+    if n is not None:
+        assert a.size == n, (a.shape, n)
+    return a
+
+
+def make_params(**kw):
+    p = dict(DEFAULTS)
+    # grid origin and the GPU precision switch do not enter the oracle's
+    # arithmetic (it is always FP64 and position-free)
+    kw = {k: v for k, v in kw.items() if k not in ("x0", "precision")}
+    unknown = set(kw) - set(DEFAULTS)
+    if unknown:
+        raise KeyError(f"unknown oracle parameters {sorted(unknown)}")
+    p.update(kw)
+    s = _Params()
+    s.n[:] = [int(v) for v in p["n"]]
+    s.dx[:] = [float(v) for v in p["dx"]]
+    s.bc[:] = [int(v) for v in p["bc"]]
+    for k in ("recon", "sigma_model", "c2p_maxit", "qflux_mode"):
+        setattr(s, k, int(p[k]))
+    for k in ("gamma_eos", "kappa", "sigma0", "sigma_exp", "D_atmo", "rho_atmo",
+              "K_atmo", "atmo_tol", "c2p_tol", "c2p_wmax"):
+        setattr(s, k, float(p[k]))
+    return s
+
+
+# ------------------------------------------------------------ pointwise
+
+def metric_inverse(g6):
+    g6 = _arr(g6, 6)
+    gi = np.zeros(6)
+    sg = ctypes.c_double()
+    lib().orc_metric_inverse(_ptr(g6), _ptr(gi), ctypes.byref(sg))
+    return gi, sg.value
+
+
+def prim2con(prim, alpha=1.0, beta=(0, 0, 0), g6=(1, 0, 0, 1, 0, 1), gamma_eos=2.0):
+    prim, beta, g6 = _arr(prim, 14), _arr(beta, 3), _arr(g6, 6)
+    out = np.zeros(14)
+    lib().orc_prim2con(_ptr(prim), float(alpha), _ptr(beta), _ptr(g6),
+                       float(gamma_eos), _ptr(out))
+    return out
+
+
+def flux(d, prim, alpha=1.0, beta=(0, 0, 0), g6=(1, 0, 0, 1, 0, 1), sigma=0.0,
+         gamma_eos=2.0):
+    prim, beta, g6 = _arr(prim, 14), _arr(beta, 3), _arr(g6, 6)
+    F, U = np.zeros(14), np.zeros(14)
+    lib().orc_flux(int(d), _ptr(prim), float(alpha), _ptr(beta), _ptr(g6),
+                   float(sigma), float(gamma_eos), _ptr(F), _ptr(U))
+    return F, U
+
+
+def hlle(d, primL, primR, alpha=1.0, beta=(0, 0, 0), g6=(1, 0, 0, 1, 0, 1),
+         sigma=0.0, gamma_eos=2.0):
+    pL, pR = _arr(primL, 14), _arr(primR, 14)
+    beta, g6 = _arr(beta, 3), _arr(g6, 6)
+    F = np.zeros(14)
+    lib().orc_hlle(int(d), _ptr(pL), _ptr(pR), float(alpha), _ptr(beta),
+                   _ptr(g6), float(sigma), float(gamma_eos), _ptr(F))
+    return F
+
+
+def recon_line(method, u):
+    """Face states of a 1D line: uL[i], uR[i] at the face between u[i], u[i+1]
+    (NaN where the stencil leaves the array)."""
+    u = _arr(u)
+    n = u.size
+    uL, uR = np.zeros(n), np.zeros(n)
+    lib().orc_recon_line(int(method), n, _ptr(u), _ptr(uL), _ptr(uR))
+    return uL, uR
+
+
+def implicit_E(Estar, Bcons, v, alpha=1.0, g6=(1, 0, 0, 1, 0, 1), sigma=0.0, c=0.0):
+    Estar, Bcons, v, g6 = _arr(Estar, 3), _arr(Bcons, 3), _arr(v, 3), _arr(g6, 6)
+    out = np.zeros(3)
+    ok = lib().orc_implicit_E(_ptr(Estar), _ptr(Bcons), _ptr(v), float(alpha),
+                              _ptr(g6), float(sigma), float(c), _ptr(out))
+    if not ok:
+        raise FloatingPointError("singular implicit-E system")
+    return out
+
+
+def con2prim(params, cons, implicit, c, sigma, guess, alpha=1.0,
+             g6=(1, 0, 0, 1, 0, 1)):
+    """Returns (prim, cons_out, iterations, status)."""
+    P = params if isinstance(params, _Params) else make_params(**params)
+    cons, guess, g6 = _arr(cons, 14), _arr(guess, 14), _arr(g6, 6)
+    prim, cout = np.zeros(14), np.zeros(14)
+    it = ctypes.c_int()
+    st = lib().orc_con2prim(ctypes.byref(P), _ptr(cons), int(implicit), float(c),
+                            float(sigma), float(alpha), _ptr(g6), _ptr(guess),
+                            _ptr(prim), _ptr(cout), ctypes.byref(it))
+    return prim, cout, it.value, st
+
+
+# ------------------------------------------------------------ grid
+
+class Metric:
+    """Static 3+1 metric on the interior grid (shape (nz, ny, nx) per field)."""
+
+    def __init__(self, alpha, beta, gamma, K):
+        self.alpha = _arr(alpha)
+        self.beta = _arr(beta)
+        self.gamma = _arr(gamma)
+        self.K = _arr(K)
+
+    @classmethod
+    def flat(cls, shape):
+        N = int(np.prod(shape))
+        g = np.zeros((6, N))
+        g[0] = g[3] = g[5] = 1.0
+        return cls(np.ones(N), np.zeros((3, N)), g, np.zeros((6, N)))
+
+
+def _grid_params(params, shape_zyx):
+    p = dict(params)
+    p.setdefault("n", (shape_zyx[2], shape_zyx[1], shape_zyx[0]))
+    return make_params(**p)
+
+
+def prim2con_grid(params, metric, prim):
+    prim = _arr(prim)
+    P = _grid_params(params, prim.shape[1:])
+    cons = np.zeros_like(prim)
+    lib().orc_prim2con_grid(ctypes.byref(P), _ptr(metric.alpha), _ptr(metric.beta),
+                            _ptr(metric.gamma), _ptr(prim), _ptr(cons))
+    return cons
+
+
+def rhs(params, metric, prim, sigma_field=None, J=None):
+    """Non-stiff right-hand side F(U) of the stage whose primitives are prim.
+    J (3, ...) is the cell-centred stage current used in the charge flux;
+    None evaluates Ohm's law at the face states instead."""
+    prim = _arr(prim)
+    P = _grid_params(params, prim.shape[1:])
+    out = np.zeros_like(prim)
+    sf = None if sigma_field is None else _arr(sigma_field)
+    Jc = None if J is None else _arr(J)
+    lib().orc_rhs(ctypes.byref(P), _ptr(metric.alpha), _ptr(metric.beta),
+                  _ptr(metric.gamma), _ptr(metric.K), _ptr(sf), _ptr(prim), _ptr(Jc),
+                  _ptr(out))
+    return out
+
+
+STAT_NAMES = ("c2p_calls", "c2p_iterations", "c2p_fallbacks", "c2p_failures",
+              "atmo_floor_resets", "c2p_max_iterations", "nan")
+
+
+def step(params, metric, cons, prim, dt, nsteps=1, sigma_field=None,
+         status_out=None):
+    """Advance (cons, prim) in place by nsteps IMEX-SSP2(2,2,2) steps.
+    Returns (status, stats dict).  status 0 ok, -4 recovery failures were
+    reset to atmosphere, -5 non-finite conserved values."""
+    assert cons.dtype == np.float64 and prim.dtype == np.float64
+    assert cons.flags["C_CONTIGUOUS"] and prim.flags["C_CONTIGUOUS"]
+    P = _grid_params(params, prim.shape[1:])
+    stats = (ctypes.c_longlong * 8)()
+    sf = None if sigma_field is None else _arr(sigma_field)
+    if status_out is not None:
+        assert status_out.dtype == np.int32 and status_out.size == 3 * prim[0].size
+        lib().orc_set_status_buffer(status_out.ctypes.data)
+    st = lib().orc_step(ctypes.byref(P), _ptr(metric.alpha), _ptr(metric.beta),
+                        _ptr(metric.gamma), _ptr(metric.K), _ptr(sf), _ptr(cons),
+                        _ptr(prim), float(dt), int(nsteps), stats)
+    if status_out is not None:
+        lib().orc_set_status_buffer(None)
+    return st, dict(zip(STAT_NAMES, list(stats)[:7]))

@@ -1,0 +1,1155 @@
+/*
+ * rmhd_oracle.c -- TEST INFRASTRUCTURE ONLY (see rmhd_oracle.h).
+ *
+ * A plain FP64 CPU restatement of one IMEX-SSP2(2,2,2) step of the resistive
+ * GRMHD system of arXiv:2510.18968.  Every function names the passage it
+ * follows.  It is deliberately slow and literal: index loops over the
+ * Levi-Civita symbol, one face flux per face, no fusion.  Built with
+ * -ffp-contract=off so that no multiply-add is fused behind the reader's back.
+ *
+ * Readings of passages the paper leaves open (all listed with reasons in the
+ * design notes of the repository):
+ *  - Eq. conserved_Sij carries a sqrt(gamma) prefactor, while the S_i flux and
+ *    sources multiply S_ij by sqrt(gamma) again; the stress used here is the
+ *    undensitised one (prefactor dropped), so that flat space is unchanged and
+ *    a static pressure-only state stays static in a curved 3-metric.
+ *  - In the recovery step (iii) the cross product in the numerator of v_i is
+ *    eta_ijk calE^j calB^k (no sqrt(gamma)), the value consistent with
+ *    Eq. conserved_S.
+ *  - Sound speed (Sec. III.B): c_s^2 = Gamma(Gamma-1) eps / (1 + Gamma eps).
+ *  - Characteristic speeds: the paper's literal lambda = +-sqrt(gamma^ii)
+ *    - beta^i/alpha (Sec. III).
+ *  - Metric derivatives: 2nd-order central differences of the cell-centred
+ *    metric, ghosts of the metric follow the grid boundary condition; face
+ *    metric and face conductivity are the mean of the two adjacent cells.
+ *  - Reconstruction acts on (rho, p, v^i, E^i, B^i, psi, phi, q); a face state
+ *    with rho<=0, p<=0 or v^2>=1 falls back to the cell value (all 14).
+ *  - Stiff term stored algebraically: Dt R(i) = (calE(i) - calE*)/gamma_imex.
+ *  - Cell-centred conserved quantities inside the source terms are computed
+ *    from the stage primitives.
+ *  - Recovery: tolerance, iteration cap, a damped 4D Newton fallback on
+ *    (p, v_i) and an atmosphere reset are not given by the paper.
+ */
+#include "rmhd_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+enum { P_RHO, P_P, P_VX, P_VY, P_VZ, P_EX, P_EY, P_EZ, P_BX, P_BY, P_BZ,
+       P_PSI, P_PHI, P_Q };
+enum { C_D, C_SX, C_SY, C_SZ, C_TAU, C_BX, C_BY, C_BZ, C_EX, C_EY, C_EZ,
+       C_PHI, C_PSI, C_Q };
+
+/* gamma of the IMEX-SSP2(2,2,2) tableau (Table imex): 1 - 1/sqrt(2) */
+static double imex_gamma(void) { return 1.0 - 1.0 / sqrt(2.0); }
+
+/* Levi-Civita symbol eta_{ijk} (= eta^{ijk}), indices 0..2 */
+static double levi(int i, int j, int k)
+{
+    return (double)((i - j) * (j - k) * (k - i) / 2);
+}
+
+/* symmetric 3x3 from (xx,xy,xz,yy,yz,zz) */
+static void unpack6(const double g6[6], double g[3][3])
+{
+    g[0][0] = g6[0]; g[0][1] = g6[1]; g[0][2] = g6[2];
+    g[1][0] = g6[1]; g[1][1] = g6[3]; g[1][2] = g6[4];
+    g[2][0] = g6[2]; g[2][1] = g6[4]; g[2][2] = g6[5];
+}
+
+typedef struct {
+    double alpha, beta[3];
+    double g[3][3], gi[3][3];
+    double sg; /* sqrt(det gamma_ij) */
+} metric_pt;
+
+/* Sec. II.A: gamma^{ij} is the algebraic inverse of gamma_ij; sqrt(gamma). */
+static void make_metric(double alpha, const double beta[3], const double g6[6],
+                        metric_pt *m)
+{
+    double g[3][3];
+    unpack6(g6, g);
+    double c00 = g[1][1] * g[2][2] - g[1][2] * g[2][1];
+    double c01 = g[1][2] * g[2][0] - g[1][0] * g[2][2];
+    double c02 = g[1][0] * g[2][1] - g[1][1] * g[2][0];
+    double det = g[0][0] * c00 + g[0][1] * c01 + g[0][2] * c02;
+    double cof[3][3];
+    cof[0][0] = c00; cof[0][1] = c01; cof[0][2] = c02;
+    cof[1][0] = g[0][2] * g[2][1] - g[0][1] * g[2][2];
+    cof[1][1] = g[0][0] * g[2][2] - g[0][2] * g[2][0];
+    cof[1][2] = g[0][1] * g[2][0] - g[0][0] * g[2][1];
+    cof[2][0] = g[0][1] * g[1][2] - g[0][2] * g[1][1];
+    cof[2][1] = g[0][2] * g[1][0] - g[0][0] * g[1][2];
+    cof[2][2] = g[0][0] * g[1][1] - g[0][1] * g[1][0];
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++) {
+            m->g[i][j] = g[i][j];
+            m->gi[i][j] = cof[j][i] / det; /* adjugate / det */
+        }
+    m->sg = sqrt(det);
+    m->alpha = alpha;
+    for (int i = 0; i < 3; i++) m->beta[i] = beta ? beta[i] : 0.0;
+}
+
+void orc_metric_inverse(const double g6[6], double ginv6[6], double *sqrtg)
+{
+    static const double zero3[3] = {0, 0, 0};
+    metric_pt m;
+    make_metric(1.0, zero3, g6, &m);
+    ginv6[0] = m.gi[0][0]; ginv6[1] = m.gi[0][1]; ginv6[2] = m.gi[0][2];
+    ginv6[3] = m.gi[1][1]; ginv6[4] = m.gi[1][2]; ginv6[5] = m.gi[2][2];
+    *sqrtg = m.sg;
+}
+
+static void lower(const metric_pt *m, const double u[3], double ul[3])
+{
+    for (int i = 0; i < 3; i++) {
+        ul[i] = 0.0;
+        for (int j = 0; j < 3; j++) ul[i] += m->g[i][j] * u[j];
+    }
+}
+
+static void raise(const metric_pt *m, const double ul[3], double u[3])
+{
+    for (int i = 0; i < 3; i++) {
+        u[i] = 0.0;
+        for (int j = 0; j < 3; j++) u[i] += m->gi[i][j] * ul[j];
+    }
+}
+
+static double dot3(const double a[3], const double b[3])
+{
+    return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
+}
+
+/* Primitive quantities derived at one point (Sec. II.A, II.C). */
+typedef struct {
+    double rho, p, eps, h, W, v2;
+    double v[3], vl[3], E[3], El[3], B[3], Bl[3];
+    double E2, B2;
+} prim_pt;
+
+static void derive_prim(const double *pr, const metric_pt *m, double Gam,
+                        prim_pt *q)
+{
+    q->rho = pr[P_RHO];
+    q->p = pr[P_P];
+    for (int i = 0; i < 3; i++) {
+        q->v[i] = pr[P_VX + i];
+        q->E[i] = pr[P_EX + i];
+        q->B[i] = pr[P_BX + i];
+    }
+    lower(m, q->v, q->vl);
+    lower(m, q->E, q->El);
+    lower(m, q->B, q->Bl);
+    q->v2 = dot3(q->v, q->vl);
+    q->W = 1.0 / sqrt(1.0 - q->v2);              /* W = (1 - v^2)^(-1/2) */
+    q->eps = q->p / ((Gam - 1.0) * q->rho);      /* p = (Gamma-1) rho eps */
+    q->h = q->rho * (1.0 + q->eps) + q->p;       /* h = rho(1+eps) + p    */
+    q->E2 = dot3(q->E, q->El);
+    q->B2 = dot3(q->B, q->Bl);
+}
+
+/* Eqs. conserved_dens, conserved_tau, conserved_S and the densitised
+ * electromagnetic variables calE = sqrt(g) E, calB = sqrt(g) B,
+ * Psi = sqrt(g) psi, Phi = sqrt(g) phi, Q = sqrt(g) q (Sec. II.D). */
+static void prim_to_cons(const double *pr, const metric_pt *m, double Gam,
+                         const prim_pt *q, double *c)
+{
+    double sg = m->sg;
+    double hW2 = q->h * q->W * q->W;
+    c[C_D] = sg * q->rho * q->W;
+    c[C_TAU] = sg * (hW2 - q->p + 0.5 * (q->E2 + q->B2)) - c[C_D];
+    for (int i = 0; i < 3; i++) {
+        /* epsilon_{ijk} E^j B^k with epsilon_{ijk} = sqrt(g) eta_{ijk} */
+        double cross = 0.0;
+        for (int j = 0; j < 3; j++)
+            for (int k = 0; k < 3; k++)
+                cross += sg * levi(i, j, k) * q->E[j] * q->B[k];
+        c[C_SX + i] = sg * (hW2 * q->vl[i] + cross);
+        c[C_BX + i] = sg * q->B[i];
+        c[C_EX + i] = sg * q->E[i];
+    }
+    c[C_PHI] = sg * pr[P_PHI];
+    c[C_PSI] = sg * pr[P_PSI];
+    c[C_Q] = sg * pr[P_Q];
+    (void)Gam;
+}
+
+void orc_prim2con(const double prim[14], double alpha, const double beta[3],
+                  const double g6[6], double gamma_eos, double cons[14])
+{
+    metric_pt m;
+    prim_pt q;
+    make_metric(alpha, beta, g6, &m);
+    derive_prim(prim, &m, gamma_eos, &q);
+    prim_to_cons(prim, &m, gamma_eos, &q, cons);
+}
+
+/* Flux vector F^d of Eq. GRRMHD_flux_form in direction d.  The current in
+ * the charge flux is Ohm's law (Eq. Ohm_law) at this state, or the given
+ * value *Jd when Jd is not NULL.  Returns also the conserved vector. */
+static void flux_point(int d, const double *pr, const metric_pt *m,
+                       double sigma, double Gam, const double *Jd, double *F,
+                       double *c)
+{
+    prim_pt q;
+    derive_prim(pr, m, Gam, &q);
+    prim_to_cons(pr, m, Gam, &q, c);
+    double a = m->alpha, bd = m->beta[d], sg = m->sg;
+    double hW2 = q.h * q.W * q.W;
+
+    F[C_D] = (a * q.v[d] - bd) * c[C_D];
+    for (int i = 0; i < 3; i++) {
+        /* undensitised mixed stress S^d_i (Eq. conserved_Sij, see header) */
+        double delta = (i == d) ? 1.0 : 0.0;
+        double Sdi = hW2 * q.v[d] * q.vl[i] + delta * q.p
+                     - q.E[d] * q.El[i] - q.B[d] * q.Bl[i]
+                     + 0.5 * delta * (q.E2 + q.B2);
+        F[C_SX + i] = a * sg * Sdi - bd * c[C_SX + i];
+    }
+    double Sup_d = 0.0;
+    for (int j = 0; j < 3; j++) Sup_d += m->gi[d][j] * c[C_SX + j];
+    F[C_TAU] = a * (Sup_d - q.v[d] * c[C_D]) - bd * c[C_TAU];
+
+    double cE[3], cB[3], cEl[3], cBl[3];
+    for (int i = 0; i < 3; i++) {
+        cE[i] = c[C_EX + i];
+        cB[i] = c[C_BX + i];
+    }
+    lower(m, cE, cEl);
+    lower(m, cB, cBl);
+    for (int i = 0; i < 3; i++) {
+        double curlE = 0.0, curlB = 0.0; /* epsilon^{i d j} X_j */
+        for (int j = 0; j < 3; j++) {
+            curlE += levi(i, d, j) / sg * cEl[j];
+            curlB += levi(i, d, j) / sg * cBl[j];
+        }
+        F[C_BX + i] = a * (curlE + m->gi[i][d] * c[C_PHI]) - bd * c[C_BX + i];
+        F[C_EX + i] = -(a * (curlB - m->gi[i][d] * c[C_PSI]) + bd * c[C_EX + i]);
+    }
+    F[C_PHI] = a * c[C_BX + d] - bd * c[C_PHI];
+    F[C_PSI] = a * c[C_EX + d] - bd * c[C_PSI];
+
+    /* Ohm's law: J^d = Q v^d + W sigma [calE^d + eps^{djk} v_j calB_k
+     *                                    - (v_k calE^k) v^d]              */
+    double vxB = 0.0;
+    for (int j = 0; j < 3; j++)
+        for (int k = 0; k < 3; k++)
+            vxB += levi(d, j, k) / sg * q.vl[j] * cBl[k];
+    double vE = dot3(q.vl, cE);
+    double J = c[C_Q] * q.v[d] + q.W * sigma * (cE[d] + vxB - vE * q.v[d]);
+    if (Jd) J = *Jd;
+    F[C_Q] = a * J - bd * c[C_Q];
+}
+
+void orc_flux(int d, const double prim[14], double alpha, const double beta[3],
+              const double g6[6], double sigma, double gamma_eos,
+              double flux[14], double cons[14])
+{
+    metric_pt m;
+    make_metric(alpha, beta, g6, &m);
+    flux_point(d, prim, &m, sigma, gamma_eos, NULL, flux, cons);
+}
+
+/* HLLE flux with the light-speed characteristic speeds of Sec. III:
+ * lambda_+- = +-sqrt(gamma^dd) - beta^d/alpha. */
+static void hlle_point(int d, const double *pL, const double *pR,
+                       const metric_pt *m, double sigma, double Gam,
+                       const double *JL, const double *JR, double *F)
+{
+    double FL[14], FR[14], UL[14], UR[14];
+    flux_point(d, pL, m, sigma, Gam, JL, FL, UL);
+    flux_point(d, pR, m, sigma, Gam, JR, FR, UR);
+    double lp = sqrt(m->gi[d][d]) - m->beta[d] / m->alpha;
+    double lm = -sqrt(m->gi[d][d]) - m->beta[d] / m->alpha;
+    double ap = lp > 0.0 ? lp : 0.0;
+    double am = lm < 0.0 ? lm : 0.0;
+    for (int f = 0; f < 14; f++)
+        F[f] = (ap * FL[f] - am * FR[f] + ap * am * (UR[f] - UL[f])) / (ap - am);
+}
+
+void orc_hlle(int d, const double primL[14], const double primR[14],
+              double alpha, const double beta[3], const double g6[6],
+              double sigma, double gamma_eos, double flux[14])
+{
+    metric_pt m;
+    make_metric(alpha, beta, g6, &m);
+    hlle_point(d, primL, primR, &m, sigma, gamma_eos, NULL, NULL, flux);
+}
+
+/* ---------------- reconstruction (Sec. III: TVD and WENO) ---------------- */
+
+static double minmod2(double a, double b)
+{
+    if (a * b <= 0.0) return 0.0;
+    return fabs(a) <= fabs(b) ? a : b;
+}
+
+static double minmod3(double a, double b, double c)
+{
+    if (a > 0.0 && b > 0.0 && c > 0.0) return fmin(a, fmin(b, c));
+    if (a < 0.0 && b < 0.0 && c < 0.0) return fmax(a, fmax(b, c));
+    return 0.0;
+}
+
+/* limited slope of the middle value um|u0|up */
+static double tvd_slope(int method, double um, double u0, double up)
+{
+    if (method == 0) return minmod2(u0 - um, up - u0);           /* minmod */
+    return minmod3(2.0 * (u0 - um), 0.5 * (up - um), 2.0 * (up - u0)); /* MC2 */
+}
+
+/* Jiang-Shu WENO5 value at the face between c and d, from the stencil
+ * (a,b,c,d,e) = u_{i-2..i+2}; linear weights 1/10, 6/10, 3/10, eps 1e-6,
+ * power 2. */
+static double weno5_face(double a, double b, double c, double d, double e)
+{
+    const double eps = 1e-6;
+    double q0 = (2.0 * a - 7.0 * b + 11.0 * c) / 6.0;
+    double q1 = (-b + 5.0 * c + 2.0 * d) / 6.0;
+    double q2 = (2.0 * c + 5.0 * d - e) / 6.0;
+    double t;
+    double b0, b1, b2;
+    t = a - 2.0 * b + c;       b0 = 13.0 / 12.0 * t * t;
+    t = a - 4.0 * b + 3.0 * c; b0 += 0.25 * t * t;
+    t = b - 2.0 * c + d;       b1 = 13.0 / 12.0 * t * t;
+    t = b - d;                 b1 += 0.25 * t * t;
+    t = c - 2.0 * d + e;       b2 = 13.0 / 12.0 * t * t;
+    t = 3.0 * c - 4.0 * d + e; b2 += 0.25 * t * t;
+    double w0 = 0.1 / ((eps + b0) * (eps + b0));
+    double w1 = 0.6 / ((eps + b1) * (eps + b1));
+    double w2 = 0.3 / ((eps + b2) * (eps + b2));
+    return (w0 * q0 + w1 * q1 + w2 * q2) / (w0 + w1 + w2);
+}
+
+/* Left and right states at the face between s[2] and s[3] of the six-point
+ * stencil s[0..5] = u_{i-2..i+3}. */
+static void recon_face(int method, const double s[6], double *uL, double *uR)
+{
+    if (method == 2) {
+        *uL = weno5_face(s[0], s[1], s[2], s[3], s[4]);
+        *uR = weno5_face(s[5], s[4], s[3], s[2], s[1]);
+    } else {
+        *uL = s[2] + 0.5 * tvd_slope(method, s[1], s[2], s[3]);
+        *uR = s[3] - 0.5 * tvd_slope(method, s[2], s[3], s[4]);
+    }
+}
+
+void orc_recon_line(int method, int n, const double *u, double *uL, double *uR)
+{
+    for (int i = 0; i < n; i++) {
+        uL[i] = NAN;
+        uR[i] = NAN;
+        if (i - 2 < 0 || i + 3 > n - 1) continue;
+        double s[6];
+        for (int o = 0; o < 6; o++) s[o] = u[i - 2 + o];
+        recon_face(method, s, &uL[i], &uR[i]);
+    }
+}
+
+/* ------------- implicit electric field (Sec. III.A, Eq. 3D_NR) ------------- */
+
+/* Solve the 3x3 system A x = b by Gaussian elimination with partial pivoting;
+ * returns 0 if singular. */
+static int solve_dense(int n, double *A, double *b, double *x)
+{
+    for (int col = 0; col < n; col++) {
+        int piv = col;
+        for (int r = col + 1; r < n; r++)
+            if (fabs(A[r * n + col]) > fabs(A[piv * n + col])) piv = r;
+        if (A[piv * n + col] == 0.0) return 0;
+        if (piv != col) {
+            for (int c = 0; c < n; c++) {
+                double t = A[col * n + c];
+                A[col * n + c] = A[piv * n + c];
+                A[piv * n + c] = t;
+            }
+            double t = b[col]; b[col] = b[piv]; b[piv] = t;
+        }
+        for (int r = col + 1; r < n; r++) {
+            double f = A[r * n + col] / A[col * n + col];
+            for (int c = col; c < n; c++) A[r * n + c] -= f * A[col * n + c];
+            b[r] -= f * b[col];
+        }
+    }
+    for (int r = n - 1; r >= 0; r--) {
+        double s = b[r];
+        for (int c = r + 1; c < n; c++) s -= A[r * n + c] * x[c];
+        x[r] = s / A[r * n + r];
+    }
+    return 1;
+}
+
+/* Newton-Raphson on f(calE) = calE - calE_init
+ *   + cc * (calE + eps^{ijk} v_j calB_k - (v_k calE^k) v^i),  cc = c alpha W sigma
+ * (Eq. 3D_NR with c = a_ii Dt).  Starting from E (in/out).  Being linear in
+ * calE, one step lands on the root; further steps only polish rounding. */
+static int implicit_E_nr(const metric_pt *m, const double Estar[3],
+                         const double cB[3], const double v[3], double W,
+                         double sigma, double c, double E[3])
+{
+    double vl[3], cBl[3];
+    lower(m, v, vl);
+    lower(m, cB, cBl);
+    double cc = c * m->alpha * W * sigma;
+    double vxB[3];
+    for (int i = 0; i < 3; i++) {
+        vxB[i] = 0.0;
+        for (int j = 0; j < 3; j++)
+            for (int k = 0; k < 3; k++)
+                vxB[i] += levi(i, j, k) / m->sg * vl[j] * cBl[k];
+    }
+    for (int it = 0; it < 4; it++) {
+        double vE = dot3(vl, E);
+        double f[3], J[9], dE[3];
+        for (int i = 0; i < 3; i++) {
+            f[i] = E[i] - Estar[i] + cc * (E[i] + vxB[i] - vE * v[i]);
+            for (int j = 0; j < 3; j++)
+                J[i * 3 + j] = (i == j ? 1.0 + cc : 0.0) - cc * v[i] * vl[j];
+        }
+        if (!solve_dense(3, J, f, dE)) return 0;
+        double dmax = 0.0, emax = 0.0;
+        for (int i = 0; i < 3; i++) {
+            E[i] -= dE[i];
+            if (fabs(dE[i]) > dmax) dmax = fabs(dE[i]);
+            if (fabs(E[i]) > emax) emax = fabs(E[i]);
+        }
+        if (dmax <= 1e-15 * emax || dmax == 0.0) break;
+    }
+    return 1;
+}
+
+int orc_implicit_E(const double Estar[3], const double Bcons[3],
+                   const double v[3], double alpha, const double g6[6],
+                   double sigma, double c, double Eout[3])
+{
+    metric_pt m;
+    make_metric(alpha, NULL, g6, &m);
+    double vl[3];
+    lower(&m, v, vl);
+    double W = 1.0 / sqrt(1.0 - dot3(v, vl));
+    for (int i = 0; i < 3; i++) Eout[i] = Estar[i];
+    return implicit_E_nr(&m, Estar, Bcons, v, W, sigma, c, Eout);
+}
+
+/* ----------- recovery of primitives (Sec. III.B, steps i-v) ----------- */
+
+typedef struct {
+    const orc_params *P;
+    const metric_pt *m;
+    double D, Sl[3], tau, cB[3], cE0[3];
+    int implicit;
+    double c, sigma, v2max;
+} c2p_in;
+
+/* Step (iii): velocity, W, rho, eps from the conserved variables, the current
+ * electric field and pressure p.  Returns 0 when v^2 >= v2max or the
+ * denominator is not positive. */
+static int recover_fluid(const c2p_in *in, const double cE[3], double p,
+                         double vl[3], double v[3], double *v2, double *W,
+                         double *rho, double *eps)
+{
+    const metric_pt *m = in->m;
+    double sg = m->sg;
+    double cEl[3], cBl[3];
+    lower(m, cE, cEl);
+    lower(m, in->cB, cBl);
+    double EM = (dot3(cE, cEl) + dot3(in->cB, cBl)) / (2.0 * sg);
+    double den = in->tau + in->D + sg * p - EM;
+    for (int i = 0; i < 3; i++) {
+        double cross = 0.0; /* eta_{ijk} calE^j calB^k */
+        for (int j = 0; j < 3; j++)
+            for (int k = 0; k < 3; k++)
+                cross += levi(i, j, k) * cE[j] * in->cB[k];
+        vl[i] = (in->Sl[i] - cross) / den;
+    }
+    raise(m, vl, v);
+    *v2 = dot3(v, vl);
+    if (!(den > 0.0) || !(*v2 < in->v2max)) return 0;
+    *W = 1.0 / sqrt(1.0 - *v2);
+    *rho = in->D / (sg * *W);
+    *eps = (in->tau - in->D * (*W - 1.0) - sg * p * (*W * *W - 1.0) - EM)
+           / (in->D * *W);
+    return 1;
+}
+
+/* energy scale used in the pressure stopping test: tau + D + sqrt(g) p */
+static int p_converged(const c2p_in *in, double dp, double p)
+{
+    double sg = in->m->sg;
+    return fabs(dp) * sg <= in->P->c2p_tol * (in->tau + in->D + sg * p);
+}
+
+/* Steps (i)-(v): guess (p, v) from the previous stage; (ii) calE from the
+ * implicit solve at the current v; (iii) fluid variables; (iv) Newton update
+ * of p with f = p(rho,eps) - p, f' = v^2 c_s^2 - 1; (v) repeat.
+ * Returns 1 on convergence. */
+static int c2p_paper(const c2p_in *in, double *p_io, double v_io[3],
+                     double cE[3], double *rho_o, int *iters)
+{
+    double Gam = in->P->gamma_eos;
+    double p = *p_io, v[3] = {v_io[0], v_io[1], v_io[2]};
+    double hist[3] = {0, 0, 0};
+    for (int it = 1; it <= in->P->c2p_maxit; it++) {
+        *iters = it;
+        if (in->implicit) {
+            double vl[3];
+            lower(in->m, v, vl);
+            double v2 = dot3(v, vl);
+            if (!(v2 < in->v2max)) return 0;
+            double W = 1.0 / sqrt(1.0 - v2);
+            if (!implicit_E_nr(in->m, in->cE0, in->cB, v, W, in->sigma, in->c, cE))
+                return 0;
+        }
+        double vl[3], vn[3], v2, W, rho, eps;
+        if (!recover_fluid(in, cE, p, vl, vn, &v2, &W, &rho, &eps)) return 0;
+        double f = (Gam - 1.0) * rho * eps - p;
+        double cs2 = eps > 0.0 ? Gam * (Gam - 1.0) * eps / (1.0 + Gam * eps) : 0.0;
+        double fp = v2 * cs2 - 1.0;
+        double pn = p - f / fp;
+        if (!(pn > 0.0)) pn = 0.1 * p;
+        double dv = 0.0;
+        for (int i = 0; i < 3; i++)
+            if (fabs(vn[i] - v[i]) > dv) dv = fabs(vn[i] - v[i]);
+        double dp = pn - p;
+        p = pn;
+        for (int i = 0; i < 3; i++) v[i] = vn[i];
+        *rho_o = rho;
+        if (p_converged(in, dp, p) && dv <= in->P->c2p_tol) {
+            *p_io = p;
+            for (int i = 0; i < 3; i++) v_io[i] = v[i];
+            return 1;
+        }
+        /* divergence: three successive growing changes above the noise */
+        double sg = in->m->sg;
+        double meas = dv + fabs(dp) * sg / (in->tau + in->D + sg * p);
+        if (!isfinite(meas)) return 0;
+        if (it >= 3 && meas > hist[0] && hist[0] > hist[1] && hist[1] > hist[2]
+            && meas > 1e3 * in->P->c2p_tol)
+            return 0;
+        hist[2] = hist[1]; hist[1] = hist[0]; hist[0] = meas;
+    }
+    return 0;
+}
+
+/* Residual of the joint recovery system at x = (p, v_1, v_2, v_3):
+ *   r_i = v_i (tau + D + sqrt(g) p - EM) - (S_i - eta_ijk calE^j calB^k)
+ *   r_p = (Gamma-1) rho eps - p,
+ * with calE from the implicit solve at v; both scaled by the energy scale. */
+static int c2p_resid(const c2p_in *in, const double x[4], double r[4],
+                     double cE[3], double *rho_o, double v_o[3])
+{
+    double Gam = in->P->gamma_eos;
+    double sg = in->m->sg;
+    double p = x[0];
+    double vl[3] = {x[1], x[2], x[3]}, v[3];
+    raise(in->m, vl, v);
+    double v2 = dot3(v, vl);
+    if (!(p > 0.0) || !(v2 < in->v2max)) return 0;
+    double W = 1.0 / sqrt(1.0 - v2);
+    if (in->implicit) {
+        for (int i = 0; i < 3; i++) cE[i] = in->cE0[i];
+        if (!implicit_E_nr(in->m, in->cE0, in->cB, v, W, in->sigma, in->c, cE))
+            return 0;
+    } else {
+        for (int i = 0; i < 3; i++) cE[i] = in->cE0[i];
+    }
+    double cEl[3], cBl[3];
+    lower(in->m, cE, cEl);
+    lower(in->m, in->cB, cBl);
+    double EM = (dot3(cE, cEl) + dot3(in->cB, cBl)) / (2.0 * sg);
+    double den = in->tau + in->D + sg * p - EM;
+    double scale = in->tau + in->D + sg * p;
+    for (int i = 0; i < 3; i++) {
+        double cross = 0.0;
+        for (int j = 0; j < 3; j++)
+            for (int k = 0; k < 3; k++)
+                cross += levi(i, j, k) * cE[j] * in->cB[k];
+        r[1 + i] = (vl[i] * den - (in->Sl[i] - cross)) / scale;
+    }
+    double rho = in->D / (sg * W);
+    double eps = (in->tau - in->D * (W - 1.0) - sg * p * (W * W - 1.0) - EM)
+                 / (in->D * W);
+    r[0] = ((Gam - 1.0) * rho * eps - p) * sg / scale;
+    *rho_o = rho;
+    for (int i = 0; i < 3; i++) v_o[i] = v[i];
+    return 1;
+}
+
+static double norm4(const double r[4])
+{
+    return sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2] + r[3] * r[3]);
+}
+
+/* Fallback: damped Newton on (p, v_i) with a forward-difference Jacobian. */
+static int c2p_newton4(const c2p_in *in, double *p_io, double v_io[3],
+                       double cE[3], double *rho_o, int *iters)
+{
+    double x[4], r[4], vdummy[3], rho;
+    double vl[3];
+    lower(in->m, v_io, vl);
+    x[0] = *p_io;
+    for (int i = 0; i < 3; i++) x[1 + i] = vl[i];
+    if (!c2p_resid(in, x, r, cE, &rho, vdummy)) {
+        x[1] = x[2] = x[3] = 0.0;
+        if (!(x[0] > 0.0)) x[0] = in->P->K_atmo * pow(in->P->rho_atmo, in->P->gamma_eos);
+        if (!c2p_resid(in, x, r, cE, &rho, vdummy)) return 0;
+    }
+    for (int it = 1; it <= 50; it++) {
+        *iters = it;
+        double J[16];
+        for (int col = 0; col < 4; col++) {
+            double xh[4] = {x[0], x[1], x[2], x[3]}, rh[4], ceh[3], rhoh, vh[3];
+            double h = col == 0 ? 1e-7 * x[0] : 1e-7;
+            xh[col] += h;
+            if (!c2p_resid(in, xh, rh, ceh, &rhoh, vh)) {
+                h = -h;
+                xh[col] = x[col] + h;
+                if (!c2p_resid(in, xh, rh, ceh, &rhoh, vh)) return 0;
+            }
+            for (int row = 0; row < 4; row++) J[row * 4 + col] = (rh[row] - r[row]) / h;
+        }
+        double rhs[4] = {-r[0], -r[1], -r[2], -r[3]}, dx[4];
+        if (!solve_dense(4, J, rhs, dx)) return 0;
+        double lam = 1.0, n0 = norm4(r);
+        double xt[4], rt[4], cet[3], rhot, vt[3];
+        int accepted = 0;
+        for (int ls = 0; ls < 40; ls++) {
+            for (int i = 0; i < 4; i++) xt[i] = x[i] + lam * dx[i];
+            if (c2p_resid(in, xt, rt, cet, &rhot, vt) && norm4(rt) < n0) {
+                accepted = 1;
+                break;
+            }
+            lam *= 0.5;
+        }
+        if (!accepted) {
+            /* no decrease possible: at the rounding floor if the step is tiny */
+            double sg = in->m->sg;
+            double dvm = fmax(fabs(dx[1]), fmax(fabs(dx[2]), fabs(dx[3])));
+            if (fabs(dx[0]) * sg <= in->P->c2p_tol * (in->tau + in->D + sg * x[0])
+                && dvm <= in->P->c2p_tol)
+                break;
+            return 0;
+        }
+        double stepp = lam * dx[0];
+        double stepv = fmax(fabs(lam * dx[1]), fmax(fabs(lam * dx[2]), fabs(lam * dx[3])));
+        for (int i = 0; i < 4; i++) { x[i] = xt[i]; r[i] = rt[i]; }
+        if (p_converged(in, stepp, x[0]) && stepv <= in->P->c2p_tol) break;
+        if (it == 50) return 0;
+    }
+    double v[3];
+    if (!c2p_resid(in, x, r, cE, &rho, v)) return 0;
+    *p_io = x[0];
+    for (int i = 0; i < 3; i++) v_io[i] = v[i];
+    *rho_o = rho;
+    return 1;
+}
+
+/* Returns status: 0 converged (paper iteration), 1 converged (fallback),
+ * 2 failed -> atmosphere, 3 converged but rho < rho_atmo -> atmosphere. */
+int orc_con2prim(const orc_params *P, const double cons_in[14], int implicit,
+                 double c, double sigma, double alpha, const double g6[6],
+                 const double guess[14], double prim[14], double cons_out[14],
+                 int *iters)
+{
+    metric_pt m;
+    make_metric(alpha, NULL, g6, &m);
+    c2p_in in;
+    in.P = P;
+    in.m = &m;
+    in.D = cons_in[C_D];
+    in.tau = cons_in[C_TAU];
+    for (int i = 0; i < 3; i++) {
+        in.Sl[i] = cons_in[C_SX + i];
+        in.cB[i] = cons_in[C_BX + i];
+        in.cE0[i] = cons_in[C_EX + i];
+    }
+    in.implicit = implicit;
+    in.c = c;
+    in.sigma = sigma;
+    in.v2max = 1.0 - 1.0 / (P->c2p_wmax * P->c2p_wmax);
+
+    double p = guess[P_P], v[3] = {guess[P_VX], guess[P_VY], guess[P_VZ]};
+    double cE[3] = {in.cE0[0], in.cE0[1], in.cE0[2]};
+    double rho = 0.0;
+    int it1 = 0, it2 = 0, status;
+    if (c2p_paper(&in, &p, v, cE, &rho, &it1)) {
+        status = 0;
+    } else {
+        p = guess[P_P];
+        for (int i = 0; i < 3; i++) {
+            v[i] = guess[P_VX + i];
+            cE[i] = in.cE0[i];
+        }
+        status = c2p_newton4(&in, &p, v, cE, &rho, &it2) ? 1 : 2;
+    }
+    *iters = it1 + it2;
+    /* atmosphere floor: rho below rho_atmo (1 + atmo_tol) is reset */
+    if (status < 2 && !(rho >= P->rho_atmo * (1.0 + P->atmo_tol))) status = 3;
+
+    for (int f = 0; f < 14; f++) cons_out[f] = cons_in[f];
+    if (status >= 2) {
+        /* atmosphere: rho_atmo, v = 0, p = K rho^Gamma; calE from the
+         * implicit solve at v = 0 */
+        rho = P->rho_atmo;
+        p = P->K_atmo * pow(P->rho_atmo, P->gamma_eos);
+        v[0] = v[1] = v[2] = 0.0;
+        for (int i = 0; i < 3; i++)
+            cE[i] = implicit ? in.cE0[i] / (1.0 + c * alpha * sigma) : in.cE0[i];
+    }
+    double sg = m.sg;
+    prim[P_RHO] = rho;
+    prim[P_P] = p;
+    for (int i = 0; i < 3; i++) {
+        prim[P_VX + i] = v[i];
+        prim[P_EX + i] = cE[i] / sg;
+        prim[P_BX + i] = in.cB[i] / sg;
+        cons_out[C_EX + i] = cE[i];
+    }
+    prim[P_PSI] = cons_in[C_PSI] / sg;
+    prim[P_PHI] = cons_in[C_PHI] / sg;
+    prim[P_Q] = cons_in[C_Q] / sg;
+    if (status >= 2) {
+        double full[14];
+        orc_prim2con(prim, alpha, NULL, g6, P->gamma_eos, full);
+        cons_out[C_D] = full[C_D];
+        cons_out[C_TAU] = full[C_TAU];
+        for (int i = 0; i < 3; i++) cons_out[C_SX + i] = full[C_SX + i];
+    }
+    return status;
+}
+
+/* --------------------------- grid operations --------------------------- */
+
+typedef struct {
+    const orc_params *P;
+    const double *alpha, *beta, *gam, *K, *sigma_field;
+    int nx, ny, nz;
+    long N;
+} grid;
+
+/* boundary-condition index map: periodic wrap or copy nearest (Sec. IV) */
+static int bmap(int i, int n, int bc)
+{
+    if (n == 1) return 0;
+    if (bc == 0) return ((i % n) + n) % n;
+    return i < 0 ? 0 : (i >= n ? n - 1 : i);
+}
+
+static long cidx(const grid *G, int i, int j, int k)
+{
+    i = bmap(i, G->nx, G->P->bc[0]);
+    j = bmap(j, G->ny, G->P->bc[1]);
+    k = bmap(k, G->nz, G->P->bc[2]);
+    return ((long)k * G->ny + j) * G->nx + i;
+}
+
+static void cell_metric(const grid *G, long c, metric_pt *m)
+{
+    double beta[3], g6[6];
+    for (int i = 0; i < 3; i++) beta[i] = G->beta[i * G->N + c];
+    for (int i = 0; i < 6; i++) g6[i] = G->gam[i * G->N + c];
+    make_metric(G->alpha[c], beta, g6, m);
+}
+
+/* Conductivity models: uniform, tabulated profile, sigma0 D^gamma_sigma
+ * (Eq. sigma_evol) and sigma0 max(1 - D_atmo/D, 0)^2 (Eq. dynamo_sigma). */
+static double sigma_of(const orc_params *P, const double *field, long c, double D)
+{
+    switch (P->sigma_model) {
+    case 1: return P->sigma0 * field[c];
+    case 2: return P->sigma0 * pow(D, P->sigma_exp);
+    case 3: {
+        double t = 1.0 - P->D_atmo / D;
+        if (!(t > 0.0)) t = 0.0;
+        return P->sigma0 * t * t;
+    }
+    default: return P->sigma0;
+    }
+}
+
+static double sigma_cell_from_prim(const grid *G, const double *prim, long c)
+{
+    if (G->P->sigma_model < 2) return sigma_of(G->P, G->sigma_field, c, 0.0);
+    double pr[14], cons[14];
+    metric_pt m;
+    prim_pt q;
+    for (int f = 0; f < 14; f++) pr[f] = prim[f * G->N + c];
+    cell_metric(G, c, &m);
+    derive_prim(pr, &m, G->P->gamma_eos, &q);
+    prim_to_cons(pr, &m, G->P->gamma_eos, &q, cons);
+    return sigma_of(G->P, G->sigma_field, c, cons[C_D]);
+}
+
+/* Flux through the face between cell (i,j,k) and its +d neighbour.  With
+ * Jcell (3 x N, the cell-centred current of the stage) the charge-flux
+ * current J^d is reconstructed from it like a primitive; without it Ohm's
+ * law is evaluated at the reconstructed face states. */
+static void face_flux(const grid *G, const double *prim, const double *Jcell,
+                      int d, int i, int j, int k, double F[14])
+{
+    const orc_params *P = G->P;
+    int o[3] = {0, 0, 0};
+    double sL[15], sR[15];
+    long cL = cidx(G, i, j, k);
+    long cR = cidx(G, i + (d == 0), j + (d == 1), k + (d == 2));
+    for (int f = 0; f < 14; f++) {
+        double s[6];
+        for (int t = -2; t <= 3; t++) {
+            o[d] = t;
+            s[t + 2] = prim[f * G->N + cidx(G, i + o[0], j + o[1], k + o[2])];
+        }
+        recon_face(P->recon, s, &sL[f], &sR[f]);
+    }
+    if (Jcell) {
+        double s[6];
+        for (int t = -2; t <= 3; t++) {
+            o[d] = t;
+            s[t + 2] = Jcell[d * G->N + cidx(G, i + o[0], j + o[1], k + o[2])];
+        }
+        recon_face(P->recon, s, &sL[14], &sR[14]);
+    }
+    /* face metric: mean of the two cells */
+    double alpha = 0.5 * (G->alpha[cL] + G->alpha[cR]);
+    double beta[3], g6[6];
+    for (int a = 0; a < 3; a++)
+        beta[a] = 0.5 * (G->beta[a * G->N + cL] + G->beta[a * G->N + cR]);
+    for (int a = 0; a < 6; a++)
+        g6[a] = 0.5 * (G->gam[a * G->N + cL] + G->gam[a * G->N + cR]);
+    metric_pt m;
+    make_metric(alpha, beta, g6, &m);
+    /* unphysical reconstructed states fall back to the cell values */
+    double *side[2] = {sL, sR};
+    long cell[2] = {cL, cR};
+    for (int s = 0; s < 2; s++) {
+        double v[3] = {side[s][P_VX], side[s][P_VY], side[s][P_VZ]}, vl[3];
+        lower(&m, v, vl);
+        double v2 = dot3(v, vl);
+        if (!(side[s][P_RHO] > 0.0) || !(side[s][P_P] > 0.0) || !(v2 < 1.0)) {
+            for (int f = 0; f < 14; f++) side[s][f] = prim[f * G->N + cell[s]];
+            if (Jcell) side[s][14] = Jcell[d * G->N + cell[s]];
+        }
+    }
+    double sigma = 0.5 * (sigma_cell_from_prim(G, prim, cL)
+                          + sigma_cell_from_prim(G, prim, cR));
+    if (Jcell)
+        hlle_point(d, sL, sR, &m, sigma, P->gamma_eos, &sL[14], &sR[14], F);
+    else
+        hlle_point(d, sL, sR, &m, sigma, P->gamma_eos, NULL, NULL, F);
+}
+
+/* d(field)/dx_d at cell (i,j,k) by 2nd-order central differences */
+static double dcell(const grid *G, const double *fld, int d, int i, int j, int k)
+{
+    int n[3] = {G->nx, G->ny, G->nz};
+    if (n[d] == 1) return 0.0;
+    long cp = cidx(G, i + (d == 0), j + (d == 1), k + (d == 2));
+    long cm = cidx(G, i - (d == 0), j - (d == 1), k - (d == 2));
+    return (fld[cp] - fld[cm]) / (2.0 * G->P->dx[d]);
+}
+
+/* Source vector S of Eq. GRRMHD_flux_form without the stiff part of -alpha J
+ * (i.e. with -alpha Q v^i only, Sec. III.A split F_E / R_E). */
+static void sources(const grid *G, const double *prim, int i, int j, int k,
+                    double S[14])
+{
+    const orc_params *P = G->P;
+    long c = cidx(G, i, j, k);
+    metric_pt m;
+    cell_metric(G, c, &m);
+    double pr[14], cons[14];
+    for (int f = 0; f < 14; f++) pr[f] = prim[f * G->N + c];
+    prim_pt q;
+    derive_prim(pr, &m, P->gamma_eos, &q);
+    prim_to_cons(pr, &m, P->gamma_eos, &q, cons);
+
+    double da[3], db[3][3], dg[3][3][3], Kij[3][3];
+    double k6[6];
+    for (int a = 0; a < 6; a++) k6[a] = G->K[a * G->N + c];
+    unpack6(k6, Kij);
+    for (int d = 0; d < 3; d++) {
+        da[d] = dcell(G, G->alpha, d, i, j, k);
+        for (int a = 0; a < 3; a++) db[d][a] = dcell(G, G->beta + a * G->N, d, i, j, k);
+        double d6[6];
+        for (int a = 0; a < 6; a++) d6[a] = dcell(G, G->gam + a * G->N, d, i, j, k);
+        unpack6(d6, dg[d]); /* dg[d][a][b] = d_d gamma_ab */
+    }
+    /* Christoffel symbols Gamma^a_bc = 1/2 g^{al}(d_b g_lc + d_c g_lb - d_l g_bc) */
+    double Chr[3][3][3];
+    for (int a = 0; a < 3; a++)
+        for (int b = 0; b < 3; b++)
+            for (int cc = 0; cc < 3; cc++) {
+                double s = 0.0;
+                for (int l = 0; l < 3; l++)
+                    s += m.gi[a][l] * (dg[b][l][cc] + dg[cc][l][b] - dg[l][b][cc]);
+                Chr[a][b][cc] = 0.5 * s;
+            }
+    double Ktr = 0.0;
+    for (int a = 0; a < 3; a++)
+        for (int b = 0; b < 3; b++) Ktr += m.gi[a][b] * Kij[a][b];
+
+    /* undensitised stress with both indices up */
+    double hW2 = q.h * q.W * q.W;
+    double Sup[3][3];
+    for (int a = 0; a < 3; a++)
+        for (int b = 0; b < 3; b++)
+            Sup[a][b] = hW2 * q.v[a] * q.v[b] + m.gi[a][b] * q.p
+                        - q.E[a] * q.E[b] - q.B[a] * q.B[b]
+                        + 0.5 * m.gi[a][b] * (q.E2 + q.B2);
+    double Sl[3] = {cons[C_SX], cons[C_SY], cons[C_SZ]}, Su[3];
+    raise(&m, Sl, Su);
+    double al = m.alpha, sg = m.sg;
+
+    for (int f = 0; f < 14; f++) S[f] = 0.0;
+    for (int a = 0; a < 3; a++) {
+        double s = 0.0;
+        for (int b = 0; b < 3; b++)
+            for (int cc = 0; cc < 3; cc++) s += Sup[b][cc] * dg[a][b][cc];
+        s *= 0.5 * al * sg;
+        for (int b = 0; b < 3; b++) s += Sl[b] * db[a][b];
+        s -= (cons[C_TAU] + cons[C_D]) * da[a];
+        S[C_SX + a] = s;
+    }
+    {
+        double s = 0.0;
+        for (int a = 0; a < 3; a++)
+            for (int b = 0; b < 3; b++) s += Sup[a][b] * Kij[a][b];
+        s *= al * sg;
+        for (int a = 0; a < 3; a++) s -= Su[a] * da[a];
+        S[C_TAU] = s;
+    }
+    for (int a = 0; a < 3; a++) {
+        /* gamma^{ab} d_b alpha - alpha gamma^{bc} Gamma^a_bc */
+        double G1 = 0.0;
+        for (int b = 0; b < 3; b++) G1 += m.gi[a][b] * da[b];
+        double G2 = 0.0;
+        for (int b = 0; b < 3; b++)
+            for (int cc = 0; cc < 3; cc++) G2 += m.gi[b][cc] * Chr[a][b][cc];
+        double geo = G1 - al * G2;
+        double sB = 0.0, sE = 0.0;
+        for (int b = 0; b < 3; b++) {
+            sB -= cons[C_BX + b] * db[b][a];
+            sE -= cons[C_EX + b] * db[b][a];
+        }
+        S[C_BX + a] = sB + cons[C_PHI] * geo;
+        S[C_EX + a] = sE + cons[C_PSI] * geo - al * cons[C_Q] * q.v[a];
+    }
+    double Bda = 0.0, Eda = 0.0;
+    for (int b = 0; b < 3; b++) {
+        Bda += cons[C_BX + b] * da[b];
+        Eda += cons[C_EX + b] * da[b];
+    }
+    S[C_PHI] = -al * cons[C_PHI] * Ktr + Bda - al * P->kappa * cons[C_PHI];
+    S[C_PSI] = -al * cons[C_PSI] * Ktr + Eda + al * cons[C_Q] - al * P->kappa * cons[C_PSI];
+}
+
+/* Non-stiff right-hand side F(U) = -d_k F^k + S (Sec. II.D / III.A) */
+static void rhs_grid(const grid *G, const double *prim, const double *Jcell,
+                     double *rhs)
+{
+    const orc_params *P = G->P;
+    int n[3] = {G->nx, G->ny, G->nz};
+    long N = G->N;
+    for (long a = 0; a < 14 * N; a++) rhs[a] = 0.0;
+    for (int d = 0; d < 3; d++) {
+        if (n[d] == 1) continue;
+        /* face fluxes: face index fi = 0..n[d] lies between cells fi-1, fi */
+        int m[3] = {n[0], n[1], n[2]};
+        m[d] += 1;
+        long Mf = (long)m[0] * m[1] * m[2];
+        double *Ff = (double *)malloc(sizeof(double) * 14 * Mf);
+        for (int k = 0; k < m[2]; k++)
+            for (int j = 0; j < m[1]; j++)
+                for (int i = 0; i < m[0]; i++) {
+                    double F[14];
+                    face_flux(G, prim, Jcell, d, i - (d == 0), j - (d == 1),
+                              k - (d == 2), F);
+                    long fidx = ((long)k * m[1] + j) * m[0] + i;
+                    for (int f = 0; f < 14; f++) Ff[f * Mf + fidx] = F[f];
+                }
+        for (int k = 0; k < n[2]; k++)
+            for (int j = 0; j < n[1]; j++)
+                for (int i = 0; i < n[0]; i++) {
+                    long c = ((long)k * n[1] + j) * n[0] + i;
+                    long fm = ((long)k * m[1] + j) * m[0] + i;
+                    long fp = ((long)(k + (d == 2)) * m[1] + (j + (d == 1))) * m[0]
+                              + (i + (d == 0));
+                    for (int f = 0; f < 14; f++)
+                        rhs[f * N + c] -= (Ff[f * Mf + fp] - Ff[f * Mf + fm]) / P->dx[d];
+                }
+        free(Ff);
+    }
+    for (int k = 0; k < n[2]; k++)
+        for (int j = 0; j < n[1]; j++)
+            for (int i = 0; i < n[0]; i++) {
+                long c = ((long)k * n[1] + j) * n[0] + i;
+                double S[14];
+                sources(G, prim, i, j, k, S);
+                for (int f = 0; f < 14; f++) rhs[f * N + c] += S[f];
+            }
+}
+
+static void make_grid(grid *G, const orc_params *P, const double *alpha,
+                      const double *beta, const double *gam, const double *K,
+                      const double *sigma_field)
+{
+    G->P = P;
+    G->alpha = alpha;
+    G->beta = beta;
+    G->gam = gam;
+    G->K = K;
+    G->sigma_field = sigma_field;
+    G->nx = P->n[0];
+    G->ny = P->n[1];
+    G->nz = P->n[2];
+    G->N = (long)G->nx * G->ny * G->nz;
+}
+
+void orc_rhs(const orc_params *P, const double *alpha, const double *beta,
+             const double *gam, const double *K, const double *sigma_field,
+             const double *prim, const double *Jcell, double *rhs)
+{
+    grid G;
+    make_grid(&G, P, alpha, beta, gam, K, sigma_field);
+    rhs_grid(&G, prim, Jcell, rhs);
+}
+
+void orc_prim2con_grid(const orc_params *P, const double *alpha,
+                       const double *beta, const double *gam,
+                       const double *prim, double *cons)
+{
+    grid G;
+    make_grid(&G, P, alpha, beta, gam, NULL, NULL);
+    for (long c = 0; c < G.N; c++) {
+        metric_pt m;
+        cell_metric(&G, c, &m);
+        double pr[14], cn[14];
+        for (int f = 0; f < 14; f++) pr[f] = prim[f * G.N + c];
+        prim_pt q;
+        derive_prim(pr, &m, P->gamma_eos, &q);
+        prim_to_cons(pr, &m, P->gamma_eos, &q, cn);
+        for (int f = 0; f < 14; f++) cons[f * G.N + c] = cn[f];
+    }
+}
+
+/* Optional per-cell recovery status of the last step, 3 records per cell
+ * (stage 1, stage 2, final), for diagnostics in the tests. */
+static int *dbg_status = NULL;
+void orc_set_status_buffer(int *buf) { dbg_status = buf; }
+
+/* Pointwise recovery over the grid.  implicit: solve the stiff calE with
+ * c = gamma_imex dt; cons is updated in place (calE and, after an
+ * atmosphere reset, D, S_i, tau). */
+static void c2p_grid(const grid *G, double *cons, const double *guess,
+                     double *prim, int implicit, double c, long long stats[8],
+                     int stage)
+{
+    const orc_params *P = G->P;
+    long N = G->N;
+    for (long cell = 0; cell < N; cell++) {
+        double cin[14], g[14], pr[14], cout[14], g6[6];
+        for (int f = 0; f < 14; f++) {
+            cin[f] = cons[f * N + cell];
+            g[f] = guess[f * N + cell];
+        }
+        for (int a = 0; a < 6; a++) g6[a] = G->gam[a * N + cell];
+        double sigma = implicit ? sigma_of(P, G->sigma_field, cell, cin[C_D]) : 0.0;
+        int it = 0;
+        int st = orc_con2prim(P, cin, implicit, c, sigma, G->alpha[cell], g6, g,
+                              pr, cout, &it);
+        stats[0] += 1;
+        stats[1] += it;
+        if (st == 1) stats[2] += 1;
+        if (st == 2) stats[3] += 1;
+        if (st == 3) stats[4] += 1;
+        if (it > stats[5]) stats[5] = it;
+        if (dbg_status) dbg_status[stage * N + cell] = st;
+        for (int f = 0; f < 14; f++) {
+            prim[f * N + cell] = pr[f];
+            cons[f * N + cell] = cout[f];
+        }
+    }
+}
+
+/* Cell-centred current of an implicit stage.  Ohm's law (Eq. Ohm_law) is
+ * J = Q v + W sigma [...] and the stiff source is R_E = -alpha W sigma [...],
+ * so at the stage's root J^i = Q v^i - (Dt R_E^i) / (alpha Dt), with Dt R_E
+ * the stored stiff increment: bounded for any sigma. */
+static void stage_current(const grid *G, const double *U, const double *prim,
+                          const double *dR, double dt, double *J)
+{
+    long N = G->N;
+    for (int a = 0; a < 3; a++)
+        for (long c = 0; c < N; c++)
+            J[a * N + c] = U[C_Q * N + c] * prim[(P_VX + a) * N + c]
+                           - dR[a * N + c] / (G->alpha[c] * dt);
+}
+
+/* One IMEX-SSP2(2,2,2) step, literally Eqs. (U^(1), U^(2), IMEX3):
+ *   U1 = U^n + gamma dt R[U1]
+ *   U2 = U^n + dt F[U1] + dt ((1-2gamma) R[U1] + gamma R[U2])
+ *   U^{n+1} = U^n + dt/2 (F[U1] + F[U2]) + dt/2 (R[U1] + R[U2])
+ * R acts on calE only (Sec. III.A); each implicit stage is solved jointly
+ * with the recovery (Sec. III.B); U^{n+1} is then recovered with calE fixed. */
+int orc_step(const orc_params *P, const double *alpha, const double *beta,
+             const double *gam, const double *K, const double *sigma_field,
+             double *cons, double *prim, double dt, int nsteps,
+             long long stats[8])
+{
+    grid G;
+    make_grid(&G, P, alpha, beta, gam, K, sigma_field);
+    long N = G.N;
+    double g = imex_gamma();
+    double *U1 = (double *)malloc(sizeof(double) * 14 * N);
+    double *U2 = (double *)malloc(sizeof(double) * 14 * N);
+    double *W1 = (double *)malloc(sizeof(double) * 14 * N);
+    double *W2 = (double *)malloc(sizeof(double) * 14 * N);
+    double *F1 = (double *)malloc(sizeof(double) * 14 * N);
+    double *F2 = (double *)malloc(sizeof(double) * 14 * N);
+    double *dR1 = (double *)malloc(sizeof(double) * 3 * N);
+    double *dR2 = (double *)malloc(sizeof(double) * 3 * N);
+    double *Jc = (double *)malloc(sizeof(double) * 3 * N);
+    double *Es2 = (double *)malloc(sizeof(double) * 3 * N);
+    const double *Jarg = P->qflux_mode == 0 ? Jc : NULL;
+    int status = 0;
+    for (int s = 0; s < 8; s++) stats[s] = 0;
+    for (int step = 0; step < nsteps; step++) {
+        /* stage 1: purely implicit */
+        memcpy(U1, cons, sizeof(double) * 14 * N);
+        c2p_grid(&G, U1, prim, W1, 1, g * dt, stats, 0);
+        for (int a = 0; a < 3; a++)
+            for (long c = 0; c < N; c++)
+                dR1[a * N + c] = (U1[(C_EX + a) * N + c] - cons[(C_EX + a) * N + c]) / g;
+        /* stage 2: explicit part, then implicit */
+        stage_current(&G, U1, W1, dR1, dt, Jc);
+        rhs_grid(&G, W1, Jarg, F1);
+        for (long a = 0; a < 14 * N; a++) U2[a] = cons[a] + dt * F1[a];
+        for (int a = 0; a < 3; a++)
+            for (long c = 0; c < N; c++)
+                U2[(C_EX + a) * N + c] += (1.0 - 2.0 * g) * dR1[a * N + c];
+        for (int a = 0; a < 3; a++)   /* keep calE* of stage 2 */
+            for (long c = 0; c < N; c++) Es2[a * N + c] = U2[(C_EX + a) * N + c];
+        c2p_grid(&G, U2, W1, W2, 1, g * dt, stats, 1);
+        for (int a = 0; a < 3; a++)
+            for (long c = 0; c < N; c++)
+                dR2[a * N + c] = (U2[(C_EX + a) * N + c] - Es2[a * N + c]) / g;
+        /* final assembly (Eq. IMEX3) */
+        stage_current(&G, U2, W2, dR2, dt, Jc);
+        rhs_grid(&G, W2, Jarg, F2);
+        for (long a = 0; a < 14 * N; a++) cons[a] = cons[a] + 0.5 * dt * (F1[a] + F2[a]);
+        for (int a = 0; a < 3; a++)
+            for (long c = 0; c < N; c++)
+                cons[(C_EX + a) * N + c] += 0.5 * (dR1[a * N + c] + dR2[a * N + c]);
+        for (long a = 0; a < 14 * N; a++)
+            if (!isfinite(cons[a])) { status = -5; stats[6] = 1; }
+        /* recovery of U^{n+1} with calE fixed */
+        c2p_grid(&G, cons, W2, prim, 0, 0.0, stats, 2);
+        if (status) break;
+    }
+    free(U1); free(U2); free(W1); free(W2); free(F1); free(F2);
+    free(dR1); free(dR2); free(Jc); free(Es2);
+    if (status) return status;
+    return stats[3] > 0 ? -4 : 0;
+}
