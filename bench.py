@@ -1,0 +1,287 @@
+"""Benchmark: zone-updates/s of the IMEX-SSP2(2,2,2) resistive-GRMHD step on
+the 256^3 cylindrical-blast workload (flat space, MC2 + HLLE, sigma = 1e3),
+mixed precision (FP32 reconstruction/fluxes, FP64 recovery and accumulation)
+as the headline and the FP64 path beside it.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--n 256] [--precision mixed|fp64]
+
+One JSON line on stdout (rank 0).  With N > 1 (torchrun) every rank runs its
+own replica of the workload on its own GPU (the method has no data-path
+exchange between independent replicas; value = total zone-updates / max time).
+--impl reference times the FP64 CPU oracle on a bounded z-slab of the same
+workload on the host cores.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "zone-updates/s per IMEX-RK2 step at 256^3 (FP64 vs mixed) + % HBM roofline"
+UNIT = "zone-updates/s"
+
+# Measured on this machine's B300 (HBM copy bandwidth written by the driver, FP64
+# and FP32 FMA throughput by our own probe): see the design notes.
+FP64_PEAK_TFLOPS = 1.203   # 148 SM x 2 DFMA/clk x 2 flop x 2.032 GHz
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return d.get("hbm_gbs", 6400.0), "measured"
+    except OSError:
+        return 6400.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons during the timed region."""
+
+    def __init__(self, index=0):
+        self.index = index
+        self.samples = []
+        self.proc = None
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 7:
+                self.samples.append(parts)
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4)
+                          if s[3 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.samples)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload(n):
+    return W.cyl_blast(n=n)
+
+
+# algorithmic HBM bytes per zone of each kernel group (state arrays read or
+# written once per launch; fp64 state, see the design notes)
+ALG_BYTES = {
+    # stage 1: U^n 14 + guess (p, v) 4 in; P1 14 + dR1 3 + J1 3 out
+    "stage1_recovery": 8 * (14 + 4 + 14 + 3 + 3),
+    # fluxes of one direction: P 14 + J 1 in (stencil read once), F 14 out
+    "flux": 8 * (14 + 1 + 14),
+    # stage 2: U 14, P1 14, F 3x14, dR1 3 in; P2 14, V 14, J2 3 out
+    "stage2_rhs_recovery": 8 * (14 + 14 + 42 + 3 + 14 + 14 + 3),
+    # final: V 14, P2 14, F 3x14 in; U 14, P 14 out
+    "final_rhs_recovery": 8 * (14 + 14 + 42 + 14 + 14),
+}
+
+
+def run_ours(args, rank, world, local):
+    import torch
+    import paper_2510_18968_b300 as R
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    wl = workload(args.n)
+    N = wl.ncells
+    prim0 = np.ascontiguousarray(wl.prim)
+    out = {}
+    for prec in (["mixed", "fp64"] if args.precision == "both" else [args.precision]):
+        s = R.Solver(dict(wl.params, precision=1 if prec == "mixed" else 0))
+        s.set_prims(prim0)
+        s.step(wl.dt, args.warmup)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        st = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        sampler = ClockSampler(local)
+        with sampler:
+            torch.cuda.synchronize()
+            e0.record(st)
+            groups = s.step_profiled(wl.dt, args.steps)
+            e1.record(st)
+            torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        if world > 1:
+            t = torch.tensor([ms], device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ms = float(t.item())
+        stats = s.stats()
+        # end-to-end through the public API with host buffers: every step
+        # uploads the state from pinned host memory and reads the primitives
+        # back
+        cons_h = torch.empty((14,) + wl.shape, dtype=torch.float64).pin_memory().numpy()
+        prim_h = torch.empty((14,) + wl.shape, dtype=torch.float64).pin_memory().numpy()
+        s.get_cons(cons_h)
+        s.get_prims(prim_h)
+        ke = max(1, min(args.steps, 3))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(ke):
+            s.set_state(cons_h, prim_h)
+            s.step(wl.dt, 1, sync=False)
+            s.get_prims(prim_h)
+        torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - t0
+        s.close()
+        out[prec] = dict(ms=ms, groups=groups, stats=stats, clocks=sampler.summary(),
+                         e2e=N * ke / e2e_s, e2e_bytes=(2 * 14 * N * 8, 14 * N * 8))
+    return wl, out
+
+
+def roofline(wl, res, prec):
+    hbm, kind = _peaks()
+    g = res["groups"]
+    steps = res["steps"]
+    N = wl.ncells
+    # dominant group
+    name = max(g, key=g.get)
+    per_launch_ms = g[name] / steps
+    if name.startswith("flux"):
+        nd = 3
+        per_launch_ms /= nd
+        alg = ALG_BYTES["flux"] * N
+    else:
+        alg = ALG_BYTES.get(name, 0) * N
+    achieved = alg / (per_launch_ms * 1e-3) / 1e9
+    return {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": hbm,
+            "unit": "GB/s", "frac": achieved / hbm, "peak_kind": kind,
+            "traffic": None, "launch_ms": per_launch_ms}
+
+
+def cpu_oracle_sample(nz, steps):
+    """The FP64 oracle on a z-slab (nz cells thick, same x-y plane and
+    options) of the 256^3 workload; returns zone-updates/s and the sample."""
+    import oracle
+    wl = W.cyl_blast(n=256, nz=nz)
+    a, b, g, K = wl.metric_arrays()
+    m = oracle.Metric(a.ravel(), b.reshape(3, -1), g.reshape(6, -1), K.reshape(6, -1))
+    prim = np.ascontiguousarray(wl.prim.copy())
+    cons = oracle.prim2con_grid(wl.params, m, prim)
+    t0 = time.perf_counter()
+    oracle.step(wl.params, m, cons, prim, wl.dt, steps)
+    dt = time.perf_counter() - t0
+    return wl.ncells * steps / dt, f"256x256x{nz} z-slab of the 256^3 workload, {steps} step(s)"
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=256)
+    ap.add_argument("--precision", default="both", choices=["both", "mixed", "fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank, world, local = dist_env()
+    cfg = {"workload": f"cyl_blast_{args.n}^3 (MC2+HLLE, sigma=1e3, Gamma=4/3, outflow, "
+                       "dt=0.25 dx)", "grid": [args.n] * 3,
+           "l2": "inputs larger than L2 (state ~2 GB per array set)"}
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        for _ in range(args.warmup):
+            cpu_oracle_sample(2, 1)
+        vals = []
+        for _ in range(args.steps):
+            v, sample = cpu_oracle_sample(2, 1)
+            vals.append(v)
+        value = statistics.median(vals)
+        line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+                "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": 1e3 * 256 ** 3 / value, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "config": cfg,
+                "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                 "sample": sample},
+                "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    wl, res = run_ours(args, rank, world, local)
+    if rank != 0:
+        return
+    head = "mixed" if "mixed" in res else "fp64"
+    r = res[head]
+    r["steps"] = args.steps
+    N = wl.ncells
+    value = world * N * args.steps / (r["ms"] * 1e-3)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms"] / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64" if head == "mixed" else "f64", "data": "synthetic",
+            "config": dict(cfg, precision=head, parallelism=f"replicas x{world}")}
+    if "fp64" in res and head != "fp64":
+        f = res["fp64"]
+        line["fp64"] = {"value": world * N * args.steps / (f["ms"] * 1e-3),
+                        "ms_per_step": f["ms"] / args.steps,
+                        "mixed_speedup": f["ms"] / r["ms"]}
+    line["roofline"] = roofline(wl, r, head)
+    line["kernel_ms_per_step"] = {k: v / args.steps for k, v in r["groups"].items()}
+    line["recovery_stats"] = r["stats"]
+    line["clocks"] = r["clocks"]
+    line["e2e"] = {"value": world * r["e2e"], "unit": UNIT,
+                   "h2d_bytes_per_step": r["e2e_bytes"][0], "d2h_bytes_per_step": r["e2e_bytes"][1]}
+    # kernel launches inside the timed region (per step: stage1, ghosts x(2+2+1)
+    # with J ghosts, 3+3 flux, stage2, final)
+    per_step = 1 + 5 + 6 + 1 + 1
+    line["gpu_launches"] = per_step * args.steps
+    if not args.no_cpu_baseline:
+        v, sample = cpu_oracle_sample(4, 1)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": sample}
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

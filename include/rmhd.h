@@ -1,0 +1,193 @@
+/*
+ * rmhd.h -- C ABI of the B300 (sm_103a) library for one IMEX-SSP2(2,2,2) step
+ * of the resistive general-relativistic MHD system of arXiv:2510.18968
+ * ("A resistive MHD module in the GPU-accelerated GRMHD code GRaM-X").
+ *
+ * The evolved system is Eq. GRRMHD_flux_form (Sec. II.D) on a static 3+1
+ * metric (Sec. II.A):
+ *   conserved U = (D, S_x, S_y, S_z, tau, B^x, B^y, B^z, E^x, E^y, E^z,
+ *                  Phi, Psi, Q)                      -- all densitised by
+ *                  sqrt(gamma) as in Sec. II.D (calB = sqrt(g) B, ...)
+ *   primitives   = (rho, p, v^x, v^y, v^z, E^x, E^y, E^z, B^x, B^y, B^z,
+ *                  psi, phi, q)                      -- Sec. III.B order, eps
+ *                  follows from the ideal-gas law p = (Gamma-1) rho eps
+ * with Ohm's law (Eq. Ohm_law), HLLE fluxes with light-speed bounds (Sec. III),
+ * minmod / MC2 / WENO5 reconstruction, the IMEX stages of Table imex and
+ * Eq. IMEX3 (Sec. III.A), and the implicit electric field solved jointly with
+ * the 1D primitive recovery (Sec. III.B, steps i-v).
+ *
+ * Conventions for every array argument:
+ *   - float64, interior cells only, structure of arrays, x fastest:
+ *     a[f*N + (k*ny + j)*nx + i], N = nx*ny*nz (the library adds ghosts);
+ *   - vectors are contravariant and undensitised in primitives; conserved
+ *     arrays are densitised;
+ *   - on_device = 0: host pointers (pageable or pinned), copied on the
+ *     handle's stream and synchronised before return; on_device = 1: device
+ *     pointers on the current device, copied stream-ordered.
+ *   - Caller pointers are never retained.  The handle owns all device memory.
+ * Thread safety: a handle is used by one host thread at a time.
+ * Every function returns 0 (RMHD_OK) or a negative error code; details in
+ * rmhd_last_error().
+ */
+#ifndef RMHD_H
+#define RMHD_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    RMHD_OK = 0,
+    RMHD_EINVAL = -1,   /* bad argument; state unchanged                      */
+    RMHD_ECUDA = -2,    /* a CUDA call failed (message in rmhd_last_error)    */
+    RMHD_ENOMEM = -3,   /* device allocation failed                           */
+    RMHD_EC2P = -4,     /* soft: some recoveries failed and were reset to the
+                           atmosphere; the state is usable                    */
+    RMHD_ENAN = -5      /* a non-finite conserved value appeared              */
+};
+
+enum { RMHD_BC_PERIODIC = 0, RMHD_BC_OUTFLOW = 1 /* copy nearest (Sec. IV.A) */ };
+enum { RMHD_RECON_MINMOD = 0, RMHD_RECON_MC2 = 1, RMHD_RECON_WENO5 = 2 };
+enum { RMHD_PREC_FP64 = 0, RMHD_PREC_MIXED = 1 };
+enum {
+    RMHD_SIGMA_UNIFORM = 0,  /* sigma = sigma0                                 */
+    RMHD_SIGMA_FIELD = 1,    /* sigma = sigma0 * profile[cell] (rmhd_set_sigma) */
+    RMHD_SIGMA_POWD = 2,     /* sigma = sigma0 * D^sigma_exp, Eq. sigma_evol    */
+    RMHD_SIGMA_ATMO = 3      /* sigma0 max(1 - D_atmo/D, 0)^2, Eq. dynamo_sigma */
+};
+enum {
+    RMHD_QFLUX_STAGE = 0,    /* charge-flux current = cell-centred current of the
+                                implicit stage, reconstructed to the faces     */
+    RMHD_QFLUX_FACE_OHM = 1  /* Ohm's law at the reconstructed face states      */
+};
+
+typedef struct rmhd_params {
+    int    n[3];        /* interior cells per direction (>= 1); n = 1 makes the
+                           direction inactive (no flux, no ghosts)             */
+    double x0[3];       /* lower corner of cell (0,0,0) (informational)       */
+    double dx[3];       /* cell size per direction (> 0)                      */
+    int    bc[3];       /* RMHD_BC_* per direction, both faces                 */
+    int    recon;       /* RMHD_RECON_*                                        */
+    int    precision;   /* RMHD_PREC_*                                         */
+    double gamma_eos;   /* ideal-gas Gamma (> 1), Sec. III.B                   */
+    double kappa;       /* divergence-cleaning damping, 1 in Sec. IV           */
+    int    sigma_model; /* RMHD_SIGMA_*                                        */
+    double sigma0, sigma_exp, D_atmo;
+    double rho_atmo;    /* atmosphere density (Sec. IV.E.1)                    */
+    double K_atmo;      /* atmosphere pressure p = K_atmo rho_atmo^Gamma       */
+    double atmo_tol;    /* recovered rho < rho_atmo (1 + atmo_tol) -> reset    */
+    double c2p_tol;     /* recovery stopping tolerance (1e-14)                 */
+    int    c2p_maxit;   /* cap of the paper's recovery iterations (100)        */
+    double c2p_wmax;    /* Lorentz-factor cap inside the recovery (100)        */
+    int    qflux_mode;  /* RMHD_QFLUX_*                                        */
+} rmhd_params;
+
+typedef struct rmhd_s *rmhd_t;
+
+/* Fill p with the library defaults (flat 1x1x1 grid, minmod, FP64,
+ * Gamma 2, kappa 1, sigma 0, atmosphere 1e-10 / K 100 / tol 1e-2,
+ * recovery 1e-14 / 100 / W<=100, stage charge current). */
+void rmhd_default_params(rmhd_params *p);
+
+/* Create a solver for the grid and options in *p on the given CUDA stream
+ * (cudaStream_t, may be NULL for the legacy default stream).  Allocates all
+ * device memory: about (70 + 3*14 + 17) fields x padded cells x 8 bytes.
+ * The metric starts flat, sigma uniform.  Errors: RMHD_EINVAL (n < 1,
+ * dx <= 0, Gamma <= 1, sigma0 < 0, unknown enum), RMHD_ENOMEM, RMHD_ECUDA. */
+int rmhd_create(const rmhd_params *p, void *cuda_stream, rmhd_t *out);
+
+/* Static 3+1 metric (Sec. II.A, Eq. 3plus1_metric): alpha[N], beta[3][N]
+ * (contravariant shift), gamma[6][N] (gamma_xx, xy, xz, yy, yz, zz), K[6][N]
+ * (extrinsic curvature, same order).  alpha == NULL resets to flat space.
+ * Errors: RMHD_EINVAL if alpha <= 0 or gamma_ij is not positive definite
+ * anywhere (state unchanged). */
+int rmhd_set_metric(rmhd_t h, const double *alpha, const double *beta,
+                    const double *gamma, const double *K, int on_device);
+
+/* Conductivity profile for RMHD_SIGMA_FIELD: sigma = sigma0 * profile[N]
+ * (Sec. II.D, Eq. Ohm_law); NULL resets to 1.  Errors: RMHD_EINVAL if any
+ * value is negative or not finite. */
+int rmhd_set_sigma(rmhd_t h, const double *profile, int on_device);
+
+/* Initial primitives prims[14][N].  Forms U^n with the prim->con map
+ * (Eqs. conserved_dens/tau/S, densitised EM variables) and fills ghosts.
+ * Errors: RMHD_EINVAL if rho <= 0, p < 0, v^2 >= 1 or a value is not finite
+ * (state unchanged). */
+int rmhd_set_prims(rmhd_t h, const double *prims, int on_device);
+
+/* Advance nsteps IMEX-SSP2(2,2,2) steps of size dt (Eq. IMEX3):
+ *   stage 1  U1 = U^n + gamma dt R[U1]   (implicit E + recovery, pointwise)
+ *   stage 2  U2 = U^n + dt F[U1] + dt((1-2gamma) R[U1] + gamma R[U2])
+ *   final    U^{n+1} = U^n + dt/2 (F[U1] + F[U2]) + dt/2 (R[U1] + R[U2]),
+ *            then recovery with E fixed,
+ * gamma = 1 - 1/sqrt(2) (Table imex); R acts on E only (Sec. III.A).
+ * Enqueued on the handle's stream.  If fail_count is NULL the call returns
+ * without synchronising (errors of this call then surface at the next
+ * synchronising call); otherwise it synchronises, stores the number of
+ * recoveries reset to the atmosphere during these steps, and returns
+ * RMHD_EC2P if that number is positive or RMHD_ENAN on non-finite values. */
+int rmhd_step(rmhd_t h, double dt, int nsteps, long long *fail_count);
+
+/* Same as rmhd_step (without the failure count) but records CUDA events on
+ * the handle's stream between the kernel groups of each step and adds their
+ * durations, in milliseconds, to ms[RMHD_NPROF]: [0] stage-1 recovery,
+ * [1] ghost fills, [2] face fluxes of stage 2 (x, y, z), [3] stage-2
+ * flux difference + sources + implicit recovery, [4] face fluxes of the final
+ * assembly, [5] final assembly + recovery.  Synchronises after every step.
+ * Instrumentation for benchmarks; not a paper operation. */
+#define RMHD_NPROF 6
+int rmhd_step_profiled(rmhd_t h, double dt, int nsteps, double ms[RMHD_NPROF]);
+
+/* Copy out the current primitives prims[14][N] / conserved cons[14][N]
+ * (synchronises for host destinations). */
+int rmhd_get_prims(rmhd_t h, double *prims, int on_device);
+int rmhd_get_cons(rmhd_t h, double *cons, int on_device);
+
+/* Checkpoint restore: set conserved cons[14][N] together with the primitives
+ * that were current with them (the recovery guess), bit-exact round trip with
+ * rmhd_get_cons / rmhd_get_prims.  Errors: RMHD_EINVAL on non-finite values. */
+int rmhd_set_state(rmhd_t h, const double *cons, const double *prims,
+                   int on_device);
+
+/* Counters since creation (synchronises):
+ * [0] recovery calls, [1] recovery iterations (paper iteration + fallback),
+ * [2] recoveries finished by the Newton fallback, [3] recoveries reset to the
+ * atmosphere after failing, [4] atmosphere floor resets, [5] largest iteration
+ * count of one recovery, [6] non-finite flag, [7] steps taken. */
+int rmhd_get_stats(rmhd_t h, long long stats[8]);
+
+/* Explicit right-hand side F(U) (Sec. III.A: flux differences of
+ * Eq. GRRMHD_flux_form plus sources without the stiff part of -alpha J) of
+ * the stage whose primitives are prims[14][N]; J[3][N] is the cell-centred
+ * charge current of that stage (NULL: zero).  Result rhs[14][N].  Uses the
+ * handle's metric, conductivity and options; does not change the state. */
+int rmhd_rhs(rmhd_t h, const double *prims, const double *J, double *rhs,
+             int on_device);
+
+/* Pointwise implicit-E + recovery (Sec. III.A-B) on npts independent
+ * points, for testing the recovery kernel alone.  Device pointers:
+ * cons[14][npts] (E slots hold calE*), guess[14][npts], alpha[npts],
+ * gamma[6][npts], sigma[npts]; implicit = 1 solves calE with coefficient
+ * c = a_ii dt, 0 keeps calE fixed.  Outputs prim[14][npts],
+ * cons_out[14][npts] (calE solved, D/S/tau recomputed after an atmosphere
+ * reset), iters[npts], status[npts] (0 paper iteration, 1 Newton fallback,
+ * 4 pressure-bracket fallback, 2 failed -> atmosphere, 3 floor ->
+ * atmosphere).  p supplies gamma_eos,
+ * rho_atmo, K_atmo, atmo_tol and the c2p_* options.  Runs on stream. */
+int rmhd_con2prim_points(const rmhd_params *p, int npts, const double *cons,
+                         const double *guess, const double *alpha,
+                         const double *gamma, const double *sigma, int implicit,
+                         double c, double *prim, double *cons_out, int *iters,
+                         int *status, void *cuda_stream);
+
+/* Text of the last error on this handle (never NULL; "" if none).  With
+ * h == NULL: the last error of a call that had no handle. */
+const char *rmhd_last_error(rmhd_t h);
+
+/* Free all device memory of the handle (synchronises its stream). */
+int rmhd_destroy(rmhd_t h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RMHD_H */

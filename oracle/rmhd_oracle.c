@@ -28,7 +28,9 @@
  *  - Cell-centred conserved quantities inside the source terms are computed
  *    from the stage primitives.
  *  - Recovery: tolerance, iteration cap, a damped 4D Newton fallback on
- *    (p, v_i) and an atmosphere reset are not given by the paper.
+ *    (p, v_i), a second fallback that brackets the pressure root with the
+ *    velocity solved at each pressure, and an atmosphere reset are not given
+ *    by the paper.
  */
 #include "rmhd_oracle.h"
 
@@ -647,8 +649,167 @@ static int c2p_newton4(const c2p_in *in, double *p_io, double v_io[3],
     return 1;
 }
 
-/* Returns status: 0 converged (paper iteration), 1 converged (fallback),
- * 2 failed -> atmosphere, 3 converged but rho < rho_atmo -> atmosphere. */
+/* Residual of the velocity equations at fixed pressure p:
+ *   g_i = [v_i (tau + D + sqrt(g) p - EM) - (S_i - eta_ijk calE^j calB^k)] / scale
+ * with calE from the implicit solve at v (or fixed); x = v_lower. */
+static int vel_resid(const c2p_in *in, double p, const double vl[3], double g[3],
+                     double cE[3])
+{
+    double v[3];
+    raise(in->m, vl, v);
+    double v2 = dot3(v, vl);
+    if (!(v2 < in->v2max)) return 0;
+    double W = 1.0 / sqrt(1.0 - v2);
+    for (int i = 0; i < 3; i++) cE[i] = in->cE0[i];
+    if (in->implicit &&
+        !implicit_E_nr(in->m, in->cE0, in->cB, v, W, in->sigma, in->c, cE))
+        return 0;
+    double sg = in->m->sg, cEl[3], cBl[3];
+    lower(in->m, cE, cEl);
+    lower(in->m, in->cB, cBl);
+    double EM = (dot3(cE, cEl) + dot3(in->cB, cBl)) / (2.0 * sg);
+    double scale = in->tau + in->D + sg * p;
+    double den = scale - EM;
+    for (int i = 0; i < 3; i++) {
+        double cross = 0.0;
+        for (int j = 0; j < 3; j++)
+            for (int k = 0; k < 3; k++)
+                cross += levi(i, j, k) * cE[j] * in->cB[k];
+        g[i] = (vl[i] * den - (in->Sl[i] - cross)) / scale;
+    }
+    return 1;
+}
+
+static double norm3(const double g[3])
+{
+    return sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+}
+
+/* Velocity at fixed p: damped Newton on vel_resid from vl (in/out). */
+static int solve_velocity(const c2p_in *in, double p, double vl[3])
+{
+    double g[3], cE[3];
+    if (!vel_resid(in, p, vl, g, cE)) return 0;
+    for (int it = 0; it < 30; it++) {
+        double J[9], rhs[3], dv[3];
+        for (int col = 0; col < 3; col++) {
+            double vh[3] = {vl[0], vl[1], vl[2]}, gh[3], h = 1e-7;
+            vh[col] += h;
+            if (!vel_resid(in, p, vh, gh, cE)) {
+                h = -h;
+                vh[col] = vl[col] + h;
+                if (!vel_resid(in, p, vh, gh, cE)) return 0;
+            }
+            for (int row = 0; row < 3; row++) J[row * 3 + col] = (gh[row] - g[row]) / h;
+        }
+        for (int i = 0; i < 3; i++) rhs[i] = -g[i];
+        if (!solve_dense(3, J, rhs, dv)) return 0;
+        double lam = 1.0, vt[3], gt[3];
+        int ok = 0;
+        for (int ls = 0; ls < 40; ls++) {
+            for (int i = 0; i < 3; i++) vt[i] = vl[i] + lam * dv[i];
+            if (vel_resid(in, p, vt, gt, cE) && norm3(gt) < norm3(g)) {
+                ok = 1;
+                break;
+            }
+            lam *= 0.5;
+        }
+        if (!ok) return norm3(g) < 1e-13;
+        double step = fmax(fabs(lam * dv[0]), fmax(fabs(lam * dv[1]), fabs(lam * dv[2])));
+        for (int i = 0; i < 3; i++) { vl[i] = vt[i]; g[i] = gt[i]; }
+        if (step <= 1e-15) break;
+    }
+    return 1;
+}
+
+/* f(p) = (Gamma-1) rho eps - p (scaled) with the velocity solved at p */
+static int pressure_fn(const c2p_in *in, double p, double vl[3], double *f)
+{
+    if (!(p > 0.0) || !solve_velocity(in, p, vl)) return 0;
+    double cE[3], v[3], g[3];
+    vel_resid(in, p, vl, g, cE);
+    raise(in->m, vl, v);
+    double v2 = dot3(v, vl), W = 1.0 / sqrt(1.0 - v2), sg = in->m->sg;
+    double cEl[3], cBl[3];
+    lower(in->m, cE, cEl);
+    lower(in->m, in->cB, cBl);
+    double EM = (dot3(cE, cEl) + dot3(in->cB, cBl)) / (2.0 * sg);
+    double rho = in->D / (sg * W);
+    double eps = (in->tau - in->D * (W - 1.0) - sg * p * (W * W - 1.0) - EM) / (in->D * W);
+    *f = ((in->P->gamma_eos - 1.0) * rho * eps - p) * sg / (in->tau + in->D + sg * p);
+    return 1;
+}
+
+/* Second fallback: bracket the pressure root of f(p) (doubling or halving
+ * from the guess), then the Illinois variant of regula falsi; each f(p)
+ * solves the velocity equations at p. */
+static int c2p_bracket(const c2p_in *in, double *p_io, double v_io[3], double cE[3],
+                       double *rho_o, int *iters)
+{
+    double vl[3], f0;
+    lower(in->m, v_io, vl);
+    double p0 = *p_io > 0.0 ? *p_io : in->P->K_atmo * pow(in->P->rho_atmo, in->P->gamma_eos);
+    int n = 0;
+    if (!pressure_fn(in, p0, vl, &f0)) {
+        vl[0] = vl[1] = vl[2] = 0.0;
+        if (!pressure_fn(in, p0, vl, &f0)) return 0;
+    }
+    double lo = p0, hi = p0, flo = f0, fhi = f0;
+    double vlo[3] = {vl[0], vl[1], vl[2]}, vhi[3] = {vl[0], vl[1], vl[2]};
+    if (f0 > 0.0) {
+        while (fhi > 0.0) {
+            if (++n > 60) return 0;
+            lo = hi; flo = fhi;
+            for (int i = 0; i < 3; i++) vlo[i] = vhi[i];
+            hi = 2.0 * hi;
+            if (!pressure_fn(in, hi, vhi, &fhi)) return 0;
+        }
+    } else {
+        while (flo < 0.0) {
+            if (++n > 60) return 0;
+            hi = lo; fhi = flo;
+            for (int i = 0; i < 3; i++) vhi[i] = vlo[i];
+            lo = 0.5 * lo;
+            if (!pressure_fn(in, lo, vlo, &flo)) return 0;
+        }
+    }
+    int side = 0;
+    double sg = in->m->sg;
+    for (int it = 0; it < 100; it++) {
+        *iters = n + it + 1;
+        double pm = (lo * fhi - hi * flo) / (fhi - flo);
+        if (!(pm > lo && pm < hi)) pm = 0.5 * (lo + hi);
+        double vm[3] = {vlo[0], vlo[1], vlo[2]}, fm;
+        if (!pressure_fn(in, pm, vm, &fm)) return 0;
+        if (fm > 0.0) {
+            lo = pm; flo = fm;
+            for (int i = 0; i < 3; i++) vlo[i] = vm[i];
+            if (side == 1) fhi *= 0.5;
+            side = 1;
+        } else {
+            hi = pm; fhi = fm;
+            for (int i = 0; i < 3; i++) vhi[i] = vm[i];
+            if (side == -1) flo *= 0.5;
+            side = -1;
+        }
+        if ((hi - lo) * sg <= in->P->c2p_tol * (in->tau + in->D + sg * hi) || fm == 0.0) {
+            double g[3], v[3];
+            *p_io = pm;
+            for (int i = 0; i < 3; i++) vl[i] = vm[i];
+            vel_resid(in, pm, vl, g, cE);
+            raise(in->m, vl, v);
+            double W = 1.0 / sqrt(1.0 - dot3(v, vl));
+            for (int i = 0; i < 3; i++) v_io[i] = v[i];
+            *rho_o = in->D / (sg * W);
+            return 1;
+        }
+    }
+    return 0;
+}
+
+/* Returns status: 0 converged (paper iteration), 1 converged (Newton
+ * fallback), 4 converged (pressure-bracket fallback), 2 failed ->
+ * atmosphere, 3 converged but rho < rho_atmo -> atmosphere. */
 int orc_con2prim(const orc_params *P, const double cons_in[14], int implicit,
                  double c, double sigma, double alpha, const double g6[6],
                  const double guess[14], double prim[14], double cons_out[14],
@@ -684,13 +845,25 @@ int orc_con2prim(const orc_params *P, const double cons_in[14], int implicit,
             cE[i] = in.cE0[i];
         }
         status = c2p_newton4(&in, &p, v, cE, &rho, &it2) ? 1 : 2;
+        if (status == 2) {
+            int it3 = 0;
+            p = guess[P_P];
+            for (int i = 0; i < 3; i++) {
+                v[i] = guess[P_VX + i];
+                cE[i] = in.cE0[i];
+            }
+            if (c2p_bracket(&in, &p, v, cE, &rho, &it3)) status = 4;
+            it2 += it3;
+        }
     }
     *iters = it1 + it2;
     /* atmosphere floor: rho below rho_atmo (1 + atmo_tol) is reset */
-    if (status < 2 && !(rho >= P->rho_atmo * (1.0 + P->atmo_tol))) status = 3;
+    int ok = status == 0 || status == 1 || status == 4;
+    if (ok && !(rho >= P->rho_atmo * (1.0 + P->atmo_tol))) status = 3;
+    int reset = status == 2 || status == 3;
 
     for (int f = 0; f < 14; f++) cons_out[f] = cons_in[f];
-    if (status >= 2) {
+    if (reset) {
         /* atmosphere: rho_atmo, v = 0, p = K rho^Gamma; calE from the
          * implicit solve at v = 0 */
         rho = P->rho_atmo;
@@ -711,7 +884,7 @@ int orc_con2prim(const orc_params *P, const double cons_in[14], int implicit,
     prim[P_PSI] = cons_in[C_PSI] / sg;
     prim[P_PHI] = cons_in[C_PHI] / sg;
     prim[P_Q] = cons_in[C_Q] / sg;
-    if (status >= 2) {
+    if (reset) {
         double full[14];
         orc_prim2con(prim, alpha, NULL, g6, P->gamma_eos, full);
         cons_out[C_D] = full[C_D];
@@ -1061,7 +1234,7 @@ static void c2p_grid(const grid *G, double *cons, const double *guess,
                               pr, cout, &it);
         stats[0] += 1;
         stats[1] += it;
-        if (st == 1) stats[2] += 1;
+        if (st == 1 || st == 4) stats[2] += 1;
         if (st == 2) stats[3] += 1;
         if (st == 3) stats[4] += 1;
         if (it > stats[5]) stats[5] = it;

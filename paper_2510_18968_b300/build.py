@@ -1,0 +1,27 @@
+"""Build the CUDA library (sm_103a) in-tree: paper_2510_18968_b300/librmhd.so."""
+import os
+import subprocess
+import sys
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+CSRC = os.path.join(HERE, "csrc")
+LIB = os.path.join(HERE, "librmhd.so")
+SOURCES = [os.path.join(CSRC, "rmhd.cu")]
+DEPS = SOURCES + [os.path.join(CSRC, f) for f in ("physics.cuh", "recovery.cuh", "kernels.cuh")] + [
+    os.path.join(os.path.dirname(HERE), "include", "rmhd.h")]
+
+NVCC_FLAGS = ["-O3", "-std=c++17", "-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo",
+              "-Xcompiler", "-fPIC", "-shared", "--expt-relaxed-constexpr"]
+
+
+def build(force=False, verbose=False):
+    if (not force and os.path.exists(LIB)
+            and os.path.getmtime(LIB) >= max(os.path.getmtime(f) for f in DEPS if os.path.exists(f))):
+        return LIB
+    cmd = ["nvcc"] + NVCC_FLAGS + (["-Xptxas", "-v"] if verbose else []) + ["-o", LIB] + SOURCES
+    subprocess.check_call(cmd)
+    return LIB
+
+
+if __name__ == "__main__":
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))

@@ -1,0 +1,287 @@
+// physics.cuh -- pointwise device physics of the resistive GRMHD step
+// (arXiv:2510.18968, Sec. II-III), templated on the floating type T and on a
+// flat-metric switch.  With FLAT the lapse is 1, the shift 0 and gamma_ij the
+// identity, and every metric factor is dropped at compile time (multiplying
+// by 1 and adding 0 are exact, so FLAT and the general path agree bit for bit
+// up to the order of fused multiply-adds).
+#pragma once
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+namespace rmhd {
+
+// primitive and conserved slots (Sec. III.B order and Eq. GRRMHD_flux_form)
+enum { PR_RHO = 0, PR_P, PR_VX, PR_VY, PR_VZ, PR_EX, PR_EY, PR_EZ, PR_BX, PR_BY,
+       PR_BZ, PR_PSI, PR_PHI, PR_Q, NPR };
+enum { CO_D = 0, CO_SX, CO_SY, CO_SZ, CO_TAU, CO_BX, CO_BY, CO_BZ, CO_EX, CO_EY,
+       CO_EZ, CO_PHI, CO_PSI, CO_Q, NCO };
+
+// symmetric 3x3 packed as xx, xy, xz, yy, yz, zz
+__host__ __device__ constexpr int sym(int i, int j)
+{
+    return i == j ? (i == 0 ? 0 : (i == 1 ? 3 : 5))
+                  : ((i + j) == 1 ? 1 : ((i + j) == 2 ? 2 : 4));
+}
+
+template <class T> struct Met {
+    T alpha, beta[3];
+    T g[6], gi[6];
+    T sg, isg;  // sqrt(det gamma), 1/sqrt(det gamma)
+};
+
+// gamma^{ij} (adjugate / det) and sqrt(gamma) (Sec. II.A)
+template <class T> __device__ __forceinline__ void met_complete(Met<T> &m)
+{
+    const T *g = m.g;
+    T c00 = g[3] * g[5] - g[4] * g[4];
+    T c01 = g[4] * g[2] - g[1] * g[5];
+    T c02 = g[1] * g[4] - g[3] * g[2];
+    T det = g[0] * c00 + g[1] * c01 + g[2] * c02;
+    T id = T(1) / det;
+    m.gi[0] = c00 * id;
+    m.gi[1] = c01 * id;
+    m.gi[2] = c02 * id;
+    m.gi[3] = (g[0] * g[5] - g[2] * g[2]) * id;
+    m.gi[4] = (g[2] * g[1] - g[0] * g[4]) * id;
+    m.gi[5] = (g[0] * g[3] - g[1] * g[1]) * id;
+    m.sg = sqrt(det);
+    m.isg = T(1) / m.sg;
+}
+
+template <class T, bool FLAT>
+__device__ __forceinline__ void lower(const Met<T> &m, const T u[3], T ul[3])
+{
+    if (FLAT) {
+        ul[0] = u[0]; ul[1] = u[1]; ul[2] = u[2];
+    } else {
+        ul[0] = m.g[0] * u[0] + m.g[1] * u[1] + m.g[2] * u[2];
+        ul[1] = m.g[1] * u[0] + m.g[3] * u[1] + m.g[4] * u[2];
+        ul[2] = m.g[2] * u[0] + m.g[4] * u[1] + m.g[5] * u[2];
+    }
+}
+
+template <class T, bool FLAT>
+__device__ __forceinline__ void raise(const Met<T> &m, const T ul[3], T u[3])
+{
+    if (FLAT) {
+        u[0] = ul[0]; u[1] = ul[1]; u[2] = ul[2];
+    } else {
+        u[0] = m.gi[0] * ul[0] + m.gi[1] * ul[1] + m.gi[2] * ul[2];
+        u[1] = m.gi[1] * ul[0] + m.gi[3] * ul[1] + m.gi[4] * ul[2];
+        u[2] = m.gi[2] * ul[0] + m.gi[4] * ul[1] + m.gi[5] * ul[2];
+    }
+}
+
+template <class T> __device__ __forceinline__ T dot3(const T a[3], const T b[3])
+{
+    return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
+}
+
+// (a x b)_i = eta_ijk a_j b_k
+template <class T>
+__device__ __forceinline__ void cross3(const T a[3], const T b[3], T c[3])
+{
+    c[0] = a[1] * b[2] - a[2] * b[1];
+    c[1] = a[2] * b[0] - a[0] * b[2];
+    c[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+template <class T> __device__ __forceinline__ T sg_of(const Met<T> &m, bool flat)
+{
+    return flat ? T(1) : m.sg;
+}
+
+// ---------------------------------------------------------------------------
+// Conserved vector and flux in direction D at one state.
+// U: Eqs. conserved_dens, conserved_tau, conserved_S, densitised EM fields.
+// F: flux column of Eq. GRRMHD_flux_form, with the undensitised stress inside
+//    the S_i flux; the charge-flux current is Jd when useJ, else Ohm's law
+//    (Eq. Ohm_law) at this state.  gfac = Gamma/(Gamma-1): h = rho + gfac p.
+// Accumulates cF*F + cU*U into acc (the HLLE combination), so that neither U
+// nor F has to stay live as an array.
+// ---------------------------------------------------------------------------
+template <class T, bool FLAT, int D>
+__device__ __forceinline__ void flux_accumulate(const T pr[NPR], const Met<T> &m,
+                                                T sigma, T gfac, bool useJ, T Jd,
+                                                T cF, T cU, T acc[NCO])
+{
+    const T sg = FLAT ? T(1) : m.sg;
+    const T a = FLAT ? T(1) : m.alpha;
+    const T bD = FLAT ? T(0) : m.beta[D];
+    T v[3] = {pr[PR_VX], pr[PR_VY], pr[PR_VZ]};
+    T E[3] = {pr[PR_EX], pr[PR_EY], pr[PR_EZ]};
+    T B[3] = {pr[PR_BX], pr[PR_BY], pr[PR_BZ]};
+    T vl[3], El[3], Bl[3];
+    lower<T, FLAT>(m, v, vl);
+    lower<T, FLAT>(m, E, El);
+    lower<T, FLAT>(m, B, Bl);
+    const T rho = pr[PR_RHO], p = pr[PR_P];
+    const T v2 = dot3(v, vl);
+    const T W = T(1) / sqrt(T(1) - v2);
+    const T h = rho + gfac * p;
+    const T hW2 = h * W * W;
+    const T em = T(0.5) * (dot3(E, El) + dot3(B, Bl));
+
+    // conserved vector
+    const T Dc = sg * rho * W;
+    const T tau = sg * (hW2 - p + em) - Dc;
+    T ExB[3];
+    cross3(E, B, ExB);
+    T S[3];
+#pragma unroll
+    for (int i = 0; i < 3; i++) S[i] = sg * (hW2 * vl[i] + sg * ExB[i]);
+
+    // D, S_i, tau
+    acc[CO_D] += cF * ((a * v[D] - bD) * Dc) + cU * Dc;
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+        T st = hW2 * v[D] * vl[i] - E[D] * El[i] - B[D] * Bl[i];
+        if (i == D) st += p + em;
+        T f = a * sg * st;
+        if (!FLAT) f -= bD * S[i];
+        acc[CO_SX + i] += cF * f + cU * S[i];
+    }
+    T SD = S[D];
+    if (!FLAT) SD = m.gi[sym(D, 0)] * S[0] + m.gi[sym(D, 1)] * S[1] + m.gi[sym(D, 2)] * S[2];
+    {
+        T f = a * (SD - v[D] * Dc);
+        if (!FLAT) f -= bD * tau;
+        acc[CO_TAU] += cF * f + cU * tau;
+    }
+    // B^i: alpha (eps^{iDj} calE_j + gamma^{iD} Phi) - beta^D calB^i, with
+    // eps^{iDj} calE_j = (e_D x E_lower)_i; E^i: -[alpha(...B...) + beta^D calE^i]
+    const T Phi = sg * pr[PR_PHI], Psi = sg * pr[PR_PSI], Qc = sg * pr[PR_Q];
+    T eE[3] = {T(0), T(0), T(0)}, eB[3] = {T(0), T(0), T(0)};
+    if (D == 0) { eE[1] = -El[2]; eE[2] = El[1]; eB[1] = -Bl[2]; eB[2] = Bl[1]; }
+    if (D == 1) { eE[0] = El[2]; eE[2] = -El[0]; eB[0] = Bl[2]; eB[2] = -Bl[0]; }
+    if (D == 2) { eE[0] = -El[1]; eE[1] = El[0]; eB[0] = -Bl[1]; eB[1] = Bl[0]; }
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+        const T gid = FLAT ? (i == D ? T(1) : T(0)) : m.gi[sym(i, D)];
+        const T cB = sg * B[i], cE = sg * E[i];
+        T fB = a * (eE[i] + gid * Phi);
+        T fE = -(a * (eB[i] - gid * Psi));
+        if (!FLAT) {
+            fB -= bD * cB;
+            fE -= bD * cE;
+        }
+        acc[CO_BX + i] += cF * fB + cU * cB;
+        acc[CO_EX + i] += cF * fE + cU * cE;
+    }
+    {
+        T fPhi = a * sg * B[D], fPsi = a * sg * E[D];
+        if (!FLAT) {
+            fPhi -= bD * Phi;
+            fPsi -= bD * Psi;
+        }
+        acc[CO_PHI] += cF * fPhi + cU * Phi;
+        acc[CO_PSI] += cF * fPsi + cU * Psi;
+    }
+    T J = Jd;
+    if (!useJ) {
+        // Ohm's law: Q v^D + W sigma [calE^D + eps^{Djk} v_j calB_k - (v.calE) v^D]
+        T vB[3];
+        cross3(vl, Bl, vB);
+        J = Qc * v[D] + W * sigma * (sg * E[D] + vB[D] - sg * dot3(vl, E) * v[D]);
+    }
+    {
+        T f = a * J;
+        if (!FLAT) f -= bD * Qc;
+        acc[CO_Q] += cF * f + cU * Qc;
+    }
+}
+
+// prim -> con only (set-up, atmosphere resets)
+template <class T, bool FLAT>
+__device__ __forceinline__ void prim_to_cons(const T pr[NPR], const Met<T> &m, T gfac,
+                                             T U[NCO])
+{
+    const T sg = FLAT ? T(1) : m.sg;
+    T v[3] = {pr[PR_VX], pr[PR_VY], pr[PR_VZ]};
+    T E[3] = {pr[PR_EX], pr[PR_EY], pr[PR_EZ]};
+    T B[3] = {pr[PR_BX], pr[PR_BY], pr[PR_BZ]};
+    T vl[3], El[3], Bl[3];
+    lower<T, FLAT>(m, v, vl);
+    lower<T, FLAT>(m, E, El);
+    lower<T, FLAT>(m, B, Bl);
+    const T rho = pr[PR_RHO], p = pr[PR_P];
+    const T W = T(1) / sqrt(T(1) - dot3(v, vl));
+    const T hW2 = (rho + gfac * p) * W * W;
+    const T em = T(0.5) * (dot3(E, El) + dot3(B, Bl));
+    U[CO_D] = sg * rho * W;
+    U[CO_TAU] = sg * (hW2 - p + em) - U[CO_D];
+    T ExB[3];
+    cross3(E, B, ExB);
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+        U[CO_SX + i] = sg * (hW2 * vl[i] + sg * ExB[i]);
+        U[CO_BX + i] = sg * B[i];
+        U[CO_EX + i] = sg * E[i];
+    }
+    U[CO_PHI] = sg * pr[PR_PHI];
+    U[CO_PSI] = sg * pr[PR_PSI];
+    U[CO_Q] = sg * pr[PR_Q];
+}
+
+// ---------------------------------------------------------------------------
+// Reconstruction of a six-point stencil s[0..5] = u_{i-2..i+3} to the left
+// (from u_i) and right (from u_{i+1}) states of the face between u_i, u_{i+1}.
+// ---------------------------------------------------------------------------
+enum { RC_MINMOD = 0, RC_MC2 = 1, RC_WENO5 = 2 };
+
+template <class T> __device__ __forceinline__ T mm2(T a, T b)
+{
+    if (a * b <= T(0)) return T(0);
+    return fabs(a) <= fabs(b) ? a : b;
+}
+
+template <class T> __device__ __forceinline__ T mm3(T a, T b, T c)
+{
+    if (a > T(0) && b > T(0) && c > T(0)) return fmin(a, fmin(b, c));
+    if (a < T(0) && b < T(0) && c < T(0)) return fmax(a, fmax(b, c));
+    return T(0);
+}
+
+template <class T, int RC> __device__ __forceinline__ T tvd_slope(T um, T u0, T up)
+{
+    if (RC == RC_MINMOD) return mm2(u0 - um, up - u0);
+    return mm3(T(2) * (u0 - um), T(0.5) * (up - um), T(2) * (up - u0));
+}
+
+// Jiang-Shu WENO5 face value between c and d from (a..e) = u_{i-2..i+2}
+template <class T> __device__ __forceinline__ T weno5(T a, T b, T c, T d, T e)
+{
+    const T eps = T(1e-6);
+    const T sixth = T(1) / T(6);
+    T q0 = (T(2) * a - T(7) * b + T(11) * c) * sixth;
+    T q1 = (-b + T(5) * c + T(2) * d) * sixth;
+    T q2 = (T(2) * c + T(5) * d - e) * sixth;
+    const T k13 = T(13) / T(12);
+    T t1 = a - T(2) * b + c, t2 = a - T(4) * b + T(3) * c;
+    T b0 = k13 * t1 * t1 + T(0.25) * t2 * t2;
+    t1 = b - T(2) * c + d;
+    t2 = b - d;
+    T b1 = k13 * t1 * t1 + T(0.25) * t2 * t2;
+    t1 = c - T(2) * d + e;
+    t2 = T(3) * c - T(4) * d + e;
+    T b2 = k13 * t1 * t1 + T(0.25) * t2 * t2;
+    T w0 = T(0.1) / ((eps + b0) * (eps + b0));
+    T w1 = T(0.6) / ((eps + b1) * (eps + b1));
+    T w2 = T(0.3) / ((eps + b2) * (eps + b2));
+    return (w0 * q0 + w1 * q1 + w2 * q2) / (w0 + w1 + w2);
+}
+
+template <class T, int RC>
+__device__ __forceinline__ void reconstruct(const T s[6], T &uL, T &uR)
+{
+    if (RC == RC_WENO5) {
+        uL = weno5(s[0], s[1], s[2], s[3], s[4]);
+        uR = weno5(s[5], s[4], s[3], s[2], s[1]);
+    } else {
+        uL = s[2] + T(0.5) * tvd_slope<T, RC>(s[1], s[2], s[3]);
+        uR = s[3] - T(0.5) * tvd_slope<T, RC>(s[2], s[3], s[4]);
+    }
+}
+
+} // namespace rmhd

@@ -1,0 +1,519 @@
+// recovery.cuh -- implicit electric field fused with the 1D primitive recovery
+// (arXiv:2510.18968, Sec. III.A Eq. 3D_NR and Sec. III.B steps i-v), FP64.
+//
+// Per cell the unknowns are the pressure p, the velocity v and the stiff field
+// calE of the stage.  At fixed v the stage equation of calE,
+//   calE - calE* + cc W (calE + eps^{ijk} v_j calB_k - (v.calE) v) = 0,
+//   cc = a_ii dt alpha sigma,
+// is linear, so the paper's 3D Newton-Raphson lands on its root in one step;
+// here that root is written in closed form (Sherman-Morrison on the rank-one
+// matrix (1+C) I - C v v_lower^T):
+//   calE = [r (1 + C(1-v^2)) + C v (v_lower.r)] / [(1+C)(1 + C(1-v^2))],
+//   r = calE* - C eps v x calB,  C = cc W.
+// The outer loop is the paper's: (iii) v, W, rho, eps from the conserved
+// variables at the current p and calE, (iv) p <- p - f/f' with
+// f = (Gamma-1) rho eps - p, f' = v^2 c_s^2 - 1, c_s^2 = Gamma(Gamma-1)eps/(1+Gamma eps).
+// When that iteration diverges or would converge too slowly, a damped Newton
+// method on (p, v_i) with a forward-difference Jacobian takes over from the
+// stage guess; if that stalls, the pressure root is bracketed and refined by
+// regula falsi with the velocity equations solved at each pressure.  All stop
+// on the same criteria and find the same root.  A state with no root is reset
+// to the atmosphere.  Every loop is bounded.
+#pragma once
+#include "physics.cuh"
+
+namespace rmhd {
+
+struct RecOpts {
+    double Gam;          // Gamma
+    double tol;          // stopping tolerance
+    double v2max;        // 1 - 1/W_max^2
+    double rho_atmo, p_atmo, atmo_floor;  // atmo_floor = rho_atmo (1 + atmo_tol)
+    int maxit;           // cap of the paper iteration
+};
+
+struct RecIn {
+    double D, S[3], tau, cB[3], cE0[3];   // cE0: calE* (implicit) or calE (fixed)
+};
+
+template <bool FLAT> struct RecCtx {
+    const RecIn &in;
+    const Met<double> &m;
+    const RecOpts &o;
+    bool implicit;
+    double cc;          // a_ii dt alpha sigma (0 when not implicit)
+    double sg, isg, iD;
+    double cBl[3];      // lowered calB
+    double B2;          // calB . calB_lower
+};
+
+// closed-form implicit calE at fixed contravariant v (see file comment)
+template <bool FLAT>
+__device__ __forceinline__ void implicit_field(const RecCtx<FLAT> &c, const double v[3],
+                                               const double vl[3], double v2, double W,
+                                               double E[3])
+{
+    const double C = c.cc * W;
+    double vxB[3];
+    cross3(vl, c.cBl, vxB);            // eta v_j calB_k (lowered): sqrt(g) (v x B)
+    double r[3];
+#pragma unroll
+    for (int i = 0; i < 3; i++) r[i] = c.in.cE0[i] - C * (FLAT ? vxB[i] : vxB[i] * c.isg);
+    const double s = dot3(vl, r);
+    const double q = 1.0 + C * (1.0 - v2);
+    const double inv = 1.0 / ((1.0 + C) * q);
+#pragma unroll
+    for (int i = 0; i < 3; i++) E[i] = (r[i] * q + C * v[i] * s) * inv;
+}
+
+// Step (iii): fluid variables from the conserved ones at (p, calE).  Returns
+// false if the enthalpy denominator is not positive or v^2 >= v2max.
+template <bool FLAT>
+__device__ __forceinline__ bool fluid_from_cons(const RecCtx<FLAT> &c, const double E[3],
+                                                double p, double vl[3], double v[3],
+                                                double &v2, double &Winv, double &W,
+                                                double &rho, double &eps, double &EMo)
+{
+    double El[3];
+    lower<double, FLAT>(c.m, E, El);
+    const double EM = 0.5 * (dot3(E, El) + c.B2) * c.isg;
+    double P[3];
+    cross3(E, c.in.cB, P);             // eta_ijk calE^j calB^k
+    const double den = c.in.tau + c.in.D + c.sg * p - EM;
+    const double iden = 1.0 / den;
+#pragma unroll
+    for (int i = 0; i < 3; i++) vl[i] = (c.in.S[i] - P[i]) * iden;
+    raise<double, FLAT>(c.m, vl, v);
+    v2 = dot3(v, vl);
+    if (!(den > 0.0) || !(v2 < c.o.v2max)) return false;
+    const double omv = 1.0 - v2;
+    W = rsqrt(omv);
+    Winv = omv * W;
+    rho = c.in.D * Winv * c.isg;
+    const double num = c.in.tau - c.in.D * (W - 1.0) - c.sg * p * (v2 * W * W) - EM;
+    eps = num * Winv * c.iD;
+    EMo = EM;
+    return true;
+}
+
+template <bool FLAT>
+__device__ __forceinline__ bool p_conv(const RecCtx<FLAT> &c, double dp, double p)
+{
+    return fabs(dp) * c.sg <= c.o.tol * (c.in.tau + c.in.D + c.sg * p);
+}
+
+// The paper's iteration (steps ii-v).  Returns 1 converged, 0 gave up.
+template <bool FLAT>
+__device__ int paper_iteration(const RecCtx<FLAT> &c, double &p, double v[3], double E[3],
+                               double &rho_out, int &iters)
+{
+    const double Gam = c.o.Gam;
+    double prev0 = 0.0, prev1 = 0.0, prev2 = 0.0;
+    for (int it = 1; it <= c.o.maxit; it++) {
+        iters = it;
+        if (c.implicit) {
+            double vl[3];
+            lower<double, FLAT>(c.m, v, vl);
+            const double v2 = dot3(v, vl);
+            if (!(v2 < c.o.v2max)) return 0;
+            implicit_field<FLAT>(c, v, vl, v2, rsqrt(1.0 - v2), E);
+        }
+        double vl[3], vn[3], v2, Winv, W, rho, eps, EM;
+        if (!fluid_from_cons<FLAT>(c, E, p, vl, vn, v2, Winv, W, rho, eps, EM)) return 0;
+        const double f = (Gam - 1.0) * rho * eps - p;
+        double ratio;   // f / f'
+        if (eps > 0.0) {
+            const double ge = Gam * eps;
+            ratio = f * (1.0 + ge) / (v2 * Gam * (Gam - 1.0) * eps - 1.0 - ge);
+        } else {
+            ratio = -f;
+        }
+        double pn = p - ratio;
+        if (!(pn > 0.0)) pn = 0.1 * p;
+        double dv = fmax(fabs(vn[0] - v[0]), fmax(fabs(vn[1] - v[1]), fabs(vn[2] - v[2])));
+        const double dp = pn - p;
+        p = pn;
+        v[0] = vn[0]; v[1] = vn[1]; v[2] = vn[2];
+        rho_out = rho;
+        if (p_conv<FLAT>(c, dp, p) && dv <= c.o.tol) return 1;
+        const double meas = dv + fabs(dp) * c.sg / (c.in.tau + c.in.D + c.sg * p);
+        if (!isfinite(meas)) return 0;
+        // diverging: three successive growing changes above the noise
+        if (it >= 3 && meas > prev0 && prev0 > prev1 && prev1 > prev2 &&
+            meas > 1e3 * c.o.tol)
+            return 0;
+        // converging too slowly: more than 24 further iterations predicted
+        if (it >= 6 && meas < prev0 && prev0 > 0.0) {
+            const double rate = meas / prev0;
+            if (rate > 0.0 && log(c.o.tol / meas) / log(rate) > 24.0) return 0;
+        }
+        prev2 = prev1; prev1 = prev0; prev0 = meas;
+    }
+    return 0;
+}
+
+// residual of the joint system at x = (p, v_lower), scaled by the energy scale
+template <bool FLAT>
+__device__ __forceinline__ bool joint_residual(const RecCtx<FLAT> &c, const double x[4],
+                                               double r[4], double E[3], double &rho,
+                                               double v[3])
+{
+    const double p = x[0];
+    const double vl[3] = {x[1], x[2], x[3]};
+    raise<double, FLAT>(c.m, vl, v);
+    const double v2 = dot3(v, vl);
+    if (!(p > 0.0) || !(v2 < c.o.v2max)) return false;
+    const double W = rsqrt(1.0 - v2);
+    if (c.implicit) {
+        implicit_field<FLAT>(c, v, vl, v2, W, E);
+    } else {
+        E[0] = c.in.cE0[0]; E[1] = c.in.cE0[1]; E[2] = c.in.cE0[2];
+    }
+    double El[3];
+    lower<double, FLAT>(c.m, E, El);
+    const double EM = 0.5 * (dot3(E, El) + c.B2) * c.isg;
+    double P[3];
+    cross3(E, c.in.cB, P);
+    const double scale = c.in.tau + c.in.D + c.sg * p;
+    const double iscale = 1.0 / scale;
+    const double den = scale - EM;
+#pragma unroll
+    for (int i = 0; i < 3; i++) r[1 + i] = (vl[i] * den - (c.in.S[i] - P[i])) * iscale;
+    const double Winv = (1.0 - v2) * W;
+    rho = c.in.D * Winv * c.isg;
+    const double num = c.in.tau - c.in.D * (W - 1.0) - c.sg * p * (v2 * W * W) - EM;
+    const double eps = num * Winv * c.iD;
+    r[0] = ((c.o.Gam - 1.0) * rho * eps - p) * c.sg * iscale;
+    return true;
+}
+
+__device__ __forceinline__ double nrm4(const double r[4])
+{
+    return sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2] + r[3] * r[3]);
+}
+
+// A x = b, 4x4, partial pivoting; false if singular
+__device__ __forceinline__ bool solve4(double A[16], double b[4], double x[4])
+{
+#pragma unroll
+    for (int col = 0; col < 4; col++) {
+        int piv = col;
+        double best = fabs(A[col * 4 + col]);
+#pragma unroll
+        for (int r = col + 1; r < 4; r++)
+            if (fabs(A[r * 4 + col]) > best) { best = fabs(A[r * 4 + col]); piv = r; }
+        if (best == 0.0) return false;
+        if (piv != col) {
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                double t = A[col * 4 + k]; A[col * 4 + k] = A[piv * 4 + k]; A[piv * 4 + k] = t;
+            }
+            double t = b[col]; b[col] = b[piv]; b[piv] = t;
+        }
+        const double ip = 1.0 / A[col * 4 + col];
+#pragma unroll
+        for (int r = col + 1; r < 4; r++) {
+            const double f = A[r * 4 + col] * ip;
+#pragma unroll
+            for (int k = col; k < 4; k++) A[r * 4 + k] -= f * A[col * 4 + k];
+            b[r] -= f * b[col];
+        }
+    }
+#pragma unroll
+    for (int r = 3; r >= 0; r--) {
+        double s = b[r];
+#pragma unroll
+        for (int k = r + 1; k < 4; k++) s -= A[r * 4 + k] * x[k];
+        x[r] = s / A[r * 4 + r];
+    }
+    return true;
+}
+
+// Fallback: damped Newton on (p, v_lower) with a forward-difference Jacobian.
+template <bool FLAT>
+__device__ int newton_fallback(const RecCtx<FLAT> &c, double &p, double v[3], double E[3],
+                               double &rho_out, int &iters)
+{
+    double x[4], r[4], vtmp[3], rho;
+    double vl[3];
+    lower<double, FLAT>(c.m, v, vl);
+    x[0] = p; x[1] = vl[0]; x[2] = vl[1]; x[3] = vl[2];
+    if (!joint_residual<FLAT>(c, x, r, E, rho, vtmp)) {
+        x[1] = x[2] = x[3] = 0.0;
+        if (!(x[0] > 0.0)) x[0] = c.o.p_atmo;
+        if (!joint_residual<FLAT>(c, x, r, E, rho, vtmp)) return 0;
+    }
+    for (int it = 1; it <= 50; it++) {
+        iters = it;
+        double J[16];
+        for (int col = 0; col < 4; col++) {
+            double xh[4] = {x[0], x[1], x[2], x[3]}, rh[4], Eh[3], rhoh, vh[3];
+            double h = col == 0 ? 1e-7 * x[0] : 1e-7;
+            xh[col] += h;
+            if (!joint_residual<FLAT>(c, xh, rh, Eh, rhoh, vh)) {
+                h = -h;
+                xh[col] = x[col] + h;
+                if (!joint_residual<FLAT>(c, xh, rh, Eh, rhoh, vh)) return 0;
+            }
+            const double ih = 1.0 / h;
+            for (int row = 0; row < 4; row++) J[row * 4 + col] = (rh[row] - r[row]) * ih;
+        }
+        double b[4] = {-r[0], -r[1], -r[2], -r[3]}, dx[4];
+        if (!solve4(J, b, dx)) return 0;
+        const double n0 = nrm4(r);
+        double lam = 1.0, xt[4], rt[4], Et[3], rhot, vt[3];
+        bool ok = false;
+        for (int ls = 0; ls < 40; ls++) {
+            for (int k = 0; k < 4; k++) xt[k] = x[k] + lam * dx[k];
+            if (joint_residual<FLAT>(c, xt, rt, Et, rhot, vt) && nrm4(rt) < n0) {
+                ok = true;
+                break;
+            }
+            lam *= 0.5;
+        }
+        if (!ok) {
+            const double dvm = fmax(fabs(dx[1]), fmax(fabs(dx[2]), fabs(dx[3])));
+            if (p_conv<FLAT>(c, dx[0], x[0]) && dvm <= c.o.tol) break;
+            return 0;
+        }
+        const double sp = lam * dx[0];
+        const double sv = lam * fmax(fabs(dx[1]), fmax(fabs(dx[2]), fabs(dx[3])));
+        for (int k = 0; k < 4; k++) { x[k] = xt[k]; r[k] = rt[k]; }
+        if (p_conv<FLAT>(c, sp, x[0]) && sv <= c.o.tol) break;
+        if (it == 50) return 0;
+    }
+    if (!joint_residual<FLAT>(c, x, r, E, rho, v)) return 0;
+    p = x[0];
+    rho_out = rho;
+    return 1;
+}
+
+// Velocity equations at fixed p (x = v_lower):
+//   g_i = [v_i (tau + D + sqrt(g) p - EM) - (S_i - eta_ijk calE^j calB^k)] / scale
+template <bool FLAT>
+__device__ __forceinline__ bool vel_residual(const RecCtx<FLAT> &c, double p, const double vl[3],
+                                             double g[3], double E[3], double &v2o)
+{
+    double v[3];
+    raise<double, FLAT>(c.m, vl, v);
+    const double v2 = dot3(v, vl);
+    if (!(v2 < c.o.v2max)) return false;
+    if (c.implicit) {
+        implicit_field<FLAT>(c, v, vl, v2, rsqrt(1.0 - v2), E);
+    } else {
+        E[0] = c.in.cE0[0]; E[1] = c.in.cE0[1]; E[2] = c.in.cE0[2];
+    }
+    double El[3];
+    lower<double, FLAT>(c.m, E, El);
+    const double EM = 0.5 * (dot3(E, El) + c.B2) * c.isg;
+    double P[3];
+    cross3(E, c.in.cB, P);
+    const double scale = c.in.tau + c.in.D + c.sg * p;
+    const double iscale = 1.0 / scale;
+    const double den = scale - EM;
+#pragma unroll
+    for (int i = 0; i < 3; i++) g[i] = (vl[i] * den - (c.in.S[i] - P[i])) * iscale;
+    v2o = v2;
+    return true;
+}
+
+__device__ __forceinline__ double nrm3(const double g[3])
+{
+    return sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+}
+
+// velocity at fixed p: damped Newton with a forward-difference Jacobian
+template <bool FLAT>
+__device__ bool velocity_at(const RecCtx<FLAT> &c, double p, double vl[3])
+{
+    double g[3], E[3], v2;
+    if (!vel_residual<FLAT>(c, p, vl, g, E, v2)) return false;
+    for (int it = 0; it < 30; it++) {
+        double J[9];
+        for (int col = 0; col < 3; col++) {
+            double vh[3] = {vl[0], vl[1], vl[2]}, gh[3], h = 1e-7;
+            vh[col] += h;
+            if (!vel_residual<FLAT>(c, p, vh, gh, E, v2)) {
+                h = -h;
+                vh[col] = vl[col] + h;
+                if (!vel_residual<FLAT>(c, p, vh, gh, E, v2)) return false;
+            }
+            const double ih = 1.0 / h;
+            for (int row = 0; row < 3; row++) J[row * 3 + col] = (gh[row] - g[row]) * ih;
+        }
+        // 3x3 solve by Cramer's rule on -g
+        const double det = J[0] * (J[4] * J[8] - J[5] * J[7]) - J[1] * (J[3] * J[8] - J[5] * J[6]) +
+                           J[2] * (J[3] * J[7] - J[4] * J[6]);
+        if (!(fabs(det) > 0.0)) return false;
+        const double id = 1.0 / det;
+        const double b0 = -g[0], b1 = -g[1], b2 = -g[2];
+        double dv[3];
+        dv[0] = (b0 * (J[4] * J[8] - J[5] * J[7]) - J[1] * (b1 * J[8] - J[5] * b2) +
+                 J[2] * (b1 * J[7] - J[4] * b2)) * id;
+        dv[1] = (J[0] * (b1 * J[8] - J[5] * b2) - b0 * (J[3] * J[8] - J[5] * J[6]) +
+                 J[2] * (J[3] * b2 - b1 * J[6])) * id;
+        dv[2] = (J[0] * (J[4] * b2 - b1 * J[7]) - J[1] * (J[3] * b2 - b1 * J[6]) +
+                 b0 * (J[3] * J[7] - J[4] * J[6])) * id;
+        const double n0 = nrm3(g);
+        double lam = 1.0, vt[3], gt[3];
+        bool ok = false;
+        for (int ls = 0; ls < 40; ls++) {
+            for (int i = 0; i < 3; i++) vt[i] = vl[i] + lam * dv[i];
+            if (vel_residual<FLAT>(c, p, vt, gt, E, v2) && nrm3(gt) < n0) {
+                ok = true;
+                break;
+            }
+            lam *= 0.5;
+        }
+        if (!ok) return n0 < 1e-13;
+        const double step = lam * fmax(fabs(dv[0]), fmax(fabs(dv[1]), fabs(dv[2])));
+        for (int i = 0; i < 3; i++) { vl[i] = vt[i]; g[i] = gt[i]; }
+        if (step <= 1e-15) break;
+    }
+    return true;
+}
+
+// scaled f(p) = (Gamma-1) rho eps - p with the velocity solved at p
+template <bool FLAT>
+__device__ bool pressure_function(const RecCtx<FLAT> &c, double p, double vl[3], double &f,
+                                  double E[3], double &rho)
+{
+    if (!(p > 0.0) || !velocity_at<FLAT>(c, p, vl)) return false;
+    double g[3], v2;
+    vel_residual<FLAT>(c, p, vl, g, E, v2);
+    double El[3];
+    lower<double, FLAT>(c.m, E, El);
+    const double EM = 0.5 * (dot3(E, El) + c.B2) * c.isg;
+    const double W = rsqrt(1.0 - v2);
+    const double Winv = (1.0 - v2) * W;
+    rho = c.in.D * Winv * c.isg;
+    const double num = c.in.tau - c.in.D * (W - 1.0) - c.sg * p * (v2 * W * W) - EM;
+    const double eps = num * Winv * c.iD;
+    f = ((c.o.Gam - 1.0) * rho * eps - p) * c.sg / (c.in.tau + c.in.D + c.sg * p);
+    return true;
+}
+
+// Second fallback: bracket the pressure root (doubling or halving from the
+// guess), then Illinois regula falsi; every evaluation solves the velocity.
+template <bool FLAT>
+__device__ int bracket_fallback(const RecCtx<FLAT> &c, double &p, double v[3], double E[3],
+                                double &rho_out, int &iters)
+{
+    double vl[3], f0, rho;
+    lower<double, FLAT>(c.m, v, vl);
+    const double p0 = p > 0.0 ? p : c.o.p_atmo;
+    if (!pressure_function<FLAT>(c, p0, vl, f0, E, rho)) {
+        vl[0] = vl[1] = vl[2] = 0.0;
+        if (!pressure_function<FLAT>(c, p0, vl, f0, E, rho)) return 0;
+    }
+    double lo = p0, hi = p0, flo = f0, fhi = f0;
+    double vlo[3] = {vl[0], vl[1], vl[2]}, vhi[3] = {vl[0], vl[1], vl[2]};
+    int n = 0;
+    if (f0 > 0.0) {
+        while (fhi > 0.0) {
+            if (++n > 60) return 0;
+            lo = hi; flo = fhi;
+            for (int i = 0; i < 3; i++) vlo[i] = vhi[i];
+            hi = 2.0 * hi;
+            if (!pressure_function<FLAT>(c, hi, vhi, fhi, E, rho)) return 0;
+        }
+    } else {
+        while (flo < 0.0) {
+            if (++n > 60) return 0;
+            hi = lo; fhi = flo;
+            for (int i = 0; i < 3; i++) vhi[i] = vlo[i];
+            lo = 0.5 * lo;
+            if (!pressure_function<FLAT>(c, lo, vlo, flo, E, rho)) return 0;
+        }
+    }
+    int side = 0;
+    for (int it = 0; it < 100; it++) {
+        iters = n + it + 1;
+        double pm = (lo * fhi - hi * flo) / (fhi - flo);
+        if (!(pm > lo && pm < hi)) pm = 0.5 * (lo + hi);
+        double vm[3] = {vlo[0], vlo[1], vlo[2]}, fm;
+        if (!pressure_function<FLAT>(c, pm, vm, fm, E, rho)) return 0;
+        if (fm > 0.0) {
+            lo = pm; flo = fm;
+            for (int i = 0; i < 3; i++) vlo[i] = vm[i];
+            if (side == 1) fhi *= 0.5;
+            side = 1;
+        } else {
+            hi = pm; fhi = fm;
+            for (int i = 0; i < 3; i++) vhi[i] = vm[i];
+            if (side == -1) flo *= 0.5;
+            side = -1;
+        }
+        if ((hi - lo) * c.sg <= c.o.tol * (c.in.tau + c.in.D + c.sg * hi) || fm == 0.0) {
+            p = pm;
+            raise<double, FLAT>(c.m, vm, v);
+            rho_out = rho;
+            return 1;
+        }
+    }
+    return 0;
+}
+
+// Full pointwise recovery.  Writes the 14 primitives and the solved calE;
+// returns the status 0 (paper iteration), 1 (Newton fallback), 4 (pressure
+// bracket fallback), 2 (failed, atmosphere), 3 (rho below the floor,
+// atmosphere).  guess_p, guess_v: previous stage.
+template <bool FLAT>
+__device__ int recover(const RecIn &in, const Met<double> &m, const RecOpts &o,
+                       bool implicit, double cc, double guess_p, const double guess_v[3],
+                       double Phi, double Psi, double Q, double prim[NPR],
+                       double Eout[3], int &iters)
+{
+    RecCtx<FLAT> c{in, m, o, implicit, implicit ? cc : 0.0, 1.0, 1.0, 1.0 / in.D, {0, 0, 0}, 0.0};
+    if (!FLAT) {
+        c.sg = m.sg;
+        c.isg = m.isg;
+    }
+    lower<double, FLAT>(m, in.cB, c.cBl);
+    c.B2 = dot3(in.cB, c.cBl);
+
+    double p = guess_p, v[3] = {guess_v[0], guess_v[1], guess_v[2]};
+    double E[3] = {in.cE0[0], in.cE0[1], in.cE0[2]};
+    double rho = 0.0;
+    int it1 = 0, it2 = 0, status;
+    if (paper_iteration<FLAT>(c, p, v, E, rho, it1)) {
+        status = 0;
+    } else {
+        p = guess_p;
+        v[0] = guess_v[0]; v[1] = guess_v[1]; v[2] = guess_v[2];
+        E[0] = in.cE0[0]; E[1] = in.cE0[1]; E[2] = in.cE0[2];
+        status = newton_fallback<FLAT>(c, p, v, E, rho, it2) ? 1 : 2;
+        if (status == 2) {
+            int it3 = 0;
+            p = guess_p;
+            v[0] = guess_v[0]; v[1] = guess_v[1]; v[2] = guess_v[2];
+            E[0] = in.cE0[0]; E[1] = in.cE0[1]; E[2] = in.cE0[2];
+            if (bracket_fallback<FLAT>(c, p, v, E, rho, it3)) status = 4;
+            it2 += it3;
+        }
+    }
+    iters = it1 + it2;
+    if ((status == 0 || status == 1 || status == 4) && !(rho >= o.atmo_floor)) status = 3;
+    if (status == 2 || status == 3) {
+        rho = o.rho_atmo;
+        p = o.p_atmo;
+        v[0] = v[1] = v[2] = 0.0;
+        const double s = implicit ? 1.0 / (1.0 + c.cc) : 1.0;
+        for (int i = 0; i < 3; i++) E[i] = in.cE0[i] * s;
+    }
+    prim[PR_RHO] = rho;
+    prim[PR_P] = p;
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+        prim[PR_VX + i] = v[i];
+        prim[PR_EX + i] = FLAT ? E[i] : E[i] * c.isg;
+        prim[PR_BX + i] = FLAT ? in.cB[i] : in.cB[i] * c.isg;
+        Eout[i] = E[i];
+    }
+    prim[PR_PSI] = FLAT ? Psi : Psi * c.isg;
+    prim[PR_PHI] = FLAT ? Phi : Phi * c.isg;
+    prim[PR_Q] = FLAT ? Q : Q * c.isg;
+    return status;
+}
+
+} // namespace rmhd

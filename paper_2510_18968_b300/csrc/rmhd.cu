@@ -1,0 +1,662 @@
+// rmhd.cu -- host side of the C ABI declared in include/rmhd.h: parameter
+// checks, device memory, stage sequencing of the IMEX-SSP2(2,2,2) step
+// (arXiv:2510.18968 Sec. III.A, Eq. IMEX3) and the testing entry points.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "../../include/rmhd.h"
+#include "kernels.cuh"
+
+using namespace rmhd;
+
+namespace {
+
+const int TPB = 128;
+
+char g_noh_err[512] = "";
+
+struct Buffers {
+    double *U = nullptr, *PA = nullptr, *PB = nullptr, *V = nullptr;
+    double *dR1 = nullptr, *J1 = nullptr, *J2 = nullptr, *F[3] = {nullptr, nullptr, nullptr};
+    double *met = nullptr, *sig = nullptr, *stage = nullptr;
+    unsigned long long *stats = nullptr;
+    int *flag = nullptr;
+};
+
+} // namespace
+
+struct rmhd_s {
+    rmhd_params p;
+    cudaStream_t st;
+    StepConst K;
+    Buffers b;
+    bool flat = true;
+    bool have_state = false;
+    long long steps = 0;
+    char err[512];
+};
+
+static int set_err(rmhd_t h, int code, const char *fmt, ...)
+{
+    char *dst = h ? h->err : g_noh_err;
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(dst, 512, fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+#define CK(call)                                                                        \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess)                                                          \
+            return set_err(h, RMHD_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+static inline unsigned nblk(long long n) { return (unsigned)((n + TPB - 1) / TPB); }
+
+extern "C" void rmhd_default_params(rmhd_params *p)
+{
+    memset(p, 0, sizeof(*p));
+    for (int d = 0; d < 3; d++) {
+        p->n[d] = 1;
+        p->dx[d] = 1.0;
+        p->bc[d] = RMHD_BC_PERIODIC;
+    }
+    p->recon = RMHD_RECON_MINMOD;
+    p->precision = RMHD_PREC_FP64;
+    p->gamma_eos = 2.0;
+    p->kappa = 1.0;
+    p->sigma_model = RMHD_SIGMA_UNIFORM;
+    p->rho_atmo = 1e-10;
+    p->K_atmo = 100.0;
+    p->atmo_tol = 1e-2;
+    p->c2p_tol = 1e-14;
+    p->c2p_maxit = 100;
+    p->c2p_wmax = 100.0;
+    p->qflux_mode = RMHD_QFLUX_STAGE;
+}
+
+static int check_params(rmhd_t h, const rmhd_params *p)
+{
+    if (!p) return set_err(h, RMHD_EINVAL, "params is NULL");
+    for (int d = 0; d < 3; d++) {
+        if (p->n[d] < 1) return set_err(h, RMHD_EINVAL, "n[%d] = %d < 1", d, p->n[d]);
+        if (!(p->dx[d] > 0.0)) return set_err(h, RMHD_EINVAL, "dx[%d] must be > 0", d);
+        if (p->bc[d] != RMHD_BC_PERIODIC && p->bc[d] != RMHD_BC_OUTFLOW)
+            return set_err(h, RMHD_EINVAL, "bc[%d] = %d unknown", d, p->bc[d]);
+        if (p->n[d] > 1 && p->n[d] < 3 && p->bc[d] == RMHD_BC_PERIODIC)
+            return set_err(h, RMHD_EINVAL, "periodic direction %d needs n >= 3", d);
+    }
+    if (p->recon < 0 || p->recon > 2) return set_err(h, RMHD_EINVAL, "recon %d unknown", p->recon);
+    if (p->precision != RMHD_PREC_FP64 && p->precision != RMHD_PREC_MIXED)
+        return set_err(h, RMHD_EINVAL, "precision %d unknown", p->precision);
+    if (!(p->gamma_eos > 1.0)) return set_err(h, RMHD_EINVAL, "gamma_eos must be > 1");
+    if (p->sigma_model < 0 || p->sigma_model > 3)
+        return set_err(h, RMHD_EINVAL, "sigma_model %d unknown", p->sigma_model);
+    if (!(p->sigma0 >= 0.0)) return set_err(h, RMHD_EINVAL, "sigma0 must be >= 0");
+    if (!(p->rho_atmo > 0.0) || !(p->K_atmo >= 0.0) || !(p->atmo_tol >= 0.0))
+        return set_err(h, RMHD_EINVAL, "atmosphere parameters out of range");
+    if (!(p->c2p_tol > 0.0) || p->c2p_maxit < 1 || !(p->c2p_wmax > 1.0))
+        return set_err(h, RMHD_EINVAL, "recovery parameters out of range");
+    if (p->qflux_mode != RMHD_QFLUX_STAGE && p->qflux_mode != RMHD_QFLUX_FACE_OHM)
+        return set_err(h, RMHD_EINVAL, "qflux_mode %d unknown", p->qflux_mode);
+    return RMHD_OK;
+}
+
+static RecOpts rec_opts(const rmhd_params *p)
+{
+    RecOpts o;
+    o.Gam = p->gamma_eos;
+    o.tol = p->c2p_tol;
+    o.v2max = 1.0 - 1.0 / (p->c2p_wmax * p->c2p_wmax);
+    o.rho_atmo = p->rho_atmo;
+    o.p_atmo = p->K_atmo * pow(p->rho_atmo, p->gamma_eos);
+    o.atmo_floor = p->rho_atmo * (1.0 + p->atmo_tol);
+    o.maxit = p->c2p_maxit;
+    return o;
+}
+
+static void free_all(Buffers &b)
+{
+    double **ptrs[] = {&b.U, &b.PA, &b.PB, &b.V, &b.dR1, &b.J1, &b.J2, &b.F[0], &b.F[1],
+                       &b.F[2], &b.met, &b.sig, &b.stage};
+    for (double **q : ptrs)
+        if (*q) {
+            cudaFree(*q);
+            *q = nullptr;
+        }
+    if (b.stats) cudaFree(b.stats);
+    if (b.flag) cudaFree(b.flag);
+    b.stats = nullptr;
+    b.flag = nullptr;
+}
+
+// ------------------------------------------------------------------ launches
+
+static void launch_ghosts(rmhd_t h, double *buf, int nf)
+{
+    const Grid &G = h->K.G;
+    long long mx = 0;
+    for (int d = 0; d < 3; d++) {
+        if (!G.g[d]) continue;
+        long long c = 2LL * G.g[d] * G.n[(d + 1) % 3] * G.n[(d + 2) % 3];
+        if (c > mx) mx = c;
+    }
+    if (!mx) return;
+    dim3 grid(nblk(mx), 3);
+    k_ghosts<<<grid, TPB, 0, h->st>>>(h->K, buf, nf, 0);
+}
+
+template <class T, bool FLAT, int RC>
+static void launch_flux_rc(rmhd_t h, const double *P, const double *J)
+{
+    const Grid &G = h->K.G;
+    const Buffers &b = h->b;
+    if (G.g[0]) {
+        long long n = (long long)(G.n[0] + 1) * G.n[1] * G.n[2];
+        k_flux<T, FLAT, RC, 0><<<nblk(n), TPB, 0, h->st>>>(h->K, P, J, b.met, b.sig, b.F[0]);
+    }
+    if (G.g[1]) {
+        long long n = (long long)G.n[0] * (G.n[1] + 1) * G.n[2];
+        k_flux<T, FLAT, RC, 1><<<nblk(n), TPB, 0, h->st>>>(h->K, P, J, b.met, b.sig, b.F[1]);
+    }
+    if (G.g[2]) {
+        long long n = (long long)G.n[0] * G.n[1] * (G.n[2] + 1);
+        k_flux<T, FLAT, RC, 2><<<nblk(n), TPB, 0, h->st>>>(h->K, P, J, b.met, b.sig, b.F[2]);
+    }
+}
+
+template <class T, bool FLAT>
+static void launch_flux_t(rmhd_t h, const double *P, const double *J)
+{
+    switch (h->p.recon) {
+    case RMHD_RECON_MINMOD: launch_flux_rc<T, FLAT, RC_MINMOD>(h, P, J); break;
+    case RMHD_RECON_MC2: launch_flux_rc<T, FLAT, RC_MC2>(h, P, J); break;
+    default: launch_flux_rc<T, FLAT, RC_WENO5>(h, P, J); break;
+    }
+}
+
+static void launch_flux(rmhd_t h, const double *P, const double *J)
+{
+    const bool mixed = h->p.precision == RMHD_PREC_MIXED;
+    if (h->flat) {
+        if (mixed) launch_flux_t<float, true>(h, P, J);
+        else launch_flux_t<double, true>(h, P, J);
+    } else {
+        if (mixed) launch_flux_t<float, false>(h, P, J);
+        else launch_flux_t<double, false>(h, P, J);
+    }
+}
+
+// ev (optional): 7 events recorded between the kernel groups of the step
+template <bool FLAT> static void enqueue_step(rmhd_t h, cudaEvent_t *ev = nullptr)
+{
+    Buffers &b = h->b;
+    const StepConst &K = h->K;
+    const unsigned nb = nblk(K.G.N);
+    auto mark = [&](int i) { if (ev) cudaEventRecord(ev[i], h->st); };
+    mark(0);
+    k_stage1<FLAT><<<nb, TPB, 0, h->st>>>(K, b.U, b.PA, b.dR1, b.J1, b.met, b.sig, b.stats);
+    mark(1);
+    launch_ghosts(h, b.PA, NPR);
+    if (K.qflux == 0) launch_ghosts(h, b.J1, 3);
+    mark(2);
+    launch_flux(h, b.PA, b.J1);
+    mark(3);
+    k_stage2<FLAT><<<nb, TPB, 0, h->st>>>(K, b.U, b.PA, b.F[0], b.F[1], b.F[2], b.dR1, b.met,
+                                          b.sig, b.PB, b.V, b.J2, b.stats);
+    mark(4);
+    launch_ghosts(h, b.PB, NPR);
+    if (K.qflux == 0) launch_ghosts(h, b.J2, 3);
+    mark(5);
+    launch_flux(h, b.PB, b.J2);
+    mark(6);
+    k_final<FLAT><<<nb, TPB, 0, h->st>>>(K, b.V, b.PB, b.F[0], b.F[1], b.F[2], b.met, b.U, b.PA,
+                                         b.stats);
+    mark(7);
+    launch_ghosts(h, b.PA, NPR);
+    mark(8);
+}
+
+// copy a caller array (interior SoA, nf fields) into the staging buffer
+static int stage_in(rmhd_t h, const double *src, int nf, int on_device)
+{
+    size_t bytes = sizeof(double) * nf * (size_t)h->K.G.N;
+    CK(cudaMemcpyAsync(h->b.stage, src, bytes,
+                       on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->st));
+    return RMHD_OK;
+}
+
+static int stage_out(rmhd_t h, double *dst, int nf, int on_device)
+{
+    size_t bytes = sizeof(double) * nf * (size_t)h->K.G.N;
+    CK(cudaMemcpyAsync(dst, h->b.stage, bytes,
+                       on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->st));
+    if (!on_device) CK(cudaStreamSynchronize(h->st));
+    return RMHD_OK;
+}
+
+static int read_flag(rmhd_t h, int *v)
+{
+    CK(cudaMemcpyAsync(v, h->b.flag, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    return RMHD_OK;
+}
+
+// ------------------------------------------------------------------ API
+
+extern "C" int rmhd_create(const rmhd_params *p, void *cuda_stream, rmhd_t *out)
+{
+    rmhd_t h = nullptr;
+    if (!out) return set_err(nullptr, RMHD_EINVAL, "out is NULL");
+    *out = nullptr;
+    int rc = check_params(nullptr, p);
+    if (rc) return rc;
+    h = new rmhd_s();
+    h->p = *p;
+    h->err[0] = 0;
+    h->st = (cudaStream_t)cuda_stream;
+    StepConst &K = h->K;
+    memset(&K, 0, sizeof(K));
+    Grid &G = K.G;
+    for (int d = 0; d < 3; d++) {
+        G.n[d] = p->n[d];
+        G.g[d] = p->n[d] > 1 ? 3 : 0;
+        G.idx[d] = 1.0 / p->dx[d];
+        G.bc[d] = p->bc[d];
+    }
+    G.px = G.n[0] + 2 * G.g[0];
+    G.pxy = G.px * (G.n[1] + 2 * G.g[1]);
+    G.S = (long long)G.pxy * (G.n[2] + 2 * G.g[2]);
+    G.N = (long long)G.n[0] * G.n[1] * G.n[2];
+    K.gimex = 1.0 - 1.0 / sqrt(2.0);
+    K.gfac = p->gamma_eos / (p->gamma_eos - 1.0);
+    K.kappa = p->kappa;
+    K.sigma_model = p->sigma_model;
+    K.sigma0 = p->sigma0;
+    K.sigma_exp = p->sigma_exp;
+    K.D_atmo = p->D_atmo;
+    K.qflux = p->qflux_mode;
+    K.ro = rec_opts(p);
+
+    Buffers &b = h->b;
+    const size_t fb = sizeof(double) * (size_t)G.S;
+    struct { double **ptr; int nf; } allocs[] = {
+        {&b.U, NCO}, {&b.PA, NPR}, {&b.PB, NPR}, {&b.V, NCO}, {&b.dR1, 3}, {&b.J1, 3},
+        {&b.J2, 3}, {&b.F[0], NCO}, {&b.F[1], NCO}, {&b.F[2], NCO}, {&b.met, NMET}, {&b.sig, 1}};
+    for (auto &a : allocs) {
+        cudaError_t e = cudaMalloc((void **)a.ptr, fb * a.nf);
+        if (e != cudaSuccess) {
+            free_all(b);
+            set_err(nullptr, RMHD_ENOMEM, "cudaMalloc of %zu bytes failed: %s", fb * a.nf,
+                    cudaGetErrorString(e));
+            delete h;
+            return RMHD_ENOMEM;
+        }
+        cudaMemsetAsync(*a.ptr, 0, fb * a.nf, h->st);
+    }
+    if (cudaMalloc((void **)&b.stage, sizeof(double) * NPR * (size_t)G.N) != cudaSuccess ||
+        cudaMalloc((void **)&b.stats, sizeof(unsigned long long) * NSTAT) != cudaSuccess ||
+        cudaMalloc((void **)&b.flag, sizeof(int)) != cudaSuccess) {
+        free_all(b);
+        set_err(nullptr, RMHD_ENOMEM, "cudaMalloc of staging buffers failed");
+        delete h;
+        return RMHD_ENOMEM;
+    }
+    cudaMemsetAsync(b.stats, 0, sizeof(unsigned long long) * NSTAT, h->st);
+    // flat metric, unit conductivity profile; the state comes from
+    // rmhd_set_prims or rmhd_set_state
+    rc = rmhd_set_metric(h, nullptr, nullptr, nullptr, nullptr, 0);
+    if (!rc) rc = rmhd_set_sigma(h, nullptr, 0);
+    if (rc) {
+        free_all(b);
+        delete h;
+        return rc;
+    }
+    *out = h;
+    return RMHD_OK;
+}
+
+// fill field f of a padded buffer with a constant (interior and ghosts)
+__global__ void k_fill(double *a, long long n, double v)
+{
+    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t < n) a[t] = v;
+}
+
+// flags any interior cell whose metric differs from flat space
+__global__ void k_not_flat(const StepConst K, const double *__restrict__ met, int *flag)
+{
+    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= K.G.N) return;
+    int i, j, k;
+    interior_coords(K.G, t, i, j, k);
+    const long long c = cell_at(K.G, i, j, k);
+    const double flat[NMET] = {1, 0, 0, 0, 1, 0, 0, 1, 0, 1, 0, 0, 0, 0, 0, 0};
+    for (int f = 0; f < NMET; f++)
+        if (met[f * K.G.S + c] != flat[f]) {
+            atomicOr(flag, 1);
+            return;
+        }
+}
+
+extern "C" int rmhd_set_metric(rmhd_t h, const double *alpha, const double *beta,
+                               const double *gamma, const double *K4, int on_device)
+{
+    if (!h) return set_err(nullptr, RMHD_EINVAL, "handle is NULL");
+    const Grid &G = h->K.G;
+    const long long S = G.S;
+    double *met = h->b.met;
+    if (!alpha) {
+        // flat space
+        const double vals[NMET] = {1, 0, 0, 0, 1, 0, 0, 1, 0, 1, 0, 0, 0, 0, 0, 0};
+        for (int f = 0; f < NMET; f++)
+            k_fill<<<nblk(S), TPB, 0, h->st>>>(met + f * S, S, vals[f]);
+        CK(cudaGetLastError());
+        CK(cudaStreamSynchronize(h->st));
+        h->flat = true;
+        return RMHD_OK;
+    }
+    if (!beta || !gamma || !K4) return set_err(h, RMHD_EINVAL, "beta, gamma and K are required");
+    // stage the 16 fields through a temporary padded copy so that a rejected
+    // metric leaves the current one in place
+    double *tmp = nullptr;
+    CK(cudaMalloc((void **)&tmp, sizeof(double) * NMET * (size_t)S));
+    const double *src[4] = {alpha, beta, gamma, K4};
+    const int nf[4] = {1, 3, 6, 6};
+    int off = 0;
+    int rc = RMHD_OK;
+    for (int a = 0; a < 4 && !rc; a++) {
+        rc = stage_in(h, src[a], nf[a], on_device);
+        if (!rc) k_scatter<<<nblk(G.N), TPB, 0, h->st>>>(h->K, h->b.stage, tmp + off * S, nf[a]);
+        off += nf[a];
+    }
+    if (!rc) {
+        launch_ghosts(h, tmp, NMET);
+        cudaMemsetAsync(h->b.flag, 0, sizeof(int), h->st);
+        k_check_metric<<<nblk(G.N), TPB, 0, h->st>>>(h->K, tmp, h->b.flag);
+        int bad = 0;
+        rc = read_flag(h, &bad);
+        if (!rc && bad) rc = set_err(h, RMHD_EINVAL, "metric rejected: alpha <= 0, gamma_ij not "
+                                                     "positive definite, or non-finite values");
+    }
+    if (!rc) {
+        cudaMemcpyAsync(met, tmp, sizeof(double) * NMET * (size_t)S, cudaMemcpyDeviceToDevice,
+                        h->st);
+        // a metric equal to flat space everywhere selects the flat kernels
+        cudaMemsetAsync(h->b.flag, 0, sizeof(int), h->st);
+        k_not_flat<<<nblk(G.N), TPB, 0, h->st>>>(h->K, tmp, h->b.flag);
+        int curved = 1;
+        rc = read_flag(h, &curved);
+        h->flat = !rc && !curved;
+    }
+    cudaFree(tmp);
+    return rc;
+}
+
+extern "C" int rmhd_set_sigma(rmhd_t h, const double *profile, int on_device)
+{
+    if (!h) return set_err(nullptr, RMHD_EINVAL, "handle is NULL");
+    const Grid &G = h->K.G;
+    if (!profile) {
+        k_fill<<<nblk(G.S), TPB, 0, h->st>>>(h->b.sig, G.S, 1.0);
+        CK(cudaGetLastError());
+        CK(cudaStreamSynchronize(h->st));
+        return RMHD_OK;
+    }
+    int rc = stage_in(h, profile, 1, on_device);
+    if (rc) return rc;
+    cudaMemsetAsync(h->b.flag, 0, sizeof(int), h->st);
+    k_check_finite<<<nblk(G.N), TPB, 0, h->st>>>(G.N, h->b.stage, h->b.flag);
+    int bad = 0;
+    // negative values: reuse the finiteness kernel on -x via a host check below
+    rc = read_flag(h, &bad);
+    if (rc) return rc;
+    if (bad) return set_err(h, RMHD_EINVAL, "sigma profile has non-finite values");
+    // negativity check on the staged copy (host side, small cost at set-up)
+    {
+        size_t n = (size_t)G.N;
+        double *hb = (double *)malloc(sizeof(double) * n);
+        if (!hb) return set_err(h, RMHD_ENOMEM, "host buffer");
+        CK(cudaMemcpy(hb, h->b.stage, sizeof(double) * n, cudaMemcpyDeviceToHost));
+        for (size_t i = 0; i < n; i++)
+            if (hb[i] < 0.0) {
+                free(hb);
+                return set_err(h, RMHD_EINVAL, "sigma profile has negative values");
+            }
+        free(hb);
+    }
+    k_scatter<<<nblk(G.N), TPB, 0, h->st>>>(h->K, h->b.stage, h->b.sig, 1);
+    launch_ghosts(h, h->b.sig, 1);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(h->st));
+    return RMHD_OK;
+}
+
+extern "C" int rmhd_set_prims(rmhd_t h, const double *prims, int on_device)
+{
+    if (!h) return set_err(nullptr, RMHD_EINVAL, "handle is NULL");
+    if (!prims) return set_err(h, RMHD_EINVAL, "prims is NULL");
+    const Grid &G = h->K.G;
+    int rc = stage_in(h, prims, NPR, on_device);
+    if (rc) return rc;
+    // scatter into PB first: validate before touching the state
+    k_scatter<<<nblk(G.N), TPB, 0, h->st>>>(h->K, h->b.stage, h->b.PB, NPR);
+    cudaMemsetAsync(h->b.flag, 0, sizeof(int), h->st);
+    if (h->flat)
+        k_prim2con<true><<<nblk(G.N), TPB, 0, h->st>>>(h->K, h->b.PB, h->b.met, h->b.V, h->b.flag);
+    else
+        k_prim2con<false><<<nblk(G.N), TPB, 0, h->st>>>(h->K, h->b.PB, h->b.met, h->b.V, h->b.flag);
+    int bad = 0;
+    rc = read_flag(h, &bad);
+    if (rc) return rc;
+    if (bad) return set_err(h, RMHD_EINVAL, "prims rejected: rho <= 0, p < 0, v^2 >= 1 or "
+                                            "non-finite values");
+    CK(cudaMemcpyAsync(h->b.PA, h->b.PB, sizeof(double) * NPR * (size_t)G.S,
+                       cudaMemcpyDeviceToDevice, h->st));
+    CK(cudaMemcpyAsync(h->b.U, h->b.V, sizeof(double) * NCO * (size_t)G.S,
+                       cudaMemcpyDeviceToDevice, h->st));
+    launch_ghosts(h, h->b.PA, NPR);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(h->st));
+    h->have_state = true;
+    return RMHD_OK;
+}
+
+extern "C" int rmhd_set_state(rmhd_t h, const double *cons, const double *prims, int on_device)
+{
+    if (!h) return set_err(nullptr, RMHD_EINVAL, "handle is NULL");
+    if (!cons || !prims) return set_err(h, RMHD_EINVAL, "cons and prims are required");
+    const Grid &G = h->K.G;
+    int bad = 0, rc;
+    const double *src[2] = {cons, prims};
+    double *dst[2] = {h->b.U, h->b.PA};
+    // validate both before committing
+    for (int a = 0; a < 2; a++) {
+        rc = stage_in(h, src[a], NPR, on_device);
+        if (rc) return rc;
+        cudaMemsetAsync(h->b.flag, 0, sizeof(int), h->st);
+        k_check_finite<<<nblk(NPR * G.N), TPB, 0, h->st>>>(NPR * G.N, h->b.stage, h->b.flag);
+        rc = read_flag(h, &bad);
+        if (rc) return rc;
+        if (bad) return set_err(h, RMHD_EINVAL, "state has non-finite values");
+    }
+    for (int a = 0; a < 2; a++) {
+        rc = stage_in(h, src[a], NPR, on_device);
+        if (rc) return rc;
+        k_scatter<<<nblk(G.N), TPB, 0, h->st>>>(h->K, h->b.stage, dst[a], NPR);
+    }
+    launch_ghosts(h, h->b.PA, NPR);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(h->st));
+    h->have_state = true;
+    return RMHD_OK;
+}
+
+extern "C" int rmhd_step(rmhd_t h, double dt, int nsteps, long long *fail_count)
+{
+    if (!h) return set_err(nullptr, RMHD_EINVAL, "handle is NULL");
+    if (!(dt > 0.0) || !isfinite(dt)) return set_err(h, RMHD_EINVAL, "dt must be > 0");
+    if (nsteps < 0) return set_err(h, RMHD_EINVAL, "nsteps must be >= 0");
+    if (!h->have_state) return set_err(h, RMHD_EINVAL, "no state: call rmhd_set_prims first");
+    h->K.dt = dt;
+    unsigned long long before[NSTAT];
+    if (fail_count) {
+        CK(cudaMemcpyAsync(before, h->b.stats, sizeof(before), cudaMemcpyDeviceToHost, h->st));
+        CK(cudaStreamSynchronize(h->st));
+    }
+    for (int s = 0; s < nsteps; s++) {
+        if (h->flat) enqueue_step<true>(h);
+        else enqueue_step<false>(h);
+    }
+    CK(cudaGetLastError());
+    h->steps += nsteps;
+    if (!fail_count) return RMHD_OK;
+    unsigned long long after[NSTAT];
+    CK(cudaMemcpyAsync(after, h->b.stats, sizeof(after), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    *fail_count = (long long)(after[ST_FAIL] - before[ST_FAIL]);
+    if (after[ST_NAN]) return set_err(h, RMHD_ENAN, "non-finite conserved values");
+    if (*fail_count > 0)
+        return set_err(h, RMHD_EC2P, "%lld recoveries reset to the atmosphere", *fail_count);
+    return RMHD_OK;
+}
+
+extern "C" int rmhd_step_profiled(rmhd_t h, double dt, int nsteps, double ms[RMHD_NPROF])
+{
+    if (!h || !ms) return set_err(h, RMHD_EINVAL, "NULL argument");
+    if (!(dt > 0.0) || !isfinite(dt) || nsteps < 0)
+        return set_err(h, RMHD_EINVAL, "dt must be > 0 and nsteps >= 0");
+    if (!h->have_state) return set_err(h, RMHD_EINVAL, "no state: call rmhd_set_prims first");
+    h->K.dt = dt;
+    for (int g = 0; g < RMHD_NPROF; g++) ms[g] = 0.0;
+    cudaEvent_t ev[9];
+    for (int i = 0; i < 9; i++) CK(cudaEventCreate(&ev[i]));
+    int rc = RMHD_OK;
+    for (int s = 0; s < nsteps && !rc; s++) {
+        if (h->flat) enqueue_step<true>(h, ev);
+        else enqueue_step<false>(h, ev);
+        cudaError_t e = cudaEventSynchronize(ev[8]);
+        if (e != cudaSuccess) {
+            rc = set_err(h, RMHD_ECUDA, "step failed: %s", cudaGetErrorString(e));
+            break;
+        }
+        // groups: stage1, ghosts, fluxes of stage 2, stage2, fluxes of the
+        // final assembly, final
+        const int from[RMHD_NPROF] = {0, 1, 2, 3, 5, 6};
+        const int to[RMHD_NPROF] = {1, 2, 3, 4, 6, 7};
+        for (int g = 0; g < RMHD_NPROF; g++) {
+            float t = 0.f;
+            cudaEventElapsedTime(&t, ev[from[g]], ev[to[g]]);
+            ms[g] += t;
+        }
+        float t1 = 0.f, t2 = 0.f;
+        cudaEventElapsedTime(&t1, ev[4], ev[5]);
+        cudaEventElapsedTime(&t2, ev[7], ev[8]);
+        ms[1] += t1 + t2;
+    }
+    for (int i = 0; i < 9; i++) cudaEventDestroy(ev[i]);
+    if (!rc) h->steps += nsteps;
+    return rc;
+}
+
+extern "C" int rmhd_get_prims(rmhd_t h, double *prims, int on_device)
+{
+    if (!h || !prims) return set_err(h, RMHD_EINVAL, "NULL argument");
+    k_gather<<<nblk(h->K.G.N), TPB, 0, h->st>>>(h->K, h->b.PA, h->b.stage, NPR);
+    CK(cudaGetLastError());
+    return stage_out(h, prims, NPR, on_device);
+}
+
+extern "C" int rmhd_get_cons(rmhd_t h, double *cons, int on_device)
+{
+    if (!h || !cons) return set_err(h, RMHD_EINVAL, "NULL argument");
+    k_gather<<<nblk(h->K.G.N), TPB, 0, h->st>>>(h->K, h->b.U, h->b.stage, NCO);
+    CK(cudaGetLastError());
+    return stage_out(h, cons, NCO, on_device);
+}
+
+extern "C" int rmhd_get_stats(rmhd_t h, long long stats[8])
+{
+    if (!h || !stats) return set_err(h, RMHD_EINVAL, "NULL argument");
+    unsigned long long s[NSTAT];
+    CK(cudaMemcpyAsync(s, h->b.stats, sizeof(s), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    stats[0] = (long long)s[ST_CALLS];
+    stats[1] = (long long)s[ST_ITERS];
+    stats[2] = (long long)s[ST_FALLBACK];
+    stats[3] = (long long)s[ST_FAIL];
+    stats[4] = (long long)s[ST_FLOOR];
+    stats[5] = (long long)s[ST_MAXIT];
+    stats[6] = (long long)s[ST_NAN];
+    stats[7] = h->steps;
+    return RMHD_OK;
+}
+
+extern "C" int rmhd_rhs(rmhd_t h, const double *prims, const double *J, double *rhs,
+                        int on_device)
+{
+    if (!h || !prims || !rhs) return set_err(h, RMHD_EINVAL, "NULL argument");
+    const Grid &G = h->K.G;
+    int rc = stage_in(h, prims, NPR, on_device);
+    if (rc) return rc;
+    k_scatter<<<nblk(G.N), TPB, 0, h->st>>>(h->K, h->b.stage, h->b.PB, NPR);
+    if (J) {
+        rc = stage_in(h, J, 3, on_device);
+        if (rc) return rc;
+        k_scatter<<<nblk(G.N), TPB, 0, h->st>>>(h->K, h->b.stage, h->b.J2, 3);
+    } else {
+        CK(cudaMemsetAsync(h->b.J2, 0, sizeof(double) * 3 * (size_t)G.S, h->st));
+    }
+    launch_ghosts(h, h->b.PB, NPR);
+    launch_ghosts(h, h->b.J2, 3);
+    launch_flux(h, h->b.PB, h->b.J2);
+    if (h->flat)
+        k_rhs<true><<<nblk(G.N), TPB, 0, h->st>>>(h->K, h->b.PB, h->b.F[0], h->b.F[1], h->b.F[2],
+                                                  h->b.met, h->b.stage);
+    else
+        k_rhs<false><<<nblk(G.N), TPB, 0, h->st>>>(h->K, h->b.PB, h->b.F[0], h->b.F[1], h->b.F[2],
+                                                   h->b.met, h->b.stage);
+    CK(cudaGetLastError());
+    return stage_out(h, rhs, NCO, on_device);
+}
+
+extern "C" int rmhd_con2prim_points(const rmhd_params *p, int npts, const double *cons,
+                                    const double *guess, const double *alpha,
+                                    const double *gamma, const double *sigma, int implicit,
+                                    double c, double *prim, double *cons_out, int *iters,
+                                    int *status, void *cuda_stream)
+{
+    rmhd_t h = nullptr;
+    if (!p) return set_err(h, RMHD_EINVAL, "params is NULL");
+    if (npts < 0) return set_err(h, RMHD_EINVAL, "npts < 0");
+    if (npts == 0) return RMHD_OK;
+    if (!cons || !guess || !alpha || !gamma || !prim || !cons_out || !iters || !status ||
+        (implicit && !sigma))
+        return set_err(h, RMHD_EINVAL, "NULL array");
+    if (!(p->gamma_eos > 1.0) || !(p->c2p_tol > 0.0) || p->c2p_maxit < 1 || !(p->c2p_wmax > 1.0))
+        return set_err(h, RMHD_EINVAL, "recovery parameters out of range");
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    k_recover_points<<<nblk(npts), TPB, 0, st>>>(rec_opts(p), npts, cons, guess, alpha, gamma,
+                                                 sigma, implicit, c,
+                                                 p->gamma_eos / (p->gamma_eos - 1.0), prim,
+                                                 cons_out, iters, status);
+    CK(cudaGetLastError());
+    return RMHD_OK;
+}
+
+extern "C" const char *rmhd_last_error(rmhd_t h) { return h ? h->err : g_noh_err; }
+
+extern "C" int rmhd_destroy(rmhd_t h)
+{
+    if (!h) return RMHD_OK;
+    cudaStreamSynchronize(h->st);
+    free_all(h->b);
+    delete h;
+    return RMHD_OK;
+}

@@ -252,7 +252,7 @@ def test_con2prim_round_trip_fixed_E(gam_eos):
         guess[1] *= 1.0 + 0.05 * rng.standard_normal()
         guess[2:5] *= 1.0 + 0.02 * rng.standard_normal()
         out, cout, it, st = oracle.con2prim(P, Ux, 0, 0.0, 0.0, guess, alpha, g6)
-        assert st in (0, 1)
+        assert st in (0, 1, 4)
         scale = np.abs(px).max()
         assert np.allclose(out, px, rtol=1e-12, atol=1e-12 * scale), (out - px, st, it)
         assert np.array_equal(cout, Ux)
@@ -275,7 +275,7 @@ def test_con2prim_round_trip_implicit(cs):
         guess[1] *= 1.0 + 0.02 * rng.standard_normal()
         guess[2:5] *= 1.0 + 0.01 * rng.standard_normal()
         out, cout, it, st = oracle.con2prim(P, Ustar, 1, c, sigma, guess, alpha, g6)
-        if st >= 2:
+        if st in (2, 3):
             fails += 1
             continue
         scale = np.abs(px).max()
@@ -298,7 +298,7 @@ def test_con2prim_root_is_the_only_bracketed_root():
         c = 0.25
         sigma = cs / c
         out, _, _, st = oracle.con2prim(P, Ustar, 1, c, sigma, prim, 1.0, g6)
-        assert st in (0, 1)
+        assert st in (0, 1, 4)
         D, S, tau, cB, E0 = Ustar[0], Ustar[1:4], Ustar[4], Ustar[5:8], Ustar[8:11]
 
         def fluid(p, v):
@@ -342,3 +342,32 @@ def test_con2prim_resets_unphysical_state_to_atmosphere():
     assert out[0] == 1e-6 and out[1] == 100.0 * 1e-12 and not out[2:5].any()
     assert out[8] == 0.2
     assert cout[0] == 1e-6 and cout[1] == 0.0
+
+
+def _hard_cases():
+    import os
+    d = np.load(os.path.join(os.path.dirname(__file__), "golden", "recovery_hard_cases.npz"))
+    return {k: d[k] for k in d.files}
+
+
+def test_pressure_bracket_recovers_states_where_newton_stalls():
+    """Stage inputs from the magnetised blast front (tests/golden, written by
+    make_recovery_cases.py from the oracle) on which the paper iteration and
+    the 4D Newton fail: the bracket finds a root, checked independently by
+    re-forming D, S_i, tau from the returned primitives and re-solving the
+    implicit field (Eq. 3D_NR) at the returned velocity."""
+    d = _hard_cases()
+    gam = float(d["gamma_eos"])
+    P = oracle.make_params(gamma_eos=gam, rho_atmo=1e-10)
+    for i in range(d["cons"].shape[1]):
+        cin, guess = d["cons"][:, i], d["guess"][:, i]
+        out, cout, it, st = oracle.con2prim(P, cin, 1, float(d["c"]), float(d["sigma"]), guess)
+        assert st == 4, st
+        # the returned calE solves the stage equation at the returned v
+        E = oracle.implicit_E(cin[8:11], cin[5:8], out[2:5], sigma=float(d["sigma"]),
+                              c=float(d["c"]))
+        assert np.allclose(E, cout[8:11], rtol=1e-12, atol=1e-15)
+        # and prim -> con of the returned state gives back D, S_i, tau
+        U = oracle.prim2con(out, 1.0, (0, 0, 0), (1, 0, 0, 1, 0, 1), gam)
+        scale = cin[4] + cin[0] + out[1]
+        assert np.abs(U[:5] - cin[:5]).max() < 1e-12 * scale
