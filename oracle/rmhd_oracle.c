@@ -27,9 +27,11 @@
  *  - Stiff term stored algebraically: Dt R(i) = (calE(i) - calE*)/gamma_imex.
  *  - Cell-centred conserved quantities inside the source terms are computed
  *    from the stage primitives.
- *  - Recovery: tolerance, iteration cap, a damped 4D Newton fallback on
- *    (p, v_i), a second fallback that brackets the pressure root with the
- *    velocity solved at each pressure, and an atmosphere reset are not given
+ *  - Recovery: tolerance, iteration cap, divergence / slow-convergence
+ *    stops, a damped 4D Newton fallback on (p, v_i), a second fallback that
+ *    brackets the pressure root with the velocity solved at each pressure, a
+ *    rerun of the paper iteration to its cap when it was stopped for being
+ *    slow and both fallbacks failed, and an atmosphere reset are not given
  *    by the paper.
  */
 #include "rmhd_oracle.h"
@@ -488,12 +490,22 @@ static int p_converged(const c2p_in *in, double dp, double p)
  * implicit solve at the current v; (iii) fluid variables; (iv) Newton update
  * of p with f = p(rho,eps) - p, f' = v^2 c_s^2 - 1; (v) repeat.
  * Returns 1 on convergence. */
+/* Gives up (returns 0) when the iterate leaves the physical region, when the
+ * change grows three times in a row above the rounding noise (divergence),
+ * or, if allow_slow is 0, when after 6 iterations the observed contraction
+ * rate predicts more than 24 further iterations (slow convergence: the
+ * Newton fallback is cheaper).  *slow_stop tells which. */
 static int c2p_paper(const c2p_in *in, double *p_io, double v_io[3],
-                     double cE[3], double *rho_o, int *iters)
+                     double cE[3], double *rho_o, int *iters, int allow_slow,
+                     int *slow_stop)
 {
     double Gam = in->P->gamma_eos;
     double p = *p_io, v[3] = {v_io[0], v_io[1], v_io[2]};
     double hist[3] = {0, 0, 0};
+    /* energy scale at the guess, for the change measure */
+    double sg0 = in->m->sg;
+    double scale0 = (in->tau + in->D + sg0 * p) / sg0;
+    *slow_stop = 0;
     for (int it = 1; it <= in->P->c2p_maxit; it++) {
         *iters = it;
         if (in->implicit) {
@@ -525,12 +537,18 @@ static int c2p_paper(const c2p_in *in, double *p_io, double v_io[3],
             return 1;
         }
         /* divergence: three successive growing changes above the noise */
-        double sg = in->m->sg;
-        double meas = dv + fabs(dp) * sg / (in->tau + in->D + sg * p);
+        double meas = dv + fabs(dp) / scale0;
         if (!isfinite(meas)) return 0;
         if (it >= 3 && meas > hist[0] && hist[0] > hist[1] && hist[1] > hist[2]
             && meas > 1e3 * in->P->c2p_tol)
             return 0;
+        if (!allow_slow && it >= 6 && meas < hist[0] && hist[0] > 0.0) {
+            double rate = meas / hist[0];
+            if (rate > 0.0 && log(in->P->c2p_tol / meas) / log(rate) > 24.0) {
+                *slow_stop = 1;
+                return 0;
+            }
+        }
         hist[2] = hist[1]; hist[1] = hist[0]; hist[0] = meas;
     }
     return 0;
@@ -835,8 +853,8 @@ int orc_con2prim(const orc_params *P, const double cons_in[14], int implicit,
     double p = guess[P_P], v[3] = {guess[P_VX], guess[P_VY], guess[P_VZ]};
     double cE[3] = {in.cE0[0], in.cE0[1], in.cE0[2]};
     double rho = 0.0;
-    int it1 = 0, it2 = 0, status;
-    if (c2p_paper(&in, &p, v, cE, &rho, &it1)) {
+    int it1 = 0, it2 = 0, status, slow = 0;
+    if (c2p_paper(&in, &p, v, cE, &rho, &it1, 0, &slow)) {
         status = 0;
     } else {
         p = guess[P_P];
@@ -854,6 +872,18 @@ int orc_con2prim(const orc_params *P, const double cons_in[14], int implicit,
             }
             if (c2p_bracket(&in, &p, v, cE, &rho, &it3)) status = 4;
             it2 += it3;
+        }
+        if (status == 2 && slow) {
+            /* both fallbacks failed on a state the paper iteration was
+             * converging on, slowly: let it run to its cap */
+            int it4 = 0, dummy;
+            p = guess[P_P];
+            for (int i = 0; i < 3; i++) {
+                v[i] = guess[P_VX + i];
+                cE[i] = in.cE0[i];
+            }
+            if (c2p_paper(&in, &p, v, cE, &rho, &it4, 1, &dummy)) status = 0;
+            it2 += it4;
         }
     }
     *iters = it1 + it2;

@@ -8,6 +8,12 @@
 // per-direction face fluxes all share that layout, so a cell (or the face on
 // its low side) has the same offset in every array.
 //
+// The explicit part (primitives read by the stencil, stage currents, face
+// fluxes, right-hand side) is stored and computed in T: double on the FP64
+// path, float on the mixed path.  U^n, V, U^{n+1}, the stiff increments and
+// the recovery are FP64 on both; the recovery guess (p, v^i) is kept in FP64
+// in G (on the FP64 path G aliases fields 1..4 of the primitive buffer).
+//
 // Per step (one thread per cell or face, grid-stride free 1D launches):
 //   stage1  U^n, P^n          -> P1 (in place), dR1 = Dt R[U1], J1   (recovery)
 //   ghosts  P1, J1
@@ -35,6 +41,7 @@ struct Grid {
 struct StepConst {
     Grid G;
     double dt, gimex;     // dt, gamma of Table imex
+    double idt, igimex;   // 1/dt, 1/gamma
     double gfac;          // Gamma / (Gamma - 1)
     double kappa;
     int sigma_model;
@@ -104,11 +111,13 @@ __device__ __forceinline__ double sigma_cell(const StepConst &K, const double *s
 }
 
 // warp-aggregated recovery statistics
+// (call = false: only the iterations of a recovery finished by a later pass)
 __device__ __forceinline__ void record_stats(unsigned long long *st, bool active, int status,
-                                             int iters)
+                                             int iters, bool call = true)
 {
     const unsigned full = 0xffffffffu;
     unsigned it = active ? (unsigned)iters : 0u;
+    active = active && call;
     unsigned fb = active && (status == 1 || status == 4);
     unsigned fl = active && status == 2, fr = active && status == 3;
     unsigned ca = active ? 1u : 0u;
@@ -130,16 +139,16 @@ __device__ __forceinline__ void record_stats(unsigned long long *st, bool active
 
 // ---------------------------------------------------------------- set-up
 
-// interior SoA (14 x N) <-> padded SoA (nf x S)
-__global__ void k_scatter(const StepConst K, const double *__restrict__ src, double *dst,
-                          int nf)
+// interior SoA (nf x N, FP64) <-> padded SoA (nf x S)
+template <class T>
+__global__ void k_scatter(const StepConst K, const double *__restrict__ src, T *dst, int nf)
 {
     long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (t >= K.G.N) return;
     int i, j, k;
     interior_coords(K.G, t, i, j, k);
     long long c = cell_at(K.G, i, j, k);
-    for (int f = 0; f < nf; f++) dst[f * K.G.S + c] = src[f * K.G.N + t];
+    for (int f = 0; f < nf; f++) dst[f * K.G.S + c] = (T)src[f * K.G.N + t];
 }
 
 __global__ void k_gather(const StepConst K, const double *__restrict__ src, double *dst, int nf)
@@ -155,7 +164,7 @@ __global__ void k_gather(const StepConst K, const double *__restrict__ src, doub
 // Ghost layers of direction blockIdx.y's active dims: periodic wrap or copy of
 // the nearest interior cell (Sec. IV: Neumann/outflow).  Only the slabs
 // across each face are filled; edge and corner ghosts are never read.
-__global__ void k_ghosts(const StepConst K, double *buf, int nf, int d0)
+template <class T> __global__ void k_ghosts(const StepConst K, T *buf, int nf, int d0)
 {
     const Grid &G = K.G;
     const int d = d0 + blockIdx.y;
@@ -185,9 +194,37 @@ __global__ void k_ghosts(const StepConst K, double *buf, int nf, int d0)
     for (int f = 0; f < nf; f++) buf[f * G.S + dc] = buf[f * G.S + sc];
 }
 
-// U = prim->con(P) over the interior; flags unphysical input
+// interior FP64 primitives -> padded primitives in T and the FP64 guess G
+template <class T>
+__global__ void k_scatter_prims(const StepConst K, const double *__restrict__ src, T *P,
+                                double *Gs)
+{
+    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= K.G.N) return;
+    int i, j, k;
+    interior_coords(K.G, t, i, j, k);
+    long long c = cell_at(K.G, i, j, k);
+    for (int f = 0; f < NPR; f++) P[f * K.G.S + c] = (T)src[f * K.G.N + t];
+    for (int f = 0; f < 4; f++) Gs[f * K.G.S + c] = src[(PR_P + f) * K.G.N + t];
+}
+
+// padded primitives (T) with p, v^i from G -> interior FP64
+template <class T>
+__global__ void k_gather_prims(const StepConst K, const T *__restrict__ P,
+                               const double *__restrict__ Gs, double *dst)
+{
+    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= K.G.N) return;
+    int i, j, k;
+    interior_coords(K.G, t, i, j, k);
+    long long c = cell_at(K.G, i, j, k);
+    for (int f = 0; f < NPR; f++) dst[f * K.G.N + t] = (double)P[f * K.G.S + c];
+    for (int f = 0; f < 4; f++) dst[(PR_P + f) * K.G.N + t] = Gs[f * K.G.S + c];
+}
+
+// U = prim->con of interior FP64 primitives src; flags unphysical input
 template <bool FLAT>
-__global__ void k_prim2con(const StepConst K, const double *__restrict__ P,
+__global__ void k_prim2con(const StepConst K, const double *__restrict__ src,
                            const double *__restrict__ met, double *U, int *bad)
 {
     long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -200,7 +237,7 @@ __global__ void k_prim2con(const StepConst K, const double *__restrict__ P,
     double pr[NPR], u[NCO];
     bool ok = true;
     for (int f = 0; f < NPR; f++) {
-        pr[f] = P[f * K.G.S + c];
+        pr[f] = src[f * K.G.N + t];
         ok = ok && isfinite(pr[f]);
     }
     double v[3] = {pr[PR_VX], pr[PR_VY], pr[PR_VZ]}, vl[3];
@@ -246,10 +283,10 @@ __global__ void k_check_finite(long long n, const double *__restrict__ a, int *b
 // stage current J^D when K.qflux == 0), fall back to first order on an
 // unphysical side, mean face metric and conductivity, HLLE (Sec. III).
 template <class T, bool FLAT, int RC, int D>
-__global__ void __launch_bounds__(128) k_flux(const StepConst K, const double *__restrict__ P,
-                                              const double *__restrict__ Jc,
+__global__ void __launch_bounds__(128) k_flux(const StepConst K, const T *__restrict__ P,
+                                              const T *__restrict__ Jc,
                                               const double *__restrict__ met,
-                                              const double *__restrict__ sig, double *F)
+                                              const double *__restrict__ sig, T *F)
 {
     const Grid &G = K.G;
     long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -268,7 +305,7 @@ __global__ void __launch_bounds__(128) k_flux(const StepConst K, const double *_
     T pL[NPR], pR[NPR];
 #pragma unroll
     for (int f = 0; f < NPR; f++) {
-        const double *q = P + f * S + cL;
+        const T *q = P + f * S + cL;
         T st[6];
         if (RC == RC_WENO5) {
 #pragma unroll
@@ -283,7 +320,7 @@ __global__ void __launch_bounds__(128) k_flux(const StepConst K, const double *_
     T JL = T(0), JR = T(0);
     const bool useJ = K.qflux == 0;
     if (useJ) {
-        const double *q = Jc + D * S + cL;
+        const T *q = Jc + D * S + cL;
         T st[6];
         if (RC == RC_WENO5) {
 #pragma unroll
@@ -339,9 +376,10 @@ __global__ void __launch_bounds__(128) k_flux(const StepConst K, const double *_
             const long long cc = sd == 0 ? cL : cR;
             Met<double> mc;
             load_metric<FLAT>(met, S, cc, mc);
-            double v[3] = {P[PR_VX * S + cc], P[PR_VY * S + cc], P[PR_VZ * S + cc]}, vl[3];
+            double v[3] = {(double)P[PR_VX * S + cc], (double)P[PR_VY * S + cc],
+                           (double)P[PR_VZ * S + cc]}, vl[3];
             lower<double, FLAT>(mc, v, vl);
-            double Dc = mc.sg * P[PR_RHO * S + cc] / sqrt(1.0 - dot3(v, vl));
+            double Dc = mc.sg * (double)P[PR_RHO * S + cc] / sqrt(1.0 - dot3(v, vl));
             sgm += 0.5 * sigma_cell(K, sig, cc, Dc);
         }
         sigma = (T)sgm;
@@ -366,27 +404,34 @@ __global__ void __launch_bounds__(128) k_flux(const StepConst K, const double *_
     flux_accumulate<T, FLAT, D>(pL, m, sigma, gfac, useJ, JL, cFL, -cUU, acc);
     flux_accumulate<T, FLAT, D>(pR, m, sigma, gfac, useJ, JR, cFR, cUU, acc);
 #pragma unroll
-    for (int f = 0; f < NCO; f++) F[f * S + cR] = (double)acc[f];
+    for (int f = 0; f < NCO; f++) F[f * S + cR] = acc[f];
 }
 
 // Source vector of Eq. GRRMHD_flux_form without the stiff part of -alpha J
 // (Sec. III.A split), at a cell with primitives pr.  Metric derivatives:
 // second-order central differences of the cell-centred metric.
-template <bool FLAT>
-__device__ __forceinline__ void sources(const StepConst &K, const double pr[NPR],
+template <bool FLAT, class T>
+__device__ __forceinline__ void sources(const StepConst &K, const T pr_in[NPR],
                                         const double *__restrict__ met, long long c,
-                                        double Sv[NCO])
+                                        T Sv_out[NCO])
 {
-    const double kap = K.kappa;
+    const T kapT = (T)K.kappa;
     if (FLAT) {
         // only -Q v^i (E), -kappa Phi, Q - kappa Psi survive in flat space
-        for (int f = 0; f < NCO; f++) Sv[f] = 0.0;
-        const double Q = pr[PR_Q];
+        const T *pr = pr_in;
+        T *Sv = Sv_out;
+        for (int f = 0; f < NCO; f++) Sv[f] = T(0);
+        const T Q = pr[PR_Q];
+        const T kap = kapT;
         for (int a = 0; a < 3; a++) Sv[CO_EX + a] = -Q * pr[PR_VX + a];
         Sv[CO_PHI] = -kap * pr[PR_PHI];
         Sv[CO_PSI] = Q - kap * pr[PR_PSI];
         return;
     }
+    // curved metric: evaluated in FP64 from the stage primitives
+    const double kap = K.kappa;
+    double pr[NPR], Sv[NCO];
+    for (int f = 0; f < NPR; f++) pr[f] = (double)pr_in[f];
     const Grid &G = K.G;
     const long long S = G.S;
     Met<double> m;
@@ -478,26 +523,25 @@ __device__ __forceinline__ void sources(const StepConst &K, const double pr[NPR]
     Sv[CO_PSI] = -al * U[CO_PSI] * Ktr + Eda + al * U[CO_Q] - al * kap * U[CO_PSI];
     Sv[CO_D] = 0.0;
     Sv[CO_Q] = 0.0;
+    for (int f = 0; f < NCO; f++) Sv_out[f] = (T)Sv[f];
 }
 
-// explicit right-hand side F(U) at an interior cell from the face fluxes
-template <bool FLAT>
-__device__ __forceinline__ void rhs_cell(const StepConst &K, const double pr[NPR],
+// explicit right-hand side F(U) at an interior cell from the face fluxes (T)
+template <bool FLAT, class T>
+__device__ __forceinline__ void rhs_cell(const StepConst &K, const T pr[NPR],
                                          const double *__restrict__ met,
-                                         const double *__restrict__ Fx,
-                                         const double *__restrict__ Fy,
-                                         const double *__restrict__ Fz, long long c,
-                                         double r[NCO])
+                                         const T *__restrict__ Fx, const T *__restrict__ Fy,
+                                         const T *__restrict__ Fz, long long c, T r[NCO])
 {
-    sources<FLAT>(K, pr, met, c, r);
+    sources<FLAT, T>(K, pr, met, c, r);
     const Grid &G = K.G;
-    const double *Fd[3] = {Fx, Fy, Fz};
+    const T *Fd[3] = {Fx, Fy, Fz};
 #pragma unroll
     for (int d = 0; d < 3; d++) {
         if (G.g[d] == 0) continue;
         const long long s = dstride(G, d);
-        const double ih = G.idx[d];
-        const double *F = Fd[d];
+        const T ih = (T)G.idx[d];
+        const T *F = Fd[d];
 #pragma unroll
         for (int f = 0; f < NCO; f++) r[f] -= (F[f * G.S + c + s] - F[f * G.S + c]) * ih;
     }
@@ -505,184 +549,341 @@ __device__ __forceinline__ void rhs_cell(const StepConst &K, const double pr[NPR
 
 // ---------------------------------------------------------------- stages
 
+// Deferred recoveries: cells whose paper iteration does not converge are
+// appended to a work list (scratch memory of the handle) and finished by a
+// second pass with full warps, instead of holding their warp in the
+// fallback.  A record holds the stage's conserved input (14) and the guess
+// (p, v^i); when the list is full the cell falls back inline.
+enum { DREC = NCO + 4 };
+struct Defer {
+    int *count;          // records written (may exceed cap; cap is the limit)
+    int cap;             // 0: no deferral
+    int *idx;            // interior linear index of the cell
+    double *rec;         // DREC x cap, field-major
+};
+
+// warp-aggregated slot allocation; every lane of the warp must call it
+__device__ __forceinline__ int defer_slot(const Defer &df, bool want)
+{
+    const unsigned full = 0xffffffffu;
+    const unsigned mask = __ballot_sync(full, want);
+    if (!mask) return -1;
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(mask) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(df.count, __popc(mask));
+    base = __shfl_sync(full, base, leader);
+    if (!want) return -1;
+    const int slot = base + __popc(mask & ((1u << lane) - 1u));
+    return slot < df.cap ? slot : -1;
+}
+
+__device__ __forceinline__ void defer_store(const Defer &df, int slot, long long t,
+                                            const double u[NCO], double gp, const double gv[3])
+{
+    df.idx[slot] = (int)t;
+    const long long cap = df.cap;
+    for (int f = 0; f < NCO; f++) df.rec[f * cap + slot] = u[f];
+    df.rec[(NCO + 0) * cap + slot] = gp;
+    for (int a = 0; a < 3; a++) df.rec[(NCO + 1 + a) * cap + slot] = gv[a];
+}
+
+__device__ __forceinline__ void load_rec_in(const double u[NCO], RecIn &in)
+{
+    in.D = u[CO_D];
+    in.tau = u[CO_TAU];
+    for (int a = 0; a < 3; a++) {
+        in.S[a] = u[CO_SX + a];
+        in.cB[a] = u[CO_BX + a];
+        in.cE0[a] = u[CO_EX + a];
+    }
+}
+
+// primitives of a cell: all 14 in T, the recovery guess (p, v^i) in FP64
+template <class T>
+__device__ __forceinline__ void prim_write(const StepConst &K, long long c, const double pr[NPR],
+                                          T *P, double *Gs)
+{
+    const long long S = K.G.S;
+    for (int f = 0; f < NPR; f++) P[f * S + c] = (T)pr[f];
+    for (int f = 0; f < 4; f++) Gs[f * S + c] = pr[PR_P + f];
+}
+
+// outputs of stage 1 at a cell (primitives, Dt R1, stage current)
+template <class T>
+__device__ __forceinline__ void stage1_write(const StepConst &K, long long c, const double pr[NPR],
+                                             const double E[3], const double u[NCO], double alpha,
+                                             T *P, double *Gs, double *dR1, T *J1)
+{
+    const long long S = K.G.S;
+    prim_write(K, c, pr, P, Gs);
+    const double ig = K.igimex, iad = K.idt / alpha;
+    for (int a = 0; a < 3; a++) {
+        const double r = (E[a] - u[CO_EX + a]) * ig;
+        dR1[a * S + c] = r;
+        J1[a * S + c] = (T)(u[CO_Q] * pr[PR_VX + a] - r * iad);   // J = Q v - Dt R/(alpha Dt)
+    }
+}
+
+// outputs of stage 2 after its recovery (V already holds U^n + dt/2 F[U1])
+template <class T>
+__device__ __forceinline__ void stage2_write(const StepConst &K, long long c, const double p2[NPR],
+                                             const double E[3], const double us[NCO], double alpha,
+                                             const double *dR1, T *P2, double *G2, double *V,
+                                             T *J2)
+{
+    const long long S = K.G.S;
+    prim_write(K, c, p2, P2, G2);
+    const double ig = K.igimex, iad = K.idt / alpha;
+    for (int a = 0; a < 3; a++) {
+        const double r2 = (E[a] - us[CO_EX + a]) * ig;
+        V[(CO_EX + a) * S + c] += 0.5 * (dR1[a * S + c] + r2);
+        J2[a * S + c] = (T)(us[CO_Q] * p2[PR_VX + a] - r2 * iad);
+    }
+}
+
+// outputs of the final recovery (U already holds U^{n+1})
+template <bool FLAT, class T>
+__device__ __forceinline__ void final_write(const StepConst &K, long long c, const double pn[NPR],
+                                            int status, const Met<double> &m, double *U, T *P,
+                                            double *Gs)
+{
+    const long long S = K.G.S;
+    if (status == 2 || status == 3) {
+        double u2[NCO];
+        prim_to_cons<double, FLAT>(pn, m, K.gfac, u2);
+        U[CO_D * S + c] = u2[CO_D];
+        U[CO_TAU * S + c] = u2[CO_TAU];
+        for (int a = 0; a < 3; a++) U[(CO_SX + a) * S + c] = u2[CO_SX + a];
+    }
+    prim_write(K, c, pn, P, Gs);
+}
+
 // Stage 1 (purely implicit): recovery of U^n with calE solved, guess P^n.
-template <bool FLAT>
+template <bool FLAT, class T>
 __global__ void __launch_bounds__(128)
-k_stage1(const StepConst K, const double *__restrict__ U, double *P, double *dR1, double *J1,
-         const double *__restrict__ met, const double *__restrict__ sig,
+k_stage1(const StepConst K, const double *__restrict__ U, T *P, double *Gs, double *dR1, T *J1,
+         const double *__restrict__ met, const double *__restrict__ sig, const Defer df,
          unsigned long long *stats)
 {
     const Grid &G = K.G;
-    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     const bool active = t < G.N;
     int status = 0, iters = 0;
+    long long c = 0;
+    double u[NCO], pr[NPR], E[3], gp = 0.0, gv[3] = {0, 0, 0}, cc = 0.0;
+    Met<double> m;
     if (active) {
         int i, j, k;
         interior_coords(G, t, i, j, k);
-        const long long c = cell_at(G, i, j, k), S = G.S;
-        Met<double> m;
+        c = cell_at(G, i, j, k);
+        const long long S = G.S;
         load_metric<FLAT>(met, S, c, m);
+        for (int f = 0; f < NCO; f++) u[f] = U[f * S + c];
         RecIn in;
-        in.D = U[CO_D * S + c];
-        in.tau = U[CO_TAU * S + c];
-        for (int a = 0; a < 3; a++) {
-            in.S[a] = U[(CO_SX + a) * S + c];
-            in.cB[a] = U[(CO_BX + a) * S + c];
-            in.cE0[a] = U[(CO_EX + a) * S + c];
-        }
-        const double Phi = U[CO_PHI * S + c], Psi = U[CO_PSI * S + c], Q = U[CO_Q * S + c];
-        const double sigma = sigma_cell(K, sig, c, in.D);
-        const double cc = K.gimex * K.dt * m.alpha * sigma;
-        const double gp = P[PR_P * S + c];
-        const double gv[3] = {P[PR_VX * S + c], P[PR_VY * S + c], P[PR_VZ * S + c]};
-        double pr[NPR], E[3];
-        status = recover<FLAT>(in, m, K.ro, true, cc, gp, gv, Phi, Psi, Q, pr, E, iters);
-        for (int f = 0; f < NPR; f++) P[f * S + c] = pr[f];
-        const double ig = 1.0 / K.gimex;
-        const double iad = 1.0 / (m.alpha * K.dt);
-        for (int a = 0; a < 3; a++) {
-            const double r = (E[a] - in.cE0[a]) * ig;
-            dR1[a * S + c] = r;
-            // stage current J = Q v - Dt R / (alpha Dt)
-            J1[a * S + c] = Q * pr[PR_VX + a] - r * iad;
+        load_rec_in(u, in);
+        cc = K.gimex * K.dt * m.alpha * sigma_cell(K, sig, c, in.D);
+        gp = Gs[c];
+        for (int a = 0; a < 3; a++) gv[a] = Gs[(1 + a) * S + c];
+        status = recover<FLAT>(in, m, K.ro, true, cc, gp, gv, u[CO_PHI], u[CO_PSI], u[CO_Q], pr,
+                               E, iters, df.cap ? REC_PRIMARY : REC_ALL);
+    }
+    const bool want = active && status == REC_DEFER;
+    const int slot = defer_slot(df, want);
+    if (want) {
+        if (slot >= 0) {
+            defer_store(df, slot, t, u, gp, gv);
+        } else {
+            RecIn in;
+            load_rec_in(u, in);
+            int it2 = 0;
+            status = recover<FLAT>(in, m, K.ro, true, cc, gp, gv, u[CO_PHI], u[CO_PSI], u[CO_Q],
+                                   pr, E, it2, REC_FALLBACK);
+            iters += it2;
         }
     }
-    record_stats(stats, active, status, iters);
+    const bool deferred = want && slot >= 0;
+    if (active && !deferred) stage1_write(K, c, pr, E, u, m.alpha, P, Gs, dR1, J1);
+    record_stats(stats, active, status, iters, !deferred);
 }
 
 // Stage 2: U* = U^n + dt F[U1] + (1-2gamma) Dt R1 on calE; implicit recovery
 // (guess P1); V = U^n + dt/2 F[U1] + dt/2 (R1 + R2) (Eq. IMEX3 minus F[U2]).
-template <bool FLAT>
+template <bool FLAT, class T>
 __global__ void __launch_bounds__(128)
-k_stage2(const StepConst K, const double *__restrict__ U, const double *__restrict__ P1,
-         const double *__restrict__ Fx, const double *__restrict__ Fy,
-         const double *__restrict__ Fz, const double *__restrict__ dR1,
-         const double *__restrict__ met, const double *__restrict__ sig, double *P2,
-         double *V, double *J2, unsigned long long *stats)
+k_stage2(const StepConst K, const double *__restrict__ U, const T *__restrict__ P1,
+         const double *__restrict__ G1, const T *__restrict__ Fx, const T *__restrict__ Fy,
+         const T *__restrict__ Fz, const double *__restrict__ dR1,
+         const double *__restrict__ met, const double *__restrict__ sig, T *P2, double *G2,
+         double *V, T *J2, const Defer df, unsigned long long *stats)
 {
     const Grid &G = K.G;
-    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     const bool active = t < G.N;
     int status = 0, iters = 0;
+    long long c = 0;
+    double us[NCO], p2[NPR], E[3], gp = 0.0, gv[3] = {0, 0, 0}, cc = 0.0;
+    Met<double> m;
     if (active) {
         int i, j, k;
         interior_coords(G, t, i, j, k);
-        const long long c = cell_at(G, i, j, k), S = G.S;
-        double pr[NPR];
+        c = cell_at(G, i, j, k);
+        const long long S = G.S;
+        T pr[NPR];
         for (int f = 0; f < NPR; f++) pr[f] = P1[f * S + c];
-        double r[NCO];
-        rhs_cell<FLAT>(K, pr, met, Fx, Fy, Fz, c, r);
+        T r[NCO];
+        rhs_cell<FLAT, T>(K, pr, met, Fx, Fy, Fz, c, r);
         const double dt = K.dt, hdt = 0.5 * dt;
-        double us[NCO];
         for (int f = 0; f < NCO; f++) {
-            const double u = U[f * S + c];
-            us[f] = u + dt * r[f];
-            V[f * S + c] = u + hdt * r[f];
+            const double uu = U[f * S + c], rf = (double)r[f];
+            us[f] = uu + dt * rf;
+            V[f * S + c] = uu + hdt * rf;
         }
-        double r1[3];
-        for (int a = 0; a < 3; a++) {
-            r1[a] = dR1[a * S + c];
-            us[CO_EX + a] += (1.0 - 2.0 * K.gimex) * r1[a];
-        }
-        Met<double> m;
+        for (int a = 0; a < 3; a++) us[CO_EX + a] += (1.0 - 2.0 * K.gimex) * dR1[a * S + c];
         load_metric<FLAT>(met, S, c, m);
         RecIn in;
-        in.D = us[CO_D];
-        in.tau = us[CO_TAU];
-        for (int a = 0; a < 3; a++) {
-            in.S[a] = us[CO_SX + a];
-            in.cB[a] = us[CO_BX + a];
-            in.cE0[a] = us[CO_EX + a];
-        }
-        const double sigma = sigma_cell(K, sig, c, in.D);
-        const double cc = K.gimex * dt * m.alpha * sigma;
-        const double gv[3] = {pr[PR_VX], pr[PR_VY], pr[PR_VZ]};
-        double p2[NPR], E[3];
-        status = recover<FLAT>(in, m, K.ro, true, cc, pr[PR_P], gv, us[CO_PHI], us[CO_PSI],
-                               us[CO_Q], p2, E, iters);
-        for (int f = 0; f < NPR; f++) P2[f * S + c] = p2[f];
-        const double ig = 1.0 / K.gimex;
-        const double iad = 1.0 / (m.alpha * dt);
-        for (int a = 0; a < 3; a++) {
-            const double r2 = (E[a] - in.cE0[a]) * ig;
-            V[(CO_EX + a) * S + c] += 0.5 * (r1[a] + r2);
-            J2[a * S + c] = us[CO_Q] * p2[PR_VX + a] - r2 * iad;
+        load_rec_in(us, in);
+        cc = K.gimex * dt * m.alpha * sigma_cell(K, sig, c, in.D);
+        gp = G1[c];
+        for (int a = 0; a < 3; a++) gv[a] = G1[(1 + a) * S + c];
+        status = recover<FLAT>(in, m, K.ro, true, cc, gp, gv, us[CO_PHI], us[CO_PSI], us[CO_Q],
+                               p2, E, iters, df.cap ? REC_PRIMARY : REC_ALL);
+    }
+    const bool want = active && status == REC_DEFER;
+    const int slot = defer_slot(df, want);
+    if (want) {
+        if (slot >= 0) {
+            defer_store(df, slot, t, us, gp, gv);
+        } else {
+            RecIn in;
+            load_rec_in(us, in);
+            int it2 = 0;
+            status = recover<FLAT>(in, m, K.ro, true, cc, gp, gv, us[CO_PHI], us[CO_PSI],
+                                   us[CO_Q], p2, E, it2, REC_FALLBACK);
+            iters += it2;
         }
     }
-    record_stats(stats, active, status, iters);
+    const bool deferred = want && slot >= 0;
+    if (active && !deferred) stage2_write(K, c, p2, E, us, m.alpha, dR1, P2, G2, V, J2);
+    record_stats(stats, active, status, iters, !deferred);
 }
 
 // Final: U^{n+1} = V + dt/2 F[U2]; recovery with calE fixed (guess P2).
-template <bool FLAT>
+template <bool FLAT, class T>
 __global__ void __launch_bounds__(128)
-k_final(const StepConst K, const double *__restrict__ Vb, const double *__restrict__ P2,
-        const double *__restrict__ Fx, const double *__restrict__ Fy,
-        const double *__restrict__ Fz, const double *__restrict__ met, double *U, double *P,
-        unsigned long long *stats)
+k_final(const StepConst K, const double *__restrict__ Vb, const T *__restrict__ P2,
+        const double *__restrict__ G2, const T *__restrict__ Fx, const T *__restrict__ Fy,
+        const T *__restrict__ Fz, const double *__restrict__ met, double *U, T *P, double *Gs,
+        const Defer df, unsigned long long *stats)
 {
     const Grid &G = K.G;
-    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     const bool active = t < G.N;
     int status = 0, iters = 0;
+    long long c = 0;
+    double un[NCO], pn[NPR], E[3], gp = 0.0, gv[3] = {0, 0, 0};
+    Met<double> m;
     if (active) {
         int i, j, k;
         interior_coords(G, t, i, j, k);
-        const long long c = cell_at(G, i, j, k), S = G.S;
-        double pr[NPR];
+        c = cell_at(G, i, j, k);
+        const long long S = G.S;
+        T pr[NPR];
         for (int f = 0; f < NPR; f++) pr[f] = P2[f * S + c];
-        double r[NCO];
-        rhs_cell<FLAT>(K, pr, met, Fx, Fy, Fz, c, r);
+        T r[NCO];
+        rhs_cell<FLAT, T>(K, pr, met, Fx, Fy, Fz, c, r);
         const double hdt = 0.5 * K.dt;
-        double un[NCO];
         bool finite = true;
         for (int f = 0; f < NCO; f++) {
-            un[f] = Vb[f * S + c] + hdt * r[f];
+            un[f] = Vb[f * S + c] + hdt * (double)r[f];
             finite = finite && isfinite(un[f]);
+            U[f * S + c] = un[f];
         }
         if (!finite) atomicOr((unsigned long long *)&stats[ST_NAN], 1ULL);
-        Met<double> m;
         load_metric<FLAT>(met, S, c, m);
         RecIn in;
-        in.D = un[CO_D];
-        in.tau = un[CO_TAU];
-        for (int a = 0; a < 3; a++) {
-            in.S[a] = un[CO_SX + a];
-            in.cB[a] = un[CO_BX + a];
-            in.cE0[a] = un[CO_EX + a];
-        }
-        const double gv[3] = {pr[PR_VX], pr[PR_VY], pr[PR_VZ]};
-        double pn[NPR], E[3];
-        status = recover<FLAT>(in, m, K.ro, false, 0.0, pr[PR_P], gv, un[CO_PHI], un[CO_PSI],
-                               un[CO_Q], pn, E, iters);
-        if (status == 2 || status == 3) {
-            double u2[NCO];
-            prim_to_cons<double, FLAT>(pn, m, K.gfac, u2);
-            un[CO_D] = u2[CO_D];
-            un[CO_TAU] = u2[CO_TAU];
-            for (int a = 0; a < 3; a++) un[CO_SX + a] = u2[CO_SX + a];
-        }
-        for (int f = 0; f < NCO; f++) U[f * S + c] = un[f];
-        for (int f = 0; f < NPR; f++) P[f * S + c] = pn[f];
+        load_rec_in(un, in);
+        gp = G2[c];
+        for (int a = 0; a < 3; a++) gv[a] = G2[(1 + a) * S + c];
+        status = recover<FLAT>(in, m, K.ro, false, 0.0, gp, gv, un[CO_PHI], un[CO_PSI],
+                               un[CO_Q], pn, E, iters, df.cap ? REC_PRIMARY : REC_ALL);
     }
-    record_stats(stats, active, status, iters);
+    const bool want = active && status == REC_DEFER;
+    const int slot = defer_slot(df, want);
+    if (want) {
+        if (slot >= 0) {
+            defer_store(df, slot, t, un, gp, gv);
+        } else {
+            RecIn in;
+            load_rec_in(un, in);
+            int it2 = 0;
+            status = recover<FLAT>(in, m, K.ro, false, 0.0, gp, gv, un[CO_PHI], un[CO_PSI],
+                                   un[CO_Q], pn, E, it2, REC_FALLBACK);
+            iters += it2;
+        }
+    }
+    const bool deferred = want && slot >= 0;
+    if (active && !deferred) final_write<FLAT>(K, c, pn, status, m, U, P, Gs);
+    record_stats(stats, active, status, iters, !deferred);
+}
+
+// Deferred pass of stage 1 (STAGE 1), stage 2 (STAGE 2) or the final
+// recovery (STAGE 3): one thread per record, fallbacks only.  The loop bound
+// is uniform across a warp so that record_stats sees every lane.
+template <bool FLAT, int STAGE, class T>
+__global__ void __launch_bounds__(128)
+k_deferred(const StepConst K, const Defer df, const double *__restrict__ met,
+           const double *__restrict__ sig, const double *__restrict__ dR1, T *P, double *Gs,
+           double *dRo, T *J, double *V, double *U, unsigned long long *stats)
+{
+    const Grid &G = K.G;
+    const int n = min(*df.count, df.cap);
+    const long long cap = df.cap;
+    for (int base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
+        const int s = base + threadIdx.x;
+        const bool active = s < n;
+        int status = 0, iters = 0;
+        if (active) {
+            const long long t = df.idx[s];
+            int i, j, k;
+            interior_coords(G, t, i, j, k);
+            const long long c = cell_at(G, i, j, k);
+            double u[NCO], gv[3], pr[NPR], E[3];
+            for (int f = 0; f < NCO; f++) u[f] = df.rec[f * cap + s];
+            const double gp = df.rec[NCO * cap + s];
+            for (int a = 0; a < 3; a++) gv[a] = df.rec[(NCO + 1 + a) * cap + s];
+            Met<double> m;
+            load_metric<FLAT>(met, G.S, c, m);
+            RecIn in;
+            load_rec_in(u, in);
+            const bool implicit = STAGE != 3;
+            const double cc =
+                implicit ? K.gimex * K.dt * m.alpha * sigma_cell(K, sig, c, in.D) : 0.0;
+            status = recover<FLAT>(in, m, K.ro, implicit, cc, gp, gv, u[CO_PHI], u[CO_PSI],
+                                   u[CO_Q], pr, E, iters, REC_FALLBACK);
+            if (STAGE == 1) stage1_write(K, c, pr, E, u, m.alpha, P, Gs, dRo, J);
+            if (STAGE == 2) stage2_write(K, c, pr, E, u, m.alpha, dR1, P, Gs, V, J);
+            if (STAGE == 3) final_write<FLAT>(K, c, pr, status, m, U, P, Gs);
+        }
+        record_stats(stats, active, status, iters);
+    }
 }
 
 // explicit right-hand side only (testing entry point)
-template <bool FLAT>
-__global__ void k_rhs(const StepConst K, const double *__restrict__ P,
-                      const double *__restrict__ Fx, const double *__restrict__ Fy,
-                      const double *__restrict__ Fz, const double *__restrict__ met,
-                      double *out)
+template <bool FLAT, class T>
+__global__ void k_rhs(const StepConst K, const T *__restrict__ P, const T *__restrict__ Fx,
+                      const T *__restrict__ Fy, const T *__restrict__ Fz,
+                      const double *__restrict__ met, double *out)
 {
     long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (t >= K.G.N) return;
     int i, j, k;
     interior_coords(K.G, t, i, j, k);
     const long long c = cell_at(K.G, i, j, k), S = K.G.S;
-    double pr[NPR], r[NCO];
+    T pr[NPR], r[NCO];
     for (int f = 0; f < NPR; f++) pr[f] = P[f * S + c];
-    rhs_cell<FLAT>(K, pr, met, Fx, Fy, Fz, c, r);
-    for (int f = 0; f < NCO; f++) out[f * K.G.N + t] = r[f];
+    rhs_cell<FLAT, T>(K, pr, met, Fx, Fy, Fz, c, r);
+    for (int f = 0; f < NCO; f++) out[f * K.G.N + t] = (double)r[f];
 }
 
 // pointwise recovery on independent points (testing entry point)

@@ -66,19 +66,25 @@ __device__ __forceinline__ void implicit_field(const RecCtx<FLAT> &c, const doub
     for (int i = 0; i < 3; i++) E[i] = (r[i] * q + C * v[i] * s) * inv;
 }
 
-// Step (iii): fluid variables from the conserved ones at (p, calE).  Returns
-// false if the enthalpy denominator is not positive or v^2 >= v2max.
 template <bool FLAT>
-__device__ __forceinline__ bool fluid_from_cons(const RecCtx<FLAT> &c, const double E[3],
-                                                double p, double vl[3], double v[3],
-                                                double &v2, double &Winv, double &W,
-                                                double &rho, double &eps, double &EMo)
+__device__ __forceinline__ bool p_conv(const RecCtx<FLAT> &c, double dp, double p)
+{
+    return fabs(dp) * c.sg <= c.o.tol * (c.in.tau + c.in.D + c.sg * p);
+}
+
+// Step (iii) at (p, calE), division-lean form used by the paper iteration:
+// returns v_lower, v, v^2, W, 1/W and num = tau - D(W-1) - sqrt(g) p (W^2-1) - EM
+// (so that D W eps = num and rho eps = num (1-v^2)/sqrt(g)).
+template <bool FLAT>
+__device__ __forceinline__ bool fluid_step(const RecCtx<FLAT> &c, const double E[3], double p,
+                                           double vl[3], double v[3], double &v2, double &W,
+                                           double &Winv, double &num)
 {
     double El[3];
     lower<double, FLAT>(c.m, E, El);
     const double EM = 0.5 * (dot3(E, El) + c.B2) * c.isg;
     double P[3];
-    cross3(E, c.in.cB, P);             // eta_ijk calE^j calB^k
+    cross3(E, c.in.cB, P);
     const double den = c.in.tau + c.in.D + c.sg * p - EM;
     const double iden = 1.0 / den;
 #pragma unroll
@@ -89,63 +95,67 @@ __device__ __forceinline__ bool fluid_from_cons(const RecCtx<FLAT> &c, const dou
     const double omv = 1.0 - v2;
     W = rsqrt(omv);
     Winv = omv * W;
-    rho = c.in.D * Winv * c.isg;
-    const double num = c.in.tau - c.in.D * (W - 1.0) - c.sg * p * (v2 * W * W) - EM;
-    eps = num * Winv * c.iD;
-    EMo = EM;
+    num = c.in.tau - c.in.D * (W - 1.0) - c.sg * p * (v2 * W * W) - EM;
     return true;
 }
 
-template <bool FLAT>
-__device__ __forceinline__ bool p_conv(const RecCtx<FLAT> &c, double dp, double p)
-{
-    return fabs(dp) * c.sg <= c.o.tol * (c.in.tau + c.in.D + c.sg * p);
-}
-
 // The paper's iteration (steps ii-v).  Returns 1 converged, 0 gave up.
+// The Lorentz factor and lowered velocity of an iterate are carried to the
+// next implicit solve; f and f/f' are formed without dividing by D:
+//   f = (Gamma-1) num (1-v^2)/sqrt(g) - p,
+//   f/f' = f (D + Gamma num/W) / (v^2 Gamma(Gamma-1) num/W - D - Gamma num/W).
 template <bool FLAT>
 __device__ int paper_iteration(const RecCtx<FLAT> &c, double &p, double v[3], double E[3],
-                               double &rho_out, int &iters)
+                               double &rho_out, int &iters, bool allow_slow, bool &slow_stop)
 {
-    const double Gam = c.o.Gam;
+    slow_stop = false;
+    const double Gam = c.o.Gam, g1 = Gam - 1.0, gg1 = Gam * (Gam - 1.0);
+    const double D = c.in.D;
+    double vl[3];
+    lower<double, FLAT>(c.m, v, vl);
+    double v2 = dot3(v, vl);
+    if (!(v2 < c.o.v2max)) return 0;
+    double W = rsqrt(1.0 - v2);
+    // reciprocal of the energy scale at the guess, for the divergence measure
+    const double iscale0 = c.sg / (c.in.tau + D + c.sg * p);
     double prev0 = 0.0, prev1 = 0.0, prev2 = 0.0;
     for (int it = 1; it <= c.o.maxit; it++) {
         iters = it;
-        if (c.implicit) {
-            double vl[3];
-            lower<double, FLAT>(c.m, v, vl);
-            const double v2 = dot3(v, vl);
-            if (!(v2 < c.o.v2max)) return 0;
-            implicit_field<FLAT>(c, v, vl, v2, rsqrt(1.0 - v2), E);
-        }
-        double vl[3], vn[3], v2, Winv, W, rho, eps, EM;
-        if (!fluid_from_cons<FLAT>(c, E, p, vl, vn, v2, Winv, W, rho, eps, EM)) return 0;
-        const double f = (Gam - 1.0) * rho * eps - p;
-        double ratio;   // f / f'
-        if (eps > 0.0) {
-            const double ge = Gam * eps;
-            ratio = f * (1.0 + ge) / (v2 * Gam * (Gam - 1.0) * eps - 1.0 - ge);
+        if (c.implicit) implicit_field<FLAT>(c, v, vl, v2, W, E);
+        double vn[3], Winv, num;
+        if (!fluid_step<FLAT>(c, E, p, vl, vn, v2, W, Winv, num)) return 0;
+        const double omv = 1.0 - v2;
+        const double f = g1 * num * omv * c.isg - p;
+        double ratio;
+        if (num > 0.0) {
+            const double gn = Gam * num * Winv;
+            ratio = f * (D + gn) / (v2 * gg1 * num * Winv - D - gn);
         } else {
             ratio = -f;
         }
         double pn = p - ratio;
         if (!(pn > 0.0)) pn = 0.1 * p;
-        double dv = fmax(fabs(vn[0] - v[0]), fmax(fabs(vn[1] - v[1]), fabs(vn[2] - v[2])));
+        const double dv = fmax(fabs(vn[0] - v[0]), fmax(fabs(vn[1] - v[1]), fabs(vn[2] - v[2])));
         const double dp = pn - p;
         p = pn;
         v[0] = vn[0]; v[1] = vn[1]; v[2] = vn[2];
-        rho_out = rho;
-        if (p_conv<FLAT>(c, dp, p) && dv <= c.o.tol) return 1;
-        const double meas = dv + fabs(dp) * c.sg / (c.in.tau + c.in.D + c.sg * p);
+        if (p_conv<FLAT>(c, dp, p) && dv <= c.o.tol) {
+            rho_out = D * Winv * c.isg;
+            return 1;
+        }
+        const double meas = dv + fabs(dp) * iscale0;
         if (!isfinite(meas)) return 0;
         // diverging: three successive growing changes above the noise
         if (it >= 3 && meas > prev0 && prev0 > prev1 && prev1 > prev2 &&
             meas > 1e3 * c.o.tol)
             return 0;
         // converging too slowly: more than 24 further iterations predicted
-        if (it >= 6 && meas < prev0 && prev0 > 0.0) {
+        if (!allow_slow && it >= 6 && meas < prev0 && prev0 > 0.0) {
             const double rate = meas / prev0;
-            if (rate > 0.0 && log(c.o.tol / meas) / log(rate) > 24.0) return 0;
+            if (rate > 0.0 && log(c.o.tol / meas) / log(rate) > 24.0) {
+                slow_stop = true;
+                return 0;
+            }
         }
         prev2 = prev1; prev1 = prev0; prev0 = meas;
     }
@@ -454,17 +464,24 @@ __device__ int bracket_fallback(const RecCtx<FLAT> &c, double &p, double v[3], d
     return 0;
 }
 
+// phases of recover(): everything inline, only the paper iteration (a cell it
+// does not converge is handed back as REC_DEFER for a later fallback pass),
+// or only the fallbacks (the deferred pass)
+enum { REC_ALL = 0, REC_PRIMARY = 1, REC_FALLBACK = 2 };
+enum { REC_DEFER = -1 };
+
 // Full pointwise recovery.  Writes the 14 primitives and the solved calE;
 // returns the status 0 (paper iteration), 1 (Newton fallback), 4 (pressure
 // bracket fallback), 2 (failed, atmosphere), 3 (rho below the floor,
-// atmosphere).  guess_p, guess_v: previous stage.
+// atmosphere), or REC_DEFER (phase REC_PRIMARY only; nothing written).
+// guess_p, guess_v: previous stage.
 template <bool FLAT>
 __device__ int recover(const RecIn &in, const Met<double> &m, const RecOpts &o,
                        bool implicit, double cc, double guess_p, const double guess_v[3],
                        double Phi, double Psi, double Q, double prim[NPR],
-                       double Eout[3], int &iters)
+                       double Eout[3], int &iters, int phase = REC_ALL)
 {
-    RecCtx<FLAT> c{in, m, o, implicit, implicit ? cc : 0.0, 1.0, 1.0, 1.0 / in.D, {0, 0, 0}, 0.0};
+    RecCtx<FLAT> c{in, m, o, implicit, implicit ? cc : 0.0, 1.0, 1.0, 0.0, {0, 0, 0}, 0.0};
     if (!FLAT) {
         c.sg = m.sg;
         c.isg = m.isg;
@@ -476,9 +493,14 @@ __device__ int recover(const RecIn &in, const Met<double> &m, const RecOpts &o,
     double E[3] = {in.cE0[0], in.cE0[1], in.cE0[2]};
     double rho = 0.0;
     int it1 = 0, it2 = 0, status;
-    if (paper_iteration<FLAT>(c, p, v, E, rho, it1)) {
+    bool slow = false;
+    if (phase != REC_FALLBACK && paper_iteration<FLAT>(c, p, v, E, rho, it1, false, slow)) {
         status = 0;
+    } else if (phase == REC_PRIMARY) {
+        iters = it1;
+        return REC_DEFER;
     } else {
+        c.iD = 1.0 / in.D;
         p = guess_p;
         v[0] = guess_v[0]; v[1] = guess_v[1]; v[2] = guess_v[2];
         E[0] = in.cE0[0]; E[1] = in.cE0[1]; E[2] = in.cE0[2];
@@ -490,6 +512,34 @@ __device__ int recover(const RecIn &in, const Met<double> &m, const RecOpts &o,
             E[0] = in.cE0[0]; E[1] = in.cE0[1]; E[2] = in.cE0[2];
             if (bracket_fallback<FLAT>(c, p, v, E, rho, it3)) status = 4;
             it2 += it3;
+        }
+        if (status == 2) {
+            // both fallbacks failed: if the paper iteration was stopped only
+            // for being slow (decided again here in the deferred pass), let
+            // it run to its cap
+            int it4 = 0;
+            bool slow2 = false;
+            double p4 = guess_p, v4[3] = {guess_v[0], guess_v[1], guess_v[2]};
+            double E4[3] = {in.cE0[0], in.cE0[1], in.cE0[2]}, rho4 = 0.0;
+            if (phase == REC_FALLBACK || slow) {
+                if (phase == REC_FALLBACK)
+                    paper_iteration<FLAT>(c, p4, v4, E4, rho4, it4, false, slow2);
+                if ((slow || slow2)) {
+                    p4 = guess_p;
+                    v4[0] = guess_v[0]; v4[1] = guess_v[1]; v4[2] = guess_v[2];
+                    E4[0] = in.cE0[0]; E4[1] = in.cE0[1]; E4[2] = in.cE0[2];
+                    int it5 = 0;
+                    bool dummy;
+                    if (paper_iteration<FLAT>(c, p4, v4, E4, rho4, it5, true, dummy)) {
+                        status = 0;
+                        p = p4; rho = rho4;
+                        v[0] = v4[0]; v[1] = v4[1]; v[2] = v4[2];
+                        E[0] = E4[0]; E[1] = E4[1]; E[2] = E4[2];
+                    }
+                    it4 += it5;
+                }
+            }
+            it2 += it4;
         }
     }
     iters = it1 + it2;

@@ -20,11 +20,21 @@ const int TPB = 128;
 char g_noh_err[512] = "";
 
 struct Buffers {
-    double *U = nullptr, *PA = nullptr, *PB = nullptr, *V = nullptr;
-    double *dR1 = nullptr, *J1 = nullptr, *J2 = nullptr, *F[3] = {nullptr, nullptr, nullptr};
+    double *U = nullptr, *V = nullptr, *dR1 = nullptr;
+    // explicit-path buffers in the path's storage type (8 or 4 bytes)
+    void *PA = nullptr, *PB = nullptr, *J1 = nullptr, *J2 = nullptr;
+    void *F[3] = {nullptr, nullptr, nullptr};
+    // FP64 recovery guess (p, v^i); aliases fields 1..4 of PA / PB on FP64
+    double *GA = nullptr, *GB = nullptr;
+    bool own_guess = false;
     double *met = nullptr, *sig = nullptr, *stage = nullptr;
     unsigned long long *stats = nullptr;
     int *flag = nullptr;
+    // deferred-recovery work lists (scratch): counters for the three
+    // recoveries of a step, cell indices and records
+    int *dcount = nullptr, *didx = nullptr;
+    double *drec = nullptr;
+    int dcap = 0;
 };
 
 } // namespace
@@ -123,22 +133,33 @@ static RecOpts rec_opts(const rmhd_params *p)
 
 static void free_all(Buffers &b)
 {
-    double **ptrs[] = {&b.U, &b.PA, &b.PB, &b.V, &b.dR1, &b.J1, &b.J2, &b.F[0], &b.F[1],
-                       &b.F[2], &b.met, &b.sig, &b.stage};
-    for (double **q : ptrs)
+    void **ptrs[] = {(void **)&b.U, &b.PA, &b.PB, (void **)&b.V, (void **)&b.dR1, &b.J1, &b.J2,
+                     &b.F[0], &b.F[1], &b.F[2], (void **)&b.met, (void **)&b.sig,
+                     (void **)&b.stage};
+    for (void **q : ptrs)
         if (*q) {
             cudaFree(*q);
             *q = nullptr;
         }
+    if (b.own_guess) {
+        if (b.GA) cudaFree(b.GA);
+        if (b.GB) cudaFree(b.GB);
+    }
+    b.GA = b.GB = nullptr;
     if (b.stats) cudaFree(b.stats);
     if (b.flag) cudaFree(b.flag);
+    if (b.dcount) cudaFree(b.dcount);
+    if (b.didx) cudaFree(b.didx);
+    if (b.drec) cudaFree(b.drec);
     b.stats = nullptr;
     b.flag = nullptr;
+    b.dcount = b.didx = nullptr;
+    b.drec = nullptr;
 }
 
 // ------------------------------------------------------------------ launches
 
-static void launch_ghosts(rmhd_t h, double *buf, int nf)
+template <class T> static void launch_ghosts(rmhd_t h, T *buf, int nf)
 {
     const Grid &G = h->K.G;
     long long mx = 0;
@@ -149,30 +170,30 @@ static void launch_ghosts(rmhd_t h, double *buf, int nf)
     }
     if (!mx) return;
     dim3 grid(nblk(mx), 3);
-    k_ghosts<<<grid, TPB, 0, h->st>>>(h->K, buf, nf, 0);
+    k_ghosts<T><<<grid, TPB, 0, h->st>>>(h->K, buf, nf, 0);
 }
 
 template <class T, bool FLAT, int RC>
-static void launch_flux_rc(rmhd_t h, const double *P, const double *J)
+static void launch_flux_rc(rmhd_t h, const T *P, const T *J)
 {
     const Grid &G = h->K.G;
     const Buffers &b = h->b;
+    T *F0 = (T *)b.F[0], *F1 = (T *)b.F[1], *F2 = (T *)b.F[2];
     if (G.g[0]) {
         long long n = (long long)(G.n[0] + 1) * G.n[1] * G.n[2];
-        k_flux<T, FLAT, RC, 0><<<nblk(n), TPB, 0, h->st>>>(h->K, P, J, b.met, b.sig, b.F[0]);
+        k_flux<T, FLAT, RC, 0><<<nblk(n), TPB, 0, h->st>>>(h->K, P, J, b.met, b.sig, F0);
     }
     if (G.g[1]) {
         long long n = (long long)G.n[0] * (G.n[1] + 1) * G.n[2];
-        k_flux<T, FLAT, RC, 1><<<nblk(n), TPB, 0, h->st>>>(h->K, P, J, b.met, b.sig, b.F[1]);
+        k_flux<T, FLAT, RC, 1><<<nblk(n), TPB, 0, h->st>>>(h->K, P, J, b.met, b.sig, F1);
     }
     if (G.g[2]) {
         long long n = (long long)G.n[0] * G.n[1] * (G.n[2] + 1);
-        k_flux<T, FLAT, RC, 2><<<nblk(n), TPB, 0, h->st>>>(h->K, P, J, b.met, b.sig, b.F[2]);
+        k_flux<T, FLAT, RC, 2><<<nblk(n), TPB, 0, h->st>>>(h->K, P, J, b.met, b.sig, F2);
     }
 }
 
-template <class T, bool FLAT>
-static void launch_flux_t(rmhd_t h, const double *P, const double *J)
+template <class T, bool FLAT> static void launch_flux(rmhd_t h, const T *P, const T *J)
 {
     switch (h->p.recon) {
     case RMHD_RECON_MINMOD: launch_flux_rc<T, FLAT, RC_MINMOD>(h, P, J); break;
@@ -181,46 +202,80 @@ static void launch_flux_t(rmhd_t h, const double *P, const double *J)
     }
 }
 
-static void launch_flux(rmhd_t h, const double *P, const double *J)
+static Defer defer_of(rmhd_t h, int which)
 {
-    const bool mixed = h->p.precision == RMHD_PREC_MIXED;
-    if (h->flat) {
-        if (mixed) launch_flux_t<float, true>(h, P, J);
-        else launch_flux_t<double, true>(h, P, J);
-    } else {
-        if (mixed) launch_flux_t<float, false>(h, P, J);
-        else launch_flux_t<double, false>(h, P, J);
-    }
+    Defer d;
+    d.count = h->b.dcount + which;
+    d.cap = h->b.dcap;
+    d.idx = h->b.didx;
+    d.rec = h->b.drec;
+    return d;
 }
 
-// ev (optional): 7 events recorded between the kernel groups of the step
-template <bool FLAT> static void enqueue_step(rmhd_t h, cudaEvent_t *ev = nullptr)
+static unsigned deferred_blocks(rmhd_t h)
+{
+    long long want = nblk(h->b.dcap);
+    return (unsigned)(want < 148 * 8 ? (want > 0 ? want : 1) : 148 * 8);
+}
+
+// ev (optional): 9 events recorded between the kernel groups of the step
+template <bool FLAT, class T> static void enqueue_step_t(rmhd_t h, cudaEvent_t *ev)
 {
     Buffers &b = h->b;
     const StepConst &K = h->K;
     const unsigned nb = nblk(K.G.N);
     auto mark = [&](int i) { if (ev) cudaEventRecord(ev[i], h->st); };
+    const bool dfr = b.dcap > 0;
+    const unsigned nbd = deferred_blocks(h);
+    T *PA = (T *)b.PA, *PB = (T *)b.PB, *J1 = (T *)b.J1, *J2 = (T *)b.J2;
+    T *F0 = (T *)b.F[0], *F1 = (T *)b.F[1], *F2 = (T *)b.F[2];
+    if (dfr) cudaMemsetAsync(b.dcount, 0, 3 * sizeof(int), h->st);
     mark(0);
-    k_stage1<FLAT><<<nb, TPB, 0, h->st>>>(K, b.U, b.PA, b.dR1, b.J1, b.met, b.sig, b.stats);
+    k_stage1<FLAT, T><<<nb, TPB, 0, h->st>>>(K, b.U, PA, b.GA, b.dR1, J1, b.met, b.sig,
+                                             defer_of(h, 0), b.stats);
+    if (dfr)
+        k_deferred<FLAT, 1, T><<<nbd, TPB, 0, h->st>>>(K, defer_of(h, 0), b.met, b.sig, nullptr,
+                                                       PA, b.GA, b.dR1, J1, nullptr, nullptr,
+                                                       b.stats);
     mark(1);
-    launch_ghosts(h, b.PA, NPR);
-    if (K.qflux == 0) launch_ghosts(h, b.J1, 3);
+    launch_ghosts(h, PA, NPR);
+    if (K.qflux == 0) launch_ghosts(h, J1, 3);
     mark(2);
-    launch_flux(h, b.PA, b.J1);
+    launch_flux<T, FLAT>(h, PA, J1);
     mark(3);
-    k_stage2<FLAT><<<nb, TPB, 0, h->st>>>(K, b.U, b.PA, b.F[0], b.F[1], b.F[2], b.dR1, b.met,
-                                          b.sig, b.PB, b.V, b.J2, b.stats);
+    k_stage2<FLAT, T><<<nb, TPB, 0, h->st>>>(K, b.U, PA, b.GA, F0, F1, F2, b.dR1, b.met, b.sig,
+                                             PB, b.GB, b.V, J2, defer_of(h, 1), b.stats);
+    if (dfr)
+        k_deferred<FLAT, 2, T><<<nbd, TPB, 0, h->st>>>(K, defer_of(h, 1), b.met, b.sig, b.dR1,
+                                                       PB, b.GB, nullptr, J2, b.V, nullptr,
+                                                       b.stats);
     mark(4);
-    launch_ghosts(h, b.PB, NPR);
-    if (K.qflux == 0) launch_ghosts(h, b.J2, 3);
+    launch_ghosts(h, PB, NPR);
+    if (K.qflux == 0) launch_ghosts(h, J2, 3);
     mark(5);
-    launch_flux(h, b.PB, b.J2);
+    launch_flux<T, FLAT>(h, PB, J2);
     mark(6);
-    k_final<FLAT><<<nb, TPB, 0, h->st>>>(K, b.V, b.PB, b.F[0], b.F[1], b.F[2], b.met, b.U, b.PA,
-                                         b.stats);
+    k_final<FLAT, T><<<nb, TPB, 0, h->st>>>(K, b.V, PB, b.GB, F0, F1, F2, b.met, b.U, PA, b.GA,
+                                            defer_of(h, 2), b.stats);
+    if (dfr)
+        k_deferred<FLAT, 3, T><<<nbd, TPB, 0, h->st>>>(K, defer_of(h, 2), b.met, b.sig, nullptr,
+                                                       PA, b.GA, nullptr, nullptr, nullptr, b.U,
+                                                       b.stats);
     mark(7);
-    launch_ghosts(h, b.PA, NPR);
+    launch_ghosts(h, PA, NPR);
     mark(8);
+}
+
+static void enqueue_step(rmhd_t h, cudaEvent_t *ev = nullptr)
+{
+    const bool mixed = h->p.precision == RMHD_PREC_MIXED;
+    if (h->flat) {
+        if (mixed) enqueue_step_t<true, float>(h, ev);
+        else enqueue_step_t<true, double>(h, ev);
+    } else {
+        if (mixed) enqueue_step_t<false, float>(h, ev);
+        else enqueue_step_t<false, double>(h, ev);
+    }
 }
 
 // copy a caller array (interior SoA, nf fields) into the staging buffer
@@ -246,6 +301,29 @@ static int read_flag(rmhd_t h, int *v)
     CK(cudaMemcpyAsync(v, h->b.flag, sizeof(int), cudaMemcpyDeviceToHost, h->st));
     CK(cudaStreamSynchronize(h->st));
     return RMHD_OK;
+}
+
+// staged interior FP64 primitives -> padded primitives of the path's type
+// (+ FP64 guess), ghosts filled
+static void scatter_prims(rmhd_t h, void *P, double *Gs)
+{
+    const unsigned nb = nblk(h->K.G.N);
+    if (h->p.precision == RMHD_PREC_MIXED) {
+        k_scatter_prims<float><<<nb, TPB, 0, h->st>>>(h->K, h->b.stage, (float *)P, Gs);
+        launch_ghosts(h, (float *)P, NPR);
+    } else {
+        k_scatter_prims<double><<<nb, TPB, 0, h->st>>>(h->K, h->b.stage, (double *)P, Gs);
+        launch_ghosts(h, (double *)P, NPR);
+    }
+}
+
+static void gather_prims(rmhd_t h, const void *P, const double *Gs)
+{
+    const unsigned nb = nblk(h->K.G.N);
+    if (h->p.precision == RMHD_PREC_MIXED)
+        k_gather_prims<float><<<nb, TPB, 0, h->st>>>(h->K, (const float *)P, Gs, h->b.stage);
+    else
+        k_gather_prims<double><<<nb, TPB, 0, h->st>>>(h->K, (const double *)P, Gs, h->b.stage);
 }
 
 // ------------------------------------------------------------------ API
@@ -275,6 +353,7 @@ extern "C" int rmhd_create(const rmhd_params *p, void *cuda_stream, rmhd_t *out)
     G.S = (long long)G.pxy * (G.n[2] + 2 * G.g[2]);
     G.N = (long long)G.n[0] * G.n[1] * G.n[2];
     K.gimex = 1.0 - 1.0 / sqrt(2.0);
+    K.igimex = 1.0 / K.gimex;
     K.gfac = p->gamma_eos / (p->gamma_eos - 1.0);
     K.kappa = p->kappa;
     K.sigma_model = p->sigma_model;
@@ -285,20 +364,32 @@ extern "C" int rmhd_create(const rmhd_params *p, void *cuda_stream, rmhd_t *out)
     K.ro = rec_opts(p);
 
     Buffers &b = h->b;
+    const bool mixed = p->precision == RMHD_PREC_MIXED;
     const size_t fb = sizeof(double) * (size_t)G.S;
-    struct { double **ptr; int nf; } allocs[] = {
-        {&b.U, NCO}, {&b.PA, NPR}, {&b.PB, NPR}, {&b.V, NCO}, {&b.dR1, 3}, {&b.J1, 3},
-        {&b.J2, 3}, {&b.F[0], NCO}, {&b.F[1], NCO}, {&b.F[2], NCO}, {&b.met, NMET}, {&b.sig, 1}};
+    const size_t fe = (mixed ? sizeof(float) : sizeof(double)) * (size_t)G.S;
+    struct { void **ptr; size_t bytes; } allocs[] = {
+        {(void **)&b.U, fb * NCO}, {&b.PA, fe * NPR}, {&b.PB, fe * NPR},
+        {(void **)&b.V, fb * NCO}, {(void **)&b.dR1, fb * 3}, {&b.J1, fe * 3},
+        {&b.J2, fe * 3}, {&b.F[0], fe * NCO}, {&b.F[1], fe * NCO}, {&b.F[2], fe * NCO},
+        {(void **)&b.met, fb * NMET}, {(void **)&b.sig, fb},
+        {(void **)&b.GA, mixed ? fb * 4 : 0}, {(void **)&b.GB, mixed ? fb * 4 : 0}};
+    b.own_guess = mixed;
     for (auto &a : allocs) {
-        cudaError_t e = cudaMalloc((void **)a.ptr, fb * a.nf);
+        if (a.bytes == 0) continue;
+        cudaError_t e = cudaMalloc(a.ptr, a.bytes);
         if (e != cudaSuccess) {
             free_all(b);
-            set_err(nullptr, RMHD_ENOMEM, "cudaMalloc of %zu bytes failed: %s", fb * a.nf,
+            set_err(nullptr, RMHD_ENOMEM, "cudaMalloc of %zu bytes failed: %s", a.bytes,
                     cudaGetErrorString(e));
             delete h;
             return RMHD_ENOMEM;
         }
-        cudaMemsetAsync(*a.ptr, 0, fb * a.nf, h->st);
+        cudaMemsetAsync(*a.ptr, 0, a.bytes, h->st);
+    }
+    if (!mixed) {
+        // FP64: the guess is fields 1..4 (p, v^i) of the primitive buffers
+        b.GA = (double *)b.PA + G.S;
+        b.GB = (double *)b.PB + G.S;
     }
     if (cudaMalloc((void **)&b.stage, sizeof(double) * NPR * (size_t)G.N) != cudaSuccess ||
         cudaMalloc((void **)&b.stats, sizeof(unsigned long long) * NSTAT) != cudaSuccess ||
@@ -309,6 +400,22 @@ extern "C" int rmhd_create(const rmhd_params *p, void *cuda_stream, rmhd_t *out)
         return RMHD_ENOMEM;
     }
     cudaMemsetAsync(b.stats, 0, sizeof(unsigned long long) * NSTAT, h->st);
+    // deferred-recovery work list: room for half of the cells (a fuller list
+    // falls back to inline recovery)
+    {
+        long long cap = G.N / 2;
+        if (cap < 1024) cap = 1024;
+        if (cap > (1LL << 30) / DREC) cap = (1LL << 30) / DREC;
+        b.dcap = (int)cap;
+        if (cudaMalloc((void **)&b.dcount, 3 * sizeof(int)) != cudaSuccess ||
+            cudaMalloc((void **)&b.didx, sizeof(int) * (size_t)cap) != cudaSuccess ||
+            cudaMalloc((void **)&b.drec, sizeof(double) * DREC * (size_t)cap) != cudaSuccess) {
+            free_all(b);
+            set_err(nullptr, RMHD_ENOMEM, "cudaMalloc of the recovery work list failed");
+            delete h;
+            return RMHD_ENOMEM;
+        }
+    }
     // flat metric, unit conductivity profile; the state comes from
     // rmhd_set_prims or rmhd_set_state
     rc = rmhd_set_metric(h, nullptr, nullptr, nullptr, nullptr, 0);
@@ -373,7 +480,7 @@ extern "C" int rmhd_set_metric(rmhd_t h, const double *alpha, const double *beta
     int rc = RMHD_OK;
     for (int a = 0; a < 4 && !rc; a++) {
         rc = stage_in(h, src[a], nf[a], on_device);
-        if (!rc) k_scatter<<<nblk(G.N), TPB, 0, h->st>>>(h->K, h->b.stage, tmp + off * S, nf[a]);
+        if (!rc) k_scatter<double><<<nblk(G.N), TPB, 0, h->st>>>(h->K, h->b.stage, tmp + off * S, nf[a]);
         off += nf[a];
     }
     if (!rc) {
@@ -431,7 +538,7 @@ extern "C" int rmhd_set_sigma(rmhd_t h, const double *profile, int on_device)
             }
         free(hb);
     }
-    k_scatter<<<nblk(G.N), TPB, 0, h->st>>>(h->K, h->b.stage, h->b.sig, 1);
+    k_scatter<double><<<nblk(G.N), TPB, 0, h->st>>>(h->K, h->b.stage, h->b.sig, 1);
     launch_ghosts(h, h->b.sig, 1);
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(h->st));
@@ -445,23 +552,22 @@ extern "C" int rmhd_set_prims(rmhd_t h, const double *prims, int on_device)
     const Grid &G = h->K.G;
     int rc = stage_in(h, prims, NPR, on_device);
     if (rc) return rc;
-    // scatter into PB first: validate before touching the state
-    k_scatter<<<nblk(G.N), TPB, 0, h->st>>>(h->K, h->b.stage, h->b.PB, NPR);
+    // conserved values into V first: validate before touching the state
     cudaMemsetAsync(h->b.flag, 0, sizeof(int), h->st);
     if (h->flat)
-        k_prim2con<true><<<nblk(G.N), TPB, 0, h->st>>>(h->K, h->b.PB, h->b.met, h->b.V, h->b.flag);
+        k_prim2con<true><<<nblk(G.N), TPB, 0, h->st>>>(h->K, h->b.stage, h->b.met, h->b.V,
+                                                       h->b.flag);
     else
-        k_prim2con<false><<<nblk(G.N), TPB, 0, h->st>>>(h->K, h->b.PB, h->b.met, h->b.V, h->b.flag);
+        k_prim2con<false><<<nblk(G.N), TPB, 0, h->st>>>(h->K, h->b.stage, h->b.met, h->b.V,
+                                                        h->b.flag);
     int bad = 0;
     rc = read_flag(h, &bad);
     if (rc) return rc;
     if (bad) return set_err(h, RMHD_EINVAL, "prims rejected: rho <= 0, p < 0, v^2 >= 1 or "
                                             "non-finite values");
-    CK(cudaMemcpyAsync(h->b.PA, h->b.PB, sizeof(double) * NPR * (size_t)G.S,
-                       cudaMemcpyDeviceToDevice, h->st));
     CK(cudaMemcpyAsync(h->b.U, h->b.V, sizeof(double) * NCO * (size_t)G.S,
                        cudaMemcpyDeviceToDevice, h->st));
-    launch_ghosts(h, h->b.PA, NPR);
+    scatter_prims(h, h->b.PA, h->b.GA);
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(h->st));
     h->have_state = true;
@@ -475,7 +581,6 @@ extern "C" int rmhd_set_state(rmhd_t h, const double *cons, const double *prims,
     const Grid &G = h->K.G;
     int bad = 0, rc;
     const double *src[2] = {cons, prims};
-    double *dst[2] = {h->b.U, h->b.PA};
     // validate both before committing
     for (int a = 0; a < 2; a++) {
         rc = stage_in(h, src[a], NPR, on_device);
@@ -486,12 +591,12 @@ extern "C" int rmhd_set_state(rmhd_t h, const double *cons, const double *prims,
         if (rc) return rc;
         if (bad) return set_err(h, RMHD_EINVAL, "state has non-finite values");
     }
-    for (int a = 0; a < 2; a++) {
-        rc = stage_in(h, src[a], NPR, on_device);
-        if (rc) return rc;
-        k_scatter<<<nblk(G.N), TPB, 0, h->st>>>(h->K, h->b.stage, dst[a], NPR);
-    }
-    launch_ghosts(h, h->b.PA, NPR);
+    rc = stage_in(h, cons, NCO, on_device);
+    if (rc) return rc;
+    k_scatter<double><<<nblk(G.N), TPB, 0, h->st>>>(h->K, h->b.stage, h->b.U, NCO);
+    rc = stage_in(h, prims, NPR, on_device);
+    if (rc) return rc;
+    scatter_prims(h, h->b.PA, h->b.GA);
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(h->st));
     h->have_state = true;
@@ -505,14 +610,14 @@ extern "C" int rmhd_step(rmhd_t h, double dt, int nsteps, long long *fail_count)
     if (nsteps < 0) return set_err(h, RMHD_EINVAL, "nsteps must be >= 0");
     if (!h->have_state) return set_err(h, RMHD_EINVAL, "no state: call rmhd_set_prims first");
     h->K.dt = dt;
+    h->K.idt = 1.0 / dt;
     unsigned long long before[NSTAT];
     if (fail_count) {
         CK(cudaMemcpyAsync(before, h->b.stats, sizeof(before), cudaMemcpyDeviceToHost, h->st));
         CK(cudaStreamSynchronize(h->st));
     }
     for (int s = 0; s < nsteps; s++) {
-        if (h->flat) enqueue_step<true>(h);
-        else enqueue_step<false>(h);
+        enqueue_step(h);
     }
     CK(cudaGetLastError());
     h->steps += nsteps;
@@ -534,13 +639,13 @@ extern "C" int rmhd_step_profiled(rmhd_t h, double dt, int nsteps, double ms[RMH
         return set_err(h, RMHD_EINVAL, "dt must be > 0 and nsteps >= 0");
     if (!h->have_state) return set_err(h, RMHD_EINVAL, "no state: call rmhd_set_prims first");
     h->K.dt = dt;
+    h->K.idt = 1.0 / dt;
     for (int g = 0; g < RMHD_NPROF; g++) ms[g] = 0.0;
     cudaEvent_t ev[9];
     for (int i = 0; i < 9; i++) CK(cudaEventCreate(&ev[i]));
     int rc = RMHD_OK;
     for (int s = 0; s < nsteps && !rc; s++) {
-        if (h->flat) enqueue_step<true>(h, ev);
-        else enqueue_step<false>(h, ev);
+        enqueue_step(h, ev);
         cudaError_t e = cudaEventSynchronize(ev[8]);
         if (e != cudaSuccess) {
             rc = set_err(h, RMHD_ECUDA, "step failed: %s", cudaGetErrorString(e));
@@ -568,7 +673,7 @@ extern "C" int rmhd_step_profiled(rmhd_t h, double dt, int nsteps, double ms[RMH
 extern "C" int rmhd_get_prims(rmhd_t h, double *prims, int on_device)
 {
     if (!h || !prims) return set_err(h, RMHD_EINVAL, "NULL argument");
-    k_gather<<<nblk(h->K.G.N), TPB, 0, h->st>>>(h->K, h->b.PA, h->b.stage, NPR);
+    gather_prims(h, h->b.PA, h->b.GA);
     CK(cudaGetLastError());
     return stage_out(h, prims, NPR, on_device);
 }
@@ -598,6 +703,29 @@ extern "C" int rmhd_get_stats(rmhd_t h, long long stats[8])
     return RMHD_OK;
 }
 
+template <class T> static int rhs_t(rmhd_t h, const double *J, int on_device)
+{
+    const Grid &G = h->K.G;
+    T *J2 = (T *)h->b.J2, *PB = (T *)h->b.PB;
+    T *F0 = (T *)h->b.F[0], *F1 = (T *)h->b.F[1], *F2 = (T *)h->b.F[2];
+    if (J) {
+        int rc = stage_in(h, J, 3, on_device);
+        if (rc) return rc;
+        k_scatter<T><<<nblk(G.N), TPB, 0, h->st>>>(h->K, h->b.stage, J2, 3);
+    } else {
+        CK(cudaMemsetAsync(J2, 0, sizeof(T) * 3 * (size_t)G.S, h->st));
+    }
+    launch_ghosts(h, J2, 3);
+    if (h->flat) {
+        launch_flux<T, true>(h, PB, J2);
+        k_rhs<true, T><<<nblk(G.N), TPB, 0, h->st>>>(h->K, PB, F0, F1, F2, h->b.met, h->b.stage);
+    } else {
+        launch_flux<T, false>(h, PB, J2);
+        k_rhs<false, T><<<nblk(G.N), TPB, 0, h->st>>>(h->K, PB, F0, F1, F2, h->b.met, h->b.stage);
+    }
+    return RMHD_OK;
+}
+
 extern "C" int rmhd_rhs(rmhd_t h, const double *prims, const double *J, double *rhs,
                         int on_device)
 {
@@ -605,23 +733,10 @@ extern "C" int rmhd_rhs(rmhd_t h, const double *prims, const double *J, double *
     const Grid &G = h->K.G;
     int rc = stage_in(h, prims, NPR, on_device);
     if (rc) return rc;
-    k_scatter<<<nblk(G.N), TPB, 0, h->st>>>(h->K, h->b.stage, h->b.PB, NPR);
-    if (J) {
-        rc = stage_in(h, J, 3, on_device);
-        if (rc) return rc;
-        k_scatter<<<nblk(G.N), TPB, 0, h->st>>>(h->K, h->b.stage, h->b.J2, 3);
-    } else {
-        CK(cudaMemsetAsync(h->b.J2, 0, sizeof(double) * 3 * (size_t)G.S, h->st));
-    }
-    launch_ghosts(h, h->b.PB, NPR);
-    launch_ghosts(h, h->b.J2, 3);
-    launch_flux(h, h->b.PB, h->b.J2);
-    if (h->flat)
-        k_rhs<true><<<nblk(G.N), TPB, 0, h->st>>>(h->K, h->b.PB, h->b.F[0], h->b.F[1], h->b.F[2],
-                                                  h->b.met, h->b.stage);
-    else
-        k_rhs<false><<<nblk(G.N), TPB, 0, h->st>>>(h->K, h->b.PB, h->b.F[0], h->b.F[1], h->b.F[2],
-                                                   h->b.met, h->b.stage);
+    scatter_prims(h, h->b.PB, h->b.GB);
+    if (h->p.precision == RMHD_PREC_MIXED) rc = rhs_t<float>(h, J, on_device);
+    else rc = rhs_t<double>(h, J, on_device);
+    if (rc) return rc;
     CK(cudaGetLastError());
     return stage_out(h, rhs, NCO, on_device);
 }
