@@ -180,6 +180,32 @@ int rmhd_con2prim_points(const rmhd_params *p, int npts, const double *cons,
                          double c, double *prim, double *cons_out, int *iters,
                          int *status, void *cuda_stream);
 
+/* Capacity of the built-in work list of rmhd_con2prim_points_noalloc. */
+#define RMHD_NOALLOC_MAX_POINTS 65536
+
+/* rmhd_con2prim_points without any device allocation.  The paper has no
+ * counterpart: this entry point exists for callers that may not allocate
+ * device memory when they call it -- drivers that size one memory pool at
+ * start-up and treat later allocations as errors, time-critical loops that
+ * cannot pay for cudaMalloc's synchronisation and latency, and host programs
+ * that own all device memory.  Same arguments, results and statuses as
+ * rmhd_con2prim_points, computed with the stepping kernels' two-pass scheme
+ * (paper iteration, then the fallbacks for the listed points) whose work
+ * list is a fixed array compiled into the library (RMHD_NOALLOC_MAX_POINTS
+ * indices plus a counter, about 256 KB, held by every GPU that loads the
+ * library until the process exits).  npts above RMHD_NOALLOC_MAX_POINTS is
+ * rejected with RMHD_EINVAL.  The first call on a device looks up that
+ * device's copy of the array (cudaGetSymbolAddress with the device current);
+ * make that first call before any stream capture.  Calls share the one list
+ * and it keeps the previous call's contents (the counter is cleared at the
+ * start of each call): calls that overlap on the GPU race, so serialise
+ * them.  Calls no cudaMalloc / cudaFree.  Errors: rmhd_last_error(NULL). */
+int rmhd_con2prim_points_noalloc(const rmhd_params *p, int npts, const double *cons,
+                                 const double *guess, const double *alpha,
+                                 const double *gamma, const double *sigma, int implicit,
+                                 double c, double *prim, double *cons_out, int *iters,
+                                 int *status, void *cuda_stream);
+
 /* Text of the last error on this handle (never NULL; "" if none).  With
  * h == NULL: the last error of a call that had no handle. */
 const char *rmhd_last_error(rmhd_t h);

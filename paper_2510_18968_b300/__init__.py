@@ -58,6 +58,7 @@ class Params(ctypes.Structure):
 EXPORTS = ("rmhd_default_params", "rmhd_create", "rmhd_set_metric", "rmhd_set_sigma",
            "rmhd_set_prims", "rmhd_step", "rmhd_get_prims", "rmhd_get_cons",
            "rmhd_set_state", "rmhd_get_stats", "rmhd_step_profiled", "rmhd_rhs", "rmhd_con2prim_points",
+           "rmhd_con2prim_points_noalloc",
            "rmhd_last_error", "rmhd_destroy")
 
 _lib = None
@@ -90,6 +91,8 @@ def load(build_if_missing=True):
     L.rmhd_step_profiled.argtypes = [vp, d, i, ctypes.POINTER(ctypes.c_double)]
     L.rmhd_rhs.argtypes = [vp, vp, vp, vp, i]
     L.rmhd_con2prim_points.argtypes = [P, i, vp, vp, vp, vp, vp, i, d, vp, vp, vp, vp, vp]
+    L.rmhd_con2prim_points_noalloc.argtypes = [P, i, vp, vp, vp, vp, vp, i, d, vp, vp, vp, vp,
+                                               vp]
     L.rmhd_last_error.argtypes = [vp]
     L.rmhd_last_error.restype = ctypes.c_char_p
     L.rmhd_destroy.argtypes = [vp]
@@ -267,23 +270,31 @@ class Solver:
         return out
 
 
-def con2prim_points(params, cons, guess, alpha, gamma, sigma, implicit, c, stream=None):
+def con2prim_points(params, cons, guess, alpha, gamma, sigma, implicit, c, stream=None,
+                    out=None, noalloc=False):
     """Pointwise recovery on CUDA torch tensors (cons/guess (14, n), alpha (n,),
-    gamma (6, n), sigma (n,)).  Returns (prim, cons_out, iters, status)."""
+    gamma (6, n), sigma (n,)).  Returns (prim, cons_out, iters, status).
+    noalloc=True calls rmhd_con2prim_points_noalloc, the variant that uses
+    the library's built-in work list instead of allocating; pass preallocated
+    outputs in `out` = (prim, cons_out, iters, status) to allocate nothing
+    here either."""
     import torch
     L = load()
     P = params if isinstance(params, Params) else make_params(**params)
     n = int(alpha.numel())
     dev = alpha.device
-    prim = torch.empty((14, n), dtype=torch.float64, device=dev)
-    cout = torch.empty((14, n), dtype=torch.float64, device=dev)
-    iters = torch.empty(n, dtype=torch.int32, device=dev)
-    status = torch.empty(n, dtype=torch.int32, device=dev)
+    if out is None:
+        prim = torch.empty((14, n), dtype=torch.float64, device=dev)
+        cout = torch.empty((14, n), dtype=torch.float64, device=dev)
+        iters = torch.empty(n, dtype=torch.int32, device=dev)
+        status = torch.empty(n, dtype=torch.int32, device=dev)
+    else:
+        prim, cout, iters, status = out
     args = [_ptr(x, m)[0] for x, m in ((cons, 14 * n), (guess, 14 * n), (alpha, n),
                                         (gamma, 6 * n), (sigma, n))]
-    rc = L.rmhd_con2prim_points(ctypes.byref(P), n, *args, int(implicit), float(c),
-                                prim.data_ptr(), cout.data_ptr(), iters.data_ptr(),
-                                status.data_ptr(), _stream_ptr(stream))
+    fn = L.rmhd_con2prim_points_noalloc if noalloc else L.rmhd_con2prim_points
+    rc = fn(ctypes.byref(P), n, *args, int(implicit), float(c), prim.data_ptr(),
+            cout.data_ptr(), iters.data_ptr(), status.data_ptr(), _stream_ptr(stream))
     if rc:
         raise RMHDError(rc, L.rmhd_last_error(None).decode())
     return prim, cout, iters, status

@@ -6,7 +6,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "librmhd.so")
-SOURCES = [os.path.join(CSRC, "rmhd.cu")]
+SOURCES = [os.path.join(CSRC, "rmhd.cu"), os.path.join(CSRC, "noalloc.cu")]
 DEPS = SOURCES + [os.path.join(CSRC, f) for f in ("physics.cuh", "recovery.cuh", "kernels.cuh")] + [
     os.path.join(os.path.dirname(HERE), "include", "rmhd.h")]
 

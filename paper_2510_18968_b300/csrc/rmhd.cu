@@ -730,7 +730,6 @@ extern "C" int rmhd_rhs(rmhd_t h, const double *prims, const double *J, double *
                         int on_device)
 {
     if (!h || !prims || !rhs) return set_err(h, RMHD_EINVAL, "NULL argument");
-    const Grid &G = h->K.G;
     int rc = stage_in(h, prims, NPR, on_device);
     if (rc) return rc;
     scatter_prims(h, h->b.PB, h->b.GB);
@@ -766,6 +765,12 @@ extern "C" int rmhd_con2prim_points(const rmhd_params *p, int npts, const double
 }
 
 extern "C" const char *rmhd_last_error(rmhd_t h) { return h ? h->err : g_noh_err; }
+
+// error text of an entry point without a handle (used by the other source file)
+__attribute__((visibility("hidden"))) void rmhd_internal_set_error(const char *msg)
+{
+    snprintf(g_noh_err, sizeof g_noh_err, "%s", msg);
+}
 
 extern "C" int rmhd_destroy(rmhd_t h)
 {
