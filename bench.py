@@ -106,18 +106,19 @@ def workload(n):
     return W.cyl_blast(n=n)
 
 
-# algorithmic HBM bytes per zone of each kernel group (state arrays read or
-# written once per launch; fp64 state, see the design notes)
-ALG_BYTES = {
-    # stage 1: U^n 14 + guess (p, v) 4 in; P1 14 + dR1 3 + J1 3 out
-    "stage1_recovery": 8 * (14 + 4 + 14 + 3 + 3),
-    # fluxes of one direction: P 14 + J 1 in (stencil read once), F 14 out
-    "flux": 8 * (14 + 1 + 14),
-    # stage 2: U 14, P1 14, F 3x14, dR1 3 in; P2 14, V 14, J2 3 out
-    "stage2_rhs_recovery": 8 * (14 + 14 + 42 + 3 + 14 + 14 + 3),
-    # final: V 14, P2 14, F 3x14 in; U 14, P 14 out
-    "final_rhs_recovery": 8 * (14 + 14 + 42 + 14 + 14),
+# Algorithmic work per zone of each kernel group (counted from the kernel
+# source; see the design notes).  Recovery kernels: FP64 flops at ONE paper
+# iteration per cell (the least any cell needs; extra iterations and the
+# fallbacks count as overhead), FMA = 2 flops, division / square root = 1.
+# Flux kernels: per face, HBM bytes of a stencil read once (15 fields in,
+# 14 out) and flops of reconstruction + two flux states + HLLE.
+FP64_FLOPS = {  # per cell, (mixed path, FP64 path)
+    "stage1_recovery": (142, 142),
+    "stage2_rhs_recovery": (211, 303),
+    "final_rhs_recovery": (116, 208),
 }
+FLUX_FLOPS_PER_FACE = 650
+FLUX_FIELDS = 15 + 14
 
 
 def run_ours(args, rank, world, local):
@@ -176,24 +177,46 @@ def run_ours(args, rank, world, local):
     return wl, out
 
 
-def roofline(wl, res, prec):
+def kernel_rooflines(wl, res, prec, steps):
+    """Roofline of every kernel group from its live CUDA-event time."""
     hbm, kind = _peaks()
     g = res["groups"]
-    steps = res["steps"]
     N = wl.ncells
-    # dominant group
-    name = max(g, key=g.get)
-    per_launch_ms = g[name] / steps
-    if name.startswith("flux"):
-        nd = 3
-        per_launch_ms /= nd
-        alg = ALG_BYTES["flux"] * N
-    else:
-        alg = ALG_BYTES.get(name, 0) * N
-    achieved = alg / (per_launch_ms * 1e-3) / 1e9
-    return {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": hbm,
-            "unit": "GB/s", "frac": achieved / hbm, "peak_kind": kind,
-            "traffic": None, "launch_ms": per_launch_ms}
+    nd = sum(1 for d in range(3) if wl.params["n"][d] > 1)
+    out = {}
+    for name, ms in g.items():
+        if name == "ghost_fill":
+            continue
+        if name.startswith("flux"):
+            per_launch_ms = ms / steps / nd           # one direction per launch
+            faces = N                                 # ~one face per cell per direction
+            esz = 4 if prec == "mixed" else 8
+            alg = FLUX_FIELDS * esz * faces
+            ach = alg / (per_launch_ms * 1e-3) / 1e9
+            out[name] = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                         "frac": ach / hbm, "peak_kind": kind, "launch_ms": per_launch_ms,
+                         "alg_bytes_per_launch": alg,
+                         "alg_flops_per_face": FLUX_FLOPS_PER_FACE}
+        else:
+            per_launch_ms = ms / steps
+            f = FP64_FLOPS[name][0 if prec == "mixed" else 1] * N
+            ach = f / (per_launch_ms * 1e-3) / 1e12
+            out[name] = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
+                         "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
+                         "peak_kind": "derived (148 SM x 2 DFMA/clk x 2.032 GHz; measured "
+                                      "1.111 TFLOP/s FP64 FMA at 1.94 GHz)",
+                         "launch_ms": per_launch_ms, "alg_fp64_flops_per_launch": f}
+    return out
+
+
+def roofline(wl, res, prec, steps, traffic=None):
+    ks = kernel_rooflines(wl, res, prec, steps)
+    g = res["groups"]
+    name = max((k for k in g if k != "ghost_fill"), key=g.get)
+    r = dict(ks[name])
+    r["kernel"] = name
+    r["traffic"] = None if traffic is None else traffic.get((name, prec))
+    return r, ks
 
 
 def cpu_oracle_sample(nz, steps):
@@ -266,15 +289,23 @@ def main():
         line["fp64"] = {"value": world * N * args.steps / (f["ms"] * 1e-3),
                         "ms_per_step": f["ms"] / args.steps,
                         "mixed_speedup": f["ms"] / r["ms"]}
-    line["roofline"] = roofline(wl, r, head)
+    line["roofline"], line["roofline_kernels"] = roofline(wl, r, head, args.steps)
     line["kernel_ms_per_step"] = {k: v / args.steps for k, v in r["groups"].items()}
+    if "fp64" in res and head != "fp64":
+        line["fp64"]["kernel_ms_per_step"] = {k: v / args.steps
+                                             for k, v in res["fp64"]["groups"].items()}
+        line["fp64"]["roofline_kernels"] = kernel_rooflines(wl, res["fp64"], "fp64", args.steps)
     line["recovery_stats"] = r["stats"]
     line["clocks"] = r["clocks"]
     line["e2e"] = {"value": world * r["e2e"], "unit": UNIT,
                    "h2d_bytes_per_step": r["e2e_bytes"][0], "d2h_bytes_per_step": r["e2e_bytes"][1]}
-    # kernel launches inside the timed region (per step: stage1, ghosts x(2+2+1)
-    # with J ghosts, 3+3 flux, stage2, final)
-    per_step = 1 + 5 + 6 + 1 + 1
+    # kernel launches inside the timed region, per step: three recovery
+    # kernels and their deferred passes, ghost fills (primitives, and stage
+    # currents when the charge flux uses them), one flux kernel per active
+    # direction and stage
+    nd = sum(1 for d in range(3) if wl.params["n"][d] > 1)
+    ghosts = (2 if wl.params["qflux_mode"] == 0 else 1) * 2 + 1
+    per_step = 3 + 3 + ghosts + 2 * nd
     line["gpu_launches"] = per_step * args.steps
     if not args.no_cpu_baseline:
         v, sample = cpu_oracle_sample(4, 1)

@@ -65,13 +65,17 @@ __device__ __forceinline__ long long dstride(const Grid &G, int d)
     return d == 0 ? 1LL : (d == 1 ? (long long)G.px : (long long)G.pxy);
 }
 
+// linear interior index -> (i, j, k); 32-bit arithmetic (the library
+// rejects grids of 2^31 cells or more), which the GPU divides far faster
+// than 64-bit integers
 __device__ __forceinline__ void interior_coords(const Grid &G, long long t, int &i, int &j,
                                                 int &k)
 {
-    i = (int)(t % G.n[0]);
-    long long r = t / G.n[0];
-    j = (int)(r % G.n[1]);
-    k = (int)(r / G.n[1]);
+    const unsigned u = (unsigned)t, nx = (unsigned)G.n[0], ny = (unsigned)G.n[1];
+    const unsigned r = u / nx;
+    i = (int)(u - r * nx);
+    k = (int)(r / ny);
+    j = (int)(r - (unsigned)k * ny);
 }
 
 template <bool FLAT>
@@ -170,15 +174,15 @@ template <class T> __global__ void k_ghosts(const StepConst K, T *buf, int nf, i
     const int d = d0 + blockIdx.y;
     if (G.g[d] == 0) return;
     const int a = (d + 1) % 3, b = (d + 2) % 3;
-    long long per_side = (long long)G.g[d] * G.n[a] * G.n[b];
-    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const unsigned per_side = (unsigned)G.g[d] * G.n[a] * G.n[b];
+    const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= 2 * per_side) return;
-    int side = (int)(t / per_side);
-    long long r = t % per_side;
-    int layer = (int)(r % G.g[d]);
-    r /= G.g[d];
-    int ca = (int)(r % G.n[a]);
-    int cb = (int)(r / G.n[a]);
+    const int side = t >= per_side;
+    unsigned r = t - (side ? per_side : 0u);
+    const int layer = (int)(r % (unsigned)G.g[d]);
+    r /= (unsigned)G.g[d];
+    const int ca = (int)(r % (unsigned)G.n[a]);
+    const int cb = (int)(r / (unsigned)G.n[a]);
     int dst_d = side == 0 ? -1 - layer : G.n[d] + layer;
     int src_d;
     if (G.bc[d] == 0)
@@ -293,10 +297,10 @@ __global__ void __launch_bounds__(128) k_flux(const StepConst K, const T *__rest
     int m0 = G.n[0] + (D == 0), m1 = G.n[1] + (D == 1);
     long long nf = (long long)m0 * m1 * (G.n[2] + (D == 2));
     if (t >= nf) return;
-    int i = (int)(t % m0);
-    long long r = t / m0;
-    int j = (int)(r % m1);
-    int k = (int)(r / m1);
+    const unsigned u = (unsigned)t, r = u / (unsigned)m0;
+    int i = (int)(u - r * (unsigned)m0);
+    int k = (int)(r / (unsigned)m1);
+    int j = (int)(r - (unsigned)k * (unsigned)m1);
     const long long cR = cell_at(G, i, j, k);
     const long long s = dstride(G, D);
     const long long cL = cR - s;
@@ -549,12 +553,13 @@ __device__ __forceinline__ void rhs_cell(const StepConst &K, const T pr[NPR],
 
 // ---------------------------------------------------------------- stages
 
-// Deferred recoveries: cells whose paper iteration does not converge are
-// appended to a work list (scratch memory of the handle) and finished by a
-// second pass with full warps, instead of holding their warp in the
-// fallback.  A record holds the stage's conserved input (14) and the guess
+// Deferred recoveries: cells whose paper iteration is still undecided after
+// the first pass's iterations are appended, with their iterate, to a work
+// list (scratch memory of the handle); a second pass with full warps resumes
+// them where they stopped (and runs the fallbacks), instead of letting one
+// slow cell hold its warp.  A record holds the stage's conserved input (14) and the guess
 // (p, v^i); when the list is full the cell falls back inline.
-enum { DREC = NCO + 4 };
+enum { DREC = NCO + 4 + PSTATE };
 struct Defer {
     int *count;          // records written (may exceed cap; cap is the limit)
     int cap;             // 0: no deferral
@@ -579,13 +584,15 @@ __device__ __forceinline__ int defer_slot(const Defer &df, bool want)
 }
 
 __device__ __forceinline__ void defer_store(const Defer &df, int slot, long long t,
-                                            const double u[NCO], double gp, const double gv[3])
+                                            const double u[NCO], double gp, const double gv[3],
+                                            const PaperState &ps)
 {
     df.idx[slot] = (int)t;
     const long long cap = df.cap;
     for (int f = 0; f < NCO; f++) df.rec[f * cap + slot] = u[f];
     df.rec[(NCO + 0) * cap + slot] = gp;
     for (int a = 0; a < 3; a++) df.rec[(NCO + 1 + a) * cap + slot] = gv[a];
+    pstate_save(ps, df.rec + (NCO + 4) * cap + slot, cap);
 }
 
 __device__ __forceinline__ void load_rec_in(const double u[NCO], RecIn &in)
@@ -673,6 +680,7 @@ k_stage1(const StepConst K, const double *__restrict__ U, T *P, double *Gs, doub
     long long c = 0;
     double u[NCO], pr[NPR], E[3], gp = 0.0, gv[3] = {0, 0, 0}, cc = 0.0;
     Met<double> m;
+    PaperState ps;
     if (active) {
         int i, j, k;
         interior_coords(G, t, i, j, k);
@@ -686,25 +694,25 @@ k_stage1(const StepConst K, const double *__restrict__ U, T *P, double *Gs, doub
         gp = Gs[c];
         for (int a = 0; a < 3; a++) gv[a] = Gs[(1 + a) * S + c];
         status = recover<FLAT>(in, m, K.ro, true, cc, gp, gv, u[CO_PHI], u[CO_PSI], u[CO_Q], pr,
-                               E, iters, df.cap ? REC_PRIMARY : REC_ALL);
+                               E, iters, df.cap ? REC_FIRST : REC_ALL, &ps);
     }
     const bool want = active && status == REC_DEFER;
     const int slot = defer_slot(df, want);
     if (want) {
         if (slot >= 0) {
-            defer_store(df, slot, t, u, gp, gv);
+            defer_store(df, slot, t, u, gp, gv, ps);
         } else {
             RecIn in;
             load_rec_in(u, in);
             int it2 = 0;
             status = recover<FLAT>(in, m, K.ro, true, cc, gp, gv, u[CO_PHI], u[CO_PSI], u[CO_Q],
-                                   pr, E, it2, REC_FALLBACK);
-            iters += it2;
+                                   pr, E, it2, REC_ALL);
+            iters = it2;
         }
     }
     const bool deferred = want && slot >= 0;
     if (active && !deferred) stage1_write(K, c, pr, E, u, m.alpha, P, Gs, dR1, J1);
-    record_stats(stats, active, status, iters, !deferred);
+    record_stats(stats, active, status, deferred ? 0 : iters, !deferred);
 }
 
 // Stage 2: U* = U^n + dt F[U1] + (1-2gamma) Dt R1 on calE; implicit recovery
@@ -724,6 +732,7 @@ k_stage2(const StepConst K, const double *__restrict__ U, const T *__restrict__ 
     long long c = 0;
     double us[NCO], p2[NPR], E[3], gp = 0.0, gv[3] = {0, 0, 0}, cc = 0.0;
     Met<double> m;
+    PaperState ps;
     if (active) {
         int i, j, k;
         interior_coords(G, t, i, j, k);
@@ -747,25 +756,25 @@ k_stage2(const StepConst K, const double *__restrict__ U, const T *__restrict__ 
         gp = G1[c];
         for (int a = 0; a < 3; a++) gv[a] = G1[(1 + a) * S + c];
         status = recover<FLAT>(in, m, K.ro, true, cc, gp, gv, us[CO_PHI], us[CO_PSI], us[CO_Q],
-                               p2, E, iters, df.cap ? REC_PRIMARY : REC_ALL);
+                               p2, E, iters, df.cap ? REC_FIRST : REC_ALL, &ps);
     }
     const bool want = active && status == REC_DEFER;
     const int slot = defer_slot(df, want);
     if (want) {
         if (slot >= 0) {
-            defer_store(df, slot, t, us, gp, gv);
+            defer_store(df, slot, t, us, gp, gv, ps);
         } else {
             RecIn in;
             load_rec_in(us, in);
             int it2 = 0;
             status = recover<FLAT>(in, m, K.ro, true, cc, gp, gv, us[CO_PHI], us[CO_PSI],
-                                   us[CO_Q], p2, E, it2, REC_FALLBACK);
-            iters += it2;
+                                   us[CO_Q], p2, E, it2, REC_ALL);
+            iters = it2;
         }
     }
     const bool deferred = want && slot >= 0;
     if (active && !deferred) stage2_write(K, c, p2, E, us, m.alpha, dR1, P2, G2, V, J2);
-    record_stats(stats, active, status, iters, !deferred);
+    record_stats(stats, active, status, deferred ? 0 : iters, !deferred);
 }
 
 // Final: U^{n+1} = V + dt/2 F[U2]; recovery with calE fixed (guess P2).
@@ -783,6 +792,7 @@ k_final(const StepConst K, const double *__restrict__ Vb, const T *__restrict__ 
     long long c = 0;
     double un[NCO], pn[NPR], E[3], gp = 0.0, gv[3] = {0, 0, 0};
     Met<double> m;
+    PaperState ps;
     if (active) {
         int i, j, k;
         interior_coords(G, t, i, j, k);
@@ -806,25 +816,25 @@ k_final(const StepConst K, const double *__restrict__ Vb, const T *__restrict__ 
         gp = G2[c];
         for (int a = 0; a < 3; a++) gv[a] = G2[(1 + a) * S + c];
         status = recover<FLAT>(in, m, K.ro, false, 0.0, gp, gv, un[CO_PHI], un[CO_PSI],
-                               un[CO_Q], pn, E, iters, df.cap ? REC_PRIMARY : REC_ALL);
+                               un[CO_Q], pn, E, iters, df.cap ? REC_FIRST : REC_ALL, &ps);
     }
     const bool want = active && status == REC_DEFER;
     const int slot = defer_slot(df, want);
     if (want) {
         if (slot >= 0) {
-            defer_store(df, slot, t, un, gp, gv);
+            defer_store(df, slot, t, un, gp, gv, ps);
         } else {
             RecIn in;
             load_rec_in(un, in);
             int it2 = 0;
             status = recover<FLAT>(in, m, K.ro, false, 0.0, gp, gv, un[CO_PHI], un[CO_PSI],
-                                   un[CO_Q], pn, E, it2, REC_FALLBACK);
-            iters += it2;
+                                   un[CO_Q], pn, E, it2, REC_ALL);
+            iters = it2;
         }
     }
     const bool deferred = want && slot >= 0;
     if (active && !deferred) final_write<FLAT>(K, c, pn, status, m, U, P, Gs);
-    record_stats(stats, active, status, iters, !deferred);
+    record_stats(stats, active, status, deferred ? 0 : iters, !deferred);
 }
 
 // Deferred pass of stage 1 (STAGE 1), stage 2 (STAGE 2) or the final
@@ -852,6 +862,8 @@ k_deferred(const StepConst K, const Defer df, const double *__restrict__ met,
             for (int f = 0; f < NCO; f++) u[f] = df.rec[f * cap + s];
             const double gp = df.rec[NCO * cap + s];
             for (int a = 0; a < 3; a++) gv[a] = df.rec[(NCO + 1 + a) * cap + s];
+            PaperState ps;
+            pstate_load(ps, df.rec + (NCO + 4) * cap + s, cap);
             Met<double> m;
             load_metric<FLAT>(met, G.S, c, m);
             RecIn in;
@@ -860,7 +872,7 @@ k_deferred(const StepConst K, const Defer df, const double *__restrict__ met,
             const double cc =
                 implicit ? K.gimex * K.dt * m.alpha * sigma_cell(K, sig, c, in.D) : 0.0;
             status = recover<FLAT>(in, m, K.ro, implicit, cc, gp, gv, u[CO_PHI], u[CO_PSI],
-                                   u[CO_Q], pr, E, iters, REC_FALLBACK);
+                                   u[CO_Q], pr, E, iters, REC_RESUME, &ps);
             if (STAGE == 1) stage1_write(K, c, pr, E, u, m.alpha, P, Gs, dRo, J);
             if (STAGE == 2) stage2_write(K, c, pr, E, u, m.alpha, dR1, P, Gs, V, J);
             if (STAGE == 3) final_write<FLAT>(K, c, pr, status, m, U, P, Gs);

@@ -30,6 +30,7 @@ struct RecOpts {
     double v2max;        // 1 - 1/W_max^2
     double rho_atmo, p_atmo, atmo_floor;  // atmo_floor = rho_atmo (1 + atmo_tol)
     int maxit;           // cap of the paper iteration
+    int first_cap;       // paper iterations of the first pass (REC_FIRST)
 };
 
 struct RecIn {
@@ -99,67 +100,140 @@ __device__ __forceinline__ bool fluid_step(const RecCtx<FLAT> &c, const double E
     return true;
 }
 
-// The paper's iteration (steps ii-v).  Returns 1 converged, 0 gave up.
+// Iterate of the paper's iteration, complete enough to stop after any
+// iteration and continue later with bit-identical arithmetic.
+enum { PSTATE = 15 };
+struct PaperState {
+    int it;                   // iterations done
+    double p, v[3], vl[3];    // current iterate
+    double v2, W;             // of v
+    double prev0, prev1, prev2;  // change measures of the last iterations
+    int outcome;              // -1 undecided, 0 gave up (fallbacks next)
+    int slow;                 // gave up for slow convergence
+};
+
+__device__ __forceinline__ void pstate_save(const PaperState &s, double *dst, long long stride)
+{
+    const double vals[PSTATE] = {(double)s.it, s.p,     s.v[0],  s.v[1],  s.v[2],
+                                 s.vl[0],      s.vl[1], s.vl[2], s.v2,    s.W,
+                                 s.prev0,      s.prev1, s.prev2, (double)s.outcome,
+                                 (double)s.slow};
+    for (int k = 0; k < PSTATE; k++) dst[k * stride] = vals[k];
+}
+
+__device__ __forceinline__ void pstate_load(PaperState &s, const double *src, long long stride)
+{
+    s.it = (int)src[0];
+    s.p = src[1 * stride];
+    for (int a = 0; a < 3; a++) {
+        s.v[a] = src[(2 + a) * stride];
+        s.vl[a] = src[(5 + a) * stride];
+    }
+    s.v2 = src[8 * stride];
+    s.W = src[9 * stride];
+    s.prev0 = src[10 * stride];
+    s.prev1 = src[11 * stride];
+    s.prev2 = src[12 * stride];
+    s.outcome = (int)src[13 * stride];
+    s.slow = (int)src[14 * stride];
+}
+
+// Start of the paper iteration at the guess; false if the guess is outside
+// the physical region.
+template <bool FLAT>
+__device__ __forceinline__ bool paper_start(const RecCtx<FLAT> &c, double p, const double v[3],
+                                            PaperState &s)
+{
+    s.it = 0;
+    s.p = p;
+    for (int a = 0; a < 3; a++) s.v[a] = v[a];
+    lower<double, FLAT>(c.m, s.v, s.vl);
+    s.v2 = dot3(s.v, s.vl);
+    if (!(s.v2 < c.o.v2max)) return false;
+    s.W = rsqrt(1.0 - s.v2);
+    s.prev0 = s.prev1 = s.prev2 = 0.0;
+    s.outcome = -1;
+    s.slow = 0;
+    return true;
+}
+
+// The paper's iteration (steps ii-v) from state s, up to iteration `limit`.
+// Returns 1 converged, 0 gave up, -1 reached `limit` (< maxit) undecided.
 // The Lorentz factor and lowered velocity of an iterate are carried to the
 // next implicit solve; f and f/f' are formed without dividing by D:
 //   f = (Gamma-1) num (1-v^2)/sqrt(g) - p,
 //   f/f' = f (D + Gamma num/W) / (v^2 Gamma(Gamma-1) num/W - D - Gamma num/W).
+// p_guess fixes the energy scale of the change measure.
 template <bool FLAT>
-__device__ int paper_iteration(const RecCtx<FLAT> &c, double &p, double v[3], double E[3],
-                               double &rho_out, int &iters, bool allow_slow, bool &slow_stop)
+__device__ int paper_run(const RecCtx<FLAT> &c, PaperState &s, double p_guess, int limit,
+                         double E[3], double &rho_out, bool allow_slow, bool &slow_stop)
 {
     slow_stop = false;
     const double Gam = c.o.Gam, g1 = Gam - 1.0, gg1 = Gam * (Gam - 1.0);
     const double D = c.in.D;
-    double vl[3];
-    lower<double, FLAT>(c.m, v, vl);
-    double v2 = dot3(v, vl);
-    if (!(v2 < c.o.v2max)) return 0;
-    double W = rsqrt(1.0 - v2);
-    // reciprocal of the energy scale at the guess, for the divergence measure
-    const double iscale0 = c.sg / (c.in.tau + D + c.sg * p);
-    double prev0 = 0.0, prev1 = 0.0, prev2 = 0.0;
-    for (int it = 1; it <= c.o.maxit; it++) {
-        iters = it;
-        if (c.implicit) implicit_field<FLAT>(c, v, vl, v2, W, E);
+    const double iscale0 = c.sg / (c.in.tau + D + c.sg * p_guess);
+    const int last = limit < c.o.maxit ? limit : c.o.maxit;
+    while (s.it < last) {
+        const int it = ++s.it;
+        if (c.implicit) implicit_field<FLAT>(c, s.v, s.vl, s.v2, s.W, E);
         double vn[3], Winv, num;
-        if (!fluid_step<FLAT>(c, E, p, vl, vn, v2, W, Winv, num)) return 0;
-        const double omv = 1.0 - v2;
-        const double f = g1 * num * omv * c.isg - p;
+        if (!fluid_step<FLAT>(c, E, s.p, s.vl, vn, s.v2, s.W, Winv, num)) return 0;
+        const double omv = 1.0 - s.v2;
+        const double f = g1 * num * omv * c.isg - s.p;
         double ratio;
         if (num > 0.0) {
             const double gn = Gam * num * Winv;
-            ratio = f * (D + gn) / (v2 * gg1 * num * Winv - D - gn);
+            ratio = f * (D + gn) / (s.v2 * gg1 * num * Winv - D - gn);
         } else {
             ratio = -f;
         }
-        double pn = p - ratio;
-        if (!(pn > 0.0)) pn = 0.1 * p;
-        const double dv = fmax(fabs(vn[0] - v[0]), fmax(fabs(vn[1] - v[1]), fabs(vn[2] - v[2])));
-        const double dp = pn - p;
-        p = pn;
-        v[0] = vn[0]; v[1] = vn[1]; v[2] = vn[2];
-        if (p_conv<FLAT>(c, dp, p) && dv <= c.o.tol) {
+        double pn = s.p - ratio;
+        if (!(pn > 0.0)) pn = 0.1 * s.p;
+        const double dv =
+            fmax(fabs(vn[0] - s.v[0]), fmax(fabs(vn[1] - s.v[1]), fabs(vn[2] - s.v[2])));
+        const double dp = pn - s.p;
+        s.p = pn;
+        s.v[0] = vn[0]; s.v[1] = vn[1]; s.v[2] = vn[2];
+        if (p_conv<FLAT>(c, dp, s.p) && dv <= c.o.tol) {
             rho_out = D * Winv * c.isg;
             return 1;
         }
         const double meas = dv + fabs(dp) * iscale0;
         if (!isfinite(meas)) return 0;
         // diverging: three successive growing changes above the noise
-        if (it >= 3 && meas > prev0 && prev0 > prev1 && prev1 > prev2 &&
+        if (it >= 3 && meas > s.prev0 && s.prev0 > s.prev1 && s.prev1 > s.prev2 &&
             meas > 1e3 * c.o.tol)
             return 0;
         // converging too slowly: more than 24 further iterations predicted
-        if (!allow_slow && it >= 6 && meas < prev0 && prev0 > 0.0) {
-            const double rate = meas / prev0;
+        if (!allow_slow && it >= 6 && meas < s.prev0 && s.prev0 > 0.0) {
+            const double rate = meas / s.prev0;
             if (rate > 0.0 && log(c.o.tol / meas) / log(rate) > 24.0) {
                 slow_stop = true;
                 return 0;
             }
         }
-        prev2 = prev1; prev1 = prev0; prev0 = meas;
+        s.prev2 = s.prev1; s.prev1 = s.prev0; s.prev0 = meas;
     }
-    return 0;
+    return s.it >= c.o.maxit ? 0 : -1;
+}
+
+// The paper's iteration from the guess, to its cap.  Returns 1 converged,
+// 0 gave up.
+template <bool FLAT>
+__device__ int paper_iteration(const RecCtx<FLAT> &c, double &p, double v[3], double E[3],
+                               double &rho_out, int &iters, bool allow_slow, bool &slow_stop)
+{
+    PaperState s;
+    slow_stop = false;
+    if (!paper_start<FLAT>(c, p, v, s)) {
+        iters = 0;
+        return 0;
+    }
+    const int r = paper_run<FLAT>(c, s, p, c.o.maxit, E, rho_out, allow_slow, slow_stop);
+    iters = s.it;
+    p = s.p;
+    v[0] = s.v[0]; v[1] = s.v[1]; v[2] = s.v[2];
+    return r == 1;
 }
 
 // residual of the joint system at x = (p, v_lower), scaled by the energy scale
@@ -467,7 +541,11 @@ __device__ int bracket_fallback(const RecCtx<FLAT> &c, double &p, double v[3], d
 // phases of recover(): everything inline, only the paper iteration (a cell it
 // does not converge is handed back as REC_DEFER for a later fallback pass),
 // or only the fallbacks (the deferred pass)
-enum { REC_ALL = 0, REC_PRIMARY = 1, REC_FALLBACK = 2 };
+// REC_FIRST: at most RecOpts::first_cap paper iterations; a point still
+// undecided then is handed back with its iterate in *ps, and a later pass
+// with REC_RESUME continues from exactly there (same arithmetic, same
+// decisions, same result as REC_ALL inline).
+enum { REC_ALL = 0, REC_PRIMARY = 1, REC_FALLBACK = 2, REC_FIRST = 3, REC_RESUME = 4 };
 enum { REC_DEFER = -1 };
 
 // Full pointwise recovery.  Writes the 14 primitives and the solved calE;
@@ -479,7 +557,8 @@ template <bool FLAT>
 __device__ int recover(const RecIn &in, const Met<double> &m, const RecOpts &o,
                        bool implicit, double cc, double guess_p, const double guess_v[3],
                        double Phi, double Psi, double Q, double prim[NPR],
-                       double Eout[3], int &iters, int phase = REC_ALL)
+                       double Eout[3], int &iters, int phase = REC_ALL,
+                       PaperState *ps = nullptr)
 {
     RecCtx<FLAT> c{in, m, o, implicit, implicit ? cc : 0.0, 1.0, 1.0, 0.0, {0, 0, 0}, 0.0};
     if (!FLAT) {
@@ -494,7 +573,47 @@ __device__ int recover(const RecIn &in, const Met<double> &m, const RecOpts &o,
     double rho = 0.0;
     int it1 = 0, it2 = 0, status;
     bool slow = false;
-    if (phase != REC_FALLBACK && paper_iteration<FLAT>(c, p, v, E, rho, it1, false, slow)) {
+    int first = -2;   // REC_FIRST / REC_RESUME outcome of the paper iteration
+    if (phase == REC_FIRST || phase == REC_RESUME) {
+        PaperState s;
+        if (phase == REC_FIRST) {
+            // undecided or given up: both go to the second pass
+            if (!paper_start<FLAT>(c, p, v, s)) {
+                s.it = 0;
+                s.p = p;
+                first = 0;
+            } else {
+                first = paper_run<FLAT>(c, s, guess_p, o.first_cap, E, rho, false, slow);
+            }
+            if (first != 1) {
+                s.outcome = first;
+                s.slow = slow ? 1 : 0;
+                *ps = s;
+                iters = s.it;
+                return REC_DEFER;
+            }
+        } else {
+            s = *ps;
+            if (s.outcome == 0) {
+                first = 0;
+                slow = s.slow != 0;
+            } else {
+                first = paper_run<FLAT>(c, s, guess_p, o.maxit, E, rho, false, slow);
+            }
+        }
+        it1 = s.it;
+        p = s.p;
+        v[0] = s.v[0]; v[1] = s.v[1]; v[2] = s.v[2];
+    }
+    // outcome of the paper iteration: 1 converged, 0 gave up
+    int paper;
+    if (first != -2)
+        paper = first;
+    else if (phase == REC_FALLBACK)
+        paper = 0;
+    else
+        paper = paper_iteration<FLAT>(c, p, v, E, rho, it1, false, slow) ? 1 : 0;
+    if (paper == 1) {
         status = 0;
     } else if (phase == REC_PRIMARY) {
         iters = it1;

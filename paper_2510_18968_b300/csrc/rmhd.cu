@@ -102,6 +102,14 @@ static int check_params(rmhd_t h, const rmhd_params *p)
         if (p->n[d] > 1 && p->n[d] < 3 && p->bc[d] == RMHD_BC_PERIODIC)
             return set_err(h, RMHD_EINVAL, "periodic direction %d needs n >= 3", d);
     }
+    {
+        // every padded field, and 14 of them together, must be indexable in
+        // 32 bits (kernel index arithmetic)
+        double cells = 1.0;
+        for (int d = 0; d < 3; d++) cells *= (double)(p->n[d] + (p->n[d] > 1 ? 7 : 1));
+        if (cells * 2.0 >= 2147483648.0)
+            return set_err(h, RMHD_EINVAL, "grid too large: %.0f padded cells", cells);
+    }
     if (p->recon < 0 || p->recon > 2) return set_err(h, RMHD_EINVAL, "recon %d unknown", p->recon);
     if (p->precision != RMHD_PREC_FP64 && p->precision != RMHD_PREC_MIXED)
         return set_err(h, RMHD_EINVAL, "precision %d unknown", p->precision);
@@ -128,6 +136,7 @@ static RecOpts rec_opts(const rmhd_params *p)
     o.p_atmo = p->K_atmo * pow(p->rho_atmo, p->gamma_eos);
     o.atmo_floor = p->rho_atmo * (1.0 + p->atmo_tol);
     o.maxit = p->c2p_maxit;
+    o.first_cap = p->c2p_maxit;   // first pass: the whole paper iteration
     return o;
 }
 
