@@ -80,6 +80,10 @@ typedef struct rmhd_params {
     int    c2p_maxit;   /* cap of the paper's recovery iterations (100)        */
     double c2p_wmax;    /* Lorentz-factor cap inside the recovery (100)        */
     int    qflux_mode;  /* RMHD_QFLUX_*                                        */
+    int    c2p_first_pass; /* paper iterations a cell may take in the stepping
+                           kernels' first recovery pass before it is listed
+                           for the second pass (resumed where it stopped);
+                           0 = the whole iteration (default)                 */
 } rmhd_params;
 
 typedef struct rmhd_s *rmhd_t;

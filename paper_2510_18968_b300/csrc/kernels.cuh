@@ -411,6 +411,155 @@ __global__ void __launch_bounds__(128) k_flux(const StepConst K, const T *__rest
     for (int f = 0; f < NCO; f++) F[f * S + cR] = acc[f];
 }
 
+// Reconstruction of cell c along D: its state at the face below (m) and
+// above (p) for the 14 primitives and, when J != nullptr, the current J^D.
+template <class T, int RC>
+__device__ __forceinline__ void cell_faces(const T *__restrict__ P, const T *__restrict__ Jc,
+                                           long long S, long long c, long long s, int D,
+                                           T m[NPR + 1], T p[NPR + 1])
+{
+#pragma unroll
+    for (int f = 0; f <= NPR; f++) {
+        if (f == NPR && !Jc) break;
+        const T *q = f < NPR ? P + f * S + c : Jc + D * S + c;
+        if (RC == RC_WENO5) {
+            const T a = q[-2 * s], b = q[-s], cc = q[0], d = q[s], e = q[2 * s];
+            p[f] = weno5(a, b, cc, d, e);
+            m[f] = weno5(e, d, cc, b, a);
+        } else {
+            const T a = q[-s], b = q[0], d = q[s];
+            const T h = T(0.5) * tvd_slope<T, RC>(a, b, d);
+            p[f] = b + h;
+            m[f] = b - h;
+        }
+    }
+}
+
+// Face fluxes in direction D for a run of M consecutive faces per thread:
+// every cell is reconstructed once and its upper face state is carried to
+// the next face in registers (the per-face kernel above reconstructs each
+// cell twice).  Face f lies between cells f-1 and f along D and is stored at
+// cell f.  Same arithmetic per face as k_flux.
+template <class T, bool FLAT, int RC, int D, int M>
+__global__ void __launch_bounds__(128) k_flux_run(const StepConst K, const T *__restrict__ P,
+                                                  const T *__restrict__ Jc,
+                                                  const double *__restrict__ met,
+                                                  const double *__restrict__ sig, T *F)
+{
+    const Grid &G = K.G;
+    const unsigned nrun = (unsigned)((G.n[D] + 1 + M - 1) / M);
+    // thread -> (run along D, the two other coordinates), x fastest
+    const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned e0, e1, run;
+    const unsigned n0 = D == 0 ? nrun : (unsigned)G.n[0];
+    const unsigned n1 = D == 1 ? nrun : (unsigned)G.n[1];
+    const unsigned n2 = D == 2 ? nrun : (unsigned)G.n[2];
+    if (t >= n0 * n1 * n2) return;
+    const unsigned q0 = t / n0;
+    const unsigned i0 = t - q0 * n0;
+    const unsigned i2 = q0 / n1;
+    const unsigned i1 = q0 - i2 * n1;
+    int ijk[3] = {(int)i0, (int)i1, (int)i2};
+    run = (unsigned)ijk[D];
+    (void)e0; (void)e1;
+    const int f0 = (int)run * M;
+    const int fend = min(f0 + M, G.n[D] + 1);
+    ijk[D] = f0 - 1;
+    const long long s = dstride(G, D);
+    const long long S = G.S;
+    long long c = cell_at(G, ijk[0], ijk[1], ijk[2]);   // cell f0 - 1
+    const bool useJ = K.qflux == 0;
+    const T *Jp = useJ ? Jc : nullptr;
+    T mL[NPR + 1], pL[NPR + 1];                          // of the cell below the face
+    cell_faces<T, RC>(P, Jp, S, c, s, D, mL, pL);
+    const T gfac = (T)K.gfac;
+    for (int f = f0; f < fend; f++) {
+        const long long cL = c, cR = c + s;
+        T mR[NPR + 1], pR[NPR + 1];
+        cell_faces<T, RC>(P, Jp, S, cR, s, D, mR, pR);
+        // face state arrays: left = upper state of cL, right = lower state of cR
+        T sL[NPR], sR[NPR];
+#pragma unroll
+        for (int k = 0; k < NPR; k++) {
+            sL[k] = pL[k];
+            sR[k] = mR[k];
+        }
+        T JL = useJ ? pL[NPR] : T(0), JR = useJ ? mR[NPR] : T(0);
+        Met<T> m;
+        if (FLAT) {
+            m.alpha = T(1);
+            m.beta[0] = m.beta[1] = m.beta[2] = T(0);
+            m.g[0] = m.g[3] = m.g[5] = T(1);
+            m.g[1] = m.g[2] = m.g[4] = T(0);
+            m.gi[0] = m.gi[3] = m.gi[5] = T(1);
+            m.gi[1] = m.gi[2] = m.gi[4] = T(0);
+            m.sg = m.isg = T(1);
+        } else {
+            m.alpha = (T)(0.5 * (met[M_ALPHA * S + cL] + met[M_ALPHA * S + cR]));
+            for (int a = 0; a < 3; a++)
+                m.beta[a] = (T)(0.5 * (met[(M_BETA + a) * S + cL] + met[(M_BETA + a) * S + cR]));
+            for (int a = 0; a < 6; a++)
+                m.g[a] = (T)(0.5 * (met[(M_GAMMA + a) * S + cL] + met[(M_GAMMA + a) * S + cR]));
+            met_complete(m);
+        }
+#pragma unroll
+        for (int sd = 0; sd < 2; sd++) {
+            T *q = sd == 0 ? sL : sR;
+            T v[3] = {q[PR_VX], q[PR_VY], q[PR_VZ]}, vl[3];
+            lower<T, FLAT>(m, v, vl);
+            if (!(q[PR_RHO] > T(0)) || !(q[PR_P] > T(0)) || !(dot3(v, vl) < T(1))) {
+                const long long cc = sd == 0 ? cL : cR;
+#pragma unroll
+                for (int k = 0; k < NPR; k++) q[k] = P[k * S + cc];
+                if (useJ) {
+                    if (sd == 0) JL = Jc[D * S + cc];
+                    else JR = Jc[D * S + cc];
+                }
+            }
+        }
+        T sigma = (T)K.sigma0;
+        if (K.sigma_model == 1) {
+            sigma = (T)(K.sigma0 * 0.5 * (sig[cL] + sig[cR]));
+        } else if (K.sigma_model >= 2) {
+            double sgm = 0.0;
+            for (int sd = 0; sd < 2; sd++) {
+                const long long cc = sd == 0 ? cL : cR;
+                Met<double> mc;
+                load_metric<FLAT>(met, S, cc, mc);
+                double v[3] = {(double)P[PR_VX * S + cc], (double)P[PR_VY * S + cc],
+                               (double)P[PR_VZ * S + cc]}, vl[3];
+                lower<double, FLAT>(mc, v, vl);
+                double Dc = mc.sg * (double)P[PR_RHO * S + cc] / sqrt(1.0 - dot3(v, vl));
+                sgm += 0.5 * sigma_cell(K, sig, cc, Dc);
+            }
+            sigma = (T)sgm;
+        }
+        T cFL, cFR, cUU;
+        if (FLAT) {
+            cFL = T(0.5); cFR = T(0.5); cUU = T(-0.5);
+        } else {
+            const T sq = sqrt(m.gi[sym(D, D)]);
+            const T bs = m.beta[D] / m.alpha;
+            T ap = sq - bs, am = -sq - bs;
+            ap = ap > T(0) ? ap : T(0);
+            am = am < T(0) ? am : T(0);
+            const T inv = T(1) / (ap - am);
+            cFL = ap * inv; cFR = -am * inv; cUU = ap * am * inv;
+        }
+        T acc[NCO];
+#pragma unroll
+        for (int k = 0; k < NCO; k++) acc[k] = T(0);
+        flux_accumulate<T, FLAT, D>(sL, m, sigma, gfac, useJ, JL, cFL, -cUU, acc);
+        flux_accumulate<T, FLAT, D>(sR, m, sigma, gfac, useJ, JR, cFR, cUU, acc);
+#pragma unroll
+        for (int k = 0; k < NCO; k++) F[k * S + cR] = acc[k];
+        // slide: the cell above becomes the cell below
+#pragma unroll
+        for (int k = 0; k <= NPR; k++) pL[k] = pR[k];
+        c = cR;
+    }
+}
+
 // Source vector of Eq. GRRMHD_flux_form without the stiff part of -alpha J
 // (Sec. III.A split), at a cell with primitives pr.  Metric derivatives:
 // second-order central differences of the cell-centred metric.
@@ -624,7 +773,7 @@ __device__ __forceinline__ void stage1_write(const StepConst &K, long long c, co
 {
     const long long S = K.G.S;
     prim_write(K, c, pr, P, Gs);
-    const double ig = K.igimex, iad = K.idt / alpha;
+    const double ig = K.igimex, iad = alpha == 1.0 ? K.idt : K.idt / alpha;
     for (int a = 0; a < 3; a++) {
         const double r = (E[a] - u[CO_EX + a]) * ig;
         dR1[a * S + c] = r;
@@ -641,7 +790,7 @@ __device__ __forceinline__ void stage2_write(const StepConst &K, long long c, co
 {
     const long long S = K.G.S;
     prim_write(K, c, p2, P2, G2);
-    const double ig = K.igimex, iad = K.idt / alpha;
+    const double ig = K.igimex, iad = alpha == 1.0 ? K.idt : K.idt / alpha;
     for (int a = 0; a < 3; a++) {
         const double r2 = (E[a] - us[CO_EX + a]) * ig;
         V[(CO_EX + a) * S + c] += 0.5 * (dR1[a * S + c] + r2);

@@ -37,6 +37,11 @@ struct RecIn {
     double D, S[3], tau, cB[3], cE0[3];   // cE0: calE* (implicit) or calE (fixed)
 };
 
+template <bool FLAT> struct RecCtx;
+// sqrt(gamma) and its inverse, folded to 1 on a flat metric
+template <bool FLAT> __device__ __forceinline__ double sgv(const RecCtx<FLAT> &c);
+template <bool FLAT> __device__ __forceinline__ double isgv(const RecCtx<FLAT> &c);
+
 template <bool FLAT> struct RecCtx {
     const RecIn &in;
     const Met<double> &m;
@@ -47,6 +52,15 @@ template <bool FLAT> struct RecCtx {
     double cBl[3];      // lowered calB
     double B2;          // calB . calB_lower
 };
+
+template <bool FLAT> __device__ __forceinline__ double sgv(const RecCtx<FLAT> &c)
+{
+    return FLAT ? 1.0 : c.sg;
+}
+template <bool FLAT> __device__ __forceinline__ double isgv(const RecCtx<FLAT> &c)
+{
+    return FLAT ? 1.0 : c.isg;
+}
 
 // closed-form implicit calE at fixed contravariant v (see file comment)
 template <bool FLAT>
@@ -70,7 +84,7 @@ __device__ __forceinline__ void implicit_field(const RecCtx<FLAT> &c, const doub
 template <bool FLAT>
 __device__ __forceinline__ bool p_conv(const RecCtx<FLAT> &c, double dp, double p)
 {
-    return fabs(dp) * c.sg <= c.o.tol * (c.in.tau + c.in.D + c.sg * p);
+    return fabs(dp) * sgv(c) <= c.o.tol * (c.in.tau + c.in.D + sgv(c) * p);
 }
 
 // Step (iii) at (p, calE), division-lean form used by the paper iteration:
@@ -83,10 +97,10 @@ __device__ __forceinline__ bool fluid_step(const RecCtx<FLAT> &c, const double E
 {
     double El[3];
     lower<double, FLAT>(c.m, E, El);
-    const double EM = 0.5 * (dot3(E, El) + c.B2) * c.isg;
+    const double EM = 0.5 * (dot3(E, El) + c.B2) * isgv(c);
     double P[3];
     cross3(E, c.in.cB, P);
-    const double den = c.in.tau + c.in.D + c.sg * p - EM;
+    const double den = c.in.tau + c.in.D + sgv(c) * p - EM;
     const double iden = 1.0 / den;
 #pragma unroll
     for (int i = 0; i < 3; i++) vl[i] = (c.in.S[i] - P[i]) * iden;
@@ -96,7 +110,7 @@ __device__ __forceinline__ bool fluid_step(const RecCtx<FLAT> &c, const double E
     const double omv = 1.0 - v2;
     W = rsqrt(omv);
     Winv = omv * W;
-    num = c.in.tau - c.in.D * (W - 1.0) - c.sg * p * (v2 * W * W) - EM;
+    num = c.in.tau - c.in.D * (W - 1.0) - sgv(c) * p * (v2 * W * W) - EM;
     return true;
 }
 
@@ -150,7 +164,9 @@ __device__ __forceinline__ bool paper_start(const RecCtx<FLAT> &c, double p, con
     lower<double, FLAT>(c.m, s.v, s.vl);
     s.v2 = dot3(s.v, s.vl);
     if (!(s.v2 < c.o.v2max)) return false;
-    s.W = rsqrt(1.0 - s.v2);
+    // the first implicit solve needs W of the guess; with calE fixed the
+    // first use of W is after fluid_step has set it
+    s.W = c.implicit ? rsqrt(1.0 - s.v2) : 0.0;
     s.prev0 = s.prev1 = s.prev2 = 0.0;
     s.outcome = -1;
     s.slow = 0;
@@ -171,7 +187,9 @@ __device__ int paper_run(const RecCtx<FLAT> &c, PaperState &s, double p_guess, i
     slow_stop = false;
     const double Gam = c.o.Gam, g1 = Gam - 1.0, gg1 = Gam * (Gam - 1.0);
     const double D = c.in.D;
-    const double iscale0 = c.sg / (c.in.tau + D + c.sg * p_guess);
+    // scale of the change measure (energy at the guess), needed only from
+    // the second iteration on
+    double iscale0 = 0.0;
     const int last = limit < c.o.maxit ? limit : c.o.maxit;
     while (s.it < last) {
         const int it = ++s.it;
@@ -179,7 +197,7 @@ __device__ int paper_run(const RecCtx<FLAT> &c, PaperState &s, double p_guess, i
         double vn[3], Winv, num;
         if (!fluid_step<FLAT>(c, E, s.p, s.vl, vn, s.v2, s.W, Winv, num)) return 0;
         const double omv = 1.0 - s.v2;
-        const double f = g1 * num * omv * c.isg - s.p;
+        const double f = g1 * num * omv * isgv(c) - s.p;
         double ratio;
         if (num > 0.0) {
             const double gn = Gam * num * Winv;
@@ -195,9 +213,10 @@ __device__ int paper_run(const RecCtx<FLAT> &c, PaperState &s, double p_guess, i
         s.p = pn;
         s.v[0] = vn[0]; s.v[1] = vn[1]; s.v[2] = vn[2];
         if (p_conv<FLAT>(c, dp, s.p) && dv <= c.o.tol) {
-            rho_out = D * Winv * c.isg;
+            rho_out = D * Winv * isgv(c);
             return 1;
         }
+        if (iscale0 == 0.0) iscale0 = sgv(c) / (c.in.tau + D + sgv(c) * p_guess);
         const double meas = dv + fabs(dp) * iscale0;
         if (!isfinite(meas)) return 0;
         // diverging: three successive growing changes above the noise

@@ -121,6 +121,7 @@ static int check_params(rmhd_t h, const rmhd_params *p)
         return set_err(h, RMHD_EINVAL, "atmosphere parameters out of range");
     if (!(p->c2p_tol > 0.0) || p->c2p_maxit < 1 || !(p->c2p_wmax > 1.0))
         return set_err(h, RMHD_EINVAL, "recovery parameters out of range");
+    if (p->c2p_first_pass < 0) return set_err(h, RMHD_EINVAL, "c2p_first_pass must be >= 0");
     if (p->qflux_mode != RMHD_QFLUX_STAGE && p->qflux_mode != RMHD_QFLUX_FACE_OHM)
         return set_err(h, RMHD_EINVAL, "qflux_mode %d unknown", p->qflux_mode);
     return RMHD_OK;
@@ -136,7 +137,7 @@ static RecOpts rec_opts(const rmhd_params *p)
     o.p_atmo = p->K_atmo * pow(p->rho_atmo, p->gamma_eos);
     o.atmo_floor = p->rho_atmo * (1.0 + p->atmo_tol);
     o.maxit = p->c2p_maxit;
-    o.first_cap = p->c2p_maxit;   // first pass: the whole paper iteration
+    o.first_cap = p->c2p_first_pass > 0 ? p->c2p_first_pass : p->c2p_maxit;
     return o;
 }
 
@@ -182,23 +183,35 @@ template <class T> static void launch_ghosts(rmhd_t h, T *buf, int nf)
     k_ghosts<T><<<grid, TPB, 0, h->st>>>(h->K, buf, nf, 0);
 }
 
+// faces per thread of the run flux kernel (FP64 path)
+const int FLUX_RUN = 8;
+
+// FP64: the run kernel reconstructs each cell once (ALU-bound path); FP32:
+// one thread per face keeps more loads in flight (latency-bound path)
 template <class T, bool FLAT, int RC>
 static void launch_flux_rc(rmhd_t h, const T *P, const T *J)
 {
     const Grid &G = h->K.G;
     const Buffers &b = h->b;
-    T *F0 = (T *)b.F[0], *F1 = (T *)b.F[1], *F2 = (T *)b.F[2];
+    T *Fd[3] = {(T *)b.F[0], (T *)b.F[1], (T *)b.F[2]};
+    const int M = FLUX_RUN;
+    const bool run = sizeof(T) == sizeof(double);
+    auto nthreads = [&](int d) {
+        long long n = 1;
+        for (int a = 0; a < 3; a++) n *= a == d ? (run ? (G.n[a] + 1 + M - 1) / M : G.n[a] + 1) : G.n[a];
+        return n;
+    };
     if (G.g[0]) {
-        long long n = (long long)(G.n[0] + 1) * G.n[1] * G.n[2];
-        k_flux<T, FLAT, RC, 0><<<nblk(n), TPB, 0, h->st>>>(h->K, P, J, b.met, b.sig, F0);
+        if (run) k_flux_run<T, FLAT, RC, 0, M><<<nblk(nthreads(0)), TPB, 0, h->st>>>(h->K, P, J, b.met, b.sig, Fd[0]);
+        else k_flux<T, FLAT, RC, 0><<<nblk(nthreads(0)), TPB, 0, h->st>>>(h->K, P, J, b.met, b.sig, Fd[0]);
     }
     if (G.g[1]) {
-        long long n = (long long)G.n[0] * (G.n[1] + 1) * G.n[2];
-        k_flux<T, FLAT, RC, 1><<<nblk(n), TPB, 0, h->st>>>(h->K, P, J, b.met, b.sig, F1);
+        if (run) k_flux_run<T, FLAT, RC, 1, M><<<nblk(nthreads(1)), TPB, 0, h->st>>>(h->K, P, J, b.met, b.sig, Fd[1]);
+        else k_flux<T, FLAT, RC, 1><<<nblk(nthreads(1)), TPB, 0, h->st>>>(h->K, P, J, b.met, b.sig, Fd[1]);
     }
     if (G.g[2]) {
-        long long n = (long long)G.n[0] * G.n[1] * (G.n[2] + 1);
-        k_flux<T, FLAT, RC, 2><<<nblk(n), TPB, 0, h->st>>>(h->K, P, J, b.met, b.sig, F2);
+        if (run) k_flux_run<T, FLAT, RC, 2, M><<<nblk(nthreads(2)), TPB, 0, h->st>>>(h->K, P, J, b.met, b.sig, Fd[2]);
+        else k_flux<T, FLAT, RC, 2><<<nblk(nthreads(2)), TPB, 0, h->st>>>(h->K, P, J, b.met, b.sig, Fd[2]);
     }
 }
 
