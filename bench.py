@@ -120,6 +120,16 @@ FP64_FLOPS = {  # per cell, (mixed path, FP64 path)
 FLUX_FLOPS_PER_FACE = 650
 FLUX_FIELDS = 15 + 14
 
+# DRAM bytes per cell of one launch (dram__bytes_read.sum +
+# dram__bytes_write.sum from ncu on a 128^3 launch of this workload, scaled
+# by the cell count; traffic grows with the cells).  Valid for the kernels
+# as they are; re-measure after changing one.
+TRAFFIC_PER_CELL = {
+    ("stage2_rhs_recovery", "mixed"): (840.464640e6 + 438.733568e6) / 128 ** 3,
+    ("flux_stage2", "mixed"): (140.606208e6 + 78.074880e6) / 128 ** 3,
+    ("flux_stage2", "fp64"): (981.657088e6 + 511.811328e6) / 128 ** 3,
+}
+
 
 def run_ours(args, rank, world, local):
     import torch
@@ -209,13 +219,15 @@ def kernel_rooflines(wl, res, prec, steps):
     return out
 
 
-def roofline(wl, res, prec, steps, traffic=None):
+def roofline(wl, res, prec, steps):
     ks = kernel_rooflines(wl, res, prec, steps)
     g = res["groups"]
     name = max((k for k in g if k != "ghost_fill"), key=g.get)
     r = dict(ks[name])
     r["kernel"] = name
-    r["traffic"] = None if traffic is None else traffic.get((name, prec))
+    per_cell = TRAFFIC_PER_CELL.get((name, prec))
+    r["traffic"] = None if per_cell is None else per_cell * wl.ncells
+    r["traffic_unit"] = "bytes per launch (ncu, 128^3 launch scaled by cells)"
     return r, ks
 
 
