@@ -169,7 +169,19 @@ CASES = {
     "cyl_blast_hr": lambda: W.cyl_blast(n=64, nz=1, L=1.5),
     "lane_emden": lambda: W.lane_emden_star(n=20),
     "current_sheet": lambda: W.current_sheet(n=120),
+    # density-dependent conductivity (Eqs. sigma_evol, dynamo_sigma)
+    "cyl_blast_sigma_powD": lambda: _with(W.cyl_blast(n=40, nz=4), sigma_model=2,
+                                          sigma0=3e3, sigma_exp=0.5),
+    "lane_emden_sigma_atmo": lambda: _with(W.lane_emden_star(n=20), sigma_model=3,
+                                           D_atmo=1e-5),
 }
+
+
+def _with(wl, **params):
+    wl.params.update(params)
+    if params.get("sigma_model", 1) != 1:
+        wl.sigma_profile = None
+    return wl
 
 
 @pytest.mark.parametrize("name", list(CASES))
@@ -189,7 +201,8 @@ def test_one_step_matches_oracle(name):
 # everywhere for its first 20 steps on this machine, the star for 10.
 @pytest.mark.parametrize("name,nsteps", [("brio_wu", 100), ("alfven_s1e6", 100),
                                          ("current_sheet", 100), ("cyl_blast_hr", 20),
-                                         ("lane_emden", 10)])
+                                         ("lane_emden", 10), ("cyl_blast_sigma_powD", 10),
+                                         ("lane_emden_sigma_atmo", 10)])
 def test_many_steps_match_oracle(name, nsteps):
     wl = CASES[name]()
     _, so, prim_o, cons_o = run_oracle(wl, nsteps)

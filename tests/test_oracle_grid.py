@@ -67,6 +67,65 @@ def test_imex_stages_reproduce_closed_form_relaxation(z):
     assert (prim[1] > 1.0).all() or z < 1e-2      # Ohmic heating
 
 
+@pytest.mark.parametrize("model,extra,factor", [
+    (2, dict(sigma_exp=0.5), 2.0),                 # sigma0 D^(1/2), D = 4
+    (2, dict(sigma_exp=-1.0), 0.25),               # sigma0 / D
+    (3, dict(D_atmo=1.0), 0.5625),                 # sigma0 (1 - 1/4)^2
+    (3, dict(D_atmo=8.0), 0.0),                    # D below D_atmo: no conduction
+])
+def test_density_dependent_conductivity_closed_form(model, extra, factor):
+    """Conductivity models of Eqs. sigma_evol and dynamo_sigma on a uniform
+    state at rest with D = rho = 4: the stiff relaxation of calE is the
+    closed form above with sigma = factor * sigma0."""
+    prim0 = np.zeros(14)
+    prim0[0], prim0[1] = 4.0, 1.0
+    prim0[5:8] = [0.06, 0.08, 0.0]
+    prim0[8:11] = [0.3, 0.4, 0.0]
+    sigma0, dt = 40.0, 0.05
+    wl = _uniform(4, prim0, sigma=sigma0)
+    wl.params.update(sigma_model=model, **extra)
+    m, prim, cons = _init(wl)
+    c0 = cons.copy()
+    st, _ = oracle.step(wl.params, m, cons, prim, dt, 1)
+    assert st == 0
+    R = imex_amplification(factor * sigma0 * dt)
+    assert np.allclose(cons[8:11], R * c0[8:11], rtol=1e-13, atol=1e-16)
+
+
+@pytest.mark.parametrize("model,extra", [(2, dict(sigma_exp=0.7)), (3, dict(D_atmo=1.3))])
+def test_density_dependent_conductivity_uses_conserved_density(model, extra):
+    """A uniform flow keeps D = rho W uniform for the whole step, so the
+    density-dependent models must equal the uniform model with sigma0
+    replaced by its value at that D (computed here from rho and v); rho in
+    place of D would change sigma by W^0.7 or through D_atmo/D."""
+    prim0 = np.zeros(14)
+    prim0[0], prim0[1] = 2.0, 0.5
+    prim0[2:5] = [0.3, -0.2, 0.4]
+    prim0[5:8] = [0.05, 0.02, -0.03]
+    prim0[8:11] = [0.2, 0.3, -0.1]
+    W_lor = 1.0 / math.sqrt(1.0 - float(np.dot(prim0[2:5], prim0[2:5])))
+    D = prim0[0] * W_lor
+    sigma0, dt = 30.0, 0.05
+    if model == 2:
+        sig = sigma0 * D ** extra["sigma_exp"]
+    else:
+        sig = sigma0 * (1.0 - extra["D_atmo"] / D) ** 2
+    out = []
+    for params in (dict(sigma_model=model, **extra), dict(sigma_model=0, sigma0=sig)):
+        wl = _uniform(4, prim0, sigma=sigma0)
+        wl.params.update(params)
+        m, prim, cons = _init(wl)
+        st, _ = oracle.step(wl.params, m, cons, prim, dt, 1)
+        assert st == 0
+        out.append(cons.copy())
+    assert np.allclose(out[0], out[1], rtol=1e-12, atol=1e-15)
+    # and sigma matters here: the unscaled uniform model differs
+    wl = _uniform(4, prim0, sigma=sigma0)
+    m, prim, cons = _init(wl)
+    oracle.step(wl.params, m, cons, prim, dt, 1)
+    assert not np.allclose(out[0][8:11], cons[8:11], rtol=1e-6)
+
+
 def test_imex_amplification_is_second_order_and_l_stable():
     for z in (1e-2, 5e-3):
         assert abs(imex_amplification(z) - math.exp(-z)) < 0.1 * z ** 3
