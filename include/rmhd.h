@@ -58,7 +58,11 @@ enum {
 enum {
     RMHD_QFLUX_STAGE = 0,    /* charge-flux current = cell-centred current of the
                                 implicit stage, reconstructed to the faces     */
-    RMHD_QFLUX_FACE_OHM = 1  /* Ohm's law at the reconstructed face states      */
+    RMHD_QFLUX_FACE_OHM = 1, /* Ohm's law at the reconstructed face states      */
+    RMHD_QFLUX_GAUSS = 2     /* charge not evolved: after every recovery
+                                calQ = d_i calE^i by 2nd-order central
+                                differences (Gauss's law, the variant of
+                                Sec. IV.E); q = calQ / sqrt(gamma)            */
 };
 
 typedef struct rmhd_params {

@@ -1290,6 +1290,27 @@ static void stage_current(const grid *G, const double *U, const double *prim,
                            - dR[a * N + c] / (G->alpha[c] * dt);
 }
 
+/* Charge from Gauss's law instead of its evolution equation (the variant
+ * the paper tests for the magnetised star, Sec. IV.E): Q = sqrt(gamma) q =
+ * d_i calE^i, by 2nd-order central differences of the densitised field with
+ * the grid's boundary condition; q = Q / sqrt(gamma). */
+static void gauss_charge(const grid *G, double *cons, double *prim)
+{
+    long N = G->N;
+    for (int k = 0; k < G->nz; k++)
+        for (int j = 0; j < G->ny; j++)
+            for (int i = 0; i < G->nx; i++) {
+                long c = cidx(G, i, j, k);
+                double Q = 0.0;
+                for (int d = 0; d < 3; d++)
+                    Q += dcell(G, &cons[(C_EX + d) * N], d, i, j, k);
+                metric_pt m;
+                cell_metric(G, c, &m);
+                cons[C_Q * N + c] = Q;
+                prim[P_Q * N + c] = Q / m.sg;
+            }
+}
+
 /* One IMEX-SSP2(2,2,2) step, literally Eqs. (U^(1), U^(2), IMEX3):
  *   U1 = U^n + gamma dt R[U1]
  *   U2 = U^n + dt F[U1] + dt ((1-2gamma) R[U1] + gamma R[U2])
@@ -1315,13 +1336,17 @@ int orc_step(const orc_params *P, const double *alpha, const double *beta,
     double *dR2 = (double *)malloc(sizeof(double) * 3 * N);
     double *Jc = (double *)malloc(sizeof(double) * 3 * N);
     double *Es2 = (double *)malloc(sizeof(double) * 3 * N);
-    const double *Jarg = P->qflux_mode == 0 ? Jc : NULL;
+    /* mode 2 (Gauss's law) overwrites Q after every recovery, so its charge
+     * flux row is irrelevant; it is formed as in mode 0 */
+    const double *Jarg = P->qflux_mode != 1 ? Jc : NULL;
+    const int gauss = P->qflux_mode == 2;
     int status = 0;
     for (int s = 0; s < 8; s++) stats[s] = 0;
     for (int step = 0; step < nsteps; step++) {
         /* stage 1: purely implicit */
         memcpy(U1, cons, sizeof(double) * 14 * N);
         c2p_grid(&G, U1, prim, W1, 1, g * dt, stats, 0);
+        if (gauss) gauss_charge(&G, U1, W1);
         for (int a = 0; a < 3; a++)
             for (long c = 0; c < N; c++)
                 dR1[a * N + c] = (U1[(C_EX + a) * N + c] - cons[(C_EX + a) * N + c]) / g;
@@ -1335,6 +1360,7 @@ int orc_step(const orc_params *P, const double *alpha, const double *beta,
         for (int a = 0; a < 3; a++)   /* keep calE* of stage 2 */
             for (long c = 0; c < N; c++) Es2[a * N + c] = U2[(C_EX + a) * N + c];
         c2p_grid(&G, U2, W1, W2, 1, g * dt, stats, 1);
+        if (gauss) gauss_charge(&G, U2, W2);
         for (int a = 0; a < 3; a++)
             for (long c = 0; c < N; c++)
                 dR2[a * N + c] = (U2[(C_EX + a) * N + c] - Es2[a * N + c]) / g;
@@ -1349,6 +1375,7 @@ int orc_step(const orc_params *P, const double *alpha, const double *beta,
             if (!isfinite(cons[a])) { status = -5; stats[6] = 1; }
         /* recovery of U^{n+1} with calE fixed */
         c2p_grid(&G, cons, W2, prim, 0, 0.0, stats, 2);
+        if (gauss) gauss_charge(&G, cons, prim);
         if (status) break;
     }
     free(U1); free(U2); free(W1); free(W2); free(F1); free(F2);

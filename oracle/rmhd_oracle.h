@@ -42,7 +42,9 @@ typedef struct {
     double c2p_wmax;
     int    qflux_mode;    /* current in the charge flux: 0 the cell-centred
                              current of the implicit stage, reconstructed;
-                             1 Ohm's law at the reconstructed face states    */
+                             1 Ohm's law at the reconstructed face states;
+                             2 no evolved charge: Q = d_i calE^i (Gauss's
+                             law) after every recovery                      */
 } orc_params;
 
 /* pointwise pieces (exported for the pin tests) */

@@ -46,7 +46,7 @@ struct StepConst {
     double kappa;
     int sigma_model;
     double sigma0, sigma_exp, D_atmo;
-    int qflux;            // 0 stage current, 1 Ohm's law at faces
+    int qflux;            // 0 stage current, 1 Ohm's law at faces, 2 Gauss's law
     RecOpts ro;
 };
 
@@ -198,6 +198,47 @@ template <class T> __global__ void k_ghosts(const StepConst K, T *buf, int nf, i
     for (int f = 0; f < nf; f++) buf[f * G.S + dc] = buf[f * G.S + sc];
 }
 
+// Charge from Gauss's law (RMHD_QFLUX_GAUSS, the variant of Sec. IV.E):
+// calQ = d_i (sqrt(gamma) E^i) by 2nd-order central differences over the
+// stage primitives, whose ghosts hold the boundary condition; q = calQ /
+// sqrt(gamma) into P, and calQ into U when U is given (end of the step).
+template <bool FLAT, class T>
+__global__ void __launch_bounds__(128) k_gauss(const StepConst K, T *P,
+                                               const double *__restrict__ met, double *U)
+{
+    const Grid &G = K.G;
+    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= G.N) return;
+    int i, j, k;
+    interior_coords(G, t, i, j, k);
+    const long long c = cell_at(G, i, j, k);
+    const long long stride[3] = {1, G.px, G.pxy};
+    double Q = 0.0;
+    for (int d = 0; d < 3; d++) {
+        if (!G.g[d]) continue;
+        const long long cp = c + stride[d], cm = c - stride[d];
+        double sp = 1.0, sm = 1.0;
+        if (!FLAT) {
+            Met<double> mp, mm;
+            load_metric<false>(met, G.S, cp, mp);
+            load_metric<false>(met, G.S, cm, mm);
+            sp = mp.sg;
+            sm = mm.sg;
+        }
+        const double ep = sp * (double)P[(PR_EX + d) * G.S + cp];
+        const double em = sm * (double)P[(PR_EX + d) * G.S + cm];
+        Q += (ep - em) * (0.5 * G.idx[d]);
+    }
+    double sg = 1.0;
+    if (!FLAT) {
+        Met<double> m;
+        load_metric<false>(met, G.S, c, m);
+        sg = m.sg;
+    }
+    P[PR_Q * G.S + c] = (T)(Q / sg);
+    if (U) U[CO_Q * G.S + c] = Q;
+}
+
 // interior FP64 primitives -> padded primitives in T and the FP64 guess G
 template <class T>
 __global__ void k_scatter_prims(const StepConst K, const double *__restrict__ src, T *P,
@@ -284,7 +325,7 @@ __global__ void k_check_finite(long long n, const double *__restrict__ a, int *b
 
 // Face flux in direction D for the face on the low side of cell (i,j,k)
 // (between cells i-1 and i along D): reconstruct the 14 primitives (and the
-// stage current J^D when K.qflux == 0), fall back to first order on an
+// stage current J^D unless K.qflux == 1), fall back to first order on an
 // unphysical side, mean face metric and conductivity, HLLE (Sec. III).
 template <class T, bool FLAT, int RC, int D>
 __global__ void __launch_bounds__(128) k_flux(const StepConst K, const T *__restrict__ P,
@@ -322,7 +363,7 @@ __global__ void __launch_bounds__(128) k_flux(const StepConst K, const T *__rest
         reconstruct<T, RC>(st, pL[f], pR[f]);
     }
     T JL = T(0), JR = T(0);
-    const bool useJ = K.qflux == 0;
+    const bool useJ = K.qflux != 1;   // mode 2: Q row overwritten later
     if (useJ) {
         const T *q = Jc + D * S + cL;
         T st[6];
@@ -468,7 +509,7 @@ __global__ void __launch_bounds__(128) k_flux_run(const StepConst K, const T *__
     const long long s = dstride(G, D);
     const long long S = G.S;
     long long c = cell_at(G, ijk[0], ijk[1], ijk[2]);   // cell f0 - 1
-    const bool useJ = K.qflux == 0;
+    const bool useJ = K.qflux != 1;   // mode 2: Q row overwritten later
     const T *Jp = useJ ? Jc : nullptr;
     T mL[NPR + 1], pL[NPR + 1];                          // of the cell below the face
     cell_faces<T, RC>(P, Jp, S, c, s, D, mL, pL);

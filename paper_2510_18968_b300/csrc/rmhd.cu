@@ -122,7 +122,8 @@ static int check_params(rmhd_t h, const rmhd_params *p)
     if (!(p->c2p_tol > 0.0) || p->c2p_maxit < 1 || !(p->c2p_wmax > 1.0))
         return set_err(h, RMHD_EINVAL, "recovery parameters out of range");
     if (p->c2p_first_pass < 0) return set_err(h, RMHD_EINVAL, "c2p_first_pass must be >= 0");
-    if (p->qflux_mode != RMHD_QFLUX_STAGE && p->qflux_mode != RMHD_QFLUX_FACE_OHM)
+    if (p->qflux_mode != RMHD_QFLUX_STAGE && p->qflux_mode != RMHD_QFLUX_FACE_OHM &&
+        p->qflux_mode != RMHD_QFLUX_GAUSS)
         return set_err(h, RMHD_EINVAL, "qflux_mode %d unknown", p->qflux_mode);
     return RMHD_OK;
 }
@@ -240,6 +241,13 @@ static unsigned deferred_blocks(rmhd_t h)
     return (unsigned)(want < 148 * 8 ? (want > 0 ? want : 1) : 148 * 8);
 }
 
+// Gauss's-law charge of a stage (interior), then the ghosts of q
+template <bool FLAT, class T> static void gauss_charge(rmhd_t h, T *P, double *U)
+{
+    k_gauss<FLAT, T><<<nblk(h->K.G.N), TPB, 0, h->st>>>(h->K, P, h->b.met, U);
+    launch_ghosts(h, P + (size_t)PR_Q * h->K.G.S, 1);
+}
+
 // ev (optional): 9 events recorded between the kernel groups of the step
 template <bool FLAT, class T> static void enqueue_step_t(rmhd_t h, cudaEvent_t *ev)
 {
@@ -261,7 +269,8 @@ template <bool FLAT, class T> static void enqueue_step_t(rmhd_t h, cudaEvent_t *
                                                        b.stats);
     mark(1);
     launch_ghosts(h, PA, NPR);
-    if (K.qflux == 0) launch_ghosts(h, J1, 3);
+    if (K.qflux == RMHD_QFLUX_GAUSS) gauss_charge<FLAT, T>(h, PA, nullptr);
+    if (K.qflux != 1) launch_ghosts(h, J1, 3);
     mark(2);
     launch_flux<T, FLAT>(h, PA, J1);
     mark(3);
@@ -273,7 +282,8 @@ template <bool FLAT, class T> static void enqueue_step_t(rmhd_t h, cudaEvent_t *
                                                        b.stats);
     mark(4);
     launch_ghosts(h, PB, NPR);
-    if (K.qflux == 0) launch_ghosts(h, J2, 3);
+    if (K.qflux == RMHD_QFLUX_GAUSS) gauss_charge<FLAT, T>(h, PB, nullptr);
+    if (K.qflux != 1) launch_ghosts(h, J2, 3);
     mark(5);
     launch_flux<T, FLAT>(h, PB, J2);
     mark(6);
@@ -285,6 +295,7 @@ template <bool FLAT, class T> static void enqueue_step_t(rmhd_t h, cudaEvent_t *
                                                        b.stats);
     mark(7);
     launch_ghosts(h, PA, NPR);
+    if (K.qflux == RMHD_QFLUX_GAUSS) gauss_charge<FLAT, T>(h, PA, b.U);
     mark(8);
 }
 

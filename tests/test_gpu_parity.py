@@ -174,6 +174,14 @@ CASES = {
                                           sigma0=3e3, sigma_exp=0.5),
     "lane_emden_sigma_atmo": lambda: _with(W.lane_emden_star(n=20), sigma_model=3,
                                            D_atmo=1e-5),
+    # Sec. IV.A shocktube, sigma = 1e6 D^12 spanning 11 decades
+    "shocktube_sigma_D12": lambda: W.shocktube_sigma(400, sigma_exp=12.0),
+    "shocktube_sigma_D6": lambda: W.shocktube_sigma(400, sigma_exp=6.0),
+    # charge from Gauss's law instead of its evolution (Sec. IV.E variant)
+    "gauss_flat": lambda: W.gauss_smooth(24, curved=False),
+    "gauss_curved": lambda: W.gauss_smooth(24, curved=True),
+    "lane_emden_gauss": lambda: _with(W.lane_emden_star(n=20), qflux_mode=2),
+    "cyl_blast_gauss": lambda: _with(W.cyl_blast(n=40, nz=4), qflux_mode=2),
 }
 
 
@@ -202,7 +210,9 @@ def test_one_step_matches_oracle(name):
 @pytest.mark.parametrize("name,nsteps", [("brio_wu", 100), ("alfven_s1e6", 100),
                                          ("current_sheet", 100), ("cyl_blast_hr", 20),
                                          ("lane_emden", 10), ("cyl_blast_sigma_powD", 10),
-                                         ("lane_emden_sigma_atmo", 10)])
+                                         ("lane_emden_sigma_atmo", 10), ("gauss_curved", 20),
+                                         ("shocktube_sigma_D12", 640), ("shocktube_sigma_D6", 640),
+                                         ("lane_emden_gauss", 10)])
 def test_many_steps_match_oracle(name, nsteps):
     wl = CASES[name]()
     _, so, prim_o, cons_o = run_oracle(wl, nsteps)

@@ -284,3 +284,32 @@ def test_literal_face_ohm_current_is_stiff_in_the_charge_flux():
             qmax[mode, sigma] = np.abs(prim[13]).max()
     assert qmax[1, 1e6] > 1e3 * qmax[1, 1e2]
     assert qmax[0, 1e6] < 0.02 and qmax[0, 1e2] < 0.02, qmax
+
+
+@pytest.mark.parametrize("curved", [False, True])
+def test_gauss_law_charge_converges_to_evolved_charge(curved):
+    """Charge from Gauss's law (the Sec. IV.E variant) against the evolved
+    charge: on data that satisfy the constraint q = nabla_i E^i, Ampere's law
+    and charge conservation keep it satisfied, so the two runs agree in the
+    continuum and their difference must shrink at second order.  A missing
+    sqrt(gamma), a sign or a factor in the Gauss charge would leave an O(1)
+    difference (the curved case has E . grad ln sqrt(gamma) ~ q)."""
+    d = []
+    for n in (32, 64):
+        runs = []
+        for mode in (0, 2):
+            wl = W.gauss_smooth(n, curved, mode)
+            nsteps = int(round(0.25 / wl.dt))
+            st, _, prim, cons = _run(wl, nsteps)
+            assert st == 0
+            runs.append(prim)
+        d.append(np.abs(runs[0][13] - runs[1][13]).mean() / np.abs(runs[0][13]).mean())
+    assert d[1] < 0.03 and d[0] / d[1] > 3.0, d
+
+
+def test_gauss_law_charge_totals_vanish_on_a_periodic_grid():
+    """sum_cells d_i calE^i telescopes to zero on a periodic grid."""
+    wl = W.gauss_smooth(16, True, 2)
+    st, _, prim, cons = _run(wl, 3)
+    assert st == 0
+    assert abs(cons[13].sum()) < 1e-13 * np.abs(cons[13]).sum()

@@ -7,7 +7,8 @@ shape (nfields, nz, ny, nx), x fastest.
 
 The initial data follow the paper's test problems (arXiv:2510.18968 Sec. IV)
 as modified by the benchmark configurations:
-  * Brio-Wu shocktube, Sec. IV.A (variant with B^x = 0.5, B^y = +-1);
+  * Brio-Wu shocktube, Sec. IV.A (variant with B^x = 0.5, B^y = +-1), and
+    the section's own shocktube with conductivity sigma0 D^gamma_sigma;
   * circularly polarised Alfven wave, Sec. IV.D, Eqs. Bi, vyvz, Alf_vel,
     rotated onto the (1,1,1) diagonal of a periodic cube;
   * cylindrical explosion, Sec. IV.B (log-linear taper of rho and p);
@@ -15,7 +16,9 @@ as modified by the benchmark configurations:
     potential Phi, alpha = 1 + Phi, gamma_ij = (1 - 2 Phi) delta_ij, and a
     poloidal field from A_phi ~ max(p - 0.04 p_max, 0) (Sec. IV.E vector
     potential with power 1), conductivity blended by tanh at the surface;
-  * self-similar current sheet, Sec. IV.C (B^y = B0 erf(x sqrt(sigma)/(2 sqrt(t)))).
+  * self-similar current sheet, Sec. IV.C (B^y = B0 erf(x sqrt(sigma)/(2 sqrt(t))));
+  * a smooth 2D periodic state on the Gauss constraint q = nabla_i E^i, flat
+    or conformally flat, for the Gauss's-law charge variant of Sec. IV.E.
 """
 from dataclasses import dataclass, field
 from math import erf, pi, sqrt
@@ -121,6 +124,25 @@ def brio_wu(n=400, sigma=1e5, cfl=0.5, nsteps=320, axis=0):
     prim[8 + axis] = 0.5
     prim[8 + (axis + 1) % 3] = np.where(left, 1.0, -1.0)
     return Workload("brio_wu_%d" % n, P, prim, cfl * dx, nsteps)
+
+
+def shocktube_sigma(n=400, sigma0=1e6, sigma_exp=12.0, cfl=0.25, t_end=0.4):
+    """Sec. IV.A shocktube with the conductivity of Eq. sigma_evol,
+    sigma = sigma0 D^sigma_exp: left (rho, p, B^y) = (1, 1, 0.5), right
+    (0.125, 0.1, -0.5), B^x = 0, E = 0, Gamma = 2, minmod, outflow, on
+    [-0.5, 0.5] with CFL 0.25 to t = 0.4."""
+    dx = 1.0 / n
+    nn, x0, dxs = [n, 1, 1], [-0.5, -0.5 * dx, -0.5 * dx], [dx] * 3
+    P = base_params(nn, x0, dxs, [BC_OUTFLOW] * 3, "minmod", 2.0, sigma0,
+                    sigma_model=2, sigma_exp=sigma_exp)
+    X, _, _ = cell_centres(nn, x0, dxs)
+    prim = _empty_prim(X.shape)
+    left = X < 0.0
+    prim[0] = np.where(left, 1.0, 0.125)
+    prim[1] = np.where(left, 1.0, 0.1)
+    prim[9] = np.where(left, 0.5, -0.5)
+    dt = cfl * dx
+    return Workload("shocktube_sigma_D%g" % sigma_exp, P, prim, dt, int(round(t_end / dt)))
 
 
 def alfven_diag(n=128, sigma=1e6, eta=0.1, B0=1.0, gamma_eos=4.0 / 3.0,
@@ -271,6 +293,40 @@ def current_sheet(n=600, sigma=100.0, L=1.5, B0=1.0, p=50.0, rho=1.0, t0=1.0,
 
 
 # ------------------------------------------------------------------ random states
+
+def gauss_smooth(n, curved=False, qflux_mode=2):
+    """2D periodic smooth state with q = (1/sqrt(g)) d_i(sqrt(g) E^i) exactly
+    (analytic derivatives) and a divergence-free densitised B."""
+    dx = 1.0 / n
+    P = base_params((n, n, 1), (0, 0, 0), (dx, dx, dx), (0, 0, 0), "mc2", 2.0, 20.0,
+                    qflux_mode=qflux_mode)
+    x = (np.arange(n) + 0.5) * dx
+    X, Y = np.meshgrid(x, x, indexing="xy")
+    X, Y = X[None], Y[None]
+    tp, e0 = 2.0 * np.pi, 0.05
+    prim = np.zeros((14, 1, n, n))
+    prim[0] = 1.0 + 0.2 * np.sin(tp * (X + Y))
+    prim[1] = 1.0
+    prim[2], prim[3] = 0.1 * np.sin(tp * Y), 0.1 * np.cos(tp * X)
+    prim[5], prim[6] = e0 * np.sin(tp * X), e0 * np.cos(tp * Y)
+    q = tp * e0 * (np.cos(tp * X) - np.sin(tp * Y))
+    sg = np.ones_like(X)
+    kw = {}
+    if curved:
+        psi4 = 1.0 + 0.2 * np.sin(tp * X) * np.cos(tp * Y)
+        dpx = 0.2 * tp * np.cos(tp * X) * np.cos(tp * Y)
+        dpy = -0.2 * tp * np.sin(tp * X) * np.sin(tp * Y)
+        sg = psi4 ** 1.5
+        q = q + 1.5 * (prim[5] * dpx + prim[6] * dpy) / psi4   # + E . grad ln sqrt(g)
+        g = np.zeros((6, 1, n, n))
+        g[0] = g[3] = g[5] = psi4
+        kw = dict(alpha=np.ones((1, n, n)), beta=np.zeros((3, 1, n, n)), gamma=g,
+                  K=np.zeros((6, 1, n, n)))
+    prim[8] = (0.3 + 0.1 * np.cos(tp * Y)) / sg
+    prim[9] = (0.2 + 0.1 * np.sin(tp * X)) / sg
+    prim[13] = q
+    return Workload("gauss", P, prim, 0.25 * dx, 1, **kw)
+
 
 def random_metric(rng, npts, strength=0.3):
     """Random positive-definite 3-metrics gamma = I + strength*sym(A), lapse in
