@@ -216,6 +216,44 @@ int rmhd_con2prim_points_noalloc(const rmhd_params *p, int npts, const double *c
 
 /* Text of the last error on this handle (never NULL; "" if none).  With
  * h == NULL: the last error of a call that had no handle. */
+/* ---------------------------------------------------------------- adjoint
+ * Discrete adjoint of the FP64 step (the paper has none; it differentiates
+ * exactly the step rmhd_step takes: Table imex / Eq. IMEX3 for the stages,
+ * the recovery of Sec. III.B at its converged root by the implicit-function
+ * theorem).  Limiter branches, first-order fallbacks and atmosphere resets
+ * are frozen at the recorded trajectory; a cell reset to the atmosphere
+ * passes no derivative through rho, p, v (nor, after the last recovery of a
+ * step, through D, S_i, tau).  Needs precision RMHD_PREC_FP64, qflux_mode
+ * RMHD_QFLUX_STAGE and n >= 3 in every active direction (RMHD_EINVAL
+ * otherwise). */
+
+/* Set sigma0 of the conductivity model (the value rmhd_create took). */
+int rmhd_set_sigma0(rmhd_t h, double sigma0);
+
+/* Run nsteps steps of size dt from the current state, like rmhd_step, and
+ * record the trajectory for rmhd_adjoint_backward: the state (U and P,
+ * 28 FP64 fields of the padded grid) every checkpoint_every steps, plus
+ * scratch for one segment of checkpoint_every + 1 states and the adjoint
+ * fields (about 40 + 28 (nsteps / checkpoint_every + checkpoint_every)
+ * padded FP64 fields in all).  Replaces any earlier recording.  Errors:
+ * RMHD_EINVAL, RMHD_ENOMEM, RMHD_ENAN (non-finite state; nothing recorded).
+ * Atmosphere resets are not an error here (rmhd_get_stats counts them). */
+int rmhd_adjoint_forward(rmhd_t h, double dt, int nsteps, int checkpoint_every);
+
+/* Reverse sweep of the recorded steps.  lam_prims[14][N] (interior, field
+ * order of rmhd_set_prims) = dL/dP^N for a scalar loss L of the primitives
+ * after the last recorded step.  Writes grad_prims0[14][N] = dL/dP^0 (the
+ * primitives the recording started from) and, when grad_log_sigma0 is not
+ * NULL, dL/d(log sigma0) (every conductivity model is proportional to
+ * sigma0; the D-dependence of Eqs. sigma_evol, dynamo_sigma is
+ * differentiated).  Each segment is recomputed from its checkpoint.  On
+ * return the state, the statistics and the recording are as
+ * rmhd_adjoint_forward left them, so it may be called again with another
+ * lam_prims.  on_device as for rmhd_set_prims.  Errors: RMHD_EINVAL (no
+ * recording, NULL array), RMHD_ENAN (a singular recovery Jacobian). */
+int rmhd_adjoint_backward(rmhd_t h, const double *lam_prims, double *grad_prims0,
+                          double *grad_log_sigma0, int on_device);
+
 const char *rmhd_last_error(rmhd_t h);
 
 /* Free all device memory of the handle (synchronises its stream). */

@@ -59,8 +59,8 @@ class Params(ctypes.Structure):
 EXPORTS = ("rmhd_default_params", "rmhd_create", "rmhd_set_metric", "rmhd_set_sigma",
            "rmhd_set_prims", "rmhd_step", "rmhd_get_prims", "rmhd_get_cons",
            "rmhd_set_state", "rmhd_get_stats", "rmhd_step_profiled", "rmhd_rhs", "rmhd_con2prim_points",
-           "rmhd_con2prim_points_noalloc",
-           "rmhd_last_error", "rmhd_destroy")
+           "rmhd_con2prim_points_noalloc", "rmhd_set_sigma0", "rmhd_adjoint_forward",
+           "rmhd_adjoint_backward", "rmhd_last_error", "rmhd_destroy")
 
 _lib = None
 
@@ -94,6 +94,9 @@ def load(build_if_missing=True):
     L.rmhd_con2prim_points.argtypes = [P, i, vp, vp, vp, vp, vp, i, d, vp, vp, vp, vp, vp]
     L.rmhd_con2prim_points_noalloc.argtypes = [P, i, vp, vp, vp, vp, vp, i, d, vp, vp, vp, vp,
                                                vp]
+    L.rmhd_set_sigma0.argtypes = [vp, d]
+    L.rmhd_adjoint_forward.argtypes = [vp, d, i, i]
+    L.rmhd_adjoint_backward.argtypes = [vp, vp, vp, ctypes.POINTER(ctypes.c_double), i]
     L.rmhd_last_error.argtypes = [vp]
     L.rmhd_last_error.restype = ctypes.c_char_p
     L.rmhd_destroy.argtypes = [vp]
@@ -263,6 +266,31 @@ class Solver:
                  "atmo_floor_resets", "c2p_max_iterations", "nan", "steps")
         return dict(zip(names, list(s)))
 
+    # ---- adjoint
+    def set_sigma0(self, sigma0):
+        return self._check(self.L.rmhd_set_sigma0(self.h, float(sigma0)))
+
+    def adjoint_forward(self, dt, nsteps, checkpoint_every=10):
+        """nsteps steps from the current state, recorded for adjoint_backward."""
+        return self._check(self.L.rmhd_adjoint_forward(self.h, float(dt), int(nsteps),
+                                                       int(checkpoint_every)))
+
+    def adjoint_backward(self, lam_prims, out=None):
+        """(dL/dP^0, dL/dlog sigma0) for lam_prims = dL/dP^N (14, nz, ny, nx)."""
+        if out is None:
+            if _is_torch(lam_prims) and lam_prims.is_cuda:
+                import torch
+                out = torch.empty_like(lam_prims)
+            else:
+                out = np.empty((14,) + self.shape)
+        pl, d = _ptr(lam_prims, 14 * self.N)
+        po, d2 = _ptr(out, 14 * self.N)
+        if d != d2:
+            raise TypeError("lam_prims and out must both be host or both be device arrays")
+        ls = ctypes.c_double()
+        self._check(self.L.rmhd_adjoint_backward(self.h, pl, po, ctypes.byref(ls), d))
+        return out, ls.value
+
     def rhs(self, prim, J=None, out=None):
         out = np.empty((14,) + self.shape) if out is None else out
         pp, d = _ptr(prim, 14 * self.N)
@@ -300,3 +328,33 @@ def con2prim_points(params, cons, guess, alpha, gamma, sigma, implicit, c, strea
     if rc:
         raise RMHDError(rc, L.rmhd_last_error(None).decode())
     return prim, cout, iters, status
+
+
+def evolve_function():
+    """torch.autograd.Function: (P^0, log sigma0) -> P^N through nsteps FP64
+    steps; backward is the library's discrete adjoint.
+
+        P_N = evolve_function().apply(P0, log_sigma0, solver, dt, nsteps, every)
+
+    P0: CUDA float64 tensor (14, nz, ny, nx); log_sigma0: 0-d tensor."""
+    import torch
+
+    class Evolve(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, P0, log_sigma0, solver, dt, nsteps, every):
+            solver.set_sigma0(float(torch.exp(log_sigma0.detach())))
+            solver.set_prims(P0.detach().contiguous())
+            solver.adjoint_forward(dt, nsteps, every)
+            ctx.solver = solver
+            ctx.sigma_device = log_sigma0.device
+            out = torch.empty_like(P0)
+            solver.get_prims(out=out)
+            return out
+
+        @staticmethod
+        def backward(ctx, grad_out):
+            g, ls = ctx.solver.adjoint_backward(grad_out.contiguous())
+            return (g, torch.tensor(ls, dtype=torch.float64, device=ctx.sigma_device), None,
+                    None, None, None)
+
+    return Evolve

@@ -446,8 +446,9 @@ __global__ void __launch_bounds__(128) k_flux(const StepConst K, const T *__rest
     T acc[NCO];
 #pragma unroll
     for (int f = 0; f < NCO; f++) acc[f] = T(0);
-    flux_accumulate<T, FLAT, D>(pL, m, sigma, gfac, useJ, JL, cFL, -cUU, acc);
-    flux_accumulate<T, FLAT, D>(pR, m, sigma, gfac, useJ, JR, cFR, cUU, acc);
+    ArrAcc<T> aa{acc};
+    flux_accumulate<T, FLAT, D>(pL, m, sigma, gfac, useJ, JL, cFL, -cUU, aa);
+    flux_accumulate<T, FLAT, D>(pR, m, sigma, gfac, useJ, JR, cFR, cUU, aa);
 #pragma unroll
     for (int f = 0; f < NCO; f++) F[f * S + cR] = acc[f];
 }
@@ -590,8 +591,9 @@ __global__ void __launch_bounds__(128) k_flux_run(const StepConst K, const T *__
         T acc[NCO];
 #pragma unroll
         for (int k = 0; k < NCO; k++) acc[k] = T(0);
-        flux_accumulate<T, FLAT, D>(sL, m, sigma, gfac, useJ, JL, cFL, -cUU, acc);
-        flux_accumulate<T, FLAT, D>(sR, m, sigma, gfac, useJ, JR, cFR, cUU, acc);
+        ArrAcc<T> aa{acc};
+        flux_accumulate<T, FLAT, D>(sL, m, sigma, gfac, useJ, JL, cFL, -cUU, aa);
+        flux_accumulate<T, FLAT, D>(sR, m, sigma, gfac, useJ, JR, cFR, cUU, aa);
 #pragma unroll
         for (int k = 0; k < NCO; k++) F[k * S + cR] = acc[k];
         // slide: the cell above becomes the cell below
@@ -604,34 +606,22 @@ __global__ void __launch_bounds__(128) k_flux_run(const StepConst K, const T *__
 // Source vector of Eq. GRRMHD_flux_form without the stiff part of -alpha J
 // (Sec. III.A split), at a cell with primitives pr.  Metric derivatives:
 // second-order central differences of the cell-centred metric.
-template <bool FLAT, class T>
-__device__ __forceinline__ void sources(const StepConst &K, const T pr_in[NPR],
-                                        const double *__restrict__ met, long long c,
-                                        T Sv_out[NCO])
+// Sources of a cell on a curved static metric, with the primitive-dependent
+// quantities in R (double, or a dual number in the adjoint) and the metric,
+// its derivatives and K_ij in FP64.
+template <class R>
+__device__ __forceinline__ void sources_curved(const StepConst &K, const R pr[NPR],
+                                               const double *__restrict__ met, long long c,
+                                               R Sv[NCO])
 {
-    const T kapT = (T)K.kappa;
-    if (FLAT) {
-        // only -Q v^i (E), -kappa Phi, Q - kappa Psi survive in flat space
-        const T *pr = pr_in;
-        T *Sv = Sv_out;
-        for (int f = 0; f < NCO; f++) Sv[f] = T(0);
-        const T Q = pr[PR_Q];
-        const T kap = kapT;
-        for (int a = 0; a < 3; a++) Sv[CO_EX + a] = -Q * pr[PR_VX + a];
-        Sv[CO_PHI] = -kap * pr[PR_PHI];
-        Sv[CO_PSI] = Q - kap * pr[PR_PSI];
-        return;
-    }
-    // curved metric: evaluated in FP64 from the stage primitives
     const double kap = K.kappa;
-    double pr[NPR], Sv[NCO];
-    for (int f = 0; f < NPR; f++) pr[f] = (double)pr_in[f];
     const Grid &G = K.G;
     const long long S = G.S;
     Met<double> m;
     load_metric<false>(met, S, c, m);
-    double U[NCO];
-    prim_to_cons<double, false>(pr, m, K.gfac, U);
+    const Met<R> mr = met_cast<R>(m);
+    R U[NCO];
+    prim_to_cons<R, false>(pr, mr, R(K.gfac), U);
     double da[3], db[3][3], dg[3][6];
     for (int d = 0; d < 3; d++) {
         if (G.g[d] == 0) {
@@ -662,26 +652,26 @@ __device__ __forceinline__ void sources(const StepConst &K, const T pr_in[NPR],
                 s += gi[sym(b, cc)] * (2.0 * dg[b][sym(l, cc)] - dg[l][sym(b, cc)]);
         w[l] = 0.5 * s;
     }
-    double v[3] = {pr[PR_VX], pr[PR_VY], pr[PR_VZ]};
-    double E[3] = {pr[PR_EX], pr[PR_EY], pr[PR_EZ]};
-    double B[3] = {pr[PR_BX], pr[PR_BY], pr[PR_BZ]};
-    double vl[3], El[3], Bl[3];
-    lower<double, false>(m, v, vl);
-    lower<double, false>(m, E, El);
-    lower<double, false>(m, B, Bl);
-    const double W2 = 1.0 / (1.0 - dot3(v, vl));
-    const double hW2 = (pr[PR_RHO] + K.gfac * pr[PR_P]) * W2;
-    const double pem = pr[PR_P] + 0.5 * (dot3(E, El) + dot3(B, Bl));
-    double Sup[6];   // undensitised stress, indices up
+    R v[3] = {pr[PR_VX], pr[PR_VY], pr[PR_VZ]};
+    R E[3] = {pr[PR_EX], pr[PR_EY], pr[PR_EZ]};
+    R B[3] = {pr[PR_BX], pr[PR_BY], pr[PR_BZ]};
+    R vl[3], El[3], Bl[3];
+    lower<R, false>(mr, v, vl);
+    lower<R, false>(mr, E, El);
+    lower<R, false>(mr, B, Bl);
+    const R W2 = 1.0 / (1.0 - dot3(v, vl));
+    const R hW2 = (pr[PR_RHO] + K.gfac * pr[PR_P]) * W2;
+    const R pem = pr[PR_P] + 0.5 * (dot3(E, El) + dot3(B, Bl));
+    R Sup[6];   // undensitised stress, indices up
     for (int a = 0; a < 3; a++)
         for (int b = a; b < 3; b++)
             Sup[sym(a, b)] = hW2 * v[a] * v[b] + gi[sym(a, b)] * pem - E[a] * E[b] - B[a] * B[b];
     const double al = m.alpha, sg = m.sg;
-    double Su[3];
-    double Sl[3] = {U[CO_SX], U[CO_SY], U[CO_SZ]};
-    raise<double, false>(m, Sl, Su);
+    R Su[3];
+    R Sl[3] = {U[CO_SX], U[CO_SY], U[CO_SZ]};
+    raise<R, false>(mr, Sl, Su);
     for (int a = 0; a < 3; a++) {
-        double s = 0.0;
+        R s = 0.0;
         for (int b = 0; b < 3; b++)
             for (int cc = 0; cc < 3; cc++) s += Sup[sym(b, cc)] * dg[a][sym(b, cc)];
         s *= 0.5 * al * sg;
@@ -690,7 +680,7 @@ __device__ __forceinline__ void sources(const StepConst &K, const T pr_in[NPR],
         Sv[CO_SX + a] = s;
     }
     {
-        double s = Sup[0] * Kij[0] + Sup[3] * Kij[3] + Sup[5] * Kij[5] +
+        R s = Sup[0] * Kij[0] + Sup[3] * Kij[3] + Sup[5] * Kij[5] +
                    2.0 * (Sup[1] * Kij[1] + Sup[2] * Kij[2] + Sup[4] * Kij[4]);
         s *= al * sg;
         for (int a = 0; a < 3; a++) s -= Su[a] * da[a];
@@ -700,7 +690,7 @@ __device__ __forceinline__ void sources(const StepConst &K, const T pr_in[NPR],
         double G1 = gi[sym(a, 0)] * da[0] + gi[sym(a, 1)] * da[1] + gi[sym(a, 2)] * da[2];
         double G2 = gi[sym(a, 0)] * w[0] + gi[sym(a, 1)] * w[1] + gi[sym(a, 2)] * w[2];
         double geo = G1 - al * G2;
-        double sB = 0.0, sE = 0.0;
+        R sB = 0.0, sE = 0.0;
         for (int b = 0; b < 3; b++) {
             sB -= U[CO_BX + b] * db[b][a];
             sE -= U[CO_EX + b] * db[b][a];
@@ -708,7 +698,7 @@ __device__ __forceinline__ void sources(const StepConst &K, const T pr_in[NPR],
         Sv[CO_BX + a] = sB + U[CO_PHI] * geo;
         Sv[CO_EX + a] = sE + U[CO_PSI] * geo - al * U[CO_Q] * v[a];
     }
-    double Bda = 0.0, Eda = 0.0;
+    R Bda = 0.0, Eda = 0.0;
     for (int b = 0; b < 3; b++) {
         Bda += U[CO_BX + b] * da[b];
         Eda += U[CO_EX + b] * da[b];
@@ -717,7 +707,31 @@ __device__ __forceinline__ void sources(const StepConst &K, const T pr_in[NPR],
     Sv[CO_PSI] = -al * U[CO_PSI] * Ktr + Eda + al * U[CO_Q] - al * kap * U[CO_PSI];
     Sv[CO_D] = 0.0;
     Sv[CO_Q] = 0.0;
-    for (int f = 0; f < NCO; f++) Sv_out[f] = (T)Sv[f];
+}
+
+template <bool FLAT, class T>
+__device__ __forceinline__ void sources(const StepConst &K, const T pr_in[NPR],
+                                        const double *__restrict__ met, long long c,
+                                        T Sv_out[NCO])
+{
+    const T kapT = (T)K.kappa;
+    if (FLAT) {
+        // only -Q v^i (E), -kappa Phi, Q - kappa Psi survive in flat space
+        const T *pr = pr_in;
+        T *Sv = Sv_out;
+        for (int f = 0; f < NCO; f++) Sv[f] = T(0);
+        const T Q = pr[PR_Q];
+        const T kap = kapT;
+        for (int a = 0; a < 3; a++) Sv[CO_EX + a] = -Q * pr[PR_VX + a];
+        Sv[CO_PHI] = -kap * pr[PR_PHI];
+        Sv[CO_PSI] = Q - kap * pr[PR_PSI];
+    } else {
+        // curved metric: evaluated in FP64 from the stage primitives
+        double pr[NPR], Sv[NCO];
+        for (int f = 0; f < NPR; f++) pr[f] = (double)pr_in[f];
+        sources_curved<double>(K, pr, met, c, Sv);
+        for (int f = 0; f < NCO; f++) Sv_out[f] = (T)Sv[f];
+    }
 }
 
 // explicit right-hand side F(U) at an interior cell from the face fluxes (T)
@@ -907,13 +921,14 @@ k_stage1(const StepConst K, const double *__restrict__ U, T *P, double *Gs, doub
 
 // Stage 2: U* = U^n + dt F[U1] + (1-2gamma) Dt R1 on calE; implicit recovery
 // (guess P1); V = U^n + dt/2 F[U1] + dt/2 (R1 + R2) (Eq. IMEX3 minus F[U2]).
+// Us (optional): U* is also written there.
 template <bool FLAT, class T>
 __global__ void __launch_bounds__(128)
 k_stage2(const StepConst K, const double *__restrict__ U, const T *__restrict__ P1,
          const double *__restrict__ G1, const T *__restrict__ Fx, const T *__restrict__ Fy,
          const T *__restrict__ Fz, const double *__restrict__ dR1,
          const double *__restrict__ met, const double *__restrict__ sig, T *P2, double *G2,
-         double *V, T *J2, const Defer df, unsigned long long *stats)
+         double *V, T *J2, const Defer df, unsigned long long *stats, double *Us)
 {
     const Grid &G = K.G;
     const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -939,6 +954,8 @@ k_stage2(const StepConst K, const double *__restrict__ U, const T *__restrict__ 
             V[f * S + c] = uu + hdt * rf;
         }
         for (int a = 0; a < 3; a++) us[CO_EX + a] += (1.0 - 2.0 * K.gimex) * dR1[a * S + c];
+        if (Us)   // the adjoint keeps the recovery input U*
+            for (int f = 0; f < NCO; f++) Us[f * S + c] = us[f];
         load_metric<FLAT>(met, S, c, m);
         RecIn in;
         load_rec_in(us, in);

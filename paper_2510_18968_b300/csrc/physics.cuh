@@ -49,6 +49,21 @@ template <class T> __device__ __forceinline__ void met_complete(Met<T> &m)
     m.isg = T(1) / m.sg;
 }
 
+// the same metric in another arithmetic type (constants for a dual number)
+template <class R> __device__ __forceinline__ Met<R> met_cast(const Met<double> &m)
+{
+    Met<R> r;
+    r.alpha = R(m.alpha);
+    for (int a = 0; a < 3; a++) r.beta[a] = R(m.beta[a]);
+    for (int a = 0; a < 6; a++) {
+        r.g[a] = R(m.g[a]);
+        r.gi[a] = R(m.gi[a]);
+    }
+    r.sg = R(m.sg);
+    r.isg = R(m.isg);
+    return r;
+}
+
 template <class T, bool FLAT>
 __device__ __forceinline__ void lower(const Met<T> &m, const T u[3], T ul[3])
 {
@@ -99,12 +114,24 @@ template <class T> __device__ __forceinline__ T sg_of(const Met<T> &m, bool flat
 //    the S_i flux; the charge-flux current is Jd when useJ, else Ohm's law
 //    (Eq. Ohm_law) at this state.  gfac = Gamma/(Gamma-1): h = rho + gfac p.
 // Accumulates cF*F + cU*U into acc (the HLLE combination), so that neither U
-// nor F has to stay live as an array.
+// nor F has to stay live as an array.  acc.add(f, x) receives the term of
+// field f: an array (ArrAcc, the flux kernels) or a weighted sum of the
+// fields (WeightedAcc, the adjoint's lambda . (cF F + cU U)).
 // ---------------------------------------------------------------------------
-template <class T, bool FLAT, int D>
+template <class T> struct ArrAcc {
+    T *a;
+    __device__ __forceinline__ void add(int f, const T &x) { a[f] += x; }
+};
+template <class T> struct WeightedAcc {
+    const double *w;
+    T sum;
+    __device__ __forceinline__ void add(int f, const T &x) { sum += w[f] * x; }
+};
+
+template <class T, bool FLAT, int D, class Acc>
 __device__ __forceinline__ void flux_accumulate(const T pr[NPR], const Met<T> &m,
                                                 T sigma, T gfac, bool useJ, T Jd,
-                                                T cF, T cU, T acc[NCO])
+                                                T cF, T cU, Acc &acc)
 {
     const T sg = FLAT ? T(1) : m.sg;
     const T a = FLAT ? T(1) : m.alpha;
@@ -133,21 +160,21 @@ __device__ __forceinline__ void flux_accumulate(const T pr[NPR], const Met<T> &m
     for (int i = 0; i < 3; i++) S[i] = sg * (hW2 * vl[i] + sg * ExB[i]);
 
     // D, S_i, tau
-    acc[CO_D] += cF * ((a * v[D] - bD) * Dc) + cU * Dc;
+    acc.add(CO_D, cF * ((a * v[D] - bD) * Dc) + cU * Dc);
 #pragma unroll
     for (int i = 0; i < 3; i++) {
         T st = hW2 * v[D] * vl[i] - E[D] * El[i] - B[D] * Bl[i];
         if (i == D) st += p + em;
         T f = a * sg * st;
         if (!FLAT) f -= bD * S[i];
-        acc[CO_SX + i] += cF * f + cU * S[i];
+        acc.add(CO_SX + i, cF * f + cU * S[i]);
     }
     T SD = S[D];
     if (!FLAT) SD = m.gi[sym(D, 0)] * S[0] + m.gi[sym(D, 1)] * S[1] + m.gi[sym(D, 2)] * S[2];
     {
         T f = a * (SD - v[D] * Dc);
         if (!FLAT) f -= bD * tau;
-        acc[CO_TAU] += cF * f + cU * tau;
+        acc.add(CO_TAU, cF * f + cU * tau);
     }
     // B^i: alpha (eps^{iDj} calE_j + gamma^{iD} Phi) - beta^D calB^i, with
     // eps^{iDj} calE_j = (e_D x E_lower)_i; E^i: -[alpha(...B...) + beta^D calE^i]
@@ -166,8 +193,8 @@ __device__ __forceinline__ void flux_accumulate(const T pr[NPR], const Met<T> &m
             fB -= bD * cB;
             fE -= bD * cE;
         }
-        acc[CO_BX + i] += cF * fB + cU * cB;
-        acc[CO_EX + i] += cF * fE + cU * cE;
+        acc.add(CO_BX + i, cF * fB + cU * cB);
+        acc.add(CO_EX + i, cF * fE + cU * cE);
     }
     {
         T fPhi = a * sg * B[D], fPsi = a * sg * E[D];
@@ -175,8 +202,8 @@ __device__ __forceinline__ void flux_accumulate(const T pr[NPR], const Met<T> &m
             fPhi -= bD * Phi;
             fPsi -= bD * Psi;
         }
-        acc[CO_PHI] += cF * fPhi + cU * Phi;
-        acc[CO_PSI] += cF * fPsi + cU * Psi;
+        acc.add(CO_PHI, cF * fPhi + cU * Phi);
+        acc.add(CO_PSI, cF * fPsi + cU * Psi);
     }
     T J = Jd;
     if (!useJ) {
@@ -188,7 +215,7 @@ __device__ __forceinline__ void flux_accumulate(const T pr[NPR], const Met<T> &m
     {
         T f = a * J;
         if (!FLAT) f -= bD * Qc;
-        acc[CO_Q] += cF * f + cU * Qc;
+        acc.add(CO_Q, cF * f + cU * Qc);
     }
 }
 

@@ -9,6 +9,7 @@
 #include <string.h>
 
 #include "../../include/rmhd.h"
+#include "adjoint.cuh"
 #include "kernels.cuh"
 
 using namespace rmhd;
@@ -39,11 +40,44 @@ struct Buffers {
 
 } // namespace
 
+namespace {
+
+// recorded trajectory and scratch of the adjoint (FP64 path)
+struct AdjBuf {
+    bool recorded = false;
+    double dt = 0.0;
+    int nsteps = 0, every = 0, nck = 0;
+    double *ckU = nullptr, *ckP = nullptr;     // checkpoints: nck x (14 x S)
+    double *segU = nullptr, *segP = nullptr;   // one segment: (every + 1) x (14 x S)
+    double *endU = nullptr, *endP = nullptr;   // state after the recorded steps
+    double *lamU = nullptr, *lamUn = nullptr, *lamR1 = nullptr, *lamP = nullptr;
+    double *lamJ = nullptr, *lamdR1 = nullptr, *Us = nullptr;
+    double *lsig = nullptr;
+    int *bad = nullptr;
+};
+
+void free_adj(AdjBuf &a)
+{
+    double **ptrs[] = {&a.ckU, &a.ckP, &a.segU, &a.segP, &a.endU, &a.endP, &a.lamU, &a.lamUn,
+                       &a.lamR1, &a.lamP, &a.lamJ, &a.lamdR1, &a.Us, &a.lsig};
+    for (double **q : ptrs)
+        if (*q) {
+            cudaFree(*q);
+            *q = nullptr;
+        }
+    if (a.bad) cudaFree(a.bad);
+    a.bad = nullptr;
+    a.recorded = false;
+}
+
+} // namespace
+
 struct rmhd_s {
     rmhd_params p;
     cudaStream_t st;
     StepConst K;
     Buffers b;
+    AdjBuf adj;
     bool flat = true;
     bool have_state = false;
     long long steps = 0;
@@ -275,7 +309,8 @@ template <bool FLAT, class T> static void enqueue_step_t(rmhd_t h, cudaEvent_t *
     launch_flux<T, FLAT>(h, PA, J1);
     mark(3);
     k_stage2<FLAT, T><<<nb, TPB, 0, h->st>>>(K, b.U, PA, b.GA, F0, F1, F2, b.dR1, b.met, b.sig,
-                                             PB, b.GB, b.V, J2, defer_of(h, 1), b.stats);
+                                             PB, b.GB, b.V, J2, defer_of(h, 1), b.stats,
+                                             nullptr);
     if (dfr)
         k_deferred<FLAT, 2, T><<<nbd, TPB, 0, h->st>>>(K, defer_of(h, 1), b.met, b.sig, b.dR1,
                                                        PB, b.GB, nullptr, J2, b.V, nullptr,
@@ -797,6 +832,261 @@ extern "C" int rmhd_con2prim_points(const rmhd_params *p, int npts, const double
     return RMHD_OK;
 }
 
+// ------------------------------------------------------------------ adjoint
+
+extern "C" int rmhd_set_sigma0(rmhd_t h, double sigma0)
+{
+    if (!h) return set_err(nullptr, RMHD_EINVAL, "handle is NULL");
+    if (!(sigma0 >= 0.0) || !isfinite(sigma0)) return set_err(h, RMHD_EINVAL, "sigma0 must be >= 0");
+    h->p.sigma0 = sigma0;
+    h->K.sigma0 = sigma0;
+    return RMHD_OK;
+}
+
+static size_t fbytes(rmhd_t h, int nf) { return sizeof(double) * nf * (size_t)h->K.G.S; }
+
+// copy the FP64 state (U, P with the guess fields) to / from a slot
+static int save_state(rmhd_t h, double *U, double *P)
+{
+    CK(cudaMemcpyAsync(U, h->b.U, fbytes(h, NCO), cudaMemcpyDeviceToDevice, h->st));
+    CK(cudaMemcpyAsync(P, h->b.PA, fbytes(h, NPR), cudaMemcpyDeviceToDevice, h->st));
+    return RMHD_OK;
+}
+static int load_state(rmhd_t h, const double *U, const double *P)
+{
+    CK(cudaMemcpyAsync(h->b.U, U, fbytes(h, NCO), cudaMemcpyDeviceToDevice, h->st));
+    CK(cudaMemcpyAsync(h->b.PA, P, fbytes(h, NPR), cudaMemcpyDeviceToDevice, h->st));
+    return RMHD_OK;
+}
+
+// the step up to the stage-2 recovery, keeping P1 (PA), J1, U* and P2 (PB),
+// J2 with their ghosts for the adjoint
+template <bool FLAT> static void enqueue_recompute_t(rmhd_t h)
+{
+    Buffers &b = h->b;
+    const StepConst &K = h->K;
+    const unsigned nb = nblk(K.G.N);
+    const bool dfr = b.dcap > 0;
+    const unsigned nbd = deferred_blocks(h);
+    double *PA = (double *)b.PA, *PB = (double *)b.PB, *J1 = (double *)b.J1, *J2 = (double *)b.J2;
+    double *F0 = (double *)b.F[0], *F1 = (double *)b.F[1], *F2 = (double *)b.F[2];
+    if (dfr) cudaMemsetAsync(b.dcount, 0, 3 * sizeof(int), h->st);
+    k_stage1<FLAT, double><<<nb, TPB, 0, h->st>>>(K, b.U, PA, b.GA, b.dR1, J1, b.met, b.sig,
+                                                  defer_of(h, 0), b.stats);
+    if (dfr)
+        k_deferred<FLAT, 1, double><<<nbd, TPB, 0, h->st>>>(K, defer_of(h, 0), b.met, b.sig,
+                                                            nullptr, PA, b.GA, b.dR1, J1, nullptr,
+                                                            nullptr, b.stats);
+    launch_ghosts(h, PA, NPR);
+    launch_ghosts(h, J1, 3);
+    launch_flux<double, FLAT>(h, PA, J1);
+    k_stage2<FLAT, double><<<nb, TPB, 0, h->st>>>(K, b.U, PA, b.GA, F0, F1, F2, b.dR1, b.met,
+                                                  b.sig, PB, b.GB, b.V, J2, defer_of(h, 1),
+                                                  b.stats, h->adj.Us);
+    if (dfr)
+        k_deferred<FLAT, 2, double><<<nbd, TPB, 0, h->st>>>(K, defer_of(h, 1), b.met, b.sig,
+                                                            b.dR1, PB, b.GB, nullptr, J2, b.V,
+                                                            nullptr, b.stats);
+    launch_ghosts(h, PB, NPR);
+    launch_ghosts(h, J2, 3);
+}
+
+template <bool FLAT> static void launch_adj_flux(rmhd_t h, const double *P, const double *J,
+                                                 const double *lamR, double scale)
+{
+    const Grid &G = h->K.G;
+    AdjBuf &a = h->adj;
+    auto nfaces = [&](int d) {
+        long long n = 1;
+        for (int q = 0; q < 3; q++) n *= q == d ? G.n[q] + 1 : G.n[q];
+        return n;
+    };
+#define RMHD_ADJ_FLUX(RC)                                                                   \
+    do {                                                                                    \
+        if (G.g[0])                                                                         \
+            k_adj_flux<FLAT, RC, 0><<<nblk(nfaces(0)), TPB, 0, h->st>>>(                    \
+                h->K, P, J, h->b.met, lamR, scale, a.lamP, a.lamJ);                         \
+        if (G.g[1])                                                                         \
+            k_adj_flux<FLAT, RC, 1><<<nblk(nfaces(1)), TPB, 0, h->st>>>(                    \
+                h->K, P, J, h->b.met, lamR, scale, a.lamP, a.lamJ);                         \
+        if (G.g[2])                                                                         \
+            k_adj_flux<FLAT, RC, 2><<<nblk(nfaces(2)), TPB, 0, h->st>>>(                    \
+                h->K, P, J, h->b.met, lamR, scale, a.lamP, a.lamJ);                         \
+    } while (0)
+    switch (h->p.recon) {
+    case RMHD_RECON_MINMOD: RMHD_ADJ_FLUX(RC_MINMOD); break;
+    case RMHD_RECON_MC2: RMHD_ADJ_FLUX(RC_MC2); break;
+    default: RMHD_ADJ_FLUX(RC_WENO5); break;
+    }
+#undef RMHD_ADJ_FLUX
+}
+
+// lamU <- dL/dU^n from lamU = dL/dU^{n+1}; the handle holds U^n, P^n
+template <bool FLAT> static int adjoint_step_t(rmhd_t h, const double *Pnext)
+{
+    AdjBuf &a = h->adj;
+    Buffers &b = h->b;
+    const StepConst &K = h->K;
+    const unsigned nb = nblk(K.G.N);
+    // cells the final recovery reset keep no derivative in D, S_i, tau
+    k_adj_reset_mask<<<nb, TPB, 0, h->st>>>(K, Pnext, a.lamU);
+    enqueue_recompute_t<FLAT>(h);
+    const double *P1 = (const double *)b.PA, *P2 = (const double *)b.PB;
+    const double *J1 = (const double *)b.J1, *J2 = (const double *)b.J2;
+    // F(P2, J2) entered U^{n+1} with weight dt/2
+    k_adj_sources<FLAT><<<nb, TPB, 0, h->st>>>(K, P2, b.met, a.lamU, 0.5 * K.dt, a.lamP);
+    CK(cudaMemsetAsync(a.lamJ, 0, fbytes(h, 3), h->st));
+    launch_adj_flux<FLAT>(h, P2, J2, a.lamU, 0.5 * K.dt);
+    k_adj_stage2<FLAT><<<nb, TPB, 0, h->st>>>(K, a.Us, P2, b.met, b.sig, a.lamU, a.lamP, a.lamJ,
+                                              a.lamR1, a.lamdR1, a.lamUn, a.lsig, a.bad);
+    // F(P1, J1): its adjoint is lamR1
+    k_adj_sources<FLAT><<<nb, TPB, 0, h->st>>>(K, P1, b.met, a.lamR1, 1.0, a.lamP);
+    CK(cudaMemsetAsync(a.lamJ, 0, fbytes(h, 3), h->st));
+    launch_adj_flux<FLAT>(h, P1, J1, a.lamR1, 1.0);
+    k_adj_stage1<FLAT><<<nb, TPB, 0, h->st>>>(K, b.U, P1, b.met, b.sig, a.lamP, a.lamJ, a.lamdR1,
+                                              a.lamUn, a.lsig, a.bad);
+    double *t = a.lamU;
+    a.lamU = a.lamUn;
+    a.lamUn = t;
+    CK(cudaGetLastError());
+    return RMHD_OK;
+}
+
+extern "C" int rmhd_adjoint_forward(rmhd_t h, double dt, int nsteps, int checkpoint_every)
+{
+    if (!h) return set_err(nullptr, RMHD_EINVAL, "handle is NULL");
+    if (!(dt > 0.0) || !isfinite(dt)) return set_err(h, RMHD_EINVAL, "dt must be > 0");
+    if (nsteps < 1 || checkpoint_every < 1)
+        return set_err(h, RMHD_EINVAL, "nsteps and checkpoint_every must be >= 1");
+    if (!h->have_state) return set_err(h, RMHD_EINVAL, "no state: call rmhd_set_prims first");
+    if (h->p.precision != RMHD_PREC_FP64)
+        return set_err(h, RMHD_EINVAL, "the adjoint needs precision RMHD_PREC_FP64");
+    if (h->p.qflux_mode != RMHD_QFLUX_STAGE)
+        return set_err(h, RMHD_EINVAL, "the adjoint needs qflux_mode RMHD_QFLUX_STAGE");
+    for (int d = 0; d < 3; d++)
+        if (h->K.G.g[d] && h->K.G.n[d] < 3)
+            return set_err(h, RMHD_EINVAL, "the adjoint needs n >= 3 in active directions");
+    AdjBuf &a = h->adj;
+    free_adj(a);
+    a.dt = dt;
+    a.nsteps = nsteps;
+    a.every = checkpoint_every < nsteps ? checkpoint_every : nsteps;
+    a.nck = (nsteps + a.every - 1) / a.every;
+    const size_t u = fbytes(h, NCO), pz = fbytes(h, NPR);
+    struct {
+        double **p;
+        size_t n;
+    } al[] = {{&a.ckU, a.nck * u},       {&a.ckP, a.nck * pz},   {&a.segU, (a.every + 1) * u},
+              {&a.segP, (a.every + 1) * pz}, {&a.endU, u},       {&a.endP, pz},
+              {&a.lamU, u},              {&a.lamUn, u},          {&a.lamR1, u},
+              {&a.lamP, pz},             {&a.lamJ, fbytes(h, 3)}, {&a.lamdR1, fbytes(h, 3)},
+              {&a.Us, u},                {&a.lsig, sizeof(double)}};
+    for (auto &e : al) {
+        cudaError_t err = cudaMalloc((void **)e.p, e.n);
+        if (err != cudaSuccess) {
+            free_adj(a);
+            return set_err(h, RMHD_ENOMEM, "adjoint buffers: %s", cudaGetErrorString(err));
+        }
+        CK(cudaMemsetAsync(*e.p, 0, e.n, h->st));
+    }
+    CK(cudaMalloc((void **)&a.bad, sizeof(int)));
+    h->K.dt = dt;
+    h->K.idt = 1.0 / dt;
+    for (int n = 0; n < nsteps; n++) {
+        if (n % a.every == 0) {
+            int rc = save_state(h, a.ckU + (size_t)(n / a.every) * NCO * h->K.G.S,
+                                a.ckP + (size_t)(n / a.every) * NPR * h->K.G.S);
+            if (rc) return rc;
+        }
+        enqueue_step(h);
+    }
+    int rc = save_state(h, a.endU, a.endP);
+    if (rc) return rc;
+    CK(cudaGetLastError());
+    unsigned long long st[NSTAT];
+    CK(cudaMemcpyAsync(st, h->b.stats, sizeof(st), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    h->steps += nsteps;
+    if (st[ST_NAN]) return set_err(h, RMHD_ENAN, "non-finite conserved values");
+    a.recorded = true;
+    return RMHD_OK;
+}
+
+extern "C" int rmhd_adjoint_backward(rmhd_t h, const double *lam_prims, double *grad_prims0,
+                                     double *grad_log_sigma0, int on_device)
+{
+    if (!h) return set_err(nullptr, RMHD_EINVAL, "handle is NULL");
+    AdjBuf &a = h->adj;
+    if (!a.recorded) return set_err(h, RMHD_EINVAL, "no recorded steps: call rmhd_adjoint_forward");
+    if (!lam_prims || !grad_prims0) return set_err(h, RMHD_EINVAL, "NULL array");
+    const StepConst &K = h->K;
+    const Grid &G = K.G;
+    const size_t S = (size_t)G.S;
+    const unsigned nb = nblk(G.N);
+    h->K.dt = a.dt;
+    h->K.idt = 1.0 / a.dt;
+    unsigned long long stats0[NSTAT];
+    CK(cudaMemcpyAsync(stats0, h->b.stats, sizeof(stats0), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaMemsetAsync(a.lsig, 0, sizeof(double), h->st));
+    CK(cudaMemsetAsync(a.bad, 0, sizeof(int), h->st));
+    CK(cudaMemsetAsync(a.lamU, 0, fbytes(h, NCO), h->st));
+    CK(cudaMemsetAsync(a.lamUn, 0, fbytes(h, NCO), h->st));
+    // dL/dP^N -> dL/dU^N through the last recovery
+    int rc = stage_in(h, lam_prims, NPR, on_device);
+    if (rc) return rc;
+    CK(cudaMemsetAsync(a.lamP, 0, fbytes(h, NPR), h->st));
+    k_scatter<double><<<nb, TPB, 0, h->st>>>(h->K, h->b.stage, a.lamP, NPR);
+    if (h->flat)
+        k_adj_final<true><<<nb, TPB, 0, h->st>>>(h->K, a.endU, a.endP, h->b.met, a.lamP, a.lamU,
+                                                 a.bad);
+    else
+        k_adj_final<false><<<nb, TPB, 0, h->st>>>(h->K, a.endU, a.endP, h->b.met, a.lamP,
+                                                  a.lamU, a.bad);
+    for (int seg = a.nck - 1; seg >= 0; seg--) {
+        const int s0 = seg * a.every;
+        const int s1 = s0 + a.every < a.nsteps ? s0 + a.every : a.nsteps;
+        // states s0 .. s1-1 of the segment, then P^{s1}
+        rc = load_state(h, a.ckU + (size_t)seg * NCO * S, a.ckP + (size_t)seg * NPR * S);
+        if (rc) return rc;
+        for (int n = s0; n < s1; n++) {
+            rc = save_state(h, a.segU + (size_t)(n - s0) * NCO * S,
+                            a.segP + (size_t)(n - s0) * NPR * S);
+            if (rc) return rc;
+            if (n + 1 < s1) enqueue_step(h);
+        }
+        const double *Pend = seg + 1 < a.nck ? a.ckP + (size_t)(seg + 1) * NPR * S : a.endP;
+        for (int n = s1 - 1; n >= s0; n--) {
+            const double *Pnext = n + 1 == s1 ? Pend : a.segP + (size_t)(n + 1 - s0) * NPR * S;
+            rc = load_state(h, a.segU + (size_t)(n - s0) * NCO * S,
+                            a.segP + (size_t)(n - s0) * NPR * S);
+            if (rc) return rc;
+            rc = h->flat ? adjoint_step_t<true>(h, Pnext) : adjoint_step_t<false>(h, Pnext);
+            if (rc) return rc;
+        }
+    }
+    // U^0 = prim2con(P^0)
+    if (h->flat)
+        k_adj_prim2con<true><<<nb, TPB, 0, h->st>>>(h->K, a.ckP, h->b.met, a.lamU, h->b.stage);
+    else
+        k_adj_prim2con<false><<<nb, TPB, 0, h->st>>>(h->K, a.ckP, h->b.met, a.lamU,
+                                                     h->b.stage);
+    rc = stage_out(h, grad_prims0, NPR, on_device);
+    if (rc) return rc;
+    double ls = 0.0;
+    int bad = 0;
+    CK(cudaMemcpyAsync(&ls, a.lsig, sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaMemcpyAsync(&bad, a.bad, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+    // the recorded end state and the statistics are left as the forward left them
+    rc = load_state(h, a.endU, a.endP);   // the FP64 guess lives in P
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(h->b.stats, stats0, sizeof(stats0), cudaMemcpyHostToDevice, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    CK(cudaGetLastError());
+    if (grad_log_sigma0) *grad_log_sigma0 = ls;
+    if (bad) return set_err(h, RMHD_ENAN, "singular recovery Jacobian in the adjoint");
+    return RMHD_OK;
+}
+
 extern "C" const char *rmhd_last_error(rmhd_t h) { return h ? h->err : g_noh_err; }
 
 // error text of an entry point without a handle (used by the other source file)
@@ -809,6 +1099,7 @@ extern "C" int rmhd_destroy(rmhd_t h)
 {
     if (!h) return RMHD_OK;
     cudaStreamSynchronize(h->st);
+    free_adj(h->adj);
     free_all(h->b);
     delete h;
     return RMHD_OK;
