@@ -4,7 +4,11 @@ mixed precision (FP32 reconstruction/fluxes, FP64 recovery and accumulation)
 as the headline and the FP64 path beside it.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--n 256] [--precision mixed|fp64]
+                    [--n 256] [--precision mixed|fp64] [--no-adjoint]
+                    [--adjoint-n 128] [--adjoint-steps 60] [--adjoint-every 10]
+
+The "adjoint" object times the gradient of a B^y misfit after 60 steps of
+the 128^3 Alfven cube (rmhd_adjoint_forward + rmhd_adjoint_backward).
 
 One JSON line on stdout (rank 0).  With N > 1 (torchrun) every rank runs its
 own replica of the workload on its own GPU (the method has no data-path
@@ -231,6 +235,62 @@ def roofline(wl, res, prec, steps):
     return r, ks
 
 
+# Adjoint (gradient of a loss of the primitives after K steps with respect to
+# the initial primitives and log sigma0) on the 128^3 Alfven cube: algorithmic
+# FP64 work of one face-flux adjoint taken as 3x the forward face work (the
+# cheap-gradient bound of reverse mode), per face of each direction and stage.
+ADJ_FLOPS_PER_FACE = 3 * FLUX_FLOPS_PER_FACE
+
+
+def run_adjoint(args):
+    import torch
+    import paper_2510_18968_b300 as R
+    n, K, every = args.adjoint_n, args.adjoint_steps, args.adjoint_every
+    wl = W.alfven_diag(n=n, sigma=1e3)
+    dx = wl.params["dx"]
+    dV = dx[0] * dx[1] * dx[2]
+    prim0 = np.ascontiguousarray(wl.prim)
+    s = R.Solver(dict(wl.params, sigma0=2e3))
+    s.set_prims(prim0)
+    s.step(wl.dt, K)
+    target = s.get_prims()[9].copy()
+    s.close()
+    s = R.Solver(wl.params)
+    s.set_prims(prim0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s.adjoint_forward(wl.dt, K, every)
+    torch.cuda.synchronize()
+    t_f = time.perf_counter() - t0
+    PN = s.get_prims()
+    lam = np.zeros_like(PN)
+    lam[9] = 2.0 * (PN[9] - target) * dV
+    loss = float(np.sum((PN[9] - target) ** 2) * dV)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    grad, gls, groups = s.adjoint_backward(lam, profile=True)
+    torch.cuda.synchronize()
+    t_b = time.perf_counter() - t0
+    s.close()
+    N = wl.ncells
+    nd = 3
+    faces = nd * 2 * K * N          # faces of both stages of every step
+    fl_ms = groups["adjoint_flux"]
+    ach = ADJ_FLOPS_PER_FACE * faces / (fl_ms * 1e-3) / 1e12
+    return {"workload": f"alfven_diag {n}^3 (WENO5+HLLE, sigma0=1e3, Gamma=4/3, periodic), "
+                        f"{K} steps, checkpoints every {every}; loss = sum (B^y - B^y[sigma0="
+                        f"2e3])^2 dx^3",
+            "value": N * K / (t_f + t_b), "unit": "zone-updates/s (forward + gradient)",
+            "forward_s": t_f, "backward_s": t_b, "backward_over_forward": t_b / t_f,
+            "loss": loss, "dL_dlog_sigma0": gls, "grad_max": float(np.abs(grad).max()),
+            "kernel_ms": groups,
+            "roofline": {"kernel": "k_adj_flux", "bound": "alu", "achieved": ach,
+                         "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": ach / FP64_PEAK_TFLOPS,
+                         "alg_fp64_flops_per_face": ADJ_FLOPS_PER_FACE,
+                         "launch_ms": fl_ms / (nd * 2 * K), "traffic": None}}
+
+
 def cpu_oracle_sample(nz, steps):
     """The FP64 oracle on a z-slab (nz cells thick, same x-y plane and
     options) of the 256^3 workload; returns zone-updates/s and the sample."""
@@ -255,6 +315,10 @@ def main():
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--precision", default="both", choices=["both", "mixed", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--adjoint-n", type=int, default=128)
+    ap.add_argument("--adjoint-steps", type=int, default=60)
+    ap.add_argument("--adjoint-every", type=int, default=10)
     args = ap.parse_args()
     rank, world, local = dist_env()
     cfg = {"workload": f"cyl_blast_{args.n}^3 (MC2+HLLE, sigma=1e3, Gamma=4/3, outflow, "
@@ -319,6 +383,8 @@ def main():
     ghosts = (2 if wl.params["qflux_mode"] == 0 else 1) * 2 + 1
     per_step = 3 + 3 + ghosts + 2 * nd
     line["gpu_launches"] = per_step * args.steps
+    if not args.no_adjoint:
+        line["adjoint"] = run_adjoint(args)
     if not args.no_cpu_baseline:
         v, sample = cpu_oracle_sample(4, 1)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",

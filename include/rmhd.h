@@ -240,6 +240,16 @@ int rmhd_set_sigma0(rmhd_t h, double sigma0);
  * Atmosphere resets are not an error here (rmhd_get_stats counts them). */
 int rmhd_adjoint_forward(rmhd_t h, double dt, int nsteps, int checkpoint_every);
 
+/* Kernel groups timed by rmhd_adjoint_backward (ms[], when not NULL). */
+enum {
+    RMHD_ADJ_RECOMPUTE = 0,  /* segment forward steps and the per-step recompute
+                                of the stage states (forward kernels)          */
+    RMHD_ADJ_FLUX = 1,       /* adjoint of the face fluxes (k_adj_flux)         */
+    RMHD_ADJ_SOURCES = 2,    /* adjoint of the cell sources                     */
+    RMHD_ADJ_STAGES = 3,     /* adjoint of the stage recoveries and combination */
+    RMHD_NADJPROF = 4
+};
+
 /* Reverse sweep of the recorded steps.  lam_prims[14][N] (interior, field
  * order of rmhd_set_prims) = dL/dP^N for a scalar loss L of the primitives
  * after the last recorded step.  Writes grad_prims0[14][N] = dL/dP^0 (the
@@ -249,10 +259,13 @@ int rmhd_adjoint_forward(rmhd_t h, double dt, int nsteps, int checkpoint_every);
  * differentiated).  Each segment is recomputed from its checkpoint.  On
  * return the state, the statistics and the recording are as
  * rmhd_adjoint_forward left them, so it may be called again with another
- * lam_prims.  on_device as for rmhd_set_prims.  Errors: RMHD_EINVAL (no
+ * lam_prims.  on_device as for rmhd_set_prims.  ms (may be NULL): CUDA-event
+ * milliseconds of the kernel groups RMHD_ADJ_* summed over the sweep (the
+ * stream waits for each group's events).  Errors: RMHD_EINVAL (no
  * recording, NULL array), RMHD_ENAN (a singular recovery Jacobian). */
 int rmhd_adjoint_backward(rmhd_t h, const double *lam_prims, double *grad_prims0,
-                          double *grad_log_sigma0, int on_device);
+                          double *grad_log_sigma0, int on_device,
+                          double ms[RMHD_NADJPROF]);
 
 const char *rmhd_last_error(rmhd_t h);
 

@@ -96,7 +96,8 @@ def load(build_if_missing=True):
                                                vp]
     L.rmhd_set_sigma0.argtypes = [vp, d]
     L.rmhd_adjoint_forward.argtypes = [vp, d, i, i]
-    L.rmhd_adjoint_backward.argtypes = [vp, vp, vp, ctypes.POINTER(ctypes.c_double), i]
+    L.rmhd_adjoint_backward.argtypes = [vp, vp, vp, ctypes.POINTER(ctypes.c_double), i,
+                                        ctypes.POINTER(ctypes.c_double)]
     L.rmhd_last_error.argtypes = [vp]
     L.rmhd_last_error.restype = ctypes.c_char_p
     L.rmhd_destroy.argtypes = [vp]
@@ -275,8 +276,11 @@ class Solver:
         return self._check(self.L.rmhd_adjoint_forward(self.h, float(dt), int(nsteps),
                                                        int(checkpoint_every)))
 
-    def adjoint_backward(self, lam_prims, out=None):
-        """(dL/dP^0, dL/dlog sigma0) for lam_prims = dL/dP^N (14, nz, ny, nx)."""
+    ADJOINT_GROUPS = ("recompute", "adjoint_flux", "adjoint_sources", "adjoint_stages")
+
+    def adjoint_backward(self, lam_prims, out=None, profile=False):
+        """(dL/dP^0, dL/dlog sigma0) for lam_prims = dL/dP^N (14, nz, ny, nx);
+        with profile=True also a dict of CUDA-event ms per kernel group."""
         if out is None:
             if _is_torch(lam_prims) and lam_prims.is_cuda:
                 import torch
@@ -288,7 +292,10 @@ class Solver:
         if d != d2:
             raise TypeError("lam_prims and out must both be host or both be device arrays")
         ls = ctypes.c_double()
-        self._check(self.L.rmhd_adjoint_backward(self.h, pl, po, ctypes.byref(ls), d))
+        ms = (ctypes.c_double * 4)() if profile else None
+        self._check(self.L.rmhd_adjoint_backward(self.h, pl, po, ctypes.byref(ls), d, ms))
+        if profile:
+            return out, ls.value, dict(zip(self.ADJOINT_GROUPS, list(ms)))
         return out, ls.value
 
     def rhs(self, prim, J=None, out=None):

@@ -921,30 +921,84 @@ template <bool FLAT> static void launch_adj_flux(rmhd_t h, const double *P, cons
 #undef RMHD_ADJ_FLUX
 }
 
+// events bracketing the kernel groups of the backward sweep (profiling)
+struct AdjTimer {
+    bool on = false;
+    cudaStream_t st = nullptr;
+    struct Mark {
+        cudaEvent_t a, b;
+        int g;
+    };
+    Mark m[4096];
+    int n = 0;
+    int open = -1;
+    void begin(int g)
+    {
+        if (!on || n >= 4096) return;
+        cudaEventCreate(&m[n].a);
+        cudaEventCreate(&m[n].b);
+        m[n].g = g;
+        cudaEventRecord(m[n].a, st);
+        open = n++;
+    }
+    void end()
+    {
+        if (!on || open < 0) return;
+        cudaEventRecord(m[open].b, st);
+        open = -1;
+    }
+    void collect(double *ms)
+    {
+        for (int g = 0; g < RMHD_NADJPROF; g++) ms[g] = 0.0;
+        for (int i = 0; i < n; i++) {
+            float t = 0.f;
+            cudaEventElapsedTime(&t, m[i].a, m[i].b);
+            ms[m[i].g] += t;
+            cudaEventDestroy(m[i].a);
+            cudaEventDestroy(m[i].b);
+        }
+        n = 0;
+    }
+};
+
 // lamU <- dL/dU^n from lamU = dL/dU^{n+1}; the handle holds U^n, P^n
-template <bool FLAT> static int adjoint_step_t(rmhd_t h, const double *Pnext)
+template <bool FLAT> static int adjoint_step_t(rmhd_t h, const double *Pnext, AdjTimer &tm)
 {
     AdjBuf &a = h->adj;
     Buffers &b = h->b;
     const StepConst &K = h->K;
     const unsigned nb = nblk(K.G.N);
+    tm.begin(RMHD_ADJ_RECOMPUTE);
     // cells the final recovery reset keep no derivative in D, S_i, tau
     k_adj_reset_mask<<<nb, TPB, 0, h->st>>>(K, Pnext, a.lamU);
     enqueue_recompute_t<FLAT>(h);
+    tm.end();
     const double *P1 = (const double *)b.PA, *P2 = (const double *)b.PB;
     const double *J1 = (const double *)b.J1, *J2 = (const double *)b.J2;
     // F(P2, J2) entered U^{n+1} with weight dt/2
+    tm.begin(RMHD_ADJ_SOURCES);
     k_adj_sources<FLAT><<<nb, TPB, 0, h->st>>>(K, P2, b.met, a.lamU, 0.5 * K.dt, a.lamP);
     CK(cudaMemsetAsync(a.lamJ, 0, fbytes(h, 3), h->st));
+    tm.end();
+    tm.begin(RMHD_ADJ_FLUX);
     launch_adj_flux<FLAT>(h, P2, J2, a.lamU, 0.5 * K.dt);
+    tm.end();
+    tm.begin(RMHD_ADJ_STAGES);
     k_adj_stage2<FLAT><<<nb, TPB, 0, h->st>>>(K, a.Us, P2, b.met, b.sig, a.lamU, a.lamP, a.lamJ,
                                               a.lamR1, a.lamdR1, a.lamUn, a.lsig, a.bad);
+    tm.end();
     // F(P1, J1): its adjoint is lamR1
+    tm.begin(RMHD_ADJ_SOURCES);
     k_adj_sources<FLAT><<<nb, TPB, 0, h->st>>>(K, P1, b.met, a.lamR1, 1.0, a.lamP);
     CK(cudaMemsetAsync(a.lamJ, 0, fbytes(h, 3), h->st));
+    tm.end();
+    tm.begin(RMHD_ADJ_FLUX);
     launch_adj_flux<FLAT>(h, P1, J1, a.lamR1, 1.0);
+    tm.end();
+    tm.begin(RMHD_ADJ_STAGES);
     k_adj_stage1<FLAT><<<nb, TPB, 0, h->st>>>(K, b.U, P1, b.met, b.sig, a.lamP, a.lamJ, a.lamdR1,
                                               a.lamUn, a.lsig, a.bad);
+    tm.end();
     double *t = a.lamU;
     a.lamU = a.lamUn;
     a.lamUn = t;
@@ -1013,7 +1067,8 @@ extern "C" int rmhd_adjoint_forward(rmhd_t h, double dt, int nsteps, int checkpo
 }
 
 extern "C" int rmhd_adjoint_backward(rmhd_t h, const double *lam_prims, double *grad_prims0,
-                                     double *grad_log_sigma0, int on_device)
+                                     double *grad_log_sigma0, int on_device,
+                                     double ms[RMHD_NADJPROF])
 {
     if (!h) return set_err(nullptr, RMHD_EINVAL, "handle is NULL");
     AdjBuf &a = h->adj;
@@ -1025,6 +1080,10 @@ extern "C" int rmhd_adjoint_backward(rmhd_t h, const double *lam_prims, double *
     const unsigned nb = nblk(G.N);
     h->K.dt = a.dt;
     h->K.idt = 1.0 / a.dt;
+    static thread_local AdjTimer tm;
+    tm.on = ms != nullptr;
+    tm.st = h->st;
+    tm.n = 0;
     unsigned long long stats0[NSTAT];
     CK(cudaMemcpyAsync(stats0, h->b.stats, sizeof(stats0), cudaMemcpyDeviceToHost, h->st));
     CK(cudaMemsetAsync(a.lsig, 0, sizeof(double), h->st));
@@ -1046,6 +1105,7 @@ extern "C" int rmhd_adjoint_backward(rmhd_t h, const double *lam_prims, double *
         const int s0 = seg * a.every;
         const int s1 = s0 + a.every < a.nsteps ? s0 + a.every : a.nsteps;
         // states s0 .. s1-1 of the segment, then P^{s1}
+        tm.begin(RMHD_ADJ_RECOMPUTE);
         rc = load_state(h, a.ckU + (size_t)seg * NCO * S, a.ckP + (size_t)seg * NPR * S);
         if (rc) return rc;
         for (int n = s0; n < s1; n++) {
@@ -1054,13 +1114,17 @@ extern "C" int rmhd_adjoint_backward(rmhd_t h, const double *lam_prims, double *
             if (rc) return rc;
             if (n + 1 < s1) enqueue_step(h);
         }
+        tm.end();
         const double *Pend = seg + 1 < a.nck ? a.ckP + (size_t)(seg + 1) * NPR * S : a.endP;
         for (int n = s1 - 1; n >= s0; n--) {
             const double *Pnext = n + 1 == s1 ? Pend : a.segP + (size_t)(n + 1 - s0) * NPR * S;
+            tm.begin(RMHD_ADJ_RECOMPUTE);
             rc = load_state(h, a.segU + (size_t)(n - s0) * NCO * S,
                             a.segP + (size_t)(n - s0) * NPR * S);
+            tm.end();
             if (rc) return rc;
-            rc = h->flat ? adjoint_step_t<true>(h, Pnext) : adjoint_step_t<false>(h, Pnext);
+            rc = h->flat ? adjoint_step_t<true>(h, Pnext, tm)
+                         : adjoint_step_t<false>(h, Pnext, tm);
             if (rc) return rc;
         }
     }
@@ -1083,6 +1147,7 @@ extern "C" int rmhd_adjoint_backward(rmhd_t h, const double *lam_prims, double *
     CK(cudaStreamSynchronize(h->st));
     CK(cudaGetLastError());
     if (grad_log_sigma0) *grad_log_sigma0 = ls;
+    if (ms) tm.collect(ms);
     if (bad) return set_err(h, RMHD_ENAN, "singular recovery Jacobian in the adjoint");
     return RMHD_OK;
 }
