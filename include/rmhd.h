@@ -234,8 +234,9 @@ int rmhd_set_sigma0(rmhd_t h, double sigma0);
  * record the trajectory for rmhd_adjoint_backward: the state (U and P,
  * 28 FP64 fields of the padded grid) every checkpoint_every steps, plus
  * scratch for one segment of checkpoint_every + 1 states and the adjoint
- * fields (about 40 + 28 (nsteps / checkpoint_every + checkpoint_every)
- * padded FP64 fields in all).  Replaces any earlier recording.  Errors:
+ * fields (about 130 + 28 (nsteps / checkpoint_every + checkpoint_every)
+ * padded FP64 fields in all; 90 of them hold the per-face stencil
+ * contributions of the flux adjoint).  Replaces any earlier recording.  Errors:
  * RMHD_EINVAL, RMHD_ENOMEM, RMHD_ENAN (non-finite state; nothing recorded).
  * Atmosphere resets are not an error here (rmhd_get_stats counts them). */
 int rmhd_adjoint_forward(rmhd_t h, double dt, int nsteps, int checkpoint_every);
@@ -259,7 +260,8 @@ enum {
  * differentiated).  Each segment is recomputed from its checkpoint.  On
  * return the state, the statistics and the recording are as
  * rmhd_adjoint_forward left them, so it may be called again with another
- * lam_prims.  on_device as for rmhd_set_prims.  ms (may be NULL): CUDA-event
+ * lam_prims.  The sweep is deterministic (fixed summation order).
+ * on_device as for rmhd_set_prims.  ms (may be NULL): CUDA-event
  * milliseconds of the kernel groups RMHD_ADJ_* summed over the sweep (the
  * stream waits for each group's events).  Errors: RMHD_EINVAL (no
  * recording, NULL array), RMHD_ENAN (a singular recovery Jacobian). */

@@ -9,8 +9,10 @@
 //             J2 = Q* v2 - dR2/(alpha dt)
 //   final     U^{n+1} = U^n + dt/2 (F(P1, J1) + F(P2, J2)) + (dR1 + dR2)/2
 // F(P, J) = sources(P) - sum_d (F_d(i+1/2) - F_d(i-1/2))/dx_d with the face
-// flux HLLE(recon(P, J)).  The local Jacobians come from the forward device
-// code evaluated on dual numbers; the recovery is differentiated at its
+// flux HLLE(recon(P, J)).  The face flux is reversed by hand (WENO5 / TVD
+// gradients and the reverse of the one-side face physics); the sources and
+// prim-to-con Jacobians come from the forward device code evaluated on dual
+// numbers; the recovery is differentiated at its
 // converged root by the implicit-function theorem, so the iteration that
 // found the root (paper iteration or fallback) does not matter.  Branches
 // (limiters, first-order fallbacks, atmosphere resets) are frozen at the
@@ -228,22 +230,27 @@ __device__ double stage_adjoint(const StepConst &K, const Met<double> &m, const 
     return lcc * cc;
 }
 
-// block sum of v into *out (one atomic per block)
-__device__ __forceinline__ void block_add(double v, double *out)
+// Fixed-order sum of the per-cell values v (padded layout) over the
+// interior, one block: each thread sums a strided subset in order, then a
+// shared-memory tree.  *out = the sum.
+__global__ void __launch_bounds__(1024)
+k_adj_sum(const StepConst K, const double *__restrict__ v, double *out)
 {
-    __shared__ double part[32];
-    const unsigned full = 0xffffffffu;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(full, v, o);
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    if (l == 0) part[w] = v;
-    __syncthreads();
-    if (w == 0) {
-        v = l < (int)(blockDim.x >> 5) ? part[l] : 0.0;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(full, v, o);
-        if (l == 0 && v != 0.0) atomicAdd(out, v);
+    __shared__ double part[1024];
+    const Grid &G = K.G;
+    double acc = 0.0;
+    for (long long t = threadIdx.x; t < G.N; t += blockDim.x) {
+        int i, j, k;
+        interior_coords(G, t, i, j, k);
+        acc += v[cell_at(G, i, j, k)];
     }
+    part[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) part[threadIdx.x] += part[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = part[0];
 }
 
 // ------------------------------------------------------------ kernels
@@ -307,53 +314,236 @@ k_adj_sources(const StepConst K, const double *__restrict__ P, const double *__r
     }
 }
 
-// cell index of stencil coordinate x along D mapped into the interior by
-// the boundary condition (periodic wrap, outflow copy-nearest)
-__device__ __forceinline__ long long map_cell(const Grid &G, int D, long long c_at0, int x)
+// Gradient of the WENO5 face value (Jiang-Shu weights, as reconstruct
+// forms it) with respect to its five stencil values:
+//   u = sum_k w_k q_k / sum_k w_k,  w_k = d_k / (eps + beta_k)^2,
+//   du/ds = sum_k [omega_k dq_k/ds - 2 omega_k (q_k - u)/(eps + beta_k) dbeta_k/ds].
+__device__ __forceinline__ void weno5_grad(double a, double b, double c, double d, double e,
+                                           double g[5])
 {
-    const int n = G.n[D];
-    int y = x;
-    if (G.bc[D] == 0) {
-        y = x % n;
-        if (y < 0) y += n;
-    } else {
-        y = x < 0 ? 0 : (x >= n ? n - 1 : x);
-    }
-    return c_at0 + (long long)y * dstride(G, D);
+    const double eps = 1e-6, sixth = 1.0 / 6.0, k13 = 13.0 / 12.0;
+    const double q0 = (2.0 * a - 7.0 * b + 11.0 * c) * sixth;
+    const double q1 = (-b + 5.0 * c + 2.0 * d) * sixth;
+    const double q2 = (2.0 * c + 5.0 * d - e) * sixth;
+    const double t10 = a - 2.0 * b + c, t20 = a - 4.0 * b + 3.0 * c;
+    const double t11 = b - 2.0 * c + d, t21 = b - d;
+    const double t12 = c - 2.0 * d + e, t22 = 3.0 * c - 4.0 * d + e;
+    const double b0 = k13 * t10 * t10 + 0.25 * t20 * t20;
+    const double b1 = k13 * t11 * t11 + 0.25 * t21 * t21;
+    const double b2 = k13 * t12 * t12 + 0.25 * t22 * t22;
+    const double i0 = 1.0 / (eps + b0), i1 = 1.0 / (eps + b1), i2 = 1.0 / (eps + b2);
+    const double w0 = 0.1 * i0 * i0, w1 = 0.6 * i1 * i1, w2 = 0.3 * i2 * i2;
+    const double iW = 1.0 / (w0 + w1 + w2);
+    const double o0 = w0 * iW, o1 = w1 * iW, o2 = w2 * iW;
+    const double u = o0 * q0 + o1 * q1 + o2 * q2;
+    const double c0 = -2.0 * o0 * (q0 - u) * i0;
+    const double c1 = -2.0 * o1 * (q1 - u) * i1;
+    const double c2 = -2.0 * o2 * (q2 - u) * i2;
+    // dbeta_k / d(its three points), times c_k
+    const double p0 = 2.0 * k13 * t10 * c0, r0 = 0.5 * t20 * c0;
+    const double p1 = 2.0 * k13 * t11 * c1, r1 = 0.5 * t21 * c1;
+    const double p2 = 2.0 * k13 * t12 * c2, r2 = 0.5 * t22 * c2;
+    g[0] = o0 * 2.0 * sixth + p0 + r0;
+    g[1] = -o0 * 7.0 * sixth - o1 * sixth - 2.0 * p0 - 4.0 * r0 + p1 + r1;
+    g[2] = o0 * 11.0 * sixth + o1 * 5.0 * sixth + o2 * 2.0 * sixth + p0 + 3.0 * r0 - 2.0 * p1 +
+           p2 + 3.0 * r2;
+    g[3] = o1 * 2.0 * sixth + o2 * 5.0 * sixth + p1 - r1 - 2.0 * p2 - 4.0 * r2;
+    g[4] = -o2 * sixth + p2 + r2;
 }
 
-// one side of a face: lam_k = d(lambda . (cF F + cU U))/d pr_k, k < 15
-// (14 primitives and the charge-flux current J^D), forward-mode one input
-// at a time
+// gradient of the TVD slope of (um, u0, up): the selected candidate's
+template <int RC>
+__device__ __forceinline__ void tvd_slope_grad(double um, double u0, double up, double g[3])
+{
+    g[0] = g[1] = g[2] = 0.0;
+    if (RC == RC_MINMOD) {
+        const double x = u0 - um, y = up - u0;
+        if (x * y <= 0.0) return;
+        if (fabs(x) <= fabs(y)) { g[0] = -1.0; g[1] = 1.0; }
+        else { g[1] = -1.0; g[2] = 1.0; }
+        return;
+    }
+    const double a = 2.0 * (u0 - um), b = 0.5 * (up - um), c = 2.0 * (up - u0);
+    int pick = -1;   // the argument mm3 returns: fmin(a, fmin(b, c)) or fmax(...)
+    if (a > 0.0 && b > 0.0 && c > 0.0) {
+        const int bc = c < b ? 2 : 1;
+        const double vbc = bc == 2 ? c : b;
+        pick = vbc < a ? bc : 0;
+    } else if (a < 0.0 && b < 0.0 && c < 0.0) {
+        const int bc = c > b ? 2 : 1;
+        const double vbc = bc == 2 ? c : b;
+        pick = vbc > a ? bc : 0;
+    }
+    if (pick == 0) { g[0] = -2.0; g[1] = 2.0; }
+    if (pick == 1) { g[0] = -0.5; g[2] = 0.5; }
+    if (pick == 2) { g[1] = -2.0; g[2] = 2.0; }
+}
+
+// d uL / d s[0..5] and d uR / d s[0..5] of reconstruct<double, RC>
+template <int RC>
+__device__ __forceinline__ void recon_grad(const double s[6], double dL[6], double dR[6])
+{
+    for (int o = 0; o < 6; o++) dL[o] = dR[o] = 0.0;
+    if (RC == RC_WENO5) {
+        double g[5];
+        weno5_grad(s[0], s[1], s[2], s[3], s[4], g);
+        for (int k = 0; k < 5; k++) dL[k] = g[k];
+        weno5_grad(s[5], s[4], s[3], s[2], s[1], g);
+        for (int k = 0; k < 5; k++) dR[5 - k] = g[k];
+    } else {
+        double g[3];
+        tvd_slope_grad<RC>(s[1], s[2], s[3], g);
+        dL[1] = 0.5 * g[0];
+        dL[2] = 1.0 + 0.5 * g[1];
+        dL[3] = 0.5 * g[2];
+        tvd_slope_grad<RC>(s[2], s[3], s[4], g);
+        dR[2] = -0.5 * g[0];
+        dR[3] = 1.0 - 0.5 * g[1];
+        dR[4] = -0.5 * g[2];
+    }
+}
+
+// One side of a face, reverse mode written out from flux_accumulate:
+// lam_k = d/dpr_k of sum_f lf_f (cF F_f + cU U_f) at the state pr (14
+// primitives, then the charge-flux current J^D in slot 14).
 template <bool FLAT, int D>
-__device__ __forceinline__ void side_vjp(const double pr0[NPR + 1], const Met<double> &m,
+__device__ __forceinline__ void side_vjp(const double pr[NPR + 1], const Met<double> &m,
                                          double gfac, double cF, double cU, const double lf[NCO],
                                          double lam[NPR + 1])
 {
-    const Met<Dual<1>> md = met_cast<Dual<1>>(m);
-#pragma unroll 1
-    for (int kk = 0; kk <= NPR; kk++) {
-        Dual<1> pr[NPR];
-        for (int f = 0; f < NPR; f++) pr[f] = Dual<1>(pr0[f]);
-        Dual<1> J(pr0[NPR]);
-        if (kk < NPR) pr[kk].d[0] = 1.0;
-        else J.d[0] = 1.0;
-        WeightedAcc<Dual<1>> acc{lf, Dual<1>(0.0)};
-        flux_accumulate<Dual<1>, FLAT, D>(pr, md, Dual<1>(0.0), Dual<1>(gfac), true, J,
-                                          Dual<1>(cF), Dual<1>(cU), acc);
-        lam[kk] = acc.sum.d[0];
+    const double sg = FLAT ? 1.0 : m.sg, a = FLAT ? 1.0 : m.alpha;
+    const double bD = FLAT ? 0.0 : m.beta[D];
+    double wF[NCO], wU[NCO];
+#pragma unroll
+    for (int f = 0; f < NCO; f++) {
+        wF[f] = lf[f] * cF;
+        wU[f] = lf[f] * cU;
     }
+    // forward values
+    const double v[3] = {pr[PR_VX], pr[PR_VY], pr[PR_VZ]};
+    const double E[3] = {pr[PR_EX], pr[PR_EY], pr[PR_EZ]};
+    const double B[3] = {pr[PR_BX], pr[PR_BY], pr[PR_BZ]};
+    double vl[3], El[3], Bl[3];
+    lower<double, FLAT>(m, v, vl);
+    lower<double, FLAT>(m, E, El);
+    lower<double, FLAT>(m, B, Bl);
+    const double rho = pr[PR_RHO];
+    const double v2 = dot3(v, vl);
+    const double W = 1.0 / sqrt(1.0 - v2);
+    const double h = rho + gfac * pr[PR_P];
+    const double hW2 = h * W * W;
+    const double Dc = sg * rho * W;
+    // adjoints of the intermediates
+    const double lTau = wU[CO_TAU] - bD * wF[CO_TAU];
+    double lS[3], lst[3], lv[3] = {0, 0, 0}, lvl[3], lE[3], lEl[3], lB[3], lBl[3];
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+        const double gDi = FLAT ? (i == D ? 1.0 : 0.0) : m.gi[sym(D, i)];
+        lS[i] = wU[CO_SX + i] - bD * wF[CO_SX + i] + wF[CO_TAU] * a * gDi;   // S, S^D
+        lst[i] = wF[CO_SX + i] * a * sg;                                     // stress row
+        lvl[i] = lEl[i] = lBl[i] = 0.0;
+    }
+    double lDc = wF[CO_D] * (a * v[D] - bD) + wU[CO_D] - wF[CO_TAU] * a * v[D] - lTau;
+    lv[D] += (wF[CO_D] - wF[CO_TAU]) * a * Dc;
+    double lhW2 = 0.0, lp = 0.0, lem = 0.0;
+    lE[0] = lE[1] = lE[2] = lB[0] = lB[1] = lB[2] = 0.0;
+    // st_i = hW2 v^D v_i - E^D E_i - B^D B_i + delta_iD (p + em)
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+        lhW2 += lst[i] * v[D] * vl[i];
+        lv[D] += lst[i] * hW2 * vl[i];
+        lvl[i] += lst[i] * hW2 * v[D];
+        lE[D] -= lst[i] * El[i];
+        lEl[i] -= lst[i] * E[D];
+        lB[D] -= lst[i] * Bl[i];
+        lBl[i] -= lst[i] * B[D];
+    }
+    lp += lst[D];
+    lem += lst[D];
+    // S_i = sg (hW2 v_i + sg (E x B)_i)
+    double lExB[3];
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+        lhW2 += lS[i] * sg * vl[i];
+        lvl[i] += lS[i] * sg * hW2;
+        lExB[i] = lS[i] * sg * sg;
+    }
+    // tau = sg (hW2 - p + em) - D
+    lhW2 += lTau * sg;
+    lp -= lTau * sg;
+    lem += lTau * sg;
+    // E x B
+    {
+        double t[3];
+        cross3(B, lExB, t);
+        for (int i = 0; i < 3; i++) lE[i] += t[i];
+        cross3(lExB, E, t);
+        for (int i = 0; i < 3; i++) lB[i] += t[i];
+    }
+    // calB^i, calE^i rows and the cleaning potentials
+    double lPhi = wU[CO_PHI] - bD * wF[CO_PHI], lPsi = wU[CO_PSI] - bD * wF[CO_PSI];
+    double leE[3], leB[3];
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+        const double gid = FLAT ? (i == D ? 1.0 : 0.0) : m.gi[sym(i, D)];
+        leE[i] = wF[CO_BX + i] * a;
+        lPhi += wF[CO_BX + i] * a * gid;
+        leB[i] = -wF[CO_EX + i] * a;
+        lPsi += wF[CO_EX + i] * a * gid;
+        lB[i] += (wU[CO_BX + i] - bD * wF[CO_BX + i]) * sg;
+        lE[i] += (wU[CO_EX + i] - bD * wF[CO_EX + i]) * sg;
+    }
+    if (D == 0) {
+        lEl[2] -= leE[1]; lEl[1] += leE[2]; lBl[2] -= leB[1]; lBl[1] += leB[2];
+    } else if (D == 1) {
+        lEl[2] += leE[0]; lEl[0] -= leE[2]; lBl[2] += leB[0]; lBl[0] -= leB[2];
+    } else {
+        lEl[1] -= leE[0]; lEl[0] += leE[1]; lBl[1] -= leB[0]; lBl[0] += leB[1];
+    }
+    lB[D] += wF[CO_PHI] * a * sg;
+    lE[D] += wF[CO_PSI] * a * sg;
+    // em = (E.E_lower + B.B_lower)/2
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+        lE[i] += lem * El[i];
+        lB[i] += lem * Bl[i];
+    }
+    // hW2 = h W^2, h = rho + gfac p, Dc = sg rho W, W = (1 - v.v_lower)^(-1/2)
+    const double lh = lhW2 * W * W;
+    const double lW = lhW2 * 2.0 * h * W + lDc * sg * rho;
+    const double lv2 = lW * 0.5 * W * W * W;
+    lam[PR_RHO] = lh + lDc * sg * W;
+    lam[PR_P] = lp + lh * gfac;
+    double t[3];
+    lower<double, FLAT>(m, lvl, t);
+#pragma unroll
+    for (int i = 0; i < 3; i++) lam[PR_VX + i] = lv[i] + 2.0 * lv2 * vl[i] + t[i];
+    lower<double, FLAT>(m, lEl, t);
+#pragma unroll
+    for (int i = 0; i < 3; i++) lam[PR_EX + i] = lE[i] + t[i];
+    lower<double, FLAT>(m, lBl, t);
+#pragma unroll
+    for (int i = 0; i < 3; i++) lam[PR_BX + i] = lB[i] + t[i];
+    lam[PR_PSI] = lPsi * sg;
+    lam[PR_PHI] = lPhi * sg;
+    const double lQc = wU[CO_Q] - bD * wF[CO_Q];
+    lam[PR_Q] = lQc * sg;
+    lam[NPR] = wF[CO_Q] * a;   // J^D
 }
 
 // Adjoint of the face fluxes of direction D (stage current in the charge
 // flux): lambda_face = scale (lamR(cR) - lamR(cL))/dx_D from the flux
 // difference, then through HLLE, the face physics of each side and the
-// reconstruction (or the first-order fallback) into lamP and lamJ (atomic).
+// reconstruction (or the first-order fallback).  The contribution of the
+// face to each of its six stencil cells (field f, slot o = cell iD - 3 + o)
+// is stored at C[(o * 15 + f) S + face]; k_adj_gather sums them per cell.
+enum { ADJ_NF = NPR + 1, ADJ_SLOTS = 6 };
+
 template <bool FLAT, int RC, int D>
 __global__ void __launch_bounds__(128)
 k_adj_flux(const StepConst K, const double *__restrict__ P, const double *__restrict__ Jc,
            const double *__restrict__ met, const double *__restrict__ lamR, double scale,
-           double *lamP, double *lamJ)
+           double *C)
 {
     const Grid &G = K.G;
     long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -368,8 +558,6 @@ k_adj_flux(const StepConst K, const double *__restrict__ P, const double *__rest
     const long long s = dstride(G, D);
     const long long cL = cR - s;
     const long long S = G.S;
-    const int iD = D == 0 ? i : (D == 1 ? j : k);
-    const long long c0 = cR - (long long)iD * s;   // coordinate 0 along D
 
     double lf[NCO];
     bool any = false;
@@ -379,7 +567,10 @@ k_adj_flux(const StepConst K, const double *__restrict__ P, const double *__rest
         lf[f] = w * (lamR[f * S + cR] - lamR[f * S + cL]);
         any = any || lf[f] != 0.0;
     }
-    if (!any) return;
+    if (!any) {
+        for (int q = 0; q < ADJ_SLOTS * ADJ_NF; q++) C[q * S + cR] = 0.0;
+        return;
+    }
 
     // primal face states (as the flux kernel forms them)
     double pL[NPR + 1], pR[NPR + 1];
@@ -431,45 +622,74 @@ k_adj_flux(const StepConst K, const double *__restrict__ P, const double *__rest
     side_vjp<FLAT, D>(pL, m, K.gfac, cFL, -cUU, lf, lamL);
     side_vjp<FLAT, D>(pR, m, K.gfac, cFR, cUU, lf, lamRr);
 
-    // through the reconstruction to the stencil cells
+    // through the reconstruction to the six stencil cells
 #pragma unroll 1
     for (int f = 0; f <= NPR; f++) {
-        double *dst = f < NPR ? lamP + f * S : lamJ + D * S;
         const double *q = (f < NPR ? P + f * S : Jc + D * S) + cL;
-        if (!fb[0] || !fb[1]) {
-            Dual<6> st[6];
-            for (int o = 0; o < 6; o++)
-                st[o] = (RC == RC_WENO5 || (o > 0 && o < 5)) ? seed<6>(q[(o - 2) * s], o)
-                                                              : Dual<6>(0.0);
-            Dual<6> uL, uR;
-            reconstruct<Dual<6>, RC>(st, uL, uR);
-            for (int o = 0; o < 6; o++) {
-                double g = 0.0;
-                if (!fb[0]) g += lamL[f] * uL.d[o];
-                if (!fb[1]) g += lamRr[f] * uR.d[o];
-                if (g != 0.0) atomicAdd(dst + map_cell(G, D, c0, iD - 3 + o), g);
+        double st[6], dL[6], dR[6], g[6];
+        for (int o = 0; o < 6; o++)
+            st[o] = (RC == RC_WENO5 || (o > 0 && o < 5)) ? q[(o - 2) * s] : 0.0;
+        recon_grad<RC>(st, dL, dR);
+        for (int o = 0; o < 6; o++)
+            g[o] = (fb[0] ? 0.0 : lamL[f] * dL[o]) + (fb[1] ? 0.0 : lamRr[f] * dR[o]);
+        if (fb[0]) g[2] += lamL[f];    // first order: the cell below the face
+        if (fb[1]) g[3] += lamRr[f];   // the cell above
+        for (int o = 0; o < 6; o++) C[(o * ADJ_NF + f) * S + cR] = g[o];
+    }
+}
+
+// Sum of the stencil contributions of direction D's faces into every
+// interior cell, in a fixed order: lamP (14 fields) and lamJ[D] +=.  A ghost
+// position counts for the interior cell the boundary condition copies into
+// it (periodic wrap; outflow: the boundary cell).
+template <int D>
+__global__ void __launch_bounds__(128)
+k_adj_gather(const StepConst K, const double *__restrict__ C, double *lamP, double *lamJ)
+{
+    const Grid &G = K.G;
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= G.N) return;
+    int i, j, k;
+    interior_coords(G, t, i, j, k);
+    const long long c = cell_at(G, i, j, k), S = G.S, s = dstride(G, D);
+    const int x = D == 0 ? i : (D == 1 ? j : k), n = G.n[D];
+    const long long c0 = c - (long long)x * s;
+    int img[4], ni = 0;
+    img[ni++] = x;
+    if (G.bc[D] == 0) {
+        if (x - n >= -3) img[ni++] = x - n;
+        if (x + n <= n + 2) img[ni++] = x + n;
+    } else {
+        if (x == 0) { img[ni++] = -1; img[ni++] = -2; img[ni++] = -3; }
+        if (x == n - 1) { img[ni++] = n; img[ni++] = n + 1; img[ni++] = n + 2; }
+    }
+#pragma unroll 1
+    for (int f = 0; f < ADJ_NF; f++) {
+        double sum = 0.0;
+        for (int m = 0; m < ni; m++)
+            for (int o = 0; o < ADJ_SLOTS; o++) {
+                const int face = img[m] + 3 - o;
+                if (face >= 0 && face <= n) sum += C[(o * ADJ_NF + f) * S + c0 + face * s];
             }
-        }
-        if (fb[0] && lamL[f] != 0.0) atomicAdd(dst + map_cell(G, D, c0, iD - 1), lamL[f]);
-        if (fb[1] && lamRr[f] != 0.0) atomicAdd(dst + map_cell(G, D, c0, iD), lamRr[f]);
+        if (f < NPR) lamP[f * S + c] += sum;
+        else lamJ[D * S + c] += sum;
     }
 }
 
 // Stage 2 and the final combination, per cell.  In: lamU = dL/dU^{n+1},
 // lamP2 / lamJ2 from the adjoint of F(P2, J2) (with scale dt/2).  Out: the
 // adjoint of F(P1, J1) (lamR1), of Dt R1 (lamdR1), the part of dL/dU^n
-// found so far (lamUn), and dL/dlog sigma0 (summed into *lsig).
+// found so far (lamUn), and the cell's dL/dlog sigma0 (added to lsigc[c]).
 template <bool FLAT>
 __global__ void __launch_bounds__(128)
 k_adj_stage2(const StepConst K, const double *__restrict__ Us, const double *__restrict__ P2,
              const double *__restrict__ met, const double *__restrict__ sig,
              const double *__restrict__ lamU, const double *__restrict__ lamP2,
              const double *__restrict__ lamJ2, double *lamR1, double *lamdR1, double *lamUn,
-             double *lsig, int *bad)
+             double *lsigc, int *bad)
 {
     const Grid &G = K.G;
     const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    double contrib = 0.0;
     if (t < G.N) {
         int i, j, k;
         interior_coords(G, t, i, j, k);
@@ -486,7 +706,7 @@ k_adj_stage2(const StepConst K, const double *__restrict__ Us, const double *__r
             lj[a] = lamJ2[a * S + c];
             ldr[a] = 0.5 * lamU[(CO_EX + a) * S + c];   // U^{n+1} holds (dR1 + dR2)/2
         }
-        contrib = stage_adjoint<FLAT>(K, m, sig, c, us, pr, lp, lj, ldr, lus, bad);
+        lsigc[c] += stage_adjoint<FLAT>(K, m, sig, c, us, pr, lp, lj, ldr, lus, bad);
         const double dt = K.dt, hdt = 0.5 * dt, a12 = 1.0 - 2.0 * K.gimex;
         for (int f = 0; f < NCO; f++) {
             const double l = lamU[f * S + c];
@@ -496,7 +716,6 @@ k_adj_stage2(const StepConst K, const double *__restrict__ Us, const double *__r
         for (int a = 0; a < 3; a++)
             lamdR1[a * S + c] = 0.5 * lamU[(CO_EX + a) * S + c] + a12 * lus[CO_EX + a];
     }
-    block_add(contrib, lsig);
 }
 
 // Stage 1, per cell: completes lamUn = dL/dU^n.
@@ -505,11 +724,10 @@ __global__ void __launch_bounds__(128)
 k_adj_stage1(const StepConst K, const double *__restrict__ U, const double *__restrict__ P1,
              const double *__restrict__ met, const double *__restrict__ sig,
              const double *__restrict__ lamP1, const double *__restrict__ lamJ1,
-             const double *__restrict__ lamdR1, double *lamUn, double *lsig, int *bad)
+             const double *__restrict__ lamdR1, double *lamUn, double *lsigc, int *bad)
 {
     const Grid &G = K.G;
     const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    double contrib = 0.0;
     if (t < G.N) {
         int i, j, k;
         interior_coords(G, t, i, j, k);
@@ -526,10 +744,9 @@ k_adj_stage1(const StepConst K, const double *__restrict__ U, const double *__re
             lj[a] = lamJ1[a * S + c];
             ldr[a] = lamdR1[a * S + c];
         }
-        contrib = stage_adjoint<FLAT>(K, m, sig, c, u, pr, lp, lj, ldr, lu, bad);
+        lsigc[c] += stage_adjoint<FLAT>(K, m, sig, c, u, pr, lp, lj, ldr, lu, bad);
         for (int f = 0; f < NCO; f++) lamUn[f * S + c] += lu[f];
     }
-    block_add(contrib, lsig);
 }
 
 // cells whose last recovery reset them to the atmosphere: U^{n+1} holds

@@ -52,6 +52,8 @@ struct AdjBuf {
     double *endU = nullptr, *endP = nullptr;   // state after the recorded steps
     double *lamU = nullptr, *lamUn = nullptr, *lamR1 = nullptr, *lamP = nullptr;
     double *lamJ = nullptr, *lamdR1 = nullptr, *Us = nullptr;
+    double *C = nullptr;   // per-face stencil contributions: 6 x 15 x S
+    double *lsigc = nullptr;   // per-cell dL/dlog sigma0, summed at the end
     double *lsig = nullptr;
     int *bad = nullptr;
 };
@@ -59,7 +61,8 @@ struct AdjBuf {
 void free_adj(AdjBuf &a)
 {
     double **ptrs[] = {&a.ckU, &a.ckP, &a.segU, &a.segP, &a.endU, &a.endP, &a.lamU, &a.lamUn,
-                       &a.lamR1, &a.lamP, &a.lamJ, &a.lamdR1, &a.Us, &a.lsig};
+                       &a.lamR1, &a.lamP, &a.lamJ, &a.lamdR1, &a.Us, &a.lsig, &a.C,
+                       &a.lsigc};
     for (double **q : ptrs)
         if (*q) {
             cudaFree(*q);
@@ -903,15 +906,21 @@ template <bool FLAT> static void launch_adj_flux(rmhd_t h, const double *P, cons
     };
 #define RMHD_ADJ_FLUX(RC)                                                                   \
     do {                                                                                    \
-        if (G.g[0])                                                                         \
+        if (G.g[0]) {                                                                       \
             k_adj_flux<FLAT, RC, 0><<<nblk(nfaces(0)), TPB, 0, h->st>>>(                    \
-                h->K, P, J, h->b.met, lamR, scale, a.lamP, a.lamJ);                         \
-        if (G.g[1])                                                                         \
+                h->K, P, J, h->b.met, lamR, scale, a.C);                                    \
+            k_adj_gather<0><<<nblk(G.N), TPB, 0, h->st>>>(h->K, a.C, a.lamP, a.lamJ);       \
+        }                                                                                   \
+        if (G.g[1]) {                                                                       \
             k_adj_flux<FLAT, RC, 1><<<nblk(nfaces(1)), TPB, 0, h->st>>>(                    \
-                h->K, P, J, h->b.met, lamR, scale, a.lamP, a.lamJ);                         \
-        if (G.g[2])                                                                         \
+                h->K, P, J, h->b.met, lamR, scale, a.C);                                    \
+            k_adj_gather<1><<<nblk(G.N), TPB, 0, h->st>>>(h->K, a.C, a.lamP, a.lamJ);       \
+        }                                                                                   \
+        if (G.g[2]) {                                                                       \
             k_adj_flux<FLAT, RC, 2><<<nblk(nfaces(2)), TPB, 0, h->st>>>(                    \
-                h->K, P, J, h->b.met, lamR, scale, a.lamP, a.lamJ);                         \
+                h->K, P, J, h->b.met, lamR, scale, a.C);                                    \
+            k_adj_gather<2><<<nblk(G.N), TPB, 0, h->st>>>(h->K, a.C, a.lamP, a.lamJ);       \
+        }                                                                                   \
     } while (0)
     switch (h->p.recon) {
     case RMHD_RECON_MINMOD: RMHD_ADJ_FLUX(RC_MINMOD); break;
@@ -985,7 +994,7 @@ template <bool FLAT> static int adjoint_step_t(rmhd_t h, const double *Pnext, Ad
     tm.end();
     tm.begin(RMHD_ADJ_STAGES);
     k_adj_stage2<FLAT><<<nb, TPB, 0, h->st>>>(K, a.Us, P2, b.met, b.sig, a.lamU, a.lamP, a.lamJ,
-                                              a.lamR1, a.lamdR1, a.lamUn, a.lsig, a.bad);
+                                              a.lamR1, a.lamdR1, a.lamUn, a.lsigc, a.bad);
     tm.end();
     // F(P1, J1): its adjoint is lamR1
     tm.begin(RMHD_ADJ_SOURCES);
@@ -997,7 +1006,7 @@ template <bool FLAT> static int adjoint_step_t(rmhd_t h, const double *Pnext, Ad
     tm.end();
     tm.begin(RMHD_ADJ_STAGES);
     k_adj_stage1<FLAT><<<nb, TPB, 0, h->st>>>(K, b.U, P1, b.met, b.sig, a.lamP, a.lamJ, a.lamdR1,
-                                              a.lamUn, a.lsig, a.bad);
+                                              a.lamUn, a.lsigc, a.bad);
     tm.end();
     double *t = a.lamU;
     a.lamU = a.lamUn;
@@ -1034,7 +1043,8 @@ extern "C" int rmhd_adjoint_forward(rmhd_t h, double dt, int nsteps, int checkpo
               {&a.segP, (a.every + 1) * pz}, {&a.endU, u},       {&a.endP, pz},
               {&a.lamU, u},              {&a.lamUn, u},          {&a.lamR1, u},
               {&a.lamP, pz},             {&a.lamJ, fbytes(h, 3)}, {&a.lamdR1, fbytes(h, 3)},
-              {&a.Us, u},                {&a.lsig, sizeof(double)}};
+              {&a.Us, u},                {&a.lsig, sizeof(double)},
+              {&a.C, fbytes(h, ADJ_SLOTS * ADJ_NF)}, {&a.lsigc, fbytes(h, 1)}};
     for (auto &e : al) {
         cudaError_t err = cudaMalloc((void **)e.p, e.n);
         if (err != cudaSuccess) {
@@ -1086,7 +1096,7 @@ extern "C" int rmhd_adjoint_backward(rmhd_t h, const double *lam_prims, double *
     tm.n = 0;
     unsigned long long stats0[NSTAT];
     CK(cudaMemcpyAsync(stats0, h->b.stats, sizeof(stats0), cudaMemcpyDeviceToHost, h->st));
-    CK(cudaMemsetAsync(a.lsig, 0, sizeof(double), h->st));
+    CK(cudaMemsetAsync(a.lsigc, 0, fbytes(h, 1), h->st));
     CK(cudaMemsetAsync(a.bad, 0, sizeof(int), h->st));
     CK(cudaMemsetAsync(a.lamU, 0, fbytes(h, NCO), h->st));
     CK(cudaMemsetAsync(a.lamUn, 0, fbytes(h, NCO), h->st));
@@ -1136,6 +1146,7 @@ extern "C" int rmhd_adjoint_backward(rmhd_t h, const double *lam_prims, double *
                                                      h->b.stage);
     rc = stage_out(h, grad_prims0, NPR, on_device);
     if (rc) return rc;
+    k_adj_sum<<<1, 1024, 0, h->st>>>(h->K, a.lsigc, a.lsig);
     double ls = 0.0;
     int bad = 0;
     CK(cudaMemcpyAsync(&ls, a.lsig, sizeof(double), cudaMemcpyDeviceToHost, h->st));
