@@ -121,7 +121,11 @@ FP64_FLOPS = {  # per cell, (mixed path, FP64 path)
     "stage2_rhs_recovery": (211, 303),
     "final_rhs_recovery": (116, 208),
 }
-FLUX_FLOPS_PER_FACE = 650
+# face flops: 15 reconstructed fields x 2 sides (MC2 slope ~12 flops, WENO5
+# ~65 with its four divisions), two one-side flux states (~180 each: W,
+# enthalpy, EM energy, E x B, stress rows, EM rows, the HLLE accumulation)
+FLUX_FLOPS_PER_FACE_BY_RECON = {0: 30 * 10 + 360, 1: 30 * 12 + 360, 2: 30 * 65 + 360}
+FLUX_FLOPS_PER_FACE = FLUX_FLOPS_PER_FACE_BY_RECON[1]     # the MC2 blast
 FLUX_FIELDS = 15 + 14
 
 # DRAM bytes per cell of one launch (dram__bytes_read.sum +
@@ -236,10 +240,11 @@ def roofline(wl, res, prec, steps):
 
 
 # Adjoint (gradient of a loss of the primitives after K steps with respect to
-# the initial primitives and log sigma0) on the 128^3 Alfven cube: algorithmic
-# FP64 work of one face-flux adjoint taken as 3x the forward face work (the
-# cheap-gradient bound of reverse mode), per face of each direction and stage.
-ADJ_FLOPS_PER_FACE = 3 * FLUX_FLOPS_PER_FACE
+# the initial primitives and log sigma0) on the 128^3 Alfven cube (WENO5):
+# algorithmic FP64 work of one face-flux adjoint taken as 3x the forward face
+# work (the cheap-gradient bound of reverse mode), per face of each direction
+# and stage.
+ADJ_FLOPS_PER_FACE = 3 * FLUX_FLOPS_PER_FACE_BY_RECON[2]
 
 
 def run_adjoint(args):

@@ -331,7 +331,15 @@ __device__ __forceinline__ void weno5_grad(double a, double b, double c, double 
     const double b0 = k13 * t10 * t10 + 0.25 * t20 * t20;
     const double b1 = k13 * t11 * t11 + 0.25 * t21 * t21;
     const double b2 = k13 * t12 * t12 + 0.25 * t22 * t22;
-    const double i0 = 1.0 / (eps + b0), i1 = 1.0 / (eps + b1), i2 = 1.0 / (eps + b2);
+    // the three 1/(eps + beta_k) from one division
+    const double e0 = eps + b0, e1 = eps + b1, e2 = eps + b2;
+    const double r = 1.0 / (e0 * e1 * e2);   // e_k >= eps: no underflow
+    double i0 = r * (e1 * e2), i1 = r * (e0 * e2), i2 = r * (e0 * e1);
+    if (!(r > 0.0)) {   // the product overflowed (extreme stencils)
+        i0 = 1.0 / e0;
+        i1 = 1.0 / e1;
+        i2 = 1.0 / e2;
+    }
     const double w0 = 0.1 * i0 * i0, w1 = 0.6 * i1 * i1, w2 = 0.3 * i2 * i2;
     const double iW = 1.0 / (w0 + w1 + w2);
     const double o0 = w0 * iW, o1 = w1 * iW, o2 = w2 * iW;
