@@ -48,7 +48,15 @@ struct StepConst {
     double sigma0, sigma_exp, D_atmo;
     int qflux;            // 0 stage current, 1 Ohm's law at faces, 2 Gauss's law
     RecOpts ro;
+    float sigma0f, gfacf; // FP32 copies for the FP32 stencil (no FP64 conversions)
 };
+
+// a constant of StepConst in the stencil's type
+template <class T> __device__ __forceinline__ T kc(double d, float f)
+{
+    if (sizeof(T) == sizeof(float)) return (T)f;
+    return (T)d;
+}
 
 // metric fields: alpha, beta^x..z, gamma_xx..zz, K_xx..zz
 enum { M_ALPHA = 0, M_BETA = 1, M_GAMMA = 4, M_K = 10, NMET = 16 };
@@ -411,7 +419,7 @@ __global__ void __launch_bounds__(128) k_flux(const StepConst K, const T *__rest
             }
         }
     }
-    T sigma = (T)K.sigma0;
+    T sigma = kc<T>(K.sigma0, K.sigma0f);
     if (K.sigma_model == 1) {
         sigma = (T)(K.sigma0 * 0.5 * (sig[cL] + sig[cR]));
     } else if (K.sigma_model >= 2) {
@@ -442,7 +450,7 @@ __global__ void __launch_bounds__(128) k_flux(const StepConst K, const T *__rest
         const T inv = T(1) / (ap - am);
         cFL = ap * inv; cFR = -am * inv; cUU = ap * am * inv;
     }
-    const T gfac = (T)K.gfac;
+    const T gfac = kc<T>(K.gfac, K.gfacf);
     T acc[NCO];
 #pragma unroll
     for (int f = 0; f < NCO; f++) acc[f] = T(0);
@@ -451,6 +459,184 @@ __global__ void __launch_bounds__(128) k_flux(const StepConst K, const T *__rest
     flux_accumulate<T, FLAT, D>(pR, m, sigma, gfac, useJ, JR, cFR, cUU, aa);
 #pragma unroll
     for (int f = 0; f < NCO; f++) F[f * S + cR] = acc[f];
+}
+
+// Face fluxes of direction D in FP32 with the stencil staged in shared
+// memory (the mixed path).  Same arithmetic as k_flux, face for face.
+// D = 0: a block takes 128 consecutive faces of one x row and stages the
+// row's 128 + 5 cells of the 15 fields (14 primitives, J^D); D = 1, 2: a
+// block takes 32 (x) x 16 (along D) faces and stages 32 x 21 cells; every
+// thread computes four faces along D.  Coalesced loads all in flight at
+// once, then the stencil reads come from shared memory.
+template <bool FLAT, int RC, int D>
+__global__ void __launch_bounds__(128)
+k_flux_tile(const StepConst K, const float *__restrict__ P, const float *__restrict__ Jc,
+            const double *__restrict__ met, const double *__restrict__ sig, float *F)
+{
+    constexpr int TX = D == 0 ? 128 : 32;   // faces (D = 0) or cells (D > 0) along x
+    constexpr int TD = D == 0 ? 1 : 16;     // faces along D (D > 0)
+    constexpr int LX = D == 0 ? TX + 5 : TX;
+    constexpr int LD = D == 0 ? 1 : TD + 5;
+    constexpr int NF = NPR + 1;
+    __shared__ float sm[NF][LD][LX];
+    const Grid &G = K.G;
+    const long long S = G.S;
+    const long long s = dstride(G, D);
+    const bool useJ = K.qflux != 1;   // mode 2: Q row overwritten later
+    // tile origin: x0 (faces or cells), d0 (faces along D), fixed coordinates
+    int x0, d0, c1, c2;
+    if (D == 0) {
+        x0 = blockIdx.x * TX; d0 = 0; c1 = blockIdx.y; c2 = blockIdx.z;
+    } else if (D == 1) {
+        x0 = blockIdx.x * TX; d0 = blockIdx.y * TD; c1 = 0; c2 = blockIdx.z;
+    } else {
+        x0 = blockIdx.x * TX; d0 = blockIdx.z * TD; c1 = blockIdx.y; c2 = 0;
+    }
+    // stage: cells x0-3 .. x0+TX+1 of the row (D = 0), or x0..x0+TX-1 by
+    // d0-3 .. d0+TD+1 along D; only cells inside the padded grid
+    const int nf_stage = useJ ? NF : NPR;
+    for (int idx = threadIdx.x; idx < LD * LX; idx += blockDim.x) {
+        const int dl = idx / LX, xl = idx - dl * LX;
+        int ci, cj, ck;
+        bool ok;
+        if (D == 0) {
+            ci = x0 - 3 + xl; cj = c1; ck = c2;
+            ok = ci <= G.n[0] + 2;
+        } else if (D == 1) {
+            ci = x0 + xl; cj = d0 - 3 + dl; ck = c2;
+            ok = ci < G.n[0] && cj <= G.n[1] + 2;
+        } else {
+            ci = x0 + xl; cj = c1; ck = d0 - 3 + dl;
+            ok = ci < G.n[0] && ck <= G.n[2] + 2;
+        }
+        if (!ok) continue;
+        const long long c = cell_at(G, ci, cj, ck);
+        for (int f = 0; f < nf_stage; f++)
+            sm[f][dl][xl] = f < NPR ? P[f * S + c] : Jc[D * S + c];
+    }
+    __syncthreads();
+
+    const int tx = D == 0 ? threadIdx.x : (threadIdx.x & 31);
+    const int ty = D == 0 ? 0 : (threadIdx.x >> 5);
+    constexpr int PER = D == 0 ? 1 : TD / 4;
+    const float gfac = K.gfacf;
+#pragma unroll 1
+    for (int r = 0; r < PER; r++) {
+        const int dloc = D == 0 ? 0 : ty + 4 * r;
+        int fi, fj, fk;   // face = low side of cell (fi, fj, fk)
+        if (D == 0) {
+            fi = x0 + tx; fj = c1; fk = c2;
+            if (fi > G.n[0]) break;
+        } else if (D == 1) {
+            fi = x0 + tx; fj = d0 + dloc; fk = c2;
+            if (fi >= G.n[0] || fj > G.n[1]) break;
+        } else {
+            fi = x0 + tx; fj = c1; fk = d0 + dloc;
+            if (fi >= G.n[0] || fk > G.n[2]) break;
+        }
+        const long long cR = cell_at(G, fi, fj, fk);
+        const long long cL = cR - s;
+        // stencil o = 0..5: cells (face - 3 + o) along D
+        auto at = [&](int f, int o) -> float {
+            return D == 0 ? sm[f][0][tx + o] : sm[f][dloc + o][tx];
+        };
+        float pL[NPR], pR[NPR];
+#pragma unroll
+        for (int f = 0; f < NPR; f++) {
+            float st[6];
+            if (RC == RC_WENO5) {
+#pragma unroll
+                for (int o = 0; o < 6; o++) st[o] = at(f, o);
+            } else {
+#pragma unroll
+                for (int o = 1; o < 5; o++) st[o] = at(f, o);
+                st[0] = st[5] = 0.f;
+            }
+            reconstruct<float, RC>(st, pL[f], pR[f]);
+        }
+        float JL = 0.f, JR = 0.f;
+        if (useJ) {
+            float st[6];
+            if (RC == RC_WENO5) {
+#pragma unroll
+                for (int o = 0; o < 6; o++) st[o] = at(NPR, o);
+            } else {
+#pragma unroll
+                for (int o = 1; o < 5; o++) st[o] = at(NPR, o);
+                st[0] = st[5] = 0.f;
+            }
+            reconstruct<float, RC>(st, JL, JR);
+        }
+        Met<float> m;
+        if (FLAT) {
+            m.alpha = 1.f;
+            m.beta[0] = m.beta[1] = m.beta[2] = 0.f;
+            m.g[0] = m.g[3] = m.g[5] = 1.f;
+            m.g[1] = m.g[2] = m.g[4] = 0.f;
+            m.gi[0] = m.gi[3] = m.gi[5] = 1.f;
+            m.gi[1] = m.gi[2] = m.gi[4] = 0.f;
+            m.sg = m.isg = 1.f;
+        } else {
+            m.alpha = (float)(0.5 * (met[M_ALPHA * S + cL] + met[M_ALPHA * S + cR]));
+            for (int a = 0; a < 3; a++)
+                m.beta[a] = (float)(0.5 * (met[(M_BETA + a) * S + cL] + met[(M_BETA + a) * S + cR]));
+            for (int a = 0; a < 6; a++)
+                m.g[a] = (float)(0.5 * (met[(M_GAMMA + a) * S + cL] + met[(M_GAMMA + a) * S + cR]));
+            met_complete(m);
+        }
+#pragma unroll
+        for (int sd = 0; sd < 2; sd++) {
+            float *q = sd == 0 ? pL : pR;
+            float v[3] = {q[PR_VX], q[PR_VY], q[PR_VZ]}, vl[3];
+            lower<float, FLAT>(m, v, vl);
+            if (!(q[PR_RHO] > 0.f) || !(q[PR_P] > 0.f) || !(dot3(v, vl) < 1.f)) {
+                const int o = sd == 0 ? 2 : 3;
+#pragma unroll
+                for (int f = 0; f < NPR; f++) q[f] = at(f, o);
+                if (useJ) {
+                    if (sd == 0) JL = at(NPR, o);
+                    else JR = at(NPR, o);
+                }
+            }
+        }
+        float sigma = K.sigma0f;
+        if (K.sigma_model == 1) {
+            sigma = (float)(K.sigma0 * 0.5 * (sig[cL] + sig[cR]));
+        } else if (K.sigma_model >= 2) {
+            double sgm = 0.0;
+            for (int sd = 0; sd < 2; sd++) {
+                const long long cc = sd == 0 ? cL : cR;
+                Met<double> mc;
+                load_metric<FLAT>(met, S, cc, mc);
+                double v[3] = {(double)P[PR_VX * S + cc], (double)P[PR_VY * S + cc],
+                               (double)P[PR_VZ * S + cc]}, vl[3];
+                lower<double, FLAT>(mc, v, vl);
+                double Dc = mc.sg * (double)P[PR_RHO * S + cc] / sqrt(1.0 - dot3(v, vl));
+                sgm += 0.5 * sigma_cell(K, sig, cc, Dc);
+            }
+            sigma = (float)sgm;
+        }
+        float cFL, cFR, cUU;
+        if (FLAT) {
+            cFL = 0.5f; cFR = 0.5f; cUU = -0.5f;
+        } else {
+            const float sq = sqrt(m.gi[sym(D, D)]);
+            const float bs = m.beta[D] / m.alpha;
+            float ap = sq - bs, am = -sq - bs;
+            ap = ap > 0.f ? ap : 0.f;
+            am = am < 0.f ? am : 0.f;
+            const float inv = 1.f / (ap - am);
+            cFL = ap * inv; cFR = -am * inv; cUU = ap * am * inv;
+        }
+        float acc[NCO];
+#pragma unroll
+        for (int f = 0; f < NCO; f++) acc[f] = 0.f;
+        ArrAcc<float> aa{acc};
+        flux_accumulate<float, FLAT, D>(pL, m, sigma, gfac, useJ, JL, cFL, -cUU, aa);
+        flux_accumulate<float, FLAT, D>(pR, m, sigma, gfac, useJ, JR, cFR, cUU, aa);
+#pragma unroll
+        for (int f = 0; f < NCO; f++) F[f * S + cR] = acc[f];
+    }
 }
 
 // Reconstruction of cell c along D: its state at the face below (m) and
@@ -514,7 +700,7 @@ __global__ void __launch_bounds__(128) k_flux_run(const StepConst K, const T *__
     const T *Jp = useJ ? Jc : nullptr;
     T mL[NPR + 1], pL[NPR + 1];                          // of the cell below the face
     cell_faces<T, RC>(P, Jp, S, c, s, D, mL, pL);
-    const T gfac = (T)K.gfac;
+    const T gfac = kc<T>(K.gfac, K.gfacf);
     for (int f = f0; f < fend; f++) {
         const long long cL = c, cR = c + s;
         T mR[NPR + 1], pR[NPR + 1];
@@ -559,7 +745,7 @@ __global__ void __launch_bounds__(128) k_flux_run(const StepConst K, const T *__
                 }
             }
         }
-        T sigma = (T)K.sigma0;
+        T sigma = kc<T>(K.sigma0, K.sigma0f);
         if (K.sigma_model == 1) {
             sigma = (T)(K.sigma0 * 0.5 * (sig[cL] + sig[cR]));
         } else if (K.sigma_model >= 2) {

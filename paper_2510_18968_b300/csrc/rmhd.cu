@@ -221,11 +221,30 @@ template <class T> static void launch_ghosts(rmhd_t h, T *buf, int nf)
     k_ghosts<T><<<grid, TPB, 0, h->st>>>(h->K, buf, nf, 0);
 }
 
+// FP32 face fluxes through shared-memory tiles (k_flux_tile)
+template <bool FLAT, int RC>
+static void launch_flux_tile(rmhd_t h, const float *P, const float *J, float **Fd)
+{
+    const Grid &G = h->K.G;
+    const Buffers &b = h->b;
+    const unsigned n0 = G.n[0], n1 = G.n[1], n2 = G.n[2];
+    if (G.g[0])
+        k_flux_tile<FLAT, RC, 0><<<dim3((n0 + 1 + 127) / 128, n1, n2), TPB, 0, h->st>>>(
+            h->K, P, J, b.met, b.sig, Fd[0]);
+    if (G.g[1])
+        k_flux_tile<FLAT, RC, 1><<<dim3((n0 + 31) / 32, (n1 + 1 + 15) / 16, n2), TPB, 0, h->st>>>(
+            h->K, P, J, b.met, b.sig, Fd[1]);
+    if (G.g[2])
+        k_flux_tile<FLAT, RC, 2><<<dim3((n0 + 31) / 32, n1, (n2 + 1 + 15) / 16), TPB, 0, h->st>>>(
+            h->K, P, J, b.met, b.sig, Fd[2]);
+}
+
 // faces per thread of the run flux kernel (FP64 path)
 const int FLUX_RUN = 8;
 
 // FP64: the run kernel reconstructs each cell once (ALU-bound path); FP32:
-// one thread per face keeps more loads in flight (latency-bound path)
+// shared-memory tiles (k_flux_tile; one thread per face, k_flux, beyond
+// the tiles' grid-dimension limits)
 template <class T, bool FLAT, int RC>
 static void launch_flux_rc(rmhd_t h, const T *P, const T *J)
 {
@@ -239,18 +258,19 @@ static void launch_flux_rc(rmhd_t h, const T *P, const T *J)
         for (int a = 0; a < 3; a++) n *= a == d ? (run ? (G.n[a] + 1 + M - 1) / M : G.n[a] + 1) : G.n[a];
         return n;
     };
-    if (G.g[0]) {
-        if (run) k_flux_run<T, FLAT, RC, 0, M><<<nblk(nthreads(0)), TPB, 0, h->st>>>(h->K, P, J, b.met, b.sig, Fd[0]);
-        else k_flux<T, FLAT, RC, 0><<<nblk(nthreads(0)), TPB, 0, h->st>>>(h->K, P, J, b.met, b.sig, Fd[0]);
+    if (run) {
+        if (G.g[0]) k_flux_run<T, FLAT, RC, 0, M><<<nblk(nthreads(0)), TPB, 0, h->st>>>(h->K, P, J, b.met, b.sig, Fd[0]);
+        if (G.g[1]) k_flux_run<T, FLAT, RC, 1, M><<<nblk(nthreads(1)), TPB, 0, h->st>>>(h->K, P, J, b.met, b.sig, Fd[1]);
+        if (G.g[2]) k_flux_run<T, FLAT, RC, 2, M><<<nblk(nthreads(2)), TPB, 0, h->st>>>(h->K, P, J, b.met, b.sig, Fd[2]);
+        return;
     }
-    if (G.g[1]) {
-        if (run) k_flux_run<T, FLAT, RC, 1, M><<<nblk(nthreads(1)), TPB, 0, h->st>>>(h->K, P, J, b.met, b.sig, Fd[1]);
-        else k_flux<T, FLAT, RC, 1><<<nblk(nthreads(1)), TPB, 0, h->st>>>(h->K, P, J, b.met, b.sig, Fd[1]);
+    if (G.n[1] <= 65535 && G.n[2] <= 65535) {   // grid-dimension limits of the tiles
+        launch_flux_tile<FLAT, RC>(h, (const float *)P, (const float *)J, (float **)Fd);
+        return;
     }
-    if (G.g[2]) {
-        if (run) k_flux_run<T, FLAT, RC, 2, M><<<nblk(nthreads(2)), TPB, 0, h->st>>>(h->K, P, J, b.met, b.sig, Fd[2]);
-        else k_flux<T, FLAT, RC, 2><<<nblk(nthreads(2)), TPB, 0, h->st>>>(h->K, P, J, b.met, b.sig, Fd[2]);
-    }
+    if (G.g[0]) k_flux<T, FLAT, RC, 0><<<nblk(nthreads(0)), TPB, 0, h->st>>>(h->K, P, J, b.met, b.sig, Fd[0]);
+    if (G.g[1]) k_flux<T, FLAT, RC, 1><<<nblk(nthreads(1)), TPB, 0, h->st>>>(h->K, P, J, b.met, b.sig, Fd[1]);
+    if (G.g[2]) k_flux<T, FLAT, RC, 2><<<nblk(nthreads(2)), TPB, 0, h->st>>>(h->K, P, J, b.met, b.sig, Fd[2]);
 }
 
 template <class T, bool FLAT> static void launch_flux(rmhd_t h, const T *P, const T *J)
@@ -426,9 +446,11 @@ extern "C" int rmhd_create(const rmhd_params *p, void *cuda_stream, rmhd_t *out)
     K.gimex = 1.0 - 1.0 / sqrt(2.0);
     K.igimex = 1.0 / K.gimex;
     K.gfac = p->gamma_eos / (p->gamma_eos - 1.0);
+    K.gfacf = (float)K.gfac;
     K.kappa = p->kappa;
     K.sigma_model = p->sigma_model;
     K.sigma0 = p->sigma0;
+    K.sigma0f = (float)p->sigma0;
     K.sigma_exp = p->sigma_exp;
     K.D_atmo = p->D_atmo;
     K.qflux = p->qflux_mode;
@@ -843,6 +865,7 @@ extern "C" int rmhd_set_sigma0(rmhd_t h, double sigma0)
     if (!(sigma0 >= 0.0) || !isfinite(sigma0)) return set_err(h, RMHD_EINVAL, "sigma0 must be >= 0");
     h->p.sigma0 = sigma0;
     h->K.sigma0 = sigma0;
+    h->K.sigma0f = (float)sigma0;
     return RMHD_OK;
 }
 
