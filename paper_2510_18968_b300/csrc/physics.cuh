@@ -257,14 +257,28 @@ __device__ __forceinline__ void prim_to_cons(const T pr[NPR], const Met<T> &m, T
 // ---------------------------------------------------------------------------
 enum { RC_MINMOD = 0, RC_MC2 = 1, RC_WENO5 = 2 };
 
+// minmod limiters: 0 unless all arguments share a sign, else the one nearest
+// zero.  In FP32 (issue-bound stencil) written with selects and no
+// branches; in FP64 (FP64-pipe-bound) with branches, so that only the
+// needed min or max is computed.  Same value either way.
 template <class T> __device__ __forceinline__ T mm2(T a, T b)
 {
+    if (sizeof(T) == sizeof(float)) {
+        const T r = fabs(a) <= fabs(b) ? a : b;
+        return a * b <= T(0) ? T(0) : r;
+    }
     if (a * b <= T(0)) return T(0);
     return fabs(a) <= fabs(b) ? a : b;
 }
 
 template <class T> __device__ __forceinline__ T mm3(T a, T b, T c)
 {
+    if (sizeof(T) == sizeof(float)) {
+        const T mn = fmin(a, fmin(b, c)), mx = fmax(a, fmax(b, c));
+        const bool pos = (a > T(0)) & (b > T(0)) & (c > T(0));
+        const bool neg = (a < T(0)) & (b < T(0)) & (c < T(0));
+        return pos ? mn : (neg ? mx : T(0));
+    }
     if (a > T(0) && b > T(0) && c > T(0)) return fmin(a, fmin(b, c));
     if (a < T(0) && b < T(0) && c < T(0)) return fmax(a, fmax(b, c));
     return T(0);

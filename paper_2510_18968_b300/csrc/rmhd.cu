@@ -673,22 +673,21 @@ extern "C" int rmhd_set_state(rmhd_t h, const double *cons, const double *prims,
     if (!cons || !prims) return set_err(h, RMHD_EINVAL, "cons and prims are required");
     const Grid &G = h->K.G;
     int bad = 0, rc;
-    const double *src[2] = {cons, prims};
-    // validate both before committing
-    for (int a = 0; a < 2; a++) {
-        rc = stage_in(h, src[a], NPR, on_device);
-        if (rc) return rc;
-        cudaMemsetAsync(h->b.flag, 0, sizeof(int), h->st);
-        k_check_finite<<<nblk(NPR * G.N), TPB, 0, h->st>>>(NPR * G.N, h->b.stage, h->b.flag);
-        rc = read_flag(h, &bad);
-        if (rc) return rc;
-        if (bad) return set_err(h, RMHD_EINVAL, "state has non-finite values");
-    }
+    // each array crosses the bus once; both are validated before anything
+    // is committed: the conserved values wait in V (step scratch)
     rc = stage_in(h, cons, NCO, on_device);
     if (rc) return rc;
-    k_scatter<double><<<nblk(G.N), TPB, 0, h->st>>>(h->K, h->b.stage, h->b.U, NCO);
+    cudaMemsetAsync(h->b.flag, 0, sizeof(int), h->st);
+    k_check_finite<<<nblk(NCO * G.N), TPB, 0, h->st>>>(NCO * G.N, h->b.stage, h->b.flag);
+    k_scatter<double><<<nblk(G.N), TPB, 0, h->st>>>(h->K, h->b.stage, h->b.V, NCO);
     rc = stage_in(h, prims, NPR, on_device);
     if (rc) return rc;
+    k_check_finite<<<nblk(NPR * G.N), TPB, 0, h->st>>>(NPR * G.N, h->b.stage, h->b.flag);
+    rc = read_flag(h, &bad);
+    if (rc) return rc;
+    if (bad) return set_err(h, RMHD_EINVAL, "state has non-finite values");
+    CK(cudaMemcpyAsync(h->b.U, h->b.V, sizeof(double) * NCO * (size_t)G.S,
+                       cudaMemcpyDeviceToDevice, h->st));
     scatter_prims(h, h->b.PA, h->b.GA);
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(h->st));
