@@ -86,6 +86,61 @@ __device__ __forceinline__ void interior_coords(const Grid &G, long long t, int 
     j = (int)(r - (unsigned)k * ny);
 }
 
+// Cells of the recovery kernels are handed out in bricks of 32 (4 x 4 x 2,
+// or 8 x 4 in 2D, a row in 1D), so that a warp holds neighbouring cells:
+// cells that need more recovery iterations cluster in space, and a brick
+// mixes fewer of them with one-iteration cells than a 32-cell row does.
+struct Bricks {
+    int bx, by, bz;       // brick extents (bx * by * bz = 32)
+    int nbx, nby;         // bricks along x, y
+    long long threads;    // 32 x number of bricks
+};
+
+__host__ __device__ inline Bricks make_bricks(const int n[3])
+{
+    Bricks b;
+    int e[3] = {1, 1, 1};
+    const int nact = (n[0] > 1) + (n[1] > 1) + (n[2] > 1);
+    if (nact == 3) {
+        e[0] = 4; e[1] = 4; e[2] = 2;
+    } else if (nact == 2) {
+        int first = 1;   // the first active axis takes 8, the second 4
+        for (int d = 0; d < 3; d++)
+            if (n[d] > 1) { e[d] = first ? 8 : 4; first = 0; }
+    } else {
+        for (int d = 0; d < 3; d++)
+            if (n[d] > 1) e[d] = 32;
+        if (nact == 0) e[0] = 32;
+    }
+    b.bx = e[0]; b.by = e[1]; b.bz = e[2];
+    b.nbx = (n[0] + b.bx - 1) / b.bx;
+    b.nby = (n[1] + b.by - 1) / b.by;
+    const long long nbz = (n[2] + b.bz - 1) / b.bz;
+    b.threads = 32LL * b.nbx * b.nby * nbz;
+    return b;
+}
+
+// brick thread t -> interior cell (i, j, k); false if outside the grid
+__device__ __forceinline__ bool brick_coords(const Grid &G, const Bricks &b, long long t, int &i,
+                                             int &j, int &k)
+{
+    const unsigned u = (unsigned)t, br = u >> 5, l = u & 31u;
+    const unsigned qx = br % (unsigned)b.nbx, r = br / (unsigned)b.nbx;
+    const unsigned qy = r % (unsigned)b.nby, qz = r / (unsigned)b.nby;
+    const unsigned lx = l % (unsigned)b.bx, ly = (l / (unsigned)b.bx) % (unsigned)b.by;
+    const unsigned lz = l / (unsigned)(b.bx * b.by);
+    i = (int)(qx * b.bx + lx);
+    j = (int)(qy * b.by + ly);
+    k = (int)(qz * b.bz + lz);
+    return t < b.threads && i < G.n[0] && j < G.n[1] && k < G.n[2];
+}
+
+// linear interior index of (i, j, k), x fastest
+__device__ __forceinline__ long long interior_index(const Grid &G, int i, int j, int k)
+{
+    return ((long long)k * G.n[1] + j) * G.n[0] + i;
+}
+
 template <bool FLAT>
 __device__ __forceinline__ void load_metric(const double *__restrict__ met, long long S,
                                             long long c, Met<double> &m)
@@ -1065,15 +1120,15 @@ k_stage1(const StepConst K, const double *__restrict__ U, T *P, double *Gs, doub
 {
     const Grid &G = K.G;
     const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    const bool active = t < G.N;
+    const Bricks bk = make_bricks(G.n);
+    int i, j, k;
+    const bool active = brick_coords(G, bk, t, i, j, k);
     int status = 0, iters = 0;
     long long c = 0;
     double u[NCO], pr[NPR], E[3], gp = 0.0, gv[3] = {0, 0, 0}, cc = 0.0;
     Met<double> m;
     PaperState ps;
     if (active) {
-        int i, j, k;
-        interior_coords(G, t, i, j, k);
         c = cell_at(G, i, j, k);
         const long long S = G.S;
         load_metric<FLAT>(met, S, c, m);
@@ -1090,7 +1145,7 @@ k_stage1(const StepConst K, const double *__restrict__ U, T *P, double *Gs, doub
     const int slot = defer_slot(df, want);
     if (want) {
         if (slot >= 0) {
-            defer_store(df, slot, t, u, gp, gv, ps);
+            defer_store(df, slot, interior_index(G, i, j, k), u, gp, gv, ps);
         } else {
             RecIn in;
             load_rec_in(u, in);
@@ -1118,15 +1173,15 @@ k_stage2(const StepConst K, const double *__restrict__ U, const T *__restrict__ 
 {
     const Grid &G = K.G;
     const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    const bool active = t < G.N;
+    const Bricks bk = make_bricks(G.n);
+    int i, j, k;
+    const bool active = brick_coords(G, bk, t, i, j, k);
     int status = 0, iters = 0;
     long long c = 0;
     double us[NCO], p2[NPR], E[3], gp = 0.0, gv[3] = {0, 0, 0}, cc = 0.0;
     Met<double> m;
     PaperState ps;
     if (active) {
-        int i, j, k;
-        interior_coords(G, t, i, j, k);
         c = cell_at(G, i, j, k);
         const long long S = G.S;
         T pr[NPR];
@@ -1155,7 +1210,7 @@ k_stage2(const StepConst K, const double *__restrict__ U, const T *__restrict__ 
     const int slot = defer_slot(df, want);
     if (want) {
         if (slot >= 0) {
-            defer_store(df, slot, t, us, gp, gv, ps);
+            defer_store(df, slot, interior_index(G, i, j, k), us, gp, gv, ps);
         } else {
             RecIn in;
             load_rec_in(us, in);
@@ -1180,15 +1235,15 @@ k_final(const StepConst K, const double *__restrict__ Vb, const T *__restrict__ 
 {
     const Grid &G = K.G;
     const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    const bool active = t < G.N;
+    const Bricks bk = make_bricks(G.n);
+    int i, j, k;
+    const bool active = brick_coords(G, bk, t, i, j, k);
     int status = 0, iters = 0;
     long long c = 0;
     double un[NCO], pn[NPR], E[3], gp = 0.0, gv[3] = {0, 0, 0};
     Met<double> m;
     PaperState ps;
     if (active) {
-        int i, j, k;
-        interior_coords(G, t, i, j, k);
         c = cell_at(G, i, j, k);
         const long long S = G.S;
         T pr[NPR];
@@ -1215,7 +1270,7 @@ k_final(const StepConst K, const double *__restrict__ Vb, const T *__restrict__ 
     const int slot = defer_slot(df, want);
     if (want) {
         if (slot >= 0) {
-            defer_store(df, slot, t, un, gp, gv, ps);
+            defer_store(df, slot, interior_index(G, i, j, k), un, gp, gv, ps);
         } else {
             RecIn in;
             load_rec_in(un, in);

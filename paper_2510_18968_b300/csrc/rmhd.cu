@@ -310,7 +310,7 @@ template <bool FLAT, class T> static void enqueue_step_t(rmhd_t h, cudaEvent_t *
 {
     Buffers &b = h->b;
     const StepConst &K = h->K;
-    const unsigned nb = nblk(K.G.N);
+    const unsigned nb = nblk(make_bricks(K.G.n).threads);   // stage kernels: bricks
     auto mark = [&](int i) { if (ev) cudaEventRecord(ev[i], h->st); };
     const bool dfr = b.dcap > 0;
     const unsigned nbd = deferred_blocks(h);
@@ -890,7 +890,7 @@ template <bool FLAT> static void enqueue_recompute_t(rmhd_t h)
 {
     Buffers &b = h->b;
     const StepConst &K = h->K;
-    const unsigned nb = nblk(K.G.N);
+    const unsigned nb = nblk(make_bricks(K.G.n).threads);   // stage kernels: bricks
     const bool dfr = b.dcap > 0;
     const unsigned nbd = deferred_blocks(h);
     double *PA = (double *)b.PA, *PB = (double *)b.PB, *J1 = (double *)b.J1, *J2 = (double *)b.J2;
