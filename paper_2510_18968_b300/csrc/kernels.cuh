@@ -518,10 +518,12 @@ __global__ void __launch_bounds__(128) k_flux(const StepConst K, const T *__rest
 
 // Face fluxes of direction D in FP32 with the stencil staged in shared
 // memory (the mixed path).  Same arithmetic as k_flux, face for face.
-// D = 0: a block takes 128 consecutive faces of one x row and stages the
-// row's 128 + 5 cells of the 15 fields (14 primitives, J^D); D = 1, 2: a
-// block takes 32 (x) x 16 (along D) faces and stages 32 x 21 cells; every
-// thread computes four faces along D.  Coalesced loads all in flight at
+// D = 0: a block takes 128 consecutive faces of one x row (the row's last
+// block also its face n) and stages their cells, 128 + 6, of the 15 fields
+// (14 primitives, J^D); D = 1, 2: a
+// block takes 32 (x) x 16 (along D) faces (the last along D also its face
+// n) and stages 32 x 22 cells; every thread computes four or five faces
+// along D.  Coalesced loads all in flight at
 // once, then the stencil reads come from shared memory.
 template <bool FLAT, int RC, int D>
 __global__ void __launch_bounds__(128)
@@ -530,8 +532,8 @@ k_flux_tile(const StepConst K, const float *__restrict__ P, const float *__restr
 {
     constexpr int TX = D == 0 ? 128 : 32;   // faces (D = 0) or cells (D > 0) along x
     constexpr int TD = D == 0 ? 1 : 16;     // faces along D (D > 0)
-    constexpr int LX = D == 0 ? TX + 5 : TX;
-    constexpr int LD = D == 0 ? 1 : TD + 5;
+    constexpr int LX = D == 0 ? TX + 6 : TX;   // D = 0: the row's last block takes 129 faces
+    constexpr int LD = D == 0 ? 1 : TD + 6;   // D > 0: the last block along D takes 17
     constexpr int NF = NPR + 1;
     __shared__ float sm[NF][LD][LX];
     const Grid &G = K.G;
@@ -540,13 +542,19 @@ k_flux_tile(const StepConst K, const float *__restrict__ P, const float *__restr
     const bool useJ = K.qflux != 1;   // mode 2: Q row overwritten later
     // tile origin: x0 (faces or cells), d0 (faces along D), fixed coordinates
     int x0, d0, c1, c2;
+    int x_end = 0;   // D = 0: faces x0 .. x_end - 1 of the row (the last block also takes face n)
     if (D == 0) {
         x0 = blockIdx.x * TX; d0 = 0; c1 = blockIdx.y; c2 = blockIdx.z;
+        x_end = blockIdx.x + 1 == gridDim.x ? G.n[0] + 1 : x0 + TX;
     } else if (D == 1) {
         x0 = blockIdx.x * TX; d0 = blockIdx.y * TD; c1 = 0; c2 = blockIdx.z;
     } else {
         x0 = blockIdx.x * TX; d0 = blockIdx.z * TD; c1 = blockIdx.y; c2 = 0;
     }
+    // D > 0: faces d0 .. d_end - 1 along D (the last block also takes face n)
+    const int d_end = D == 0 ? 0
+                    : ((D == 1 ? blockIdx.y + 1 == gridDim.y : blockIdx.z + 1 == gridDim.z)
+                           ? G.n[D] + 1 : d0 + TD);
     // stage: cells x0-3 .. x0+TX+1 of the row (D = 0), or x0..x0+TX-1 by
     // d0-3 .. d0+TD+1 along D; only cells inside the padded grid
     const int nf_stage = useJ ? NF : NPR;
@@ -571,23 +579,23 @@ k_flux_tile(const StepConst K, const float *__restrict__ P, const float *__restr
     }
     __syncthreads();
 
-    const int tx = D == 0 ? threadIdx.x : (threadIdx.x & 31);
     const int ty = D == 0 ? 0 : (threadIdx.x >> 5);
-    constexpr int PER = D == 0 ? 1 : TD / 4;
+    constexpr int PER = D == 0 ? 2 : TD / 4 + 1;
     const float gfac = K.gfacf;
 #pragma unroll 1
     for (int r = 0; r < PER; r++) {
         const int dloc = D == 0 ? 0 : ty + 4 * r;
+        const int tx = D == 0 ? threadIdx.x + TX * r : (threadIdx.x & 31);
         int fi, fj, fk;   // face = low side of cell (fi, fj, fk)
         if (D == 0) {
             fi = x0 + tx; fj = c1; fk = c2;
-            if (fi > G.n[0]) break;
+            if (fi >= x_end) break;
         } else if (D == 1) {
             fi = x0 + tx; fj = d0 + dloc; fk = c2;
-            if (fi >= G.n[0] || fj > G.n[1]) break;
+            if (fi >= G.n[0] || fj >= d_end) break;
         } else {
             fi = x0 + tx; fj = c1; fk = d0 + dloc;
-            if (fi >= G.n[0] || fk > G.n[2]) break;
+            if (fi >= G.n[0] || fk >= d_end) break;
         }
         const long long cR = cell_at(G, fi, fj, fk);
         const long long cL = cR - s;

@@ -229,13 +229,13 @@ static void launch_flux_tile(rmhd_t h, const float *P, const float *J, float **F
     const Buffers &b = h->b;
     const unsigned n0 = G.n[0], n1 = G.n[1], n2 = G.n[2];
     if (G.g[0])
-        k_flux_tile<FLAT, RC, 0><<<dim3((n0 + 1 + 127) / 128, n1, n2), TPB, 0, h->st>>>(
+        k_flux_tile<FLAT, RC, 0><<<dim3((n0 + 127) / 128, n1, n2), TPB, 0, h->st>>>(
             h->K, P, J, b.met, b.sig, Fd[0]);
     if (G.g[1])
-        k_flux_tile<FLAT, RC, 1><<<dim3((n0 + 31) / 32, (n1 + 1 + 15) / 16, n2), TPB, 0, h->st>>>(
+        k_flux_tile<FLAT, RC, 1><<<dim3((n0 + 31) / 32, (n1 + 15) / 16, n2), TPB, 0, h->st>>>(
             h->K, P, J, b.met, b.sig, Fd[1]);
     if (G.g[2])
-        k_flux_tile<FLAT, RC, 2><<<dim3((n0 + 31) / 32, n1, (n2 + 1 + 15) / 16), TPB, 0, h->st>>>(
+        k_flux_tile<FLAT, RC, 2><<<dim3((n0 + 31) / 32, n1, (n2 + 15) / 16), TPB, 0, h->st>>>(
             h->K, P, J, b.met, b.sig, Fd[2]);
 }
 
