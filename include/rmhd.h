@@ -233,10 +233,11 @@ int rmhd_set_sigma0(rmhd_t h, double sigma0);
 /* Run nsteps steps of size dt from the current state, like rmhd_step, and
  * record the trajectory for rmhd_adjoint_backward: the state (U and P,
  * 28 FP64 fields of the padded grid) every checkpoint_every steps, plus
- * scratch for one segment of checkpoint_every + 1 states and the adjoint
- * fields (about 130 + 28 (nsteps / checkpoint_every + checkpoint_every)
- * padded FP64 fields in all; 90 of them hold the per-face stencil
- * contributions of the flux adjoint).  Replaces any earlier recording.  Errors:
+ * scratch for one segment (checkpoint_every + 1 states and the stage states
+ * of its steps, which the reverse sweep keeps instead of recomputing them)
+ * and the adjoint fields: about 210 + 28 nsteps / checkpoint_every + 76
+ * checkpoint_every padded FP64 fields in all (90 of them hold the per-face
+ * stencil contributions of the flux adjoint).  Replaces any earlier recording.  Errors:
  * RMHD_EINVAL, RMHD_ENOMEM, RMHD_ENAN (non-finite state; nothing recorded).
  * Atmosphere resets are not an error here (rmhd_get_stats counts them). */
 int rmhd_adjoint_forward(rmhd_t h, double dt, int nsteps, int checkpoint_every);

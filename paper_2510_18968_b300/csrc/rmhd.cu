@@ -49,9 +49,12 @@ struct AdjBuf {
     int nsteps = 0, every = 0, nck = 0;
     double *ckU = nullptr, *ckP = nullptr;     // checkpoints: nck x (14 x S)
     double *segU = nullptr, *segP = nullptr;   // one segment: (every + 1) x (14 x S)
+    // stage states of the segment's steps (every x: P1, P2, U* 14 x S; J1, J2 3 x S)
+    double *segP1 = nullptr, *segJ1 = nullptr, *segUs = nullptr, *segP2 = nullptr,
+           *segJ2 = nullptr;
     double *endU = nullptr, *endP = nullptr;   // state after the recorded steps
     double *lamU = nullptr, *lamUn = nullptr, *lamR1 = nullptr, *lamP = nullptr;
-    double *lamJ = nullptr, *lamdR1 = nullptr, *Us = nullptr;
+    double *lamJ = nullptr, *lamdR1 = nullptr;
     double *C = nullptr;   // per-face stencil contributions: 6 x 15 x S
     double *lsigc = nullptr;   // per-cell dL/dlog sigma0, summed at the end
     double *lsig = nullptr;
@@ -60,9 +63,10 @@ struct AdjBuf {
 
 void free_adj(AdjBuf &a)
 {
-    double **ptrs[] = {&a.ckU, &a.ckP, &a.segU, &a.segP, &a.endU, &a.endP, &a.lamU, &a.lamUn,
-                       &a.lamR1, &a.lamP, &a.lamJ, &a.lamdR1, &a.Us, &a.lsig, &a.C,
-                       &a.lsigc};
+    double **ptrs[] = {&a.ckU,  &a.ckP,   &a.segU,  &a.segP,   &a.segP1, &a.segJ1,
+                       &a.segUs, &a.segP2, &a.segJ2, &a.endU,   &a.endP,  &a.lamU,
+                       &a.lamUn, &a.lamR1, &a.lamP,  &a.lamJ,   &a.lamdR1, &a.lsig,
+                       &a.C,     &a.lsigc};
     for (double **q : ptrs)
         if (*q) {
             cudaFree(*q);
@@ -305,8 +309,11 @@ template <bool FLAT, class T> static void gauss_charge(rmhd_t h, T *P, double *U
     launch_ghosts(h, P + (size_t)PR_Q * h->K.G.S, 1);
 }
 
-// ev (optional): 9 events recorded between the kernel groups of the step
-template <bool FLAT, class T> static void enqueue_step_t(rmhd_t h, cudaEvent_t *ev)
+// The step in two parts: stages 1 and 2 (up to P2, J2 with their ghosts),
+// then the final assembly and recovery.  ev (optional): 9 events recorded
+// between the kernel groups; Us (optional): U* of stage 2 is written there.
+template <bool FLAT, class T>
+static void enqueue_stages12_t(rmhd_t h, cudaEvent_t *ev, double *Us)
 {
     Buffers &b = h->b;
     const StepConst &K = h->K;
@@ -332,8 +339,7 @@ template <bool FLAT, class T> static void enqueue_step_t(rmhd_t h, cudaEvent_t *
     launch_flux<T, FLAT>(h, PA, J1);
     mark(3);
     k_stage2<FLAT, T><<<nb, TPB, 0, h->st>>>(K, b.U, PA, b.GA, F0, F1, F2, b.dR1, b.met, b.sig,
-                                             PB, b.GB, b.V, J2, defer_of(h, 1), b.stats,
-                                             nullptr);
+                                             PB, b.GB, b.V, J2, defer_of(h, 1), b.stats, Us);
     if (dfr)
         k_deferred<FLAT, 2, T><<<nbd, TPB, 0, h->st>>>(K, defer_of(h, 1), b.met, b.sig, b.dR1,
                                                        PB, b.GB, nullptr, J2, b.V, nullptr,
@@ -343,6 +349,18 @@ template <bool FLAT, class T> static void enqueue_step_t(rmhd_t h, cudaEvent_t *
     if (K.qflux == RMHD_QFLUX_GAUSS) gauss_charge<FLAT, T>(h, PB, nullptr);
     if (K.qflux != 1) launch_ghosts(h, J2, 3);
     mark(5);
+}
+
+template <bool FLAT, class T> static void enqueue_final_t(rmhd_t h, cudaEvent_t *ev)
+{
+    Buffers &b = h->b;
+    const StepConst &K = h->K;
+    const unsigned nb = nblk(make_bricks(K.G.n).threads);
+    auto mark = [&](int i) { if (ev) cudaEventRecord(ev[i], h->st); };
+    const bool dfr = b.dcap > 0;
+    const unsigned nbd = deferred_blocks(h);
+    T *PA = (T *)b.PA, *PB = (T *)b.PB, *J2 = (T *)b.J2;
+    T *F0 = (T *)b.F[0], *F1 = (T *)b.F[1], *F2 = (T *)b.F[2];
     launch_flux<T, FLAT>(h, PB, J2);
     mark(6);
     k_final<FLAT, T><<<nb, TPB, 0, h->st>>>(K, b.V, PB, b.GB, F0, F1, F2, b.met, b.U, PA, b.GA,
@@ -355,6 +373,12 @@ template <bool FLAT, class T> static void enqueue_step_t(rmhd_t h, cudaEvent_t *
     launch_ghosts(h, PA, NPR);
     if (K.qflux == RMHD_QFLUX_GAUSS) gauss_charge<FLAT, T>(h, PA, b.U);
     mark(8);
+}
+
+template <bool FLAT, class T> static void enqueue_step_t(rmhd_t h, cudaEvent_t *ev)
+{
+    enqueue_stages12_t<FLAT, T>(h, ev, nullptr);
+    enqueue_final_t<FLAT, T>(h, ev);
 }
 
 static void enqueue_step(rmhd_t h, cudaEvent_t *ev = nullptr)
@@ -884,38 +908,6 @@ static int load_state(rmhd_t h, const double *U, const double *P)
     return RMHD_OK;
 }
 
-// the step up to the stage-2 recovery, keeping P1 (PA), J1, U* and P2 (PB),
-// J2 with their ghosts for the adjoint
-template <bool FLAT> static void enqueue_recompute_t(rmhd_t h)
-{
-    Buffers &b = h->b;
-    const StepConst &K = h->K;
-    const unsigned nb = nblk(make_bricks(K.G.n).threads);   // stage kernels: bricks
-    const bool dfr = b.dcap > 0;
-    const unsigned nbd = deferred_blocks(h);
-    double *PA = (double *)b.PA, *PB = (double *)b.PB, *J1 = (double *)b.J1, *J2 = (double *)b.J2;
-    double *F0 = (double *)b.F[0], *F1 = (double *)b.F[1], *F2 = (double *)b.F[2];
-    if (dfr) cudaMemsetAsync(b.dcount, 0, 3 * sizeof(int), h->st);
-    k_stage1<FLAT, double><<<nb, TPB, 0, h->st>>>(K, b.U, PA, b.GA, b.dR1, J1, b.met, b.sig,
-                                                  defer_of(h, 0), b.stats);
-    if (dfr)
-        k_deferred<FLAT, 1, double><<<nbd, TPB, 0, h->st>>>(K, defer_of(h, 0), b.met, b.sig,
-                                                            nullptr, PA, b.GA, b.dR1, J1, nullptr,
-                                                            nullptr, b.stats);
-    launch_ghosts(h, PA, NPR);
-    launch_ghosts(h, J1, 3);
-    launch_flux<double, FLAT>(h, PA, J1);
-    k_stage2<FLAT, double><<<nb, TPB, 0, h->st>>>(K, b.U, PA, b.GA, F0, F1, F2, b.dR1, b.met,
-                                                  b.sig, PB, b.GB, b.V, J2, defer_of(h, 1),
-                                                  b.stats, h->adj.Us);
-    if (dfr)
-        k_deferred<FLAT, 2, double><<<nbd, TPB, 0, h->st>>>(K, defer_of(h, 1), b.met, b.sig,
-                                                            b.dR1, PB, b.GB, nullptr, J2, b.V,
-                                                            nullptr, b.stats);
-    launch_ghosts(h, PB, NPR);
-    launch_ghosts(h, J2, 3);
-}
-
 template <bool FLAT> static void launch_adj_flux(rmhd_t h, const double *P, const double *J,
                                                  const double *lamR, double scale)
 {
@@ -992,20 +984,31 @@ struct AdjTimer {
     }
 };
 
-// lamU <- dL/dU^n from lamU = dL/dU^{n+1}; the handle holds U^n, P^n
-template <bool FLAT> static int adjoint_step_t(rmhd_t h, const double *Pnext, AdjTimer &tm)
+// stage states of one recorded step (slot q of the segment)
+struct StageSlot {
+    const double *U, *P1, *J1, *Us, *P2, *J2;
+};
+
+static StageSlot stage_slot(rmhd_t h, int q)
+{
+    const AdjBuf &a = h->adj;
+    const size_t S = (size_t)h->K.G.S;
+    return {a.segU + (size_t)q * NCO * S, a.segP1 + (size_t)q * NPR * S,
+            a.segJ1 + (size_t)q * 3 * S,  a.segUs + (size_t)q * NCO * S,
+            a.segP2 + (size_t)q * NPR * S, a.segJ2 + (size_t)q * 3 * S};
+}
+
+// lamU <- dL/dU^n from lamU = dL/dU^{n+1}, from the stage states of step n
+template <bool FLAT>
+static int adjoint_step_t(rmhd_t h, const StageSlot &q, const double *Pnext, AdjTimer &tm)
 {
     AdjBuf &a = h->adj;
     Buffers &b = h->b;
     const StepConst &K = h->K;
     const unsigned nb = nblk(K.G.N);
-    tm.begin(RMHD_ADJ_RECOMPUTE);
     // cells the final recovery reset keep no derivative in D, S_i, tau
     k_adj_reset_mask<<<nb, TPB, 0, h->st>>>(K, Pnext, a.lamU);
-    enqueue_recompute_t<FLAT>(h);
-    tm.end();
-    const double *P1 = (const double *)b.PA, *P2 = (const double *)b.PB;
-    const double *J1 = (const double *)b.J1, *J2 = (const double *)b.J2;
+    const double *P1 = q.P1, *P2 = q.P2, *J1 = q.J1, *J2 = q.J2;
     // F(P2, J2) entered U^{n+1} with weight dt/2
     tm.begin(RMHD_ADJ_SOURCES);
     k_adj_sources<FLAT><<<nb, TPB, 0, h->st>>>(K, P2, b.met, a.lamU, 0.5 * K.dt, a.lamP);
@@ -1015,7 +1018,7 @@ template <bool FLAT> static int adjoint_step_t(rmhd_t h, const double *Pnext, Ad
     launch_adj_flux<FLAT>(h, P2, J2, a.lamU, 0.5 * K.dt);
     tm.end();
     tm.begin(RMHD_ADJ_STAGES);
-    k_adj_stage2<FLAT><<<nb, TPB, 0, h->st>>>(K, a.Us, P2, b.met, b.sig, a.lamU, a.lamP, a.lamJ,
+    k_adj_stage2<FLAT><<<nb, TPB, 0, h->st>>>(K, q.Us, P2, b.met, b.sig, a.lamU, a.lamP, a.lamJ,
                                               a.lamR1, a.lamdR1, a.lamUn, a.lsigc, a.bad);
     tm.end();
     // F(P1, J1): its adjoint is lamR1
@@ -1027,7 +1030,7 @@ template <bool FLAT> static int adjoint_step_t(rmhd_t h, const double *Pnext, Ad
     launch_adj_flux<FLAT>(h, P1, J1, a.lamR1, 1.0);
     tm.end();
     tm.begin(RMHD_ADJ_STAGES);
-    k_adj_stage1<FLAT><<<nb, TPB, 0, h->st>>>(K, b.U, P1, b.met, b.sig, a.lamP, a.lamJ, a.lamdR1,
+    k_adj_stage1<FLAT><<<nb, TPB, 0, h->st>>>(K, q.U, P1, b.met, b.sig, a.lamP, a.lamJ, a.lamdR1,
                                               a.lamUn, a.lsigc, a.bad);
     tm.end();
     double *t = a.lamU;
@@ -1065,7 +1068,9 @@ extern "C" int rmhd_adjoint_forward(rmhd_t h, double dt, int nsteps, int checkpo
               {&a.segP, (a.every + 1) * pz}, {&a.endU, u},       {&a.endP, pz},
               {&a.lamU, u},              {&a.lamUn, u},          {&a.lamR1, u},
               {&a.lamP, pz},             {&a.lamJ, fbytes(h, 3)}, {&a.lamdR1, fbytes(h, 3)},
-              {&a.Us, u},                {&a.lsig, sizeof(double)},
+              {&a.segP1, a.every * pz},  {&a.segJ1, a.every * fbytes(h, 3)},
+              {&a.segUs, a.every * u},   {&a.segP2, a.every * pz},
+              {&a.segJ2, a.every * fbytes(h, 3)}, {&a.lsig, sizeof(double)},
               {&a.C, fbytes(h, ADJ_SLOTS * ADJ_NF)}, {&a.lsigc, fbytes(h, 1)}};
     for (auto &e : al) {
         cudaError_t err = cudaMalloc((void **)e.p, e.n);
@@ -1137,26 +1142,37 @@ extern "C" int rmhd_adjoint_backward(rmhd_t h, const double *lam_prims, double *
         const int s0 = seg * a.every;
         const int s1 = s0 + a.every < a.nsteps ? s0 + a.every : a.nsteps;
         // states s0 .. s1-1 of the segment, then P^{s1}
+        // re-run the segment from its checkpoint, keeping every step's
+        // state and stage states
         tm.begin(RMHD_ADJ_RECOMPUTE);
         rc = load_state(h, a.ckU + (size_t)seg * NCO * S, a.ckP + (size_t)seg * NPR * S);
         if (rc) return rc;
         for (int n = s0; n < s1; n++) {
-            rc = save_state(h, a.segU + (size_t)(n - s0) * NCO * S,
-                            a.segP + (size_t)(n - s0) * NPR * S);
+            const int q = n - s0;
+            rc = save_state(h, a.segU + (size_t)q * NCO * S, a.segP + (size_t)q * NPR * S);
             if (rc) return rc;
-            if (n + 1 < s1) enqueue_step(h);
+            if (h->flat) enqueue_stages12_t<true, double>(h, nullptr, a.segUs + (size_t)q * NCO * S);
+            else enqueue_stages12_t<false, double>(h, nullptr, a.segUs + (size_t)q * NCO * S);
+            CK(cudaMemcpyAsync(a.segP1 + (size_t)q * NPR * S, h->b.PA, fbytes(h, NPR),
+                               cudaMemcpyDeviceToDevice, h->st));
+            CK(cudaMemcpyAsync(a.segJ1 + (size_t)q * 3 * S, h->b.J1, fbytes(h, 3),
+                               cudaMemcpyDeviceToDevice, h->st));
+            CK(cudaMemcpyAsync(a.segP2 + (size_t)q * NPR * S, h->b.PB, fbytes(h, NPR),
+                               cudaMemcpyDeviceToDevice, h->st));
+            CK(cudaMemcpyAsync(a.segJ2 + (size_t)q * 3 * S, h->b.J2, fbytes(h, 3),
+                               cudaMemcpyDeviceToDevice, h->st));
+            if (n + 1 < s1) {
+                if (h->flat) enqueue_final_t<true, double>(h, nullptr);
+                else enqueue_final_t<false, double>(h, nullptr);
+            }
         }
         tm.end();
         const double *Pend = seg + 1 < a.nck ? a.ckP + (size_t)(seg + 1) * NPR * S : a.endP;
         for (int n = s1 - 1; n >= s0; n--) {
             const double *Pnext = n + 1 == s1 ? Pend : a.segP + (size_t)(n + 1 - s0) * NPR * S;
-            tm.begin(RMHD_ADJ_RECOMPUTE);
-            rc = load_state(h, a.segU + (size_t)(n - s0) * NCO * S,
-                            a.segP + (size_t)(n - s0) * NPR * S);
-            tm.end();
-            if (rc) return rc;
-            rc = h->flat ? adjoint_step_t<true>(h, Pnext, tm)
-                         : adjoint_step_t<false>(h, Pnext, tm);
+            const StageSlot q = stage_slot(h, n - s0);
+            rc = h->flat ? adjoint_step_t<true>(h, q, Pnext, tm)
+                         : adjoint_step_t<false>(h, q, Pnext, tm);
             if (rc) return rc;
         }
     }
