@@ -40,7 +40,11 @@ def test_param_struct_size_matches():
 @pytest.mark.parametrize("bad", [dict(n=(0, 1, 1)), dict(dx=(0.0, 1, 1)), dict(gamma_eos=1.0),
                                  dict(recon=7), dict(sigma0=-1.0), dict(bc=(5, 0, 0)),
                                  dict(precision=3), dict(qflux_mode=9), dict(c2p_tol=0.0),
-                                 dict(n=(2, 1, 1), bc=(0, 0, 0))])
+                                 dict(n=(2, 1, 1), bc=(0, 0, 0)),
+                                 # padded cells beyond 2^31 (the 32-bit index limit)
+                                 dict(n=(1300, 1300, 1300)), dict(sigma_model=4),
+                                 dict(c2p_maxit=0), dict(c2p_wmax=1.0),
+                                 dict(c2p_first_pass=-1), dict(n=(-4, 1, 1))])
 def test_create_rejects_bad_params_without_touching_the_device(bad):
     with pytest.raises(R.RMHDError) as e:
         R.Solver(R.make_params(**bad))
