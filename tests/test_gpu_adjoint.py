@@ -126,7 +126,19 @@ CASES = {
     # lapse, shift, off-diagonal 3-metric, extrinsic curvature
     "general_metric_weno5": lambda: _general_metric("weno5"),
     "general_metric_mc2": lambda: _general_metric("mc2"),
+    # conductivity models: sigma0 x profile, sigma0 D^(1/2), sigma0 (1 - D_atmo/D)^2
+    "sigma_profile": lambda: _with_sigma(_generic_smooth(True, "weno5"), 1),
+    "sigma_powD": lambda: _with_sigma(_generic_smooth(True, "weno5"), 2, sigma_exp=0.5),
+    "sigma_atmo": lambda: _with_sigma(_generic_smooth(True, "weno5"), 3, D_atmo=0.3),
 }
+
+
+def _with_sigma(wl, model, **extra):
+    wl.params.update(sigma_model=model, **extra)
+    if model == 1:
+        rng = np.random.default_rng(41)
+        wl.sigma_profile = 1.0 + 0.5 * np.tanh(_smooth_modes(wl.shape, rng, kmax=1))
+    return wl
 
 
 @pytest.mark.parametrize("name,nsteps,every", [("alfven_s1e3", 6, 4), ("alfven_s10", 6, 2),
@@ -134,7 +146,9 @@ CASES = {
                                                ("generic_minmod_curved", 4, 1),
                                                ("blast_weno5", 4, 3),
                                                ("general_metric_weno5", 4, 2),
-                                               ("general_metric_mc2", 4, 2)])
+                                               ("general_metric_mc2", 4, 2),
+                                               ("sigma_profile", 4, 2), ("sigma_powD", 4, 2),
+                                               ("sigma_atmo", 4, 2)])
 def test_adjoint_matches_oracle_finite_differences(name, nsteps, every):
     wl = CASES[name]()
     dx = wl.params["dx"]
