@@ -8,7 +8,9 @@ as the headline and the FP64 path beside it.
                     [--adjoint-n 128] [--adjoint-steps 60] [--adjoint-every 10]
 
 The "adjoint" object times the gradient of a B^y misfit after 60 steps of
-the 128^3 Alfven cube (rmhd_adjoint_forward + rmhd_adjoint_backward).
+the 128^3 Alfven cube (rmhd_adjoint_forward + rmhd_adjoint_backward); the
+"configs" object the Brio-Wu shocktube's latency per step, the 128^3
+Alfven cube and the 192^3 curved star (--no-adjoint, --no-configs skip them).
 
 One JSON line on stdout (rank 0).  With N > 1 (torchrun) every rank runs its
 own replica of the workload on its own GPU (the method has no data-path
@@ -312,6 +314,65 @@ def run_adjoint(args):
                          "launch_ms": fl_ms / (nd * 2 * K), "traffic": None}}
 
 
+def run_configs(args):
+    """The other configurations: the 400-cell Brio-Wu shocktube (launch-bound:
+    latency per step, one CUDA-graph replay per step against one launch
+    sequence per step), the 128^3 Alfven cube and the 192^3 curved star
+    (zone-updates/s of both paths, recovery statistics)."""
+    import torch
+    import paper_2510_18968_b300 as R
+    out = {}
+
+    def timed(s, dt, k, graph=True):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        st = torch.cuda.current_stream()
+        e0.record(st)
+        if graph:
+            s.step(dt, k, sync=False)
+        else:
+            for _ in range(k):
+                s.step(dt, 1, sync=False)
+        e1.record(st)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    wl = W.brio_wu(n=400)
+    s = R.Solver(wl.params)
+    s.set_prims(np.ascontiguousarray(wl.prim))
+    s.step(wl.dt, 20)
+    ms_g = timed(s, wl.dt, 300)
+    ms_l = timed(s, wl.dt, 300, graph=False)
+    s.close()
+    out["brio_wu_400"] = {"workload": "Brio-Wu 400 cells, minmod+HLLE, sigma=1e5, FP64",
+                          "ms_per_step_graph": ms_g / 300, "ms_per_step_launches": ms_l / 300}
+    for name, make in (("alfven_128", lambda: W.alfven_diag(n=128, sigma=1e4)),
+                       ("lane_emden_192", lambda: W.lane_emden_star(n=192))):
+        wl = make()
+        d = {}
+        for prec in ("mixed", "fp64"):
+            s = R.Solver(dict(wl.params, precision=1 if prec == "mixed" else 0))
+            if wl.alpha is not None:
+                a, b, g, K = wl.metric_arrays()
+                s.set_metric(np.ascontiguousarray(a), np.ascontiguousarray(b),
+                             np.ascontiguousarray(g), np.ascontiguousarray(K))
+            if wl.sigma_profile is not None:
+                s.set_sigma(np.ascontiguousarray(wl.sigma_profile))
+            s.set_prims(np.ascontiguousarray(wl.prim))
+            s.step(wl.dt, 3)
+            ms = timed(s, wl.dt, 10)
+            st = s.stats()
+            s.close()
+            d[prec] = {"value": wl.ncells * 10 / (ms * 1e-3), "ms_per_step": ms / 10,
+                       "paper_iterations_per_recovery": st["c2p_iterations"] / st["c2p_calls"],
+                       "fallbacks": st["c2p_fallbacks"], "atmosphere_resets":
+                       st["c2p_failures"] + st["atmo_floor_resets"]}
+        d["unit"] = UNIT
+        d["mixed_speedup"] = d["fp64"]["ms_per_step"] / d["mixed"]["ms_per_step"]
+        out[name] = d
+    return out
+
+
 def cpu_oracle_sample(nz, steps):
     """The FP64 oracle on a z-slab (nz cells thick, same x-y plane and
     options) of the 256^3 workload; returns zone-updates/s and the sample."""
@@ -337,6 +398,7 @@ def main():
     ap.add_argument("--precision", default="both", choices=["both", "mixed", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-configs", action="store_true")
     ap.add_argument("--adjoint-n", type=int, default=128)
     ap.add_argument("--adjoint-steps", type=int, default=60)
     ap.add_argument("--adjoint-every", type=int, default=10)
@@ -406,6 +468,8 @@ def main():
     line["gpu_launches"] = per_step * args.steps
     if not args.no_adjoint:
         line["adjoint"] = run_adjoint(args)
+    if not args.no_configs:
+        line["configs"] = run_configs(args)
     if not args.no_cpu_baseline:
         v, sample = cpu_oracle_sample(4, 1)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",

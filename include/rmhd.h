@@ -129,7 +129,9 @@ int rmhd_set_prims(rmhd_t h, const double *prims, int on_device);
  *   final    U^{n+1} = U^n + dt/2 (F[U1] + F[U2]) + dt/2 (R[U1] + R[U2]),
  *            then recovery with E fixed,
  * gamma = 1 - 1/sqrt(2) (Table imex); R acts on E only (Sec. III.A).
- * Enqueued on the handle's stream.  If fail_count is NULL the call returns
+ * Enqueued on the handle's stream; with nsteps >= 2 one step is captured
+ * as a CUDA graph (once, and again when dt or another step constant
+ * changes) and replayed nsteps times.  If fail_count is NULL the call returns
  * without synchronising (errors of this call then surface at the next
  * synchronising call); otherwise it synchronises, stores the number of
  * recoveries reset to the atmosphere during these steps, and returns

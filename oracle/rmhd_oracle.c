@@ -854,7 +854,12 @@ int orc_con2prim(const orc_params *P, const double cons_in[14], int implicit,
     double cE[3] = {in.cE0[0], in.cE0[1], in.cE0[2]};
     double rho = 0.0;
     int it1 = 0, it2 = 0, status, slow = 0;
-    if (c2p_paper(&in, &p, v, cE, &rho, &it1, 0, &slow)) {
+    /* atmosphere without iterating: rho = D / (W sqrt(gamma)) <= D / sqrt(gamma)
+     * for every velocity, so a density D / sqrt(gamma) below the floor puts
+     * every root below it (reading of the atmosphere treatment, Sec. IV.E) */
+    if (!(in.D / m.sg >= P->rho_atmo * (1.0 + P->atmo_tol))) {
+        status = 3;
+    } else if (c2p_paper(&in, &p, v, cE, &rho, &it1, 0, &slow)) {
         status = 0;
     } else {
         p = guess[P_P];

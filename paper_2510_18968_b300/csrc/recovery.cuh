@@ -593,93 +593,100 @@ __device__ int recover(const RecIn &in, const Met<double> &m, const RecOpts &o,
     int it1 = 0, it2 = 0, status;
     bool slow = false;
     int first = -2;   // REC_FIRST / REC_RESUME outcome of the paper iteration
-    if (phase == REC_FIRST || phase == REC_RESUME) {
-        PaperState s;
-        if (phase == REC_FIRST) {
-            // undecided or given up: both go to the second pass
-            if (!paper_start<FLAT>(c, p, v, s)) {
-                s.it = 0;
-                s.p = p;
-                first = 0;
-            } else {
-                first = paper_run<FLAT>(c, s, guess_p, o.first_cap, E, rho, false, slow);
-            }
-            if (first != 1) {
-                s.outcome = first;
-                s.slow = slow ? 1 : 0;
-                *ps = s;
-                iters = s.it;
-                return REC_DEFER;
-            }
-        } else {
-            s = *ps;
-            if (s.outcome == 0) {
-                first = 0;
-                slow = s.slow != 0;
-            } else {
-                first = paper_run<FLAT>(c, s, guess_p, o.maxit, E, rho, false, slow);
-            }
-        }
-        it1 = s.it;
-        p = s.p;
-        v[0] = s.v[0]; v[1] = s.v[1]; v[2] = s.v[2];
-    }
-    // outcome of the paper iteration: 1 converged, 0 gave up
-    int paper;
-    if (first != -2)
-        paper = first;
-    else if (phase == REC_FALLBACK)
-        paper = 0;
-    else
-        paper = paper_iteration<FLAT>(c, p, v, E, rho, it1, false, slow) ? 1 : 0;
-    if (paper == 1) {
-        status = 0;
-    } else if (phase == REC_PRIMARY) {
-        iters = it1;
-        return REC_DEFER;
+    // atmosphere without iterating: rho = D / (W sqrt(gamma)) <= D / sqrt(gamma)
+    // for every velocity, so below the floor there every root is reset
+    const bool atmo = !((FLAT ? in.D : in.D / m.sg) >= o.atmo_floor);
+    if (atmo) {
+        status = 3;
     } else {
-        c.iD = 1.0 / in.D;
-        p = guess_p;
-        v[0] = guess_v[0]; v[1] = guess_v[1]; v[2] = guess_v[2];
-        E[0] = in.cE0[0]; E[1] = in.cE0[1]; E[2] = in.cE0[2];
-        status = newton_fallback<FLAT>(c, p, v, E, rho, it2) ? 1 : 2;
-        if (status == 2) {
-            int it3 = 0;
+        if (phase == REC_FIRST || phase == REC_RESUME) {
+            PaperState s;
+            if (phase == REC_FIRST) {
+                // undecided or given up: both go to the second pass
+                if (!paper_start<FLAT>(c, p, v, s)) {
+                    s.it = 0;
+                    s.p = p;
+                    first = 0;
+                } else {
+                    first = paper_run<FLAT>(c, s, guess_p, o.first_cap, E, rho, false, slow);
+                }
+                if (first != 1) {
+                    s.outcome = first;
+                    s.slow = slow ? 1 : 0;
+                    *ps = s;
+                    iters = s.it;
+                    return REC_DEFER;
+                }
+            } else {
+                s = *ps;
+                if (s.outcome == 0) {
+                    first = 0;
+                    slow = s.slow != 0;
+                } else {
+                    first = paper_run<FLAT>(c, s, guess_p, o.maxit, E, rho, false, slow);
+                }
+            }
+            it1 = s.it;
+            p = s.p;
+            v[0] = s.v[0]; v[1] = s.v[1]; v[2] = s.v[2];
+        }
+        // outcome of the paper iteration: 1 converged, 0 gave up
+        int paper;
+        if (first != -2)
+            paper = first;
+        else if (phase == REC_FALLBACK)
+            paper = 0;
+        else
+            paper = paper_iteration<FLAT>(c, p, v, E, rho, it1, false, slow) ? 1 : 0;
+        if (paper == 1) {
+            status = 0;
+        } else if (phase == REC_PRIMARY) {
+            iters = it1;
+            return REC_DEFER;
+        } else {
+            c.iD = 1.0 / in.D;
             p = guess_p;
             v[0] = guess_v[0]; v[1] = guess_v[1]; v[2] = guess_v[2];
             E[0] = in.cE0[0]; E[1] = in.cE0[1]; E[2] = in.cE0[2];
-            if (bracket_fallback<FLAT>(c, p, v, E, rho, it3)) status = 4;
-            it2 += it3;
-        }
-        if (status == 2) {
-            // both fallbacks failed: if the paper iteration was stopped only
-            // for being slow (decided again here in the deferred pass), let
-            // it run to its cap
-            int it4 = 0;
-            bool slow2 = false;
-            double p4 = guess_p, v4[3] = {guess_v[0], guess_v[1], guess_v[2]};
-            double E4[3] = {in.cE0[0], in.cE0[1], in.cE0[2]}, rho4 = 0.0;
-            if (phase == REC_FALLBACK || slow) {
-                if (phase == REC_FALLBACK)
-                    paper_iteration<FLAT>(c, p4, v4, E4, rho4, it4, false, slow2);
-                if ((slow || slow2)) {
-                    p4 = guess_p;
-                    v4[0] = guess_v[0]; v4[1] = guess_v[1]; v4[2] = guess_v[2];
-                    E4[0] = in.cE0[0]; E4[1] = in.cE0[1]; E4[2] = in.cE0[2];
-                    int it5 = 0;
-                    bool dummy;
-                    if (paper_iteration<FLAT>(c, p4, v4, E4, rho4, it5, true, dummy)) {
-                        status = 0;
-                        p = p4; rho = rho4;
-                        v[0] = v4[0]; v[1] = v4[1]; v[2] = v4[2];
-                        E[0] = E4[0]; E[1] = E4[1]; E[2] = E4[2];
-                    }
-                    it4 += it5;
-                }
+            status = newton_fallback<FLAT>(c, p, v, E, rho, it2) ? 1 : 2;
+            if (status == 2) {
+                int it3 = 0;
+                p = guess_p;
+                v[0] = guess_v[0]; v[1] = guess_v[1]; v[2] = guess_v[2];
+                E[0] = in.cE0[0]; E[1] = in.cE0[1]; E[2] = in.cE0[2];
+                if (bracket_fallback<FLAT>(c, p, v, E, rho, it3)) status = 4;
+                it2 += it3;
             }
-            it2 += it4;
+            if (status == 2) {
+                // both fallbacks failed: if the paper iteration was stopped only
+                // for being slow (decided again here in the deferred pass), let
+                // it run to its cap
+                int it4 = 0;
+                bool slow2 = false;
+                double p4 = guess_p, v4[3] = {guess_v[0], guess_v[1], guess_v[2]};
+                double E4[3] = {in.cE0[0], in.cE0[1], in.cE0[2]}, rho4 = 0.0;
+                if (phase == REC_FALLBACK || slow) {
+                    if (phase == REC_FALLBACK)
+                        paper_iteration<FLAT>(c, p4, v4, E4, rho4, it4, false, slow2);
+                    if ((slow || slow2)) {
+                        p4 = guess_p;
+                        v4[0] = guess_v[0]; v4[1] = guess_v[1]; v4[2] = guess_v[2];
+                        E4[0] = in.cE0[0]; E4[1] = in.cE0[1]; E4[2] = in.cE0[2];
+                        int it5 = 0;
+                        bool dummy;
+                        if (paper_iteration<FLAT>(c, p4, v4, E4, rho4, it5, true, dummy)) {
+                            status = 0;
+                            p = p4; rho = rho4;
+                            v[0] = v4[0]; v[1] = v4[1]; v[2] = v4[2];
+                            E[0] = E4[0]; E[1] = E4[1]; E[2] = E4[2];
+                        }
+                        it4 += it5;
+                    }
+                }
+                it2 += it4;
+            }
         }
-    }
+    }   // not atmosphere
     iters = it1 + it2;
     if ((status == 0 || status == 1 || status == 4) && !(rho >= o.atmo_floor)) status = 3;
     if (status == 2 || status == 3) {

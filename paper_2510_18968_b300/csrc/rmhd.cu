@@ -79,12 +79,22 @@ void free_adj(AdjBuf &a)
 
 } // namespace
 
+// one step captured as a CUDA graph, replayed by rmhd_step (valid for the
+// step constants and metric flag it was captured with)
+struct StepGraph {
+    cudaGraphExec_t exec = nullptr;
+    StepConst K;
+    bool flat = true;
+    int precision = -1;
+};
+
 struct rmhd_s {
     rmhd_params p;
     cudaStream_t st;
     StepConst K;
     Buffers b;
     AdjBuf adj;
+    StepGraph graph;
     bool flat = true;
     bool have_state = false;
     long long steps = 0;
@@ -719,6 +729,53 @@ extern "C" int rmhd_set_state(rmhd_t h, const double *cons, const double *prims,
     return RMHD_OK;
 }
 
+// The step as a CUDA graph: captured once on a private stream (a legacy
+// default stream cannot be captured), then launched on the handle's stream.
+// Re-captured when the step constants, the metric flag or the precision
+// change.  Replaying it removes the per-kernel launch cost, which is what a
+// step of a small grid (the 1D shocktube) is made of.
+static int step_graph(rmhd_t h, cudaGraphExec_t *out)
+{
+    StepGraph &g = h->graph;
+    if (g.exec && g.flat == h->flat && g.precision == h->p.precision &&
+        memcmp(&g.K, &h->K, sizeof(StepConst)) == 0) {
+        *out = g.exec;
+        return RMHD_OK;
+    }
+    if (g.exec) {
+        cudaGraphExecDestroy(g.exec);
+        g.exec = nullptr;
+    }
+    cudaStream_t cs;
+    CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaStream_t user = h->st;
+    h->st = cs;
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        enqueue_step(h);
+        e = cudaStreamEndCapture(cs, &graph);
+    }
+    h->st = user;
+    cudaStreamDestroy(cs);
+    if (e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return set_err(h, RMHD_ECUDA, "step graph capture failed: %s", cudaGetErrorString(e));
+    }
+    e = cudaGraphInstantiate(&g.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        g.exec = nullptr;
+        return set_err(h, RMHD_ECUDA, "step graph instantiation failed: %s",
+                       cudaGetErrorString(e));
+    }
+    g.K = h->K;
+    g.flat = h->flat;
+    g.precision = h->p.precision;
+    *out = g.exec;
+    return RMHD_OK;
+}
+
 extern "C" int rmhd_step(rmhd_t h, double dt, int nsteps, long long *fail_count)
 {
     if (!h) return set_err(nullptr, RMHD_EINVAL, "handle is NULL");
@@ -732,8 +789,13 @@ extern "C" int rmhd_step(rmhd_t h, double dt, int nsteps, long long *fail_count)
         CK(cudaMemcpyAsync(before, h->b.stats, sizeof(before), cudaMemcpyDeviceToHost, h->st));
         CK(cudaStreamSynchronize(h->st));
     }
-    for (int s = 0; s < nsteps; s++) {
-        enqueue_step(h);
+    if (nsteps >= 2) {
+        cudaGraphExec_t exec = nullptr;
+        int rc = step_graph(h, &exec);
+        if (rc) return rc;
+        for (int s = 0; s < nsteps; s++) CK(cudaGraphLaunch(exec, h->st));
+    } else {
+        for (int s = 0; s < nsteps; s++) enqueue_step(h);
     }
     CK(cudaGetLastError());
     h->steps += nsteps;
@@ -1213,6 +1275,7 @@ extern "C" int rmhd_destroy(rmhd_t h)
 {
     if (!h) return RMHD_OK;
     cudaStreamSynchronize(h->st);
+    if (h->graph.exec) cudaGraphExecDestroy(h->graph.exec);
     free_adj(h->adj);
     free_all(h->b);
     delete h;

@@ -371,3 +371,32 @@ def test_pressure_bracket_recovers_states_where_newton_stalls():
         U = oracle.prim2con(out, 1.0, (0, 0, 0), (1, 0, 0, 1, 0, 1), gam)
         scale = cin[4] + cin[0] + out[1]
         assert np.abs(U[:5] - cin[:5]).max() < 1e-12 * scale
+
+
+@pytest.mark.parametrize("D_over_floor", [0.5, 0.999])
+def test_con2prim_density_below_the_floor_is_atmosphere_at_once(D_over_floor):
+    """rho = D / (W sqrt(gamma)) <= D / sqrt(gamma): when D / sqrt(gamma) is
+    below the floor rho_atmo (1 + atmo_tol) every root is below it, so the
+    recovery returns the atmosphere without iterating (status 3, 0
+    iterations), calE of the implicit solve at v = 0 = calE*/(1 + c alpha sigma)
+    and calB kept; just above the floor it iterates as usual."""
+    P = oracle.make_params(gamma_eos=2.0, rho_atmo=1e-6, K_atmo=100.0, atmo_tol=1e-2)
+    g6 = (1.21, 0.0, 0.0, 1.21, 0.0, 1.21)       # sqrt(gamma) = 1.331
+    sg = 1.331
+    floor = 1e-6 * 1.01
+    cons = np.zeros(14)
+    cons[0] = D_over_floor * floor * sg
+    cons[1], cons[4] = 1e-7, 2e-5
+    cons[5], cons[8] = 0.02, 0.03
+    guess = np.zeros(14)
+    guess[0], guess[1] = 1e-6, 1e-10
+    c, sigma, alpha = 0.05, 20.0, 0.9
+    out, cout, it, st = oracle.con2prim(P, cons, 1, c, sigma, guess, alpha=alpha, g6=g6)
+    assert st == 3 and it == 0
+    assert out[0] == 1e-6 and out[1] == 100.0 * 1e-12 and not out[2:5].any()
+    assert abs(cout[8] - 0.03 / (1.0 + c * alpha * sigma)) <= 1e-15
+    assert abs(out[8] - 0.02 / sg) <= 1e-15
+    # above the floor the same state is iterated (it need not converge)
+    cons[0] = 1.5 * floor * sg
+    _, _, it2, st2 = oracle.con2prim(P, cons, 1, c, sigma, guess, alpha=alpha, g6=g6)
+    assert it2 > 0
