@@ -146,3 +146,32 @@ def test_mixed_precision_l1_error_at_full_size(name):
     assert ec.max() < 1e-5, (name, ec)
     keep = [f for f in range(14) if not (name == "lane_emden_192" and 2 <= f <= 4)]
     assert ep[keep].max() < 1e-5, (name, ep)
+
+
+def test_long_blast_run_keeps_its_mirror_symmetry():
+    """100 steps of the 256^3 blast (FP64 path): finite, and the mirror
+    symmetries of the initial data kept to rounding (the run has recoveries
+    that fail and are reset to the atmosphere after ~20 steps; those
+    decisions come out mirror-symmetric too).  The
+    resistive system is invariant under reflections (E polar, B axial) and
+    under the global sign flip of (E, B, q, psi, phi), since the fluid sees
+    only products of the fields.  With B = (0.1, 0, 0): x -> -x with E polar
+    and B axial leaves the data unchanged; y -> -y does so combined with the
+    sign flip (E axial, B polar)."""
+    wl = W.cyl_blast(n=256)
+    s = make_solver(wl)
+    fails = s.step(wl.dt, 100)
+    p = s.get_prims()
+    s.close()
+    assert np.isfinite(p).all()
+    # odd fields under each symmetry (arrays are (field, z, y, x))
+    odd_x = [2, 5, 9, 10, 12]          # v^x; E^x; B^y, B^z; phi (div B, pseudoscalar)
+    odd_y = [3, 5, 7, 9, 11, 13]       # v^y; E^x, E^z; B^y; psi, q (flip of E)
+    scale = np.abs(p).reshape(14, -1).max(axis=1)
+    scale[11:14] = np.maximum(scale[11:14], scale[5:11].max())
+    for axis, odd in ((3, odd_x), (2, odd_y)):
+        sign = np.ones(14)
+        sign[odd] = -1.0
+        mirror = sign[:, None, None, None] * np.flip(p, axis=axis)
+        err = np.abs(p - mirror).reshape(14, -1).max(axis=1) / np.maximum(scale, 1e-300)
+        assert err.max() < 1e-9, (axis, err)
