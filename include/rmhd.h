@@ -272,6 +272,12 @@ int rmhd_adjoint_backward(rmhd_t h, const double *lam_prims, double *grad_prims0
                           double *grad_log_sigma0, int on_device,
                           double ms[RMHD_NADJPROF]);
 
+/* Testing entry point (no counterpart in the paper): out[i] = 1/x[i] as the
+ * recovery kernels compute it (Newton-Raphson refinement of a
+ * single-precision seed), for checking against FP64 division.  Device
+ * pointers, n >= 0; runs on the stream. */
+int rmhd_test_rcp64(const double *x, double *out, long long n, void *cuda_stream);
+
 const char *rmhd_last_error(rmhd_t h);
 
 /* Free all device memory of the handle (synchronises its stream). */

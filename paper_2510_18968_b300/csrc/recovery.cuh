@@ -76,7 +76,7 @@ __device__ __forceinline__ void implicit_field(const RecCtx<FLAT> &c, const doub
     for (int i = 0; i < 3; i++) r[i] = c.in.cE0[i] - C * (FLAT ? vxB[i] : vxB[i] * c.isg);
     const double s = dot3(vl, r);
     const double q = 1.0 + C * (1.0 - v2);
-    const double inv = 1.0 / ((1.0 + C) * q);
+    const double inv = rcp64((1.0 + C) * q);
 #pragma unroll
     for (int i = 0; i < 3; i++) E[i] = (r[i] * q + C * v[i] * s) * inv;
 }
@@ -101,7 +101,7 @@ __device__ __forceinline__ bool fluid_step(const RecCtx<FLAT> &c, const double E
     double P[3];
     cross3(E, c.in.cB, P);
     const double den = c.in.tau + c.in.D + sgv(c) * p - EM;
-    const double iden = 1.0 / den;
+    const double iden = rcp64(den);
 #pragma unroll
     for (int i = 0; i < 3; i++) vl[i] = (c.in.S[i] - P[i]) * iden;
     raise<double, FLAT>(c.m, vl, v);
@@ -201,7 +201,7 @@ __device__ int paper_run(const RecCtx<FLAT> &c, PaperState &s, double p_guess, i
         double ratio;
         if (num > 0.0) {
             const double gn = Gam * num * Winv;
-            ratio = f * (D + gn) / (s.v2 * gg1 * num * Winv - D - gn);
+            ratio = f * (D + gn) * rcp64(s.v2 * gg1 * num * Winv - D - gn);
         } else {
             ratio = -f;
         }
@@ -216,7 +216,7 @@ __device__ int paper_run(const RecCtx<FLAT> &c, PaperState &s, double p_guess, i
             rho_out = D * Winv * isgv(c);
             return 1;
         }
-        if (iscale0 == 0.0) iscale0 = sgv(c) / (c.in.tau + D + sgv(c) * p_guess);
+        if (iscale0 == 0.0) iscale0 = sgv(c) * rcp64(c.in.tau + D + sgv(c) * p_guess);
         const double meas = dv + fabs(dp) * iscale0;
         if (!isfinite(meas)) return 0;
         // diverging: three successive growing changes above the noise

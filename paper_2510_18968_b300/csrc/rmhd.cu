@@ -1263,6 +1263,25 @@ extern "C" int rmhd_adjoint_backward(rmhd_t h, const double *lam_prims, double *
     return RMHD_OK;
 }
 
+// ------------------------------------------------------------------ testing
+
+__global__ void k_test_rcp64(long long n, const double *__restrict__ x, double *out)
+{
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t < n) out[t] = rcp64(x[t]);
+}
+
+extern "C" int rmhd_test_rcp64(const double *x, double *out, long long n, void *cuda_stream)
+{
+    if (n < 0 || (n > 0 && (!x || !out))) return set_err(nullptr, RMHD_EINVAL, "bad arguments");
+    if (n == 0) return RMHD_OK;
+    k_test_rcp64<<<nblk(n), TPB, 0, (cudaStream_t)cuda_stream>>>(n, x, out);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return set_err(nullptr, RMHD_ECUDA, "launch failed: %s", cudaGetErrorString(e));
+    return RMHD_OK;
+}
+
 extern "C" const char *rmhd_last_error(rmhd_t h) { return h ? h->err : g_noh_err; }
 
 // error text of an entry point without a handle (used by the other source file)

@@ -349,3 +349,28 @@ def test_graph_replay_matches_single_launches():
         s.close()
     assert np.array_equal(runs[0][0], runs[1][0])
     assert np.array_equal(runs[0][1], runs[1][1])
+
+
+def test_fp64_reciprocal_of_the_recovery_matches_division(torch_cuda):
+    """The recovery's 1/x (Newton-Raphson from a single-precision seed)
+    against FP64 division: within 2 ulp over 30 decades and both signs;
+    zero, infinities, NaN and values outside the FP32 range take the
+    division."""
+    import torch
+    import paper_2510_18968_b300 as R
+    L = R.load()
+    rng = np.random.default_rng(5)
+    x = 10.0 ** rng.uniform(-30, 30, 200000) * rng.choice([-1.0, 1.0], 200000)
+    x = np.concatenate([x, [0.0, -0.0, np.inf, -np.inf, np.nan, 1e-300, 1e300, 1.0, 3.0]])
+    xd = torch.tensor(x, device="cuda")
+    out = torch.empty_like(xd)
+    assert L.rmhd_test_rcp64(xd.data_ptr(), out.data_ptr(), xd.numel(), None) == 0
+    torch.cuda.synchronize()
+    got, ref = out.cpu().numpy(), (1.0 / xd).cpu().numpy()
+    fin = np.isfinite(ref) & (ref != 0)
+    ulp = np.abs(got[fin] - ref[fin]) / np.spacing(np.abs(ref[fin]))
+    assert ulp.max() <= 2.0, ulp.max()
+    special = ~fin
+    assert np.array_equal(np.isnan(got[special]), np.isnan(ref[special]))
+    same = special & ~np.isnan(ref)
+    assert np.array_equal(got[same], ref[same])
