@@ -239,10 +239,12 @@ int rmhd_set_sigma0(rmhd_t h, double sigma0);
  * of its steps, which the reverse sweep keeps instead of recomputing them)
  * and the adjoint fields: about 210 + 28 nsteps / checkpoint_every + 76
  * checkpoint_every padded FP64 fields in all (90 of them hold the per-face
- * stencil contributions of the flux adjoint).  Replaces any earlier recording.  Errors:
+ * stencil contributions of the flux adjoint).  checkpoint_every = 0 keeps
+ * the whole tape instead (about 240 + 76 nsteps fields: 88 GB for 60 steps
+ * of a 128^3 grid), and the reverse sweep re-runs nothing.  Replaces any earlier recording.  Errors:
  * RMHD_EINVAL, RMHD_ENOMEM, RMHD_ENAN (non-finite state; nothing recorded).
  * Atmosphere resets are not an error here (rmhd_get_stats counts them). */
-int rmhd_adjoint_forward(rmhd_t h, double dt, int nsteps, int checkpoint_every);
+int rmhd_adjoint_forward(rmhd_t h, double dt, int nsteps, int checkpoint_every);  /* >= 0 */
 
 /* Kernel groups timed by rmhd_adjoint_backward (ms[], when not NULL). */
 enum {

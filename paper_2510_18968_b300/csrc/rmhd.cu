@@ -45,6 +45,7 @@ namespace {
 // recorded trajectory and scratch of the adjoint (FP64 path)
 struct AdjBuf {
     bool recorded = false;
+    bool full = false;   // every step's state and stage states kept (no re-runs)
     double dt = 0.0;
     int nsteps = 0, every = 0, nck = 0;
     double *ckU = nullptr, *ckP = nullptr;     // checkpoints: nck x (14 x S)
@@ -1102,12 +1103,37 @@ static int adjoint_step_t(rmhd_t h, const StageSlot &q, const double *Pnext, Adj
     return RMHD_OK;
 }
 
+// one FP64 step that keeps its state (U^n, P^n) and its stage states in
+// segment slot q; with final = false the step stops after stage 2
+static int record_step(rmhd_t h, int q, bool final = true)
+{
+    AdjBuf &a = h->adj;
+    const size_t S = (size_t)h->K.G.S;
+    int rc = save_state(h, a.segU + (size_t)q * NCO * S, a.segP + (size_t)q * NPR * S);
+    if (rc) return rc;
+    if (h->flat) enqueue_stages12_t<true, double>(h, nullptr, a.segUs + (size_t)q * NCO * S);
+    else enqueue_stages12_t<false, double>(h, nullptr, a.segUs + (size_t)q * NCO * S);
+    CK(cudaMemcpyAsync(a.segP1 + (size_t)q * NPR * S, h->b.PA, fbytes(h, NPR),
+                       cudaMemcpyDeviceToDevice, h->st));
+    CK(cudaMemcpyAsync(a.segJ1 + (size_t)q * 3 * S, h->b.J1, fbytes(h, 3),
+                       cudaMemcpyDeviceToDevice, h->st));
+    CK(cudaMemcpyAsync(a.segP2 + (size_t)q * NPR * S, h->b.PB, fbytes(h, NPR),
+                       cudaMemcpyDeviceToDevice, h->st));
+    CK(cudaMemcpyAsync(a.segJ2 + (size_t)q * 3 * S, h->b.J2, fbytes(h, 3),
+                       cudaMemcpyDeviceToDevice, h->st));
+    if (final) {
+        if (h->flat) enqueue_final_t<true, double>(h, nullptr);
+        else enqueue_final_t<false, double>(h, nullptr);
+    }
+    return RMHD_OK;
+}
+
 extern "C" int rmhd_adjoint_forward(rmhd_t h, double dt, int nsteps, int checkpoint_every)
 {
     if (!h) return set_err(nullptr, RMHD_EINVAL, "handle is NULL");
     if (!(dt > 0.0) || !isfinite(dt)) return set_err(h, RMHD_EINVAL, "dt must be > 0");
-    if (nsteps < 1 || checkpoint_every < 1)
-        return set_err(h, RMHD_EINVAL, "nsteps and checkpoint_every must be >= 1");
+    if (nsteps < 1 || checkpoint_every < 0)
+        return set_err(h, RMHD_EINVAL, "nsteps must be >= 1 and checkpoint_every >= 0");
     if (!h->have_state) return set_err(h, RMHD_EINVAL, "no state: call rmhd_set_prims first");
     if (h->p.precision != RMHD_PREC_FP64)
         return set_err(h, RMHD_EINVAL, "the adjoint needs precision RMHD_PREC_FP64");
@@ -1120,7 +1146,8 @@ extern "C" int rmhd_adjoint_forward(rmhd_t h, double dt, int nsteps, int checkpo
     free_adj(a);
     a.dt = dt;
     a.nsteps = nsteps;
-    a.every = checkpoint_every < nsteps ? checkpoint_every : nsteps;
+    a.full = checkpoint_every == 0;
+    a.every = a.full || checkpoint_every > nsteps ? nsteps : checkpoint_every;
     a.nck = (nsteps + a.every - 1) / a.every;
     const size_t u = fbytes(h, NCO), pz = fbytes(h, NPR);
     struct {
@@ -1151,7 +1178,13 @@ extern "C" int rmhd_adjoint_forward(rmhd_t h, double dt, int nsteps, int checkpo
                                 a.ckP + (size_t)(n / a.every) * NPR * h->K.G.S);
             if (rc) return rc;
         }
-        enqueue_step(h);
+        if (a.full) {
+            // the whole tape: the state and the stage states of every step
+            int rc = record_step(h, n);
+            if (rc) return rc;
+        } else {
+            enqueue_step(h);
+        }
     }
     int rc = save_state(h, a.endU, a.endP);
     if (rc) return rc;
@@ -1205,30 +1238,17 @@ extern "C" int rmhd_adjoint_backward(rmhd_t h, const double *lam_prims, double *
         const int s1 = s0 + a.every < a.nsteps ? s0 + a.every : a.nsteps;
         // states s0 .. s1-1 of the segment, then P^{s1}
         // re-run the segment from its checkpoint, keeping every step's
-        // state and stage states
-        tm.begin(RMHD_ADJ_RECOMPUTE);
-        rc = load_state(h, a.ckU + (size_t)seg * NCO * S, a.ckP + (size_t)seg * NPR * S);
-        if (rc) return rc;
-        for (int n = s0; n < s1; n++) {
-            const int q = n - s0;
-            rc = save_state(h, a.segU + (size_t)q * NCO * S, a.segP + (size_t)q * NPR * S);
+        // state and stage states (already kept when the whole tape is)
+        if (!a.full) {
+            tm.begin(RMHD_ADJ_RECOMPUTE);
+            rc = load_state(h, a.ckU + (size_t)seg * NCO * S, a.ckP + (size_t)seg * NPR * S);
             if (rc) return rc;
-            if (h->flat) enqueue_stages12_t<true, double>(h, nullptr, a.segUs + (size_t)q * NCO * S);
-            else enqueue_stages12_t<false, double>(h, nullptr, a.segUs + (size_t)q * NCO * S);
-            CK(cudaMemcpyAsync(a.segP1 + (size_t)q * NPR * S, h->b.PA, fbytes(h, NPR),
-                               cudaMemcpyDeviceToDevice, h->st));
-            CK(cudaMemcpyAsync(a.segJ1 + (size_t)q * 3 * S, h->b.J1, fbytes(h, 3),
-                               cudaMemcpyDeviceToDevice, h->st));
-            CK(cudaMemcpyAsync(a.segP2 + (size_t)q * NPR * S, h->b.PB, fbytes(h, NPR),
-                               cudaMemcpyDeviceToDevice, h->st));
-            CK(cudaMemcpyAsync(a.segJ2 + (size_t)q * 3 * S, h->b.J2, fbytes(h, 3),
-                               cudaMemcpyDeviceToDevice, h->st));
-            if (n + 1 < s1) {
-                if (h->flat) enqueue_final_t<true, double>(h, nullptr);
-                else enqueue_final_t<false, double>(h, nullptr);
+            for (int n = s0; n < s1; n++) {
+                rc = record_step(h, n - s0, n + 1 < s1);
+                if (rc) return rc;
             }
+            tm.end();
         }
-        tm.end();
         const double *Pend = seg + 1 < a.nck ? a.ckP + (size_t)(seg + 1) * NPR * S : a.endP;
         for (int n = s1 - 1; n >= s0; n--) {
             const double *Pnext = n + 1 == s1 ? Pend : a.segP + (size_t)(n + 1 - s0) * NPR * S;

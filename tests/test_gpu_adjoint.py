@@ -300,3 +300,22 @@ def test_autograd_function_gives_the_adjoint_gradient():
     s.close()
     assert np.abs(P0.grad.cpu().numpy() - g).max() <= 1e-12 * np.abs(g).max()
     assert abs(float(ls.grad) - gls) <= 1e-12 * abs(gls)
+
+
+def test_full_tape_gives_the_same_gradient_bit_for_bit():
+    """checkpoint_every = 0 keeps every step's states instead of re-running
+    segments; the reverse sweep sees the same states, so the gradient is
+    identical."""
+    wl = W.alfven_diag(n=8, sigma=1e3)
+    dV = np.prod(wl.params["dx"])
+    out = []
+    for every in (0, 3, 1):
+        s = make_solver(wl)
+        s.adjoint_forward(wl.dt, 7, every)
+        PN = s.get_prims()
+        lam = np.zeros_like(PN)
+        lam[9] = 2.0 * PN[9] * dV
+        out.append(s.adjoint_backward(lam))
+        s.close()
+    for g, ls in out[1:]:
+        assert np.array_equal(g, out[0][0]) and ls == out[0][1]
