@@ -1,10 +1,11 @@
-"""FP64 CPU oracle for one IMEX-SSP2(2,2,2) step of resistive GRMHD.
+"""FP64 CPU oracle for one IMEX-RK step of resistive GRMHD.
 
 TEST INFRASTRUCTURE ONLY.  This package restates, in plain C called through
 ctypes, what arXiv:2510.18968 (Sec. II-III) computes: primitive->conserved map
 (Eqs. conserved_dens/tau/S), fluxes and sources (Eq. GRRMHD_flux_form), Ohm's
 law (Eq. Ohm_law), HLLE with light-speed bounds (Sec. III), TVD/WENO5
-reconstruction, the IMEX-SSP2(2,2,2) stages (Table imex, Eq. IMEX3) and the
+reconstruction, the IMEX-SSP2(2,2,2) stages (Table imex, Eq. IMEX3) or the
+general IMEX-RK form with another of the paper's SSP tableaux, and the
 implicit-E + 1D recovery (Sec. III.B).  It shares no code with the CUDA
 library and never imports it.  Only tests/, __graft_entry__.smoke() and
 bench.py's CPU-baseline / reference legs may use it.
@@ -45,6 +46,7 @@ class _Params(ctypes.Structure):
         ("c2p_maxit", ctypes.c_int),
         ("c2p_wmax", ctypes.c_double),
         ("qflux_mode", ctypes.c_int),
+        ("imex", ctypes.c_int),
     ]
 
 
@@ -52,7 +54,7 @@ DEFAULTS = dict(n=(1, 1, 1), dx=(1.0, 1.0, 1.0), bc=(0, 0, 0), recon=0,
                 gamma_eos=2.0, kappa=1.0, sigma_model=0, sigma0=0.0,
                 sigma_exp=0.0, D_atmo=0.0, rho_atmo=1e-10, K_atmo=100.0,
                 atmo_tol=1e-2, c2p_tol=1e-14, c2p_maxit=100, c2p_wmax=100.0,
-                qflux_mode=0)
+                qflux_mode=0, imex=0)
 
 
 def lib():
@@ -77,6 +79,10 @@ def lib():
         L.orc_step.argtypes = [P, _DP, _DP, _DP, _DP, _DP, _DP, _DP, d, i,
                                ctypes.POINTER(ctypes.c_longlong)]
         L.orc_step.restype = i
+        L.orc_step_tableau.argtypes = L.orc_step.argtypes
+        L.orc_step_tableau.restype = i
+        L.orc_imex_tableau.argtypes = [i, _DP, _DP, _DP, _DP]
+        L.orc_imex_tableau.restype = i
         L.orc_set_status_buffer.argtypes = [ctypes.c_void_p]
         _lib = L
     return _lib
@@ -109,7 +115,7 @@ def make_params(**kw):
     s.n[:] = [int(v) for v in p["n"]]
     s.dx[:] = [float(v) for v in p["dx"]]
     s.bc[:] = [int(v) for v in p["bc"]]
-    for k in ("recon", "sigma_model", "c2p_maxit", "qflux_mode"):
+    for k in ("recon", "sigma_model", "c2p_maxit", "qflux_mode", "imex"):
         setattr(s, k, int(p[k]))
     for k in ("gamma_eos", "kappa", "sigma0", "sigma_exp", "D_atmo", "rho_atmo",
               "K_atmo", "atmo_tol", "c2p_tol", "c2p_wmax"):
@@ -240,9 +246,25 @@ STAT_NAMES = ("c2p_calls", "c2p_iterations", "c2p_fallbacks", "c2p_failures",
               "atmo_floor_resets", "c2p_max_iterations", "nan")
 
 
+IMEX_SCHEMES = {0: "SSP2(2,2,2)", 1: "SSP2(3,3,2)", 2: "SSP3(3,3,2)", 3: "SSP3(4,3,3)"}
+
+
+def imex_tableau(scheme):
+    """(At, wt, A, w) of an IMEX scheme (Sec. III.A), trimmed to its stages."""
+    At, A = np.zeros(16), np.zeros(16)
+    wt, w = np.zeros(4), np.zeros(4)
+    s = lib().orc_imex_tableau(int(scheme), _ptr(At), _ptr(wt), _ptr(A), _ptr(w))
+    if not s:
+        raise KeyError(f"unknown IMEX scheme {scheme}")
+    return (At.reshape(4, 4)[:s, :s].copy(), wt[:s].copy(),
+            A.reshape(4, 4)[:s, :s].copy(), w[:s].copy())
+
+
 def step(params, metric, cons, prim, dt, nsteps=1, sigma_field=None,
-         status_out=None):
-    """Advance (cons, prim) in place by nsteps IMEX-SSP2(2,2,2) steps.
+         status_out=None, general_form=False):
+    """Advance (cons, prim) in place by nsteps IMEX-RK steps with the
+    tableau params["imex"] (0: SSP2(2,2,2), Table imex, through its literal
+    equations; others, or general_form=True, through the general form).
     Returns (status, stats dict).  status 0 ok, -4 recovery failures were
     reset to atmosphere, -5 non-finite conserved values."""
     assert cons.dtype == np.float64 and prim.dtype == np.float64
@@ -253,7 +275,8 @@ def step(params, metric, cons, prim, dt, nsteps=1, sigma_field=None,
     if status_out is not None:
         assert status_out.dtype == np.int32 and status_out.size == 3 * prim[0].size
         lib().orc_set_status_buffer(status_out.ctypes.data)
-    st = lib().orc_step(ctypes.byref(P), _ptr(metric.alpha), _ptr(metric.beta),
+    fn = lib().orc_step_tableau if general_form else lib().orc_step
+    st = fn(ctypes.byref(P), _ptr(metric.alpha), _ptr(metric.beta),
                         _ptr(metric.gamma), _ptr(metric.K), _ptr(sf), _ptr(cons),
                         _ptr(prim), float(dt), int(nsteps), stats)
     if status_out is not None:

@@ -48,6 +48,107 @@ enum { C_D, C_SX, C_SY, C_SZ, C_TAU, C_BX, C_BY, C_BZ, C_EX, C_EY, C_EZ,
 /* gamma of the IMEX-SSP2(2,2,2) tableau (Table imex): 1 - 1/sqrt(2) */
 static double imex_gamma(void) { return 1.0 - 1.0 / sqrt(2.0); }
 
+/* Double Butcher tableaux (Sec. III.A): explicit At (strictly lower
+ * triangular) with weights wt, implicit A (lower triangular, DIRK) with
+ * weights w.  Scheme 0 is Table imex.  Schemes 1-3 are the other SSP
+ * schemes the paper lists (Sec. I) without printing them; their values are
+ * the ones published by Pareschi and Russo (J. Sci. Comput. 25, 2005), the
+ * paper's reference for the IMEX form:
+ *   1  SSP2(3,3,2)  At rows (1/2), (1/2, 1/2), wt = (1/3, 1/3, 1/3);
+ *                   A rows (1/4), (0, 1/4), (1/3, 1/3, 1/3), w = wt
+ *   2  SSP3(3,3,2)  At rows (1), (1/4, 1/4), wt = (1/6, 1/6, 2/3);
+ *                   A rows (g), (1-2g, g), (1/2-g, 0, g), w = wt,
+ *                   g = 1 - 1/sqrt(2)
+ *   3  SSP3(4,3,3)  At rows (0), (0, 1), (0, 1/4, 1/4),
+ *                   wt = (0, 1/6, 1/6, 2/3);
+ *                   A rows (a), (-a, a), (0, 1-a, a), (b, e, 1/2-b-e-a, a),
+ *                   w = wt, a = 0.24169426078821, b = 0.06042356519705,
+ *                   e = 0.12915286960590.
+ * Returns the number of stages, 0 for an unknown scheme. */
+typedef struct {
+    int s;
+    double At[4][4], wt[4], A[4][4], w[4];
+} imex_tab;
+
+static int imex_tableau(int scheme, imex_tab *T)
+{
+    memset(T, 0, sizeof(*T));
+    double g = imex_gamma();
+    switch (scheme) {
+    case 0:
+        T->s = 2;
+        T->At[1][0] = 1.0;
+        T->wt[0] = T->wt[1] = 0.5;
+        T->A[0][0] = g;
+        T->A[1][0] = 1.0 - 2.0 * g;
+        T->A[1][1] = g;
+        T->w[0] = T->w[1] = 0.5;
+        break;
+    case 1:
+        T->s = 3;
+        T->At[1][0] = 0.5;
+        T->At[2][0] = 0.5;
+        T->At[2][1] = 0.5;
+        T->A[0][0] = 0.25;
+        T->A[1][1] = 0.25;
+        T->A[2][0] = T->A[2][1] = T->A[2][2] = 1.0 / 3.0;
+        for (int i = 0; i < 3; i++) T->wt[i] = T->w[i] = 1.0 / 3.0;
+        break;
+    case 2:
+        T->s = 3;
+        T->At[1][0] = 1.0;
+        T->At[2][0] = 0.25;
+        T->At[2][1] = 0.25;
+        T->A[0][0] = g;
+        T->A[1][0] = 1.0 - 2.0 * g;
+        T->A[1][1] = g;
+        T->A[2][0] = 0.5 - g;
+        T->A[2][2] = g;
+        T->wt[0] = T->wt[1] = 1.0 / 6.0;
+        T->wt[2] = 2.0 / 3.0;
+        for (int i = 0; i < 3; i++) T->w[i] = T->wt[i];
+        break;
+    case 3: {
+        const double a = 0.24169426078821, b = 0.06042356519705, e = 0.12915286960590;
+        T->s = 4;
+        T->At[2][1] = 1.0;
+        T->At[3][1] = 0.25;
+        T->At[3][2] = 0.25;
+        T->A[0][0] = a;
+        T->A[1][0] = -a;
+        T->A[1][1] = a;
+        T->A[2][1] = 1.0 - a;
+        T->A[2][2] = a;
+        T->A[3][0] = b;
+        T->A[3][1] = e;
+        T->A[3][2] = 0.5 - b - e - a;
+        T->A[3][3] = a;
+        T->wt[1] = T->wt[2] = 1.0 / 6.0;
+        T->wt[3] = 2.0 / 3.0;
+        for (int i = 0; i < 4; i++) T->w[i] = T->wt[i];
+        break;
+    }
+    default:
+        return 0;
+    }
+    return T->s;
+}
+
+int orc_imex_tableau(int scheme, double At[16], double wt[4], double A[16], double w[4])
+{
+    imex_tab T;
+    int s = imex_tableau(scheme, &T);
+    for (int i = 0; i < 4; i++) {
+        wt[i] = T.wt[i];
+        w[i] = T.w[i];
+        for (int j = 0; j < 4; j++) {
+            At[4 * i + j] = T.At[i][j];
+            A[4 * i + j] = T.A[i][j];
+        }
+    }
+    return s;
+}
+
 /* Levi-Civita symbol eta_{ijk} (= eta^{ijk}), indices 0..2 */
 static double levi(int i, int j, int k)
 {
@@ -1316,16 +1417,16 @@ static void gauss_charge(const grid *G, double *cons, double *prim)
             }
 }
 
-/* One IMEX-SSP2(2,2,2) step, literally Eqs. (U^(1), U^(2), IMEX3):
+/* IMEX-SSP2(2,2,2) steps, literally Eqs. (U^(1), U^(2), IMEX3):
  *   U1 = U^n + gamma dt R[U1]
  *   U2 = U^n + dt F[U1] + dt ((1-2gamma) R[U1] + gamma R[U2])
  *   U^{n+1} = U^n + dt/2 (F[U1] + F[U2]) + dt/2 (R[U1] + R[U2])
  * R acts on calE only (Sec. III.A); each implicit stage is solved jointly
  * with the recovery (Sec. III.B); U^{n+1} is then recovered with calE fixed. */
-int orc_step(const orc_params *P, const double *alpha, const double *beta,
-             const double *gam, const double *K, const double *sigma_field,
-             double *cons, double *prim, double dt, int nsteps,
-             long long stats[8])
+static int step_ssp222(const orc_params *P, const double *alpha, const double *beta,
+                       const double *gam, const double *K, const double *sigma_field,
+                       double *cons, double *prim, double dt, int nsteps,
+                       long long stats[8])
 {
     grid G;
     make_grid(&G, P, alpha, beta, gam, K, sigma_field);
@@ -1387,4 +1488,105 @@ int orc_step(const orc_params *P, const double *alpha, const double *beta,
     free(dR1); free(dR2); free(Jc); free(Es2);
     if (status) return status;
     return stats[3] > 0 ? -4 : 0;
+}
+
+/* IMEX-RK steps in the general form of Sec. III.A with the tableau of
+ * P->imex:
+ *   U^(i)   = U^n + dt sum_{j<i} At_ij F[U^(j)] + dt sum_{j<=i} A_ij R[U^(j)]/eps
+ *   U^{n+1} = U^n + dt sum_i wt_i F[U^(i)] + dt sum_i w_i R[U^(i)]/eps.
+ * R acts on calE only.  Stage i's implicit part is solved jointly with the
+ * recovery (c = A_ii dt, guess: the previous stage's primitives, P^n for the
+ * first); its stiff increment dR_i = dt R[U^(i)]/eps is kept algebraically,
+ * (calE^(i) - calE*_i)/A_ii, calE*_i the stage's calE before the solve.
+ * Terms with a zero coefficient are skipped, and F[U^(i)] is formed only
+ * when a later row or wt uses it.  U^{n+1} is then recovered with calE
+ * fixed (guess: the last stage's primitives). */
+int orc_step_tableau(const orc_params *P, const double *alpha, const double *beta,
+                     const double *gam, const double *K, const double *sigma_field,
+                     double *cons, double *prim, double dt, int nsteps,
+                     long long stats[8])
+{
+    imex_tab T;
+    const int s = imex_tableau(P->imex, &T);
+    if (!s) return -6;
+    grid G;
+    make_grid(&G, P, alpha, beta, gam, K, sigma_field);
+    long N = G.N;
+    double *Ui = (double *)malloc(sizeof(double) * 14 * N);
+    double *Es = (double *)malloc(sizeof(double) * 3 * N);
+    double *Jc = (double *)malloc(sizeof(double) * 3 * N);
+    double *W[4], *F[4], *dR[4];
+    int needF[4];
+    for (int i = 0; i < s; i++) {
+        W[i] = (double *)malloc(sizeof(double) * 14 * N);
+        F[i] = (double *)malloc(sizeof(double) * 14 * N);
+        dR[i] = (double *)malloc(sizeof(double) * 3 * N);
+        needF[i] = T.wt[i] != 0.0;
+        for (int k = i + 1; k < s; k++) needF[i] |= T.At[k][i] != 0.0;
+    }
+    const double *Jarg = P->qflux_mode != 1 ? Jc : NULL;
+    const int gauss = P->qflux_mode == 2;
+    int status = 0;
+    for (int a = 0; a < 8; a++) stats[a] = 0;
+    for (int step = 0; step < nsteps; step++) {
+        for (int i = 0; i < s; i++) {
+            /* explicit part of the stage */
+            memcpy(Ui, cons, sizeof(double) * 14 * N);
+            for (int j = 0; j < i; j++)
+                if (T.At[i][j] != 0.0)
+                    for (long a = 0; a < 14 * N; a++) Ui[a] += dt * T.At[i][j] * F[j][a];
+            for (int j = 0; j < i; j++)
+                if (T.A[i][j] != 0.0)
+                    for (int a = 0; a < 3; a++)
+                        for (long c = 0; c < N; c++)
+                            Ui[(C_EX + a) * N + c] += T.A[i][j] * dR[j][a * N + c];
+            for (int a = 0; a < 3; a++)
+                for (long c = 0; c < N; c++) Es[a * N + c] = Ui[(C_EX + a) * N + c];
+            /* implicit part with the recovery */
+            c2p_grid(&G, Ui, i == 0 ? prim : W[i - 1], W[i], 1, T.A[i][i] * dt, stats,
+                     i == 0 ? 0 : 1);
+            if (gauss) gauss_charge(&G, Ui, W[i]);
+            for (int a = 0; a < 3; a++)
+                for (long c = 0; c < N; c++)
+                    dR[i][a * N + c] = (Ui[(C_EX + a) * N + c] - Es[a * N + c]) / T.A[i][i];
+            if (needF[i]) {
+                stage_current(&G, Ui, W[i], dR[i], dt, Jc);
+                rhs_grid(&G, W[i], Jarg, F[i]);
+            }
+        }
+        /* U^{n+1} */
+        for (int i = 0; i < s; i++)
+            if (T.wt[i] != 0.0)
+                for (long a = 0; a < 14 * N; a++) cons[a] += dt * T.wt[i] * F[i][a];
+        for (int i = 0; i < s; i++)
+            if (T.w[i] != 0.0)
+                for (int a = 0; a < 3; a++)
+                    for (long c = 0; c < N; c++)
+                        cons[(C_EX + a) * N + c] += T.w[i] * dR[i][a * N + c];
+        for (long a = 0; a < 14 * N; a++)
+            if (!isfinite(cons[a])) { status = -5; stats[6] = 1; }
+        c2p_grid(&G, cons, W[s - 1], prim, 0, 0.0, stats, 2);
+        if (gauss) gauss_charge(&G, cons, prim);
+        if (status) break;
+    }
+    for (int i = 0; i < s; i++) {
+        free(W[i]);
+        free(F[i]);
+        free(dR[i]);
+    }
+    free(Ui); free(Es); free(Jc);
+    if (status) return status;
+    return stats[3] > 0 ? -4 : 0;
+}
+
+/* Steps with the scheme of P->imex: Table imex through its literal
+ * equations, the other tableaux through the general form. */
+int orc_step(const orc_params *P, const double *alpha, const double *beta,
+             const double *gam, const double *K, const double *sigma_field,
+             double *cons, double *prim, double dt, int nsteps,
+             long long stats[8])
+{
+    if (P->imex == 0)
+        return step_ssp222(P, alpha, beta, gam, K, sigma_field, cons, prim, dt, nsteps, stats);
+    return orc_step_tableau(P, alpha, beta, gam, K, sigma_field, cons, prim, dt, nsteps, stats);
 }

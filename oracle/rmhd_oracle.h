@@ -1,7 +1,8 @@
 /*
  * rmhd_oracle.h -- TEST INFRASTRUCTURE ONLY.
  *
- * Plain, slow, FP64 CPU restatement of one IMEX-SSP2(2,2,2) step of the
+ * Plain, slow, FP64 CPU restatement of one IMEX-RK step (SSP2(2,2,2) of
+ * Table imex, or another of the paper's SSP tableaux) of the
  * resistive GRMHD system of arXiv:2510.18968 ("A resistive MHD module in the
  * GPU-accelerated GRMHD code GRaM-X"), Sec. II-III.  It exists so that the
  * CUDA path can be checked against something written independently from the
@@ -45,6 +46,8 @@ typedef struct {
                              1 Ohm's law at the reconstructed face states;
                              2 no evolved charge: Q = d_i calE^i (Gauss's
                              law) after every recovery                      */
+    int    imex;          /* IMEX-RK tableau: 0 SSP2(2,2,2) (Table imex),
+                             1 SSP2(3,3,2), 2 SSP3(3,3,2), 3 SSP3(4,3,3)     */
 } orc_params;
 
 /* pointwise pieces (exported for the pin tests) */
@@ -73,6 +76,17 @@ void orc_rhs(const orc_params *P, const double *alpha, const double *beta,
 void orc_prim2con_grid(const orc_params *P, const double *alpha,
                        const double *beta, const double *gam,
                        const double *prim, double *cons);
+/* tableau of an IMEX scheme (row-major 4x4, zero-padded); returns the
+ * number of stages, 0 for an unknown scheme */
+int  orc_imex_tableau(int scheme, double At[16], double wt[4], double A[16],
+                      double w[4]);
+/* the general IMEX-RK form with P->imex's tableau (any scheme, 0 included;
+ * orc_step runs scheme 0 through its literal equations instead).  Returns
+ * -6 for an unknown scheme. */
+int  orc_step_tableau(const orc_params *P, const double *alpha, const double *beta,
+                      const double *gam, const double *K, const double *sigma_field,
+                      double *cons, double *prim, double dt, int nsteps,
+                      long long stats[8]);
 int  orc_step(const orc_params *P, const double *alpha, const double *beta,
               const double *gam, const double *K, const double *sigma_field,
               double *cons, double *prim, double dt, int nsteps,
