@@ -346,7 +346,8 @@ def run_configs(args):
     """The other configurations: the 400-cell Brio-Wu shocktube (launch-bound:
     latency per step, one CUDA-graph replay per step against one launch
     sequence per step), the 128^3 Alfven cube and the 192^3 curved star
-    (zone-updates/s of both paths, recovery statistics)."""
+    (zone-updates/s of both paths, recovery statistics), and the 256^3 blast
+    with each of the paper's IMEX schemes."""
     import torch
     import paper_2510_18968_b300 as R
     out = {}
@@ -398,6 +399,25 @@ def run_configs(args):
         d["unit"] = UNIT
         d["mixed_speedup"] = d["fp64"]["ms_per_step"] / d["mixed"]["ms_per_step"]
         out[name] = d
+    # the paper's four IMEX schemes on the 256^3 blast (one more implicit
+    # stage and face-flux evaluation than Table imex for the other three)
+    wl = W.cyl_blast(n=256)
+    d = {"workload": "cylindrical blast 256^3 (the headline workload), per IMEX scheme",
+         "unit": UNIT}
+    for scheme, label in ((0, "SSP2(2,2,2)"), (1, "SSP2(3,3,2)"), (2, "SSP3(3,3,2)"),
+                          (3, "SSP3(4,3,3)")):
+        e = {}
+        for prec in ("mixed", "fp64"):
+            s = R.Solver(dict(wl.params, precision=1 if prec == "mixed" else 0, imex=scheme))
+            s.set_prims(np.ascontiguousarray(wl.prim))
+            s.step(wl.dt, 3)
+            ms = timed(s, wl.dt, 10)
+            st = s.stats()
+            s.close()
+            e[prec] = {"value": wl.ncells * 10 / (ms * 1e-3), "ms_per_step": ms / 10,
+                       "paper_iterations_per_recovery": st["c2p_iterations"] / st["c2p_calls"]}
+        d[label] = e
+    out["imex_schemes_cyl_blast_256"] = d
     return out
 
 

@@ -65,6 +65,19 @@ enum {
                                 Sec. IV.E); q = calQ / sqrt(gamma)            */
 };
 
+enum {
+    /* IMEX-RK schemes (Sec. III.A, general form with a double Butcher
+       tableau; the paper lists all four in Sec. I and prints only the
+       first, Table imex; the others carry the coefficients published by
+       Pareschi & Russo, J. Sci. Comput. 25 (2005)) */
+    RMHD_IMEX_SSP222 = 0,    /* 2 stages, Eq. IMEX3 (default)                */
+    RMHD_IMEX_SSP2332 = 1,   /* SSP2(3,3,2): 3 stages, 2nd order             */
+    RMHD_IMEX_SSP3332 = 2,   /* SSP3(3,3,2): 3 stages, 2nd order, explicit
+                                part 3rd order                               */
+    RMHD_IMEX_SSP3433 = 3    /* SSP3(4,3,3): 4 stages, 3rd order; its first
+                                stage's F has weight 0 and is not formed     */
+};
+
 typedef struct rmhd_params {
     int    n[3];        /* interior cells per direction (>= 1); n = 1 makes the
                            direction inactive (no flux, no ghosts)             */
@@ -88,6 +101,7 @@ typedef struct rmhd_params {
                            kernels' first recovery pass before it is listed
                            for the second pass (resumed where it stopped);
                            0 = the whole iteration (default)                 */
+    int    imex;        /* RMHD_IMEX_* (the adjoint needs RMHD_IMEX_SSP222)    */
 } rmhd_params;
 
 typedef struct rmhd_s *rmhd_t;
@@ -99,7 +113,9 @@ void rmhd_default_params(rmhd_params *p);
 
 /* Create a solver for the grid and options in *p on the given CUDA stream
  * (cudaStream_t, may be NULL for the legacy default stream).  Allocates all
- * device memory: about (70 + 3*14 + 17) fields x padded cells x 8 bytes.
+ * device memory: about (70 + 3*14 + 17) fields x padded cells x 8 bytes,
+ * plus 14 (s - 1) + 3 s fields for an s-stage scheme other than
+ * RMHD_IMEX_SSP222.
  * The metric starts flat, sigma uniform.  Errors: RMHD_EINVAL (n < 1,
  * dx <= 0, Gamma <= 1, sigma0 < 0, unknown enum), RMHD_ENOMEM, RMHD_ECUDA. */
 int rmhd_create(const rmhd_params *p, void *cuda_stream, rmhd_t *out);
@@ -123,12 +139,18 @@ int rmhd_set_sigma(rmhd_t h, const double *profile, int on_device);
  * (state unchanged). */
 int rmhd_set_prims(rmhd_t h, const double *prims, int on_device);
 
-/* Advance nsteps IMEX-SSP2(2,2,2) steps of size dt (Eq. IMEX3):
+/* Advance nsteps IMEX-RK steps of size dt.  With RMHD_IMEX_SSP222
+ * (Eq. IMEX3):
  *   stage 1  U1 = U^n + gamma dt R[U1]   (implicit E + recovery, pointwise)
  *   stage 2  U2 = U^n + dt F[U1] + dt((1-2gamma) R[U1] + gamma R[U2])
  *   final    U^{n+1} = U^n + dt/2 (F[U1] + F[U2]) + dt/2 (R[U1] + R[U2]),
  *            then recovery with E fixed,
- * gamma = 1 - 1/sqrt(2) (Table imex); R acts on E only (Sec. III.A).
+ * gamma = 1 - 1/sqrt(2) (Table imex); R acts on E only (Sec. III.A).  The
+ * other schemes follow the general form of Sec. III.A,
+ *   U^(i) = U^n + dt sum_{j<i} At_ij F[U^(j)] + dt sum_{j<=i} A_ij R[U^(j)],
+ *   U^{n+1} = U^n + dt sum_i wt_i F[U^(i)] + dt sum_i w_i R[U^(i)],
+ * each stage's implicit part solved with the recovery (guess: the previous
+ * stage's primitives), then U^{n+1} recovered with E fixed.
  * Enqueued on the handle's stream; with nsteps >= 2 one step is captured
  * as a CUDA graph (once, and again when dt or another step constant
  * changes) and replayed nsteps times.  If fail_count is NULL the call returns
@@ -143,7 +165,9 @@ int rmhd_step(rmhd_t h, double dt, int nsteps, long long *fail_count);
  * durations, in milliseconds, to ms[RMHD_NPROF]: [0] stage-1 recovery,
  * [1] ghost fills, [2] face fluxes of stage 2 (x, y, z), [3] stage-2
  * flux difference + sources + implicit recovery, [4] face fluxes of the final
- * assembly, [5] final assembly + recovery.  Synchronises after every step.
+ * assembly, [5] final assembly + recovery.  With more stages, [2] and [3]
+ * sum over stages 2..s (their row combinations counted in [3]) and [5]
+ * includes the combination of the weights.  Synchronises after every step.
  * Instrumentation for benchmarks; not a paper operation. */
 #define RMHD_NPROF 6
 int rmhd_step_profiled(rmhd_t h, double dt, int nsteps, double ms[RMHD_NPROF]);

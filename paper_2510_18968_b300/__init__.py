@@ -53,6 +53,7 @@ class Params(ctypes.Structure):
         ("c2p_wmax", ctypes.c_double),
         ("qflux_mode", ctypes.c_int),
         ("c2p_first_pass", ctypes.c_int),
+        ("imex", ctypes.c_int),
     ]
 
 
@@ -121,7 +122,7 @@ def make_params(**kw):
         elif k in ("x0", "dx"):
             getattr(p, k)[:] = [float(x) for x in v]
         elif k in ("recon", "precision", "sigma_model", "c2p_maxit", "qflux_mode",
-                   "c2p_first_pass"):
+                   "c2p_first_pass", "imex"):
             setattr(p, k, int(v))
         elif k in ("gamma_eos", "kappa", "sigma0", "sigma_exp", "D_atmo", "rho_atmo",
                    "K_atmo", "atmo_tol", "c2p_tol", "c2p_wmax"):

@@ -49,6 +49,7 @@ struct StepConst {
     int qflux;            // 0 stage current, 1 Ohm's law at faces, 2 Gauss's law
     RecOpts ro;
     float sigma0f, gfacf; // FP32 copies for the FP32 stencil (no FP64 conversions)
+    double wlast;         // weight of the last stage's F in U^{n+1} (1/2 in Table imex)
 };
 
 // a constant of StepConst in the stencil's type
@@ -1124,12 +1125,15 @@ __device__ __forceinline__ void final_write(const StepConst &K, long long c, con
 // the latency of the FP64 reciprocals better than three blocks without
 // spills (measured: stage 2 and the final kernel 3-12% faster; five blocks
 // spill too much).
-// Stage 1 (purely implicit): recovery of U^n with calE solved, guess P^n.
+// Stage 1 (purely implicit): recovery of U^n with calE solved, guess P^n
+// (Gin; may be Gs, read and written at the same cell).  Also any stage of
+// the general IMEX form, with U its explicit part (k_combine) and
+// K.gimex = the stage's diagonal coefficient A_ii.
 template <bool FLAT, class T>
 __global__ void __launch_bounds__(128, 4)
-k_stage1(const StepConst K, const double *__restrict__ U, T *P, double *Gs, double *dR1, T *J1,
-         const double *__restrict__ met, const double *__restrict__ sig, const Defer df,
-         unsigned long long *stats)
+k_stage1(const StepConst K, const double *__restrict__ U, T *P, const double *Gin, double *Gs,
+         double *dR1, T *J1, const double *__restrict__ met, const double *__restrict__ sig,
+         const Defer df, unsigned long long *stats)
 {
     const Grid &G = K.G;
     const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -1149,8 +1153,8 @@ k_stage1(const StepConst K, const double *__restrict__ U, T *P, double *Gs, doub
         RecIn in;
         load_rec_in(u, in);
         cc = K.gimex * K.dt * m.alpha * sigma_cell(K, sig, c, in.D);
-        gp = Gs[c];
-        for (int a = 0; a < 3; a++) gv[a] = Gs[(1 + a) * S + c];
+        gp = Gin[c];
+        for (int a = 0; a < 3; a++) gv[a] = Gin[(1 + a) * S + c];
         status = recover<FLAT>(in, m, K.ro, true, cc, gp, gv, u[CO_PHI], u[CO_PSI], u[CO_Q], pr,
                                E, iters, df.cap ? REC_FIRST : REC_ALL, &ps);
     }
@@ -1238,7 +1242,9 @@ k_stage2(const StepConst K, const double *__restrict__ U, const T *__restrict__ 
     record_stats(stats, active, status, deferred ? 0 : iters, !deferred);
 }
 
-// Final: U^{n+1} = V + dt/2 F[U2]; recovery with calE fixed (guess P2).
+// Final: U^{n+1} = V + wlast dt F[U_s] (wlast = 1/2 in Table imex, V then
+// holding U^n + dt/2 F[U1] + dt/2 (R1 + R2)); recovery with calE fixed
+// (guess: the last stage's primitives).
 template <bool FLAT, class T>
 __global__ void __launch_bounds__(128, 4)
 k_final(const StepConst K, const double *__restrict__ Vb, const T *__restrict__ P2,
@@ -1263,7 +1269,7 @@ k_final(const StepConst K, const double *__restrict__ Vb, const T *__restrict__ 
         for (int f = 0; f < NPR; f++) pr[f] = P2[f * S + c];
         T r[NCO];
         rhs_cell<FLAT, T>(K, pr, met, Fx, Fy, Fz, c, r);
-        const double hdt = 0.5 * K.dt;
+        const double hdt = K.wlast * K.dt;
         bool finite = true;
         for (int f = 0; f < NCO; f++) {
             un[f] = Vb[f * S + c] + hdt * (double)r[f];
@@ -1296,6 +1302,60 @@ k_final(const StepConst K, const double *__restrict__ Vb, const T *__restrict__ 
     const bool deferred = want && slot >= 0;
     if (active && !deferred) final_write<FLAT>(K, c, pn, status, m, U, P, Gs);
     record_stats(stats, active, status, deferred ? 0 : iters, !deferred);
+}
+
+// One row of the general IMEX-RK form (Sec. III.A) for the tableaux other
+// than Table imex: out = U^n + dt sum_{j<nF} aF_j F_j, and on calE also
+// + sum_{j<nR} aR_j Dt R_j.  A stage row (i) gives the stage's explicit
+// part, which k_stage1 then solves implicitly; the last row (the weights,
+// without the last stage's F) gives V for k_final.  F_jnew, when jnew >= 0,
+// is formed here from the face fluxes of its stage (primitives P) and, if a
+// later row needs it, kept in Fst; the other F_j come from Fst.
+struct ImexRow {
+    double aF[4], aR[4];
+    int nF, nR, jnew, store;
+};
+
+template <bool FLAT, class T>
+__global__ void __launch_bounds__(128)
+k_combine(const StepConst K, const ImexRow row, const double *__restrict__ U,
+          const T *__restrict__ P, const T *__restrict__ Fx, const T *__restrict__ Fy,
+          const T *__restrict__ Fz, const double *__restrict__ met, double *Fst,
+          const double *__restrict__ dRs, double *out)
+{
+    const Grid &G = K.G;
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= G.N) return;
+    int i, j, k;
+    interior_coords(G, t, i, j, k);
+    const long long c = cell_at(G, i, j, k), S = G.S;
+    double rn[NCO];
+#pragma unroll
+    for (int f = 0; f < NCO; f++) rn[f] = 0.0;
+    if (row.jnew >= 0) {
+        T pr[NPR], r[NCO];
+        for (int f = 0; f < NPR; f++) pr[f] = P[f * S + c];
+        rhs_cell<FLAT, T>(K, pr, met, Fx, Fy, Fz, c, r);
+#pragma unroll
+        for (int f = 0; f < NCO; f++) rn[f] = (double)r[f];
+        if (row.store)
+#pragma unroll
+            for (int f = 0; f < NCO; f++) Fst[((long long)row.jnew * NCO + f) * S + c] = rn[f];
+    }
+#pragma unroll
+    for (int f = 0; f < NCO; f++) {
+        double acc = 0.0;
+        for (int q = 0; q < row.nF; q++) {
+            if (row.aF[q] == 0.0) continue;
+            const double F = q == row.jnew ? rn[f] : Fst[((long long)q * NCO + f) * S + c];
+            acc += row.aF[q] * F;
+        }
+        double u = U[f * S + c] + K.dt * acc;
+        if (f >= CO_EX && f < CO_EX + 3)
+            for (int q = 0; q < row.nR; q++)
+                if (row.aR[q] != 0.0) u += row.aR[q] * dRs[((long long)q * 3 + f - CO_EX) * S + c];
+        out[f * S + c] = u;
+    }
 }
 
 // Deferred pass of stage 1 (STAGE 1), stage 2 (STAGE 2) or the final

@@ -1,6 +1,7 @@
 // rmhd.cu -- host side of the C ABI declared in include/rmhd.h: parameter
 // checks, device memory, stage sequencing of the IMEX-SSP2(2,2,2) step
-// (arXiv:2510.18968 Sec. III.A, Eq. IMEX3) and the testing entry points.
+// (arXiv:2510.18968 Sec. III.A, Eq. IMEX3) and of the general IMEX-RK form
+// for the other SSP tableaux, and the testing entry points.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdarg.h>
@@ -17,6 +18,7 @@ using namespace rmhd;
 namespace {
 
 const int TPB = 128;
+const int NDEFER = 8;   // deferred-recovery counters: one per recovery of a step
 
 char g_noh_err[512] = "";
 
@@ -36,7 +38,81 @@ struct Buffers {
     int *dcount = nullptr, *didx = nullptr;
     double *drec = nullptr;
     int dcap = 0;
+    // general IMEX form (schemes other than Table imex): the F of earlier
+    // stages that later rows use (NCO x S each) and every stage's Dt R (3 x S
+    // each); V holds each row's combination
+    double *Fst = nullptr, *dRs = nullptr;
 };
+
+// Double Butcher tableaux of the IMEX-RK schemes (Sec. III.A).  Table imex
+// (scheme 0) is printed in the paper; schemes 1-3 are the SSP schemes it
+// lists in Sec. I, with the coefficients published by Pareschi and Russo
+// (J. Sci. Comput. 25, 2005).
+struct Tableau {
+    int s = 0;
+    double At[4][4] = {}, wt[4] = {}, A[4][4] = {}, w[4] = {};
+};
+
+Tableau tableau(int scheme)
+{
+    Tableau T;
+    const double g = 1.0 - 1.0 / sqrt(2.0);
+    if (scheme == RMHD_IMEX_SSP222) {
+        T.s = 2;
+        T.At[1][0] = 1.0;
+        T.A[0][0] = g;
+        T.A[1][0] = 1.0 - 2.0 * g;
+        T.A[1][1] = g;
+        T.wt[0] = T.wt[1] = 0.5;
+    } else if (scheme == RMHD_IMEX_SSP2332) {
+        T.s = 3;
+        T.At[1][0] = T.At[2][0] = T.At[2][1] = 0.5;
+        T.A[0][0] = T.A[1][1] = 0.25;
+        T.A[2][0] = T.A[2][1] = T.A[2][2] = 1.0 / 3.0;
+        T.wt[0] = T.wt[1] = T.wt[2] = 1.0 / 3.0;
+    } else if (scheme == RMHD_IMEX_SSP3332) {
+        T.s = 3;
+        T.At[1][0] = 1.0;
+        T.At[2][0] = T.At[2][1] = 0.25;
+        T.A[0][0] = T.A[1][1] = T.A[2][2] = g;
+        T.A[1][0] = 1.0 - 2.0 * g;
+        T.A[2][0] = 0.5 - g;
+        T.wt[0] = T.wt[1] = 1.0 / 6.0;
+        T.wt[2] = 2.0 / 3.0;
+    } else if (scheme == RMHD_IMEX_SSP3433) {
+        const double a = 0.24169426078821, be = 0.06042356519705, et = 0.12915286960590;
+        T.s = 4;
+        T.At[2][1] = 1.0;
+        T.At[3][1] = T.At[3][2] = 0.25;
+        for (int i = 0; i < 4; i++) T.A[i][i] = a;
+        T.A[1][0] = -a;
+        T.A[2][1] = 1.0 - a;
+        T.A[3][0] = be;
+        T.A[3][1] = et;
+        T.A[3][2] = 0.5 - be - et - a;
+        T.wt[1] = T.wt[2] = 1.0 / 6.0;
+        T.wt[3] = 2.0 / 3.0;
+    }
+    for (int i = 0; i < T.s; i++) T.w[i] = T.wt[i];   // every scheme here has w = wt
+    return T;
+}
+
+// F of stage j is formed (its face fluxes computed) when a later row or
+// the weights use it; kept in Fst when a row after the next one, or the
+// weights (j < s-1), use it
+bool f_needed(const Tableau &T, int j)
+{
+    bool need = T.wt[j] != 0.0;
+    for (int k = j + 1; k < T.s; k++) need = need || T.At[k][j] != 0.0;
+    return need;
+}
+
+bool f_stored(const Tableau &T, int j)
+{
+    bool keep = j < T.s - 1 && T.wt[j] != 0.0;
+    for (int k = j + 2; k < T.s; k++) keep = keep || T.At[k][j] != 0.0;
+    return keep;
+}
 
 } // namespace
 
@@ -141,6 +217,7 @@ extern "C" void rmhd_default_params(rmhd_params *p)
     p->c2p_maxit = 100;
     p->c2p_wmax = 100.0;
     p->qflux_mode = RMHD_QFLUX_STAGE;
+    p->imex = RMHD_IMEX_SSP222;
 }
 
 static int check_params(rmhd_t h, const rmhd_params *p)
@@ -177,6 +254,8 @@ static int check_params(rmhd_t h, const rmhd_params *p)
     if (p->qflux_mode != RMHD_QFLUX_STAGE && p->qflux_mode != RMHD_QFLUX_FACE_OHM &&
         p->qflux_mode != RMHD_QFLUX_GAUSS)
         return set_err(h, RMHD_EINVAL, "qflux_mode %d unknown", p->qflux_mode);
+    if (p->imex < RMHD_IMEX_SSP222 || p->imex > RMHD_IMEX_SSP3433)
+        return set_err(h, RMHD_EINVAL, "imex scheme %d unknown", p->imex);
     return RMHD_OK;
 }
 
@@ -198,7 +277,7 @@ static void free_all(Buffers &b)
 {
     void **ptrs[] = {(void **)&b.U, &b.PA, &b.PB, (void **)&b.V, (void **)&b.dR1, &b.J1, &b.J2,
                      &b.F[0], &b.F[1], &b.F[2], (void **)&b.met, (void **)&b.sig,
-                     (void **)&b.stage};
+                     (void **)&b.stage, (void **)&b.Fst, (void **)&b.dRs};
     for (void **q : ptrs)
         if (*q) {
             cudaFree(*q);
@@ -334,9 +413,9 @@ static void enqueue_stages12_t(rmhd_t h, cudaEvent_t *ev, double *Us)
     const unsigned nbd = deferred_blocks(h);
     T *PA = (T *)b.PA, *PB = (T *)b.PB, *J1 = (T *)b.J1, *J2 = (T *)b.J2;
     T *F0 = (T *)b.F[0], *F1 = (T *)b.F[1], *F2 = (T *)b.F[2];
-    if (dfr) cudaMemsetAsync(b.dcount, 0, 3 * sizeof(int), h->st);
+    if (dfr) cudaMemsetAsync(b.dcount, 0, NDEFER * sizeof(int), h->st);
     mark(0);
-    k_stage1<FLAT, T><<<nb, TPB, 0, h->st>>>(K, b.U, PA, b.GA, b.dR1, J1, b.met, b.sig,
+    k_stage1<FLAT, T><<<nb, TPB, 0, h->st>>>(K, b.U, PA, b.GA, b.GA, b.dR1, J1, b.met, b.sig,
                                              defer_of(h, 0), b.stats);
     if (dfr)
         k_deferred<FLAT, 1, T><<<nbd, TPB, 0, h->st>>>(K, defer_of(h, 0), b.met, b.sig, nullptr,
@@ -392,9 +471,123 @@ template <bool FLAT, class T> static void enqueue_step_t(rmhd_t h, cudaEvent_t *
     enqueue_final_t<FLAT, T>(h, ev);
 }
 
-static void enqueue_step(rmhd_t h, cudaEvent_t *ev = nullptr)
+// events of a profiled step of the general form: the time between two
+// consecutive marks is added to the group (RMHD_NPROF index) of the later
+struct ProfMarks {
+    static const int MAX = 48;
+    cudaEvent_t ev[MAX];
+    int grp[MAX];
+    int n = 0;
+};
+
+// One step of the general IMEX form (schemes other than Table imex).  Stage
+// i: k_combine forms its explicit part in V (and F of stage i-1 from the
+// face fluxes of its primitives), k_stage1 with gimex = A_ii solves the
+// implicit part with the recovery and writes the stage's primitives, Dt R_i
+// and current.  The stages alternate between the two primitive buffers so
+// that the last one lands in PB; the final recovery writes PA.  The face
+// fluxes of a stage are computed only when a later row or the weights use
+// its F.
+template <bool FLAT, class T> static void enqueue_general_t(rmhd_t h, ProfMarks *pm)
+{
+    Buffers &b = h->b;
+    const StepConst &K = h->K;
+    const Tableau tab = tableau(h->p.imex);
+    const int s = tab.s;
+    const long long S = K.G.S;
+    const unsigned nb = nblk(make_bricks(K.G.n).threads), nbc = nblk(K.G.N);
+    const bool dfr = b.dcap > 0;
+    const unsigned nbd = deferred_blocks(h);
+    auto mark = [&](int g) {
+        if (pm && pm->n < ProfMarks::MAX) {
+            pm->grp[pm->n] = g;
+            cudaEventRecord(pm->ev[pm->n++], h->st);
+        }
+    };
+    T *Pb[2] = {(T *)b.PA, (T *)b.PB};
+    double *Gb[2] = {b.GA, b.GB};
+    T *J = (T *)b.J1;
+    T *F0 = (T *)b.F[0], *F1 = (T *)b.F[1], *F2 = (T *)b.F[2];
+    if (dfr) cudaMemsetAsync(b.dcount, 0, NDEFER * sizeof(int), h->st);
+    mark(-1);
+    int prev = 0;   // buffer of the previous stage's primitives (P^n: PA)
+    for (int i = 0; i < s; i++) {
+        const int cur = (s - 1 - i) % 2 == 0 ? 1 : 0;
+        StepConst Ki = K;
+        Ki.gimex = tab.A[i][i];
+        Ki.igimex = 1.0 / tab.A[i][i];
+        const double *Uin = b.U;
+        if (i > 0) {
+            ImexRow row = {};
+            row.nF = row.nR = i;
+            for (int j = 0; j < i; j++) {
+                row.aF[j] = tab.At[i][j];
+                row.aR[j] = tab.A[i][j];
+            }
+            row.jnew = f_needed(tab, i - 1) ? i - 1 : -1;
+            row.store = f_stored(tab, i - 1) ? 1 : 0;
+            k_combine<FLAT, T><<<nbc, TPB, 0, h->st>>>(K, row, b.U, Pb[prev], F0, F1, F2, b.met,
+                                                       b.Fst, b.dRs, b.V);
+            Uin = b.V;
+        }
+        double *dRi = b.dRs + (size_t)i * 3 * S;
+        k_stage1<FLAT, T><<<nb, TPB, 0, h->st>>>(Ki, Uin, Pb[cur], Gb[prev], Gb[cur], dRi, J,
+                                                 b.met, b.sig, defer_of(h, i), b.stats);
+        if (dfr)
+            k_deferred<FLAT, 1, T><<<nbd, TPB, 0, h->st>>>(Ki, defer_of(h, i), b.met, b.sig,
+                                                           nullptr, Pb[cur], Gb[cur], dRi, J,
+                                                           nullptr, nullptr, b.stats);
+        mark(i == 0 ? 0 : 3);
+        if (f_needed(tab, i)) {
+            launch_ghosts(h, Pb[cur], NPR);
+            if (K.qflux == RMHD_QFLUX_GAUSS) gauss_charge<FLAT, T>(h, Pb[cur], nullptr);
+            if (K.qflux != RMHD_QFLUX_FACE_OHM) launch_ghosts(h, J, 3);
+            mark(1);
+            if (i < s - 1) {
+                launch_flux<T, FLAT>(h, Pb[cur], J);
+                mark(2);
+            }
+        }
+        prev = cur;
+    }
+    // U^{n+1} = [U^n + dt sum_{j<s-1} wt_j F_j + sum_j w_j Dt R_j] + wt_{s-1} dt F_{s-1}
+    launch_flux<T, FLAT>(h, Pb[prev], J);
+    mark(4);
+    ImexRow row = {};
+    row.nF = s - 1;
+    row.nR = s;
+    for (int j = 0; j < s; j++) {
+        if (j < s - 1) row.aF[j] = tab.wt[j];
+        row.aR[j] = tab.w[j];
+    }
+    row.jnew = -1;
+    k_combine<FLAT, T><<<nbc, TPB, 0, h->st>>>(K, row, b.U, Pb[prev], F0, F1, F2, b.met, b.Fst,
+                                               b.dRs, b.V);
+    k_final<FLAT, T><<<nb, TPB, 0, h->st>>>(K, b.V, Pb[prev], Gb[prev], F0, F1, F2, b.met, b.U,
+                                            Pb[0], Gb[0], defer_of(h, s), b.stats);
+    if (dfr)
+        k_deferred<FLAT, 3, T><<<nbd, TPB, 0, h->st>>>(K, defer_of(h, s), b.met, b.sig, nullptr,
+                                                       Pb[0], Gb[0], nullptr, nullptr, nullptr,
+                                                       b.U, b.stats);
+    mark(5);
+    launch_ghosts(h, Pb[0], NPR);
+    if (K.qflux == RMHD_QFLUX_GAUSS) gauss_charge<FLAT, T>(h, Pb[0], b.U);
+    mark(1);
+}
+
+static void enqueue_step(rmhd_t h, cudaEvent_t *ev = nullptr, ProfMarks *pm = nullptr)
 {
     const bool mixed = h->p.precision == RMHD_PREC_MIXED;
+    if (h->p.imex != RMHD_IMEX_SSP222) {
+        if (h->flat) {
+            if (mixed) enqueue_general_t<true, float>(h, pm);
+            else enqueue_general_t<true, double>(h, pm);
+        } else {
+            if (mixed) enqueue_general_t<false, float>(h, pm);
+            else enqueue_general_t<false, double>(h, pm);
+        }
+        return;
+    }
     if (h->flat) {
         if (mixed) enqueue_step_t<true, float>(h, ev);
         else enqueue_step_t<true, double>(h, ev);
@@ -480,6 +673,8 @@ extern "C" int rmhd_create(const rmhd_params *p, void *cuda_stream, rmhd_t *out)
     G.N = (long long)G.n[0] * G.n[1] * G.n[2];
     K.gimex = 1.0 - 1.0 / sqrt(2.0);
     K.igimex = 1.0 / K.gimex;
+    const Tableau tab = tableau(p->imex);
+    K.wlast = tab.wt[tab.s - 1];
     K.gfac = p->gamma_eos / (p->gamma_eos - 1.0);
     K.gfacf = (float)K.gfac;
     K.kappa = p->kappa;
@@ -495,12 +690,16 @@ extern "C" int rmhd_create(const rmhd_params *p, void *cuda_stream, rmhd_t *out)
     const bool mixed = p->precision == RMHD_PREC_MIXED;
     const size_t fb = sizeof(double) * (size_t)G.S;
     const size_t fe = (mixed ? sizeof(float) : sizeof(double)) * (size_t)G.S;
+    const bool general = p->imex != RMHD_IMEX_SSP222;
+    const size_t nstore = tab.s - 1;   // Fst slot j holds F of stage j (j < s-1)
     struct { void **ptr; size_t bytes; } allocs[] = {
         {(void **)&b.U, fb * NCO}, {&b.PA, fe * NPR}, {&b.PB, fe * NPR},
         {(void **)&b.V, fb * NCO}, {(void **)&b.dR1, fb * 3}, {&b.J1, fe * 3},
         {&b.J2, fe * 3}, {&b.F[0], fe * NCO}, {&b.F[1], fe * NCO}, {&b.F[2], fe * NCO},
         {(void **)&b.met, fb * NMET}, {(void **)&b.sig, fb},
-        {(void **)&b.GA, mixed ? fb * 4 : 0}, {(void **)&b.GB, mixed ? fb * 4 : 0}};
+        {(void **)&b.GA, mixed ? fb * 4 : 0}, {(void **)&b.GB, mixed ? fb * 4 : 0},
+        {(void **)&b.Fst, general ? fb * NCO * nstore : 0},
+        {(void **)&b.dRs, general ? fb * 3 * tab.s : 0}};
     b.own_guess = mixed;
     for (auto &a : allocs) {
         if (a.bytes == 0) continue;
@@ -535,7 +734,7 @@ extern "C" int rmhd_create(const rmhd_params *p, void *cuda_stream, rmhd_t *out)
         if (cap < 1024) cap = 1024;
         if (cap > (1LL << 30) / DREC) cap = (1LL << 30) / DREC;
         b.dcap = (int)cap;
-        if (cudaMalloc((void **)&b.dcount, 3 * sizeof(int)) != cudaSuccess ||
+        if (cudaMalloc((void **)&b.dcount, NDEFER * sizeof(int)) != cudaSuccess ||
             cudaMalloc((void **)&b.didx, sizeof(int) * (size_t)cap) != cudaSuccess ||
             cudaMalloc((void **)&b.drec, sizeof(double) * DREC * (size_t)cap) != cudaSuccess) {
             free_all(b);
@@ -820,6 +1019,28 @@ extern "C" int rmhd_step_profiled(rmhd_t h, double dt, int nsteps, double ms[RMH
     h->K.dt = dt;
     h->K.idt = 1.0 / dt;
     for (int g = 0; g < RMHD_NPROF; g++) ms[g] = 0.0;
+    if (h->p.imex != RMHD_IMEX_SSP222) {
+        ProfMarks pm;
+        for (int i = 0; i < ProfMarks::MAX; i++) CK(cudaEventCreate(&pm.ev[i]));
+        int rc = RMHD_OK;
+        for (int st = 0; st < nsteps && !rc; st++) {
+            pm.n = 0;
+            enqueue_step(h, nullptr, &pm);
+            cudaError_t e = cudaEventSynchronize(pm.ev[pm.n - 1]);
+            if (e != cudaSuccess) {
+                rc = set_err(h, RMHD_ECUDA, "step failed: %s", cudaGetErrorString(e));
+                break;
+            }
+            for (int k = 1; k < pm.n; k++) {
+                float t = 0.f;
+                cudaEventElapsedTime(&t, pm.ev[k - 1], pm.ev[k]);
+                ms[pm.grp[k]] += t;
+            }
+        }
+        for (int i = 0; i < ProfMarks::MAX; i++) cudaEventDestroy(pm.ev[i]);
+        if (!rc) h->steps += nsteps;
+        return rc;
+    }
     cudaEvent_t ev[9];
     for (int i = 0; i < 9; i++) CK(cudaEventCreate(&ev[i]));
     int rc = RMHD_OK;
@@ -1139,6 +1360,8 @@ extern "C" int rmhd_adjoint_forward(rmhd_t h, double dt, int nsteps, int checkpo
         return set_err(h, RMHD_EINVAL, "the adjoint needs precision RMHD_PREC_FP64");
     if (h->p.qflux_mode != RMHD_QFLUX_STAGE)
         return set_err(h, RMHD_EINVAL, "the adjoint needs qflux_mode RMHD_QFLUX_STAGE");
+    if (h->p.imex != RMHD_IMEX_SSP222)
+        return set_err(h, RMHD_EINVAL, "the adjoint needs imex RMHD_IMEX_SSP222");
     for (int d = 0; d < 3; d++)
         if (h->K.G.g[d] && h->K.G.n[d] < 3)
             return set_err(h, RMHD_EINVAL, "the adjoint needs n >= 3 in active directions");

@@ -35,6 +35,7 @@ def test_param_struct_size_matches():
     assert all(b == 0xAB for b in bytes(buf)[size:]), "C struct larger than the binding's"
     p = R.make_params()
     assert tuple(p.n) == (1, 1, 1) and p.gamma_eos == 2.0 and p.c2p_tol == 1e-14
+    assert p.imex == 0
 
 
 @pytest.mark.parametrize("bad", [dict(n=(0, 1, 1)), dict(dx=(0.0, 1, 1)), dict(gamma_eos=1.0),
@@ -44,7 +45,8 @@ def test_param_struct_size_matches():
                                  # padded cells beyond 2^31 (the 32-bit index limit)
                                  dict(n=(1300, 1300, 1300)), dict(sigma_model=4),
                                  dict(c2p_maxit=0), dict(c2p_wmax=1.0),
-                                 dict(c2p_first_pass=-1), dict(n=(-4, 1, 1))])
+                                 dict(c2p_first_pass=-1), dict(n=(-4, 1, 1)),
+                                 dict(imex=4), dict(imex=-1)])
 def test_create_rejects_bad_params_without_touching_the_device(bad):
     with pytest.raises(R.RMHDError) as e:
         R.Solver(R.make_params(**bad))

@@ -100,6 +100,38 @@ def test_one_step_at_full_size_matches_oracle_on_samples(name):
     assert ep.max() < 1e-12, (name, ep)
 
 
+@pytest.mark.parametrize("scheme", [1, 3])
+def test_general_imex_form_at_full_size_matches_oracle_on_samples(scheme):
+    """The 256^3 blast with SSP2(3,3,2) / SSP3(4,3,3), one step: three face
+    flux evaluations lie on the longest chain of a step (F of stages 1-3 or
+    2-4), so the oracle's box reaches three stencils."""
+    rng = np.random.default_rng(9)
+    wl = W.cyl_blast(n=256)
+    wl.params["imex"] = scheme
+    X, Y, _ = W.cell_centres(wl.params["n"], wl.params["x0"], wl.params["dx"])
+    r = np.sqrt(X * X + Y * Y)
+    active = (r > 0.6) & (r < 1.2)
+    half = 3 * RADIUS[wl.params["recon"]] + 1
+    s = make_solver(wl)
+    s.step(wl.dt, 1)
+    cons_g, prim_g = s.get_cons(), s.get_prims()
+    s.close()
+    picks = _samples(wl, rng, 16, half + 1, active)
+    full_scale_c = np.abs(cons_g).reshape(14, -1).max(axis=1)[:, None]
+    full_scale_p = np.abs(prim_g).reshape(14, -1).max(axis=1)[:, None]
+    dx = wl.params["dx"]
+    for c in picks:
+        co, po = _oracle_centre(wl, c, half)
+        cg = cons_g[(slice(None),) + c][:, None]
+        pg = prim_g[(slice(None),) + c][:, None]
+        ec = state_error(np.concatenate([cg, full_scale_c], axis=1),
+                         np.concatenate([co[:, None], full_scale_c], axis=1), "cons", dx)
+        ep = state_error(np.concatenate([pg, full_scale_p], axis=1),
+                         np.concatenate([po[:, None], full_scale_p], axis=1), "prim", dx)
+        assert ec.max() < 1e-12, (c, ec)
+        assert ep.max() < 1e-12, (c, ep)
+
+
 def test_full_size_conservation_periodic():
     """Property at any size: the periodic 128^3 Alfven wave conserves D, S_i,
     tau, calB^i and Q to rounding over 5 steps (no sources in flat space)."""
