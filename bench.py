@@ -126,8 +126,24 @@ def job_value(n_cells, steps, world, max_ms):
     return world * n_cells * steps / (max_ms * 1e-3)
 
 
-def workload(n):
-    return W.cyl_blast(n=n)
+def workload(n, imex=0):
+    wl = W.cyl_blast(n=n)
+    wl.params["imex"] = imex
+    return wl
+
+
+IMEX_LABELS = {0: "SSP2(2,2,2)", 1: "SSP2(3,3,2)", 2: "SSP3(3,3,2)", 3: "SSP3(4,3,3)"}
+# Structure of the general IMEX form per scheme (from its tableaux): the rows
+# after the first stage as (nonzero explicit coefficients, nonzero implicit
+# off-diagonal coefficients, F of the previous stage formed in the row), the
+# weights row as (nonzero wt, nonzero w), and the stages whose F is formed
+# (one face-flux pass each).  Table imex: one row (1, 1, True), weights (2, 2).
+IMEX_ROWS = {
+    0: ([(1, 1, True)], (2, 2), 2),
+    1: ([(1, 0, True), (2, 2, True)], (3, 3), 3),
+    2: ([(1, 1, True), (2, 1, True)], (3, 3), 3),
+    3: ([(0, 1, False), (1, 1, True), (2, 3, True)], (3, 3), 3),
+}
 
 
 # Algorithmic work per zone of each kernel group (counted from the kernel
@@ -145,9 +161,26 @@ FP64_FIXED = {  # per cell, (mixed path, FP64 path)
 }
 
 
-def fp64_flops(name, prec, iters):
-    fixed = FP64_FIXED[name][0 if prec == "mixed" else 1]
+# the FP64 path forms the flux difference and sources in FP64 (92 flops)
+RHS_FP64 = 92
+
+
+def fp64_flops(name, prec, iters, imex=0):
+    """Algorithmic FP64 flops per cell of one launch of a recovery group.
+    The general IMEX form (imex > 0) counts, per row, 2 flops per field and
+    nonzero coefficient of its combination (the average over the rows that
+    one launch of the stage-row kernel runs) on top of the recovery."""
     per = PAPER_ITER_FLOPS["fixed_E" if name == "final_rhs_recovery" else "implicit"]
+    if imex == 0 or name == "stage1_recovery":
+        fixed = FP64_FIXED[name][0 if prec == "mixed" else 1]
+        return fixed + iters * per
+    rows, (nw, nwr), _ = IMEX_ROWS[imex]
+    rhs = RHS_FP64 if prec == "fp64" else 0
+    if name == "stage2_rhs_recovery":
+        fixed = sum(28 + 2 * 14 * nf + 2 * 3 * nr + (rhs if formed else 0)
+                    for nf, nr, formed in rows) / len(rows)
+    else:
+        fixed = 16 + 2 * 14 * nw + 2 * 3 * nwr + rhs
     return fixed + iters * per
 # face flops: 15 reconstructed fields x 2 sides (MC2 slope ~12 flops, WENO5
 # ~65 with its four divisions), two one-side flux states (~180 each: W,
@@ -169,6 +202,19 @@ TRAFFIC_PER_CELL = {
 }
 
 
+def launches_per_step(wl):
+    """Kernels one step launches: a recovery kernel and its deferred pass per
+    stage and for the final recovery, the ghost fills (primitives, and the
+    stage currents when the charge flux uses them) of every stage whose F is
+    formed and of the result, one flux kernel per active direction and
+    formed F."""
+    nd = sum(1 for d in range(3) if wl.params["n"][d] > 1)
+    rows, _, nflux = IMEX_ROWS[wl.params.get("imex", 0)]
+    stages = len(rows) + 1
+    ghosts = nflux * (2 if wl.params["qflux_mode"] == 0 else 1) + 1
+    return 2 * (stages + 1) + ghosts + nflux * nd
+
+
 def run_ours(args, rank, world, local):
     import torch
     import paper_2510_18968_b300 as R
@@ -177,7 +223,7 @@ def run_ours(args, rank, world, local):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    wl = workload(args.n)
+    wl = workload(args.n, args.imex)
     N = wl.ncells
     prim0 = np.ascontiguousarray(wl.prim)
     out = {}
@@ -231,12 +277,19 @@ def kernel_rooflines(wl, res, prec, steps):
     g = res["groups"]
     N = wl.ncells
     nd = sum(1 for d in range(3) if wl.params["n"][d] > 1)
+    imex = wl.params.get("imex", 0)
+    rows, _, nflux = IMEX_ROWS[imex]
+    # launches per step of each group: the stage-row group runs one recovery
+    # kernel per row, the flux group of the stages one pass per formed F
+    # before the last
+    per_step = {"stage2_rhs_recovery": len(rows), "flux_stage2": nd * (nflux - 1),
+                "flux_final": nd}
     out = {}
     for name, ms in g.items():
-        if name == "ghost_fill":
+        if name == "ghost_fill" or ms <= 0.0:
             continue
         if name.startswith("flux"):
-            per_launch_ms = ms / steps / nd           # one direction per launch
+            per_launch_ms = ms / steps / per_step[name]   # one direction per launch
             faces = N                                 # ~one face per cell per direction
             esz = 4 if prec == "mixed" else 8
             alg = FLUX_FIELDS * esz * faces
@@ -246,8 +299,8 @@ def kernel_rooflines(wl, res, prec, steps):
                          "alg_bytes_per_launch": alg,
                          "alg_flops_per_face": FLUX_FLOPS_PER_FACE}
         else:
-            per_launch_ms = ms / steps
-            f = fp64_flops(name, prec, res["iters"]) * N
+            per_launch_ms = ms / steps / per_step.get(name, 1)
+            f = fp64_flops(name, prec, res["iters"], imex) * N
             ach = f / (per_launch_ms * 1e-3) / 1e12
             out[name] = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
                          "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
@@ -407,25 +460,36 @@ def run_configs(args):
     for scheme, label in ((0, "SSP2(2,2,2)"), (1, "SSP2(3,3,2)"), (2, "SSP3(3,3,2)"),
                           (3, "SSP3(4,3,3)")):
         e = {}
+        wl.params["imex"] = scheme
         for prec in ("mixed", "fp64"):
-            s = R.Solver(dict(wl.params, precision=1 if prec == "mixed" else 0, imex=scheme))
+            s = R.Solver(dict(wl.params, precision=1 if prec == "mixed" else 0))
             s.set_prims(np.ascontiguousarray(wl.prim))
             s.step(wl.dt, 3)
             ms = timed(s, wl.dt, 10)
+            # kernel groups of three more steps (events between the groups)
+            st0 = s.stats()
+            groups = s.step_profiled(wl.dt, 3)
             st = s.stats()
             s.close()
+            iters = ((st["c2p_iterations"] - st0["c2p_iterations"]) /
+                     max(1, st["c2p_calls"] - st0["c2p_calls"]))
+            ks = kernel_rooflines(wl, {"groups": groups, "iters": iters}, prec, 3)
+            top = max((k for k in groups if k != "ghost_fill"), key=groups.get)
             e[prec] = {"value": wl.ncells * 10 / (ms * 1e-3), "ms_per_step": ms / 10,
-                       "paper_iterations_per_recovery": st["c2p_iterations"] / st["c2p_calls"]}
+                       "paper_iterations_per_recovery": iters,
+                       "kernel_ms_per_step": {k: v / 3 for k, v in groups.items()},
+                       "roofline": dict(ks[top], kernel=top)}
         d[label] = e
     out["imex_schemes_cyl_blast_256"] = d
     return out
 
 
-def cpu_oracle_sample(nz, steps):
+def cpu_oracle_sample(nz, steps, imex=0):
     """The FP64 oracle on a z-slab (nz cells thick, same x-y plane and
     options) of the 256^3 workload; returns zone-updates/s and the sample."""
     import oracle
     wl = W.cyl_blast(n=256, nz=nz)
+    wl.params["imex"] = imex
     a, b, g, K = wl.metric_arrays()
     m = oracle.Metric(a.ravel(), b.reshape(3, -1), g.reshape(6, -1), K.reshape(6, -1))
     prim = np.ascontiguousarray(wl.prim.copy())
@@ -436,9 +500,10 @@ def cpu_oracle_sample(nz, steps):
     return wl.ncells * steps / dt, f"256x256x{nz} z-slab of the 256^3 workload, {steps} step(s)"
 
 
-def _oracle_worker(nz, steps, barrier, out):
+def _oracle_worker(nz, steps, barrier, out, imex=0):
     import oracle
     wl = W.cyl_blast(n=256, nz=nz)
+    wl.params["imex"] = imex
     a, b, g, K = wl.metric_arrays()
     m = oracle.Metric(a.ravel(), b.reshape(3, -1), g.reshape(6, -1), K.reshape(6, -1))
     prim = np.ascontiguousarray(wl.prim.copy())
@@ -456,7 +521,7 @@ def host_cores():
         return os.cpu_count() or 1
 
 
-def cpu_oracle_parallel(nz, steps, procs=None):
+def cpu_oracle_parallel(nz, steps, procs=None, imex=0):
     """The single-threaded FP64 oracle, unchanged, run as `procs` concurrent
     processes (spawned: the parent may hold a CUDA context), each on its own
     256 x 256 x nz z-slab of the 256^3 workload; they start together after
@@ -465,7 +530,7 @@ def cpu_oracle_parallel(nz, steps, procs=None):
     procs = procs or min(host_cores(), 64)
     ctx = mpr.get_context("spawn")
     barrier, out = ctx.Barrier(procs), ctx.Queue()
-    ps = [ctx.Process(target=_oracle_worker, args=(nz, steps, barrier, out))
+    ps = [ctx.Process(target=_oracle_worker, args=(nz, steps, barrier, out, imex))
           for _ in range(procs)]
     for p in ps:
         p.start()
@@ -488,22 +553,24 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-configs", action="store_true")
+    ap.add_argument("--imex", type=int, default=0, choices=[0, 1, 2, 3],
+                    help="IMEX scheme of the timed workload (0: SSP2(2,2,2), Table imex)")
     ap.add_argument("--adjoint-n", type=int, default=128)
     ap.add_argument("--adjoint-steps", type=int, default=60)
     ap.add_argument("--adjoint-every", type=int, default=10)
     args = ap.parse_args()
     rank, world, local = dist_env()
     cfg = {"workload": f"cyl_blast_{args.n}^3 (MC2+HLLE, sigma=1e3, Gamma=4/3, outflow, "
-                       "dt=0.25 dx)", "grid": [args.n] * 3,
+                       "dt=0.25 dx)", "grid": [args.n] * 3, "imex": IMEX_LABELS[args.imex],
            "l2": "inputs larger than L2 (state ~2 GB per array set)"}
 
     if args.impl == "reference":
         if rank != 0:
             return
-        cpu_oracle_sample(2, 1)   # warm-up: page in the oracle and its inputs
+        cpu_oracle_sample(2, 1, args.imex)   # warm-up: page in the oracle and its inputs
         vals = []
         for _ in range(args.steps):
-            v, cores, per_core, sample = cpu_oracle_parallel(2, 1)
+            v, cores, per_core, sample = cpu_oracle_parallel(2, 1, imex=args.imex)
             vals.append(v)
         value = statistics.median(vals)
         line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
@@ -550,16 +617,13 @@ def main():
     # kernels and their deferred passes, ghost fills (primitives, and stage
     # currents when the charge flux uses them), one flux kernel per active
     # direction and stage
-    nd = sum(1 for d in range(3) if wl.params["n"][d] > 1)
-    ghosts = (2 if wl.params["qflux_mode"] == 0 else 1) * 2 + 1
-    per_step = 3 + 3 + ghosts + 2 * nd
-    line["gpu_launches"] = per_step * args.steps
+    line["gpu_launches"] = launches_per_step(wl) * args.steps
     if not args.no_adjoint:
         line["adjoint"] = run_adjoint(args)
     if not args.no_configs:
         line["configs"] = run_configs(args)
     if not args.no_cpu_baseline:
-        v, cores, per_core, sample = cpu_oracle_parallel(2, 1)
+        v, cores, per_core, sample = cpu_oracle_parallel(2, 1, imex=args.imex)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                                 "per_core": per_core, "sample": sample}
     print(json.dumps(line))

@@ -49,7 +49,6 @@ struct StepConst {
     int qflux;            // 0 stage current, 1 Ohm's law at faces, 2 Gauss's law
     RecOpts ro;
     float sigma0f, gfacf; // FP32 copies for the FP32 stencil (no FP64 conversions)
-    double wlast;         // weight of the last stage's F in U^{n+1} (1/2 in Table imex)
 };
 
 // a constant of StepConst in the stencil's type
@@ -1126,9 +1125,8 @@ __device__ __forceinline__ void final_write(const StepConst &K, long long c, con
 // spills (measured: stage 2 and the final kernel 3-12% faster; five blocks
 // spill too much).
 // Stage 1 (purely implicit): recovery of U^n with calE solved, guess P^n
-// (Gin; may be Gs, read and written at the same cell).  Also any stage of
-// the general IMEX form, with U its explicit part (k_combine) and
-// K.gimex = the stage's diagonal coefficient A_ii.
+// (Gin; may be Gs, read and written at the same cell).  Also the first
+// stage of the general IMEX form, with K.gimex = A_11.
 template <bool FLAT, class T>
 __global__ void __launch_bounds__(128, 4)
 k_stage1(const StepConst K, const double *__restrict__ U, T *P, const double *Gin, double *Gs,
@@ -1242,9 +1240,7 @@ k_stage2(const StepConst K, const double *__restrict__ U, const T *__restrict__ 
     record_stats(stats, active, status, deferred ? 0 : iters, !deferred);
 }
 
-// Final: U^{n+1} = V + wlast dt F[U_s] (wlast = 1/2 in Table imex, V then
-// holding U^n + dt/2 F[U1] + dt/2 (R1 + R2)); recovery with calE fixed
-// (guess: the last stage's primitives).
+// Final: U^{n+1} = V + dt/2 F[U2]; recovery with calE fixed (guess P2).
 template <bool FLAT, class T>
 __global__ void __launch_bounds__(128, 4)
 k_final(const StepConst K, const double *__restrict__ Vb, const T *__restrict__ P2,
@@ -1269,7 +1265,7 @@ k_final(const StepConst K, const double *__restrict__ Vb, const T *__restrict__ 
         for (int f = 0; f < NPR; f++) pr[f] = P2[f * S + c];
         T r[NCO];
         rhs_cell<FLAT, T>(K, pr, met, Fx, Fy, Fz, c, r);
-        const double hdt = K.wlast * K.dt;
+        const double hdt = 0.5 * K.dt;
         bool finite = true;
         for (int f = 0; f < NCO; f++) {
             un[f] = Vb[f * S + c] + hdt * (double)r[f];
@@ -1305,57 +1301,170 @@ k_final(const StepConst K, const double *__restrict__ Vb, const T *__restrict__ 
 }
 
 // One row of the general IMEX-RK form (Sec. III.A) for the tableaux other
-// than Table imex: out = U^n + dt sum_{j<nF} aF_j F_j, and on calE also
-// + sum_{j<nR} aR_j Dt R_j.  A stage row (i) gives the stage's explicit
-// part, which k_stage1 then solves implicitly; the last row (the weights,
-// without the last stage's F) gives V for k_final.  F_jnew, when jnew >= 0,
-// is formed here from the face fluxes of its stage (primitives P) and, if a
-// later row needs it, kept in Fst; the other F_j come from Fst.
+// than Table imex, at one cell: u = U^n + dt sum_q aF_q F_q, and on calE
+// also + sum_q aR_q Dt R_q.  F_jnew (jnew >= 0, coefficient anew) is formed
+// here from the face fluxes of its stage (primitives Pp) and, if a later row
+// needs it (store), kept in Fst; the other F_q, those whose bit is set in
+// fmask, come from Fst, and the Dt R_q of the bits of rmask (the nonzero
+// coefficients: the FP64 pipe does no compares).
 struct ImexRow {
-    double aF[4], aR[4];
-    int nF, nR, jnew, store;
+    double aF[4], aR[4], anew;
+    int fmask, rmask, jnew, store;
 };
 
 template <bool FLAT, class T>
-__global__ void __launch_bounds__(128)
-k_combine(const StepConst K, const ImexRow row, const double *__restrict__ U,
-          const T *__restrict__ P, const T *__restrict__ Fx, const T *__restrict__ Fy,
-          const T *__restrict__ Fz, const double *__restrict__ met, double *Fst,
-          const double *__restrict__ dRs, double *out)
+__device__ __forceinline__ void row_combine(const StepConst &K, const ImexRow &row,
+                                            const double *U, const T *__restrict__ Pp,
+                                            const T *__restrict__ Fx, const T *__restrict__ Fy,
+                                            const T *__restrict__ Fz,
+                                            const double *__restrict__ met, double *Fst,
+                                            const double *__restrict__ dRs, long long c,
+                                            double u[NCO])
+{
+    const long long S = K.G.S;
+    double acc[NCO];
+#pragma unroll
+    for (int f = 0; f < NCO; f++) acc[f] = 0.0;
+    if (row.jnew >= 0) {
+        T pr[NPR], r[NCO];
+        for (int f = 0; f < NPR; f++) pr[f] = Pp[f * S + c];
+        rhs_cell<FLAT, T>(K, pr, met, Fx, Fy, Fz, c, r);
+        double *Fn = Fst + (long long)row.jnew * NCO * S + c;
+#pragma unroll
+        for (int f = 0; f < NCO; f++) {
+            const double rf = (double)r[f];
+            if (row.store) Fn[f * S] = rf;
+            acc[f] = row.anew * rf;
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        if (!((row.fmask >> q) & 1)) continue;
+        const double a = row.aF[q];
+#pragma unroll
+        for (int f = 0; f < NCO; f++) acc[f] += a * Fst[((long long)q * NCO + f) * S + c];
+    }
+#pragma unroll
+    for (int f = 0; f < NCO; f++) u[f] = U[f * S + c] + K.dt * acc[f];
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        if (!((row.rmask >> q) & 1)) continue;
+#pragma unroll
+        for (int a = 0; a < 3; a++) u[CO_EX + a] += row.aR[q] * dRs[((long long)q * 3 + a) * S + c];
+    }
+}
+
+// Stage i >= 2 of the general form: its explicit part (row i of the
+// tableaux, F of stage i-1 formed here), then the implicit part solved with
+// the recovery (K.gimex = A_ii, guess: stage i-1's primitives Gp) -> the
+// stage's primitives P, guess Gs, Dt R_i and current J.
+template <bool FLAT, class T>
+__global__ void __launch_bounds__(128, 4)
+k_stage_row(const StepConst K, const ImexRow row, const double *__restrict__ U,
+            const T *__restrict__ Pp, const double *__restrict__ Gp, const T *__restrict__ Fx,
+            const T *__restrict__ Fy, const T *__restrict__ Fz, double *Fst,
+            const double *__restrict__ dRs, const double *__restrict__ met,
+            const double *__restrict__ sig, T *P, double *Gs, double *dRi, T *J, const Defer df,
+            unsigned long long *stats)
 {
     const Grid &G = K.G;
     const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (t >= G.N) return;
+    const Bricks bk = make_bricks(G.n);
     int i, j, k;
-    interior_coords(G, t, i, j, k);
-    const long long c = cell_at(G, i, j, k), S = G.S;
-    double rn[NCO];
-#pragma unroll
-    for (int f = 0; f < NCO; f++) rn[f] = 0.0;
-    if (row.jnew >= 0) {
-        T pr[NPR], r[NCO];
-        for (int f = 0; f < NPR; f++) pr[f] = P[f * S + c];
-        rhs_cell<FLAT, T>(K, pr, met, Fx, Fy, Fz, c, r);
-#pragma unroll
-        for (int f = 0; f < NCO; f++) rn[f] = (double)r[f];
-        if (row.store)
-#pragma unroll
-            for (int f = 0; f < NCO; f++) Fst[((long long)row.jnew * NCO + f) * S + c] = rn[f];
+    const bool active = brick_coords(G, bk, t, i, j, k);
+    int status = 0, iters = 0;
+    long long c = 0;
+    double us[NCO], pr[NPR], E[3], gp = 0.0, gv[3] = {0, 0, 0}, cc = 0.0;
+    Met<double> m;
+    PaperState ps;
+    if (active) {
+        c = cell_at(G, i, j, k);
+        const long long S = G.S;
+        row_combine<FLAT, T>(K, row, U, Pp, Fx, Fy, Fz, met, Fst, dRs, c, us);
+        load_metric<FLAT>(met, S, c, m);
+        RecIn in;
+        load_rec_in(us, in);
+        cc = K.gimex * K.dt * m.alpha * sigma_cell(K, sig, c, in.D);
+        gp = Gp[c];
+        for (int a = 0; a < 3; a++) gv[a] = Gp[(1 + a) * S + c];
+        status = recover<FLAT>(in, m, K.ro, true, cc, gp, gv, us[CO_PHI], us[CO_PSI], us[CO_Q],
+                               pr, E, iters, df.cap ? REC_FIRST : REC_ALL, &ps);
     }
-#pragma unroll
-    for (int f = 0; f < NCO; f++) {
-        double acc = 0.0;
-        for (int q = 0; q < row.nF; q++) {
-            if (row.aF[q] == 0.0) continue;
-            const double F = q == row.jnew ? rn[f] : Fst[((long long)q * NCO + f) * S + c];
-            acc += row.aF[q] * F;
+    const bool want = active && status == REC_DEFER;
+    const int slot = defer_slot(df, want);
+    if (want) {
+        if (slot >= 0) {
+            defer_store(df, slot, interior_index(G, i, j, k), us, gp, gv, ps);
+        } else {
+            RecIn in;
+            load_rec_in(us, in);
+            int it2 = 0;
+            status = recover<FLAT>(in, m, K.ro, true, cc, gp, gv, us[CO_PHI], us[CO_PSI],
+                                   us[CO_Q], pr, E, it2, REC_ALL);
+            iters = it2;
         }
-        double u = U[f * S + c] + K.dt * acc;
-        if (f >= CO_EX && f < CO_EX + 3)
-            for (int q = 0; q < row.nR; q++)
-                if (row.aR[q] != 0.0) u += row.aR[q] * dRs[((long long)q * 3 + f - CO_EX) * S + c];
-        out[f * S + c] = u;
     }
+    const bool deferred = want && slot >= 0;
+    if (active && !deferred) stage1_write(K, c, pr, E, us, m.alpha, P, Gs, dRi, J);
+    record_stats(stats, active, status, deferred ? 0 : iters, !deferred);
+}
+
+// Final of the general form: U^{n+1} from the weights row (F of the last
+// stage formed here), written over U^n in place (each cell reads its own
+// U^n first); recovery with calE fixed (guess: the last stage's primitives).
+template <bool FLAT, class T>
+__global__ void __launch_bounds__(128, 4)
+k_final_row(const StepConst K, const ImexRow row, const T *__restrict__ Pp,
+            const double *__restrict__ Gp, const T *__restrict__ Fx, const T *__restrict__ Fy,
+            const T *__restrict__ Fz, double *Fst, const double *__restrict__ dRs,
+            const double *__restrict__ met, double *U, T *P, double *Gs, const Defer df,
+            unsigned long long *stats)
+{
+    const Grid &G = K.G;
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const Bricks bk = make_bricks(G.n);
+    int i, j, k;
+    const bool active = brick_coords(G, bk, t, i, j, k);
+    int status = 0, iters = 0;
+    long long c = 0;
+    double un[NCO], pn[NPR], E[3], gp = 0.0, gv[3] = {0, 0, 0};
+    Met<double> m;
+    PaperState ps;
+    if (active) {
+        c = cell_at(G, i, j, k);
+        const long long S = G.S;
+        row_combine<FLAT, T>(K, row, U, Pp, Fx, Fy, Fz, met, Fst, dRs, c, un);
+        bool finite = true;
+        for (int f = 0; f < NCO; f++) {
+            finite = finite && isfinite(un[f]);
+            U[f * S + c] = un[f];
+        }
+        if (!finite) atomicOr((unsigned long long *)&stats[ST_NAN], 1ULL);
+        load_metric<FLAT>(met, S, c, m);
+        RecIn in;
+        load_rec_in(un, in);
+        gp = Gp[c];
+        for (int a = 0; a < 3; a++) gv[a] = Gp[(1 + a) * S + c];
+        status = recover<FLAT>(in, m, K.ro, false, 0.0, gp, gv, un[CO_PHI], un[CO_PSI],
+                               un[CO_Q], pn, E, iters, df.cap ? REC_FIRST : REC_ALL, &ps);
+    }
+    const bool want = active && status == REC_DEFER;
+    const int slot = defer_slot(df, want);
+    if (want) {
+        if (slot >= 0) {
+            defer_store(df, slot, interior_index(G, i, j, k), un, gp, gv, ps);
+        } else {
+            RecIn in;
+            load_rec_in(un, in);
+            int it2 = 0;
+            status = recover<FLAT>(in, m, K.ro, false, 0.0, gp, gv, un[CO_PHI], un[CO_PSI],
+                                   un[CO_Q], pn, E, it2, REC_ALL);
+            iters = it2;
+        }
+    }
+    const bool deferred = want && slot >= 0;
+    if (active && !deferred) final_write<FLAT>(K, c, pn, status, m, U, P, Gs);
+    record_stats(stats, active, status, deferred ? 0 : iters, !deferred);
 }
 
 // Deferred pass of stage 1 (STAGE 1), stage 2 (STAGE 2) or the final

@@ -39,8 +39,8 @@ struct Buffers {
     double *drec = nullptr;
     int dcap = 0;
     // general IMEX form (schemes other than Table imex): the F of earlier
-    // stages that later rows use (NCO x S each) and every stage's Dt R (3 x S
-    // each); V holds each row's combination
+    // stages that later rows use (NCO x S each, slot j = stage j) and every
+    // stage's Dt R (3 x S each)
     double *Fst = nullptr, *dRs = nullptr;
 };
 
@@ -481,13 +481,14 @@ struct ProfMarks {
 };
 
 // One step of the general IMEX form (schemes other than Table imex).  Stage
-// i: k_combine forms its explicit part in V (and F of stage i-1 from the
-// face fluxes of its primitives), k_stage1 with gimex = A_ii solves the
-// implicit part with the recovery and writes the stage's primitives, Dt R_i
-// and current.  The stages alternate between the two primitive buffers so
-// that the last one lands in PB; the final recovery writes PA.  The face
-// fluxes of a stage are computed only when a later row or the weights use
-// its F.
+// 1: k_stage1 with gimex = A_11 on U^n.  Stage i >= 2: k_stage_row forms
+// the row's explicit part (F of stage i-1 from the face fluxes of its
+// primitives) and solves the implicit part with the recovery (gimex = A_ii),
+// writing the stage's primitives, Dt R_i and current.  The stages alternate
+// between the two primitive buffers so that the last one lands in PB;
+// k_final_row forms U^{n+1} from the weights in place and recovers it into
+// PA.  The face fluxes of a stage are computed only when a later row or the
+// weights use its F.
 template <bool FLAT, class T> static void enqueue_general_t(rmhd_t h, ProfMarks *pm)
 {
     Buffers &b = h->b;
@@ -495,7 +496,7 @@ template <bool FLAT, class T> static void enqueue_general_t(rmhd_t h, ProfMarks 
     const Tableau tab = tableau(h->p.imex);
     const int s = tab.s;
     const long long S = K.G.S;
-    const unsigned nb = nblk(make_bricks(K.G.n).threads), nbc = nblk(K.G.N);
+    const unsigned nb = nblk(make_bricks(K.G.n).threads);
     const bool dfr = b.dcap > 0;
     const unsigned nbd = deferred_blocks(h);
     auto mark = [&](int g) {
@@ -516,23 +517,28 @@ template <bool FLAT, class T> static void enqueue_general_t(rmhd_t h, ProfMarks 
         StepConst Ki = K;
         Ki.gimex = tab.A[i][i];
         Ki.igimex = 1.0 / tab.A[i][i];
-        const double *Uin = b.U;
-        if (i > 0) {
+        double *dRi = b.dRs + (size_t)i * 3 * S;
+        if (i == 0) {
+            k_stage1<FLAT, T><<<nb, TPB, 0, h->st>>>(Ki, b.U, Pb[cur], Gb[prev], Gb[cur], dRi, J,
+                                                     b.met, b.sig, defer_of(h, i), b.stats);
+        } else {
+            // F of stage i-1 is formed here when any row or the weights use
+            // it (its own coefficient in this row may be zero); the earlier
+            // F come from Fst
             ImexRow row = {};
-            row.nF = row.nR = i;
+            row.jnew = f_needed(tab, i - 1) ? i - 1 : -1;
+            row.store = f_stored(tab, i - 1) ? 1 : 0;
+            row.anew = tab.At[i][i - 1];
             for (int j = 0; j < i; j++) {
                 row.aF[j] = tab.At[i][j];
                 row.aR[j] = tab.A[i][j];
+                row.fmask |= j != row.jnew && tab.At[i][j] != 0.0 ? 1 << j : 0;
+                row.rmask |= tab.A[i][j] != 0.0 ? 1 << j : 0;
             }
-            row.jnew = f_needed(tab, i - 1) ? i - 1 : -1;
-            row.store = f_stored(tab, i - 1) ? 1 : 0;
-            k_combine<FLAT, T><<<nbc, TPB, 0, h->st>>>(K, row, b.U, Pb[prev], F0, F1, F2, b.met,
-                                                       b.Fst, b.dRs, b.V);
-            Uin = b.V;
+            k_stage_row<FLAT, T><<<nb, TPB, 0, h->st>>>(Ki, row, b.U, Pb[prev], Gb[prev], F0, F1,
+                                                        F2, b.Fst, b.dRs, b.met, b.sig, Pb[cur],
+                                                        Gb[cur], dRi, J, defer_of(h, i), b.stats);
         }
-        double *dRi = b.dRs + (size_t)i * 3 * S;
-        k_stage1<FLAT, T><<<nb, TPB, 0, h->st>>>(Ki, Uin, Pb[cur], Gb[prev], Gb[cur], dRi, J,
-                                                 b.met, b.sig, defer_of(h, i), b.stats);
         if (dfr)
             k_deferred<FLAT, 1, T><<<nbd, TPB, 0, h->st>>>(Ki, defer_of(h, i), b.met, b.sig,
                                                            nullptr, Pb[cur], Gb[cur], dRi, J,
@@ -543,28 +549,25 @@ template <bool FLAT, class T> static void enqueue_general_t(rmhd_t h, ProfMarks 
             if (K.qflux == RMHD_QFLUX_GAUSS) gauss_charge<FLAT, T>(h, Pb[cur], nullptr);
             if (K.qflux != RMHD_QFLUX_FACE_OHM) launch_ghosts(h, J, 3);
             mark(1);
-            if (i < s - 1) {
-                launch_flux<T, FLAT>(h, Pb[cur], J);
-                mark(2);
-            }
+            launch_flux<T, FLAT>(h, Pb[cur], J);
+            mark(i < s - 1 ? 2 : 4);
         }
         prev = cur;
     }
-    // U^{n+1} = [U^n + dt sum_{j<s-1} wt_j F_j + sum_j w_j Dt R_j] + wt_{s-1} dt F_{s-1}
-    launch_flux<T, FLAT>(h, Pb[prev], J);
-    mark(4);
+    // U^{n+1} = U^n + dt sum_j wt_j F_j + sum_j w_j Dt R_j, F_{s-1} formed here
     ImexRow row = {};
-    row.nF = s - 1;
-    row.nR = s;
+    row.jnew = s - 1;
+    row.store = 0;
+    row.anew = tab.wt[s - 1];
     for (int j = 0; j < s; j++) {
-        if (j < s - 1) row.aF[j] = tab.wt[j];
+        row.aF[j] = tab.wt[j];
         row.aR[j] = tab.w[j];
+        row.fmask |= j != row.jnew && tab.wt[j] != 0.0 ? 1 << j : 0;
+        row.rmask |= tab.w[j] != 0.0 ? 1 << j : 0;
     }
-    row.jnew = -1;
-    k_combine<FLAT, T><<<nbc, TPB, 0, h->st>>>(K, row, b.U, Pb[prev], F0, F1, F2, b.met, b.Fst,
-                                               b.dRs, b.V);
-    k_final<FLAT, T><<<nb, TPB, 0, h->st>>>(K, b.V, Pb[prev], Gb[prev], F0, F1, F2, b.met, b.U,
-                                            Pb[0], Gb[0], defer_of(h, s), b.stats);
+    k_final_row<FLAT, T><<<nb, TPB, 0, h->st>>>(K, row, Pb[prev], Gb[prev], F0, F1, F2, b.Fst,
+                                                b.dRs, b.met, b.U, Pb[0], Gb[0], defer_of(h, s),
+                                                b.stats);
     if (dfr)
         k_deferred<FLAT, 3, T><<<nbd, TPB, 0, h->st>>>(K, defer_of(h, s), b.met, b.sig, nullptr,
                                                        Pb[0], Gb[0], nullptr, nullptr, nullptr,
@@ -674,7 +677,6 @@ extern "C" int rmhd_create(const rmhd_params *p, void *cuda_stream, rmhd_t *out)
     K.gimex = 1.0 - 1.0 / sqrt(2.0);
     K.igimex = 1.0 / K.gimex;
     const Tableau tab = tableau(p->imex);
-    K.wlast = tab.wt[tab.s - 1];
     K.gfac = p->gamma_eos / (p->gamma_eos - 1.0);
     K.gfacf = (float)K.gfac;
     K.kappa = p->kappa;
