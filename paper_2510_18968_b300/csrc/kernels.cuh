@@ -702,6 +702,185 @@ k_flux_tile(const StepConst K, const float *__restrict__ P, const float *__restr
     }
 }
 
+// FP32 face fluxes along y or z (D > 0) for the TVD reconstructions,
+// walking: lane t of a warp owns the line x = x0 + t along D and the
+// block's four warps walk consecutive runs of FW faces along it, so that
+// loads and flux stores stay coalesced along x.  The block's cells (15
+// fields: primitives and J^D) with their halo are staged in shared memory,
+// [field][position along D][lane] with a row pitch of 33 words.  Each cell
+// is reconstructed once (one slope for its states at the face below and
+// above, same arithmetic as reconstruct()); a face takes the upper state of
+// the cell below, carried in registers from the previous face, and the
+// lower state of the cell above.  The last block along D also takes face
+// n_D (its last warp walks one face more).
+constexpr int FW = 2;          // faces per warp run
+constexpr int FB = 4 * FW;     // faces per block along D (the last block: one more)
+
+// TVD states of the cell s[1] (stencil s[0..2]) at its lower (uM) and
+// upper (uP) faces from one slope, the arithmetic of reconstruct()
+template <class T, int RC>
+__device__ __forceinline__ void recon_cell(const T s[3], T &uM, T &uP)
+{
+    const T sl = tvd_slope<T, RC>(s[0], s[1], s[2]);
+    uP = s[1] + T(0.5) * sl;
+    uM = s[1] - T(0.5) * sl;
+}
+
+template <bool FLAT, int RC, int D>
+__global__ void __launch_bounds__(128)
+k_flux_walk(const StepConst K, const float *__restrict__ P, const float *__restrict__ Jc,
+            const double *__restrict__ met, const double *__restrict__ sig, float *F)
+{
+    static_assert(D > 0 && RC != RC_WENO5, "TVD faces along y and z only (else k_flux_tile)");
+    constexpr int NF = NPR + 1;
+    constexpr int LD = FB + 7;     // cells f0-3 .. f0+FB+3 along D
+    constexpr int PITCH = 33;
+    __shared__ float sm[NF * LD * PITCH];
+    const Grid &G = K.G;
+    const long long S = G.S;
+    const long long s = dstride(G, D);
+    const bool useJ = K.qflux != 1;   // mode 2: Q row overwritten later
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    // block origin: first face f0 along D, first line x0 = t0, the remaining
+    // coordinate c2 (z for D = 1, y for D = 2)
+    int f0, t0, c2;
+    bool last;
+    if (D == 1) {
+        f0 = blockIdx.y * FB; t0 = blockIdx.x * 32; c2 = blockIdx.z;
+        last = blockIdx.y + 1 == gridDim.y;
+    } else {
+        f0 = blockIdx.z * FB; t0 = blockIdx.x * 32; c2 = blockIdx.y;
+        last = blockIdx.z + 1 == gridDim.z;
+    }
+    const int nD = G.n[D], nT = G.n[0];
+    const int f_end = last ? nD + 1 : f0 + FB;      // faces f0 .. f_end-1
+    // cell of line t, position d along D (d = 0: cell f0-3)
+    auto cell = [&](int t, int d) -> long long {
+        const int a = f0 - 3 + d, b = t0 + t;
+        if (D == 1) return cell_at(G, b, a, c2);
+        return cell_at(G, b, c2, a);
+    };
+    // stage cells f0-3 .. f_end+1 along D of the block's lines (x fastest)
+    const int nd_stage = f_end + 2 - (f0 - 3);
+    const int nf_stage = useJ ? NF : NPR;
+    for (int idx = threadIdx.x; idx < 32 * nd_stage; idx += blockDim.x) {
+        const int d = idx >> 5, t = idx & 31;
+        if (t0 + t >= nT) continue;
+        const long long c = cell(t, d);
+        for (int f = 0; f < nf_stage; f++)
+            sm[(f * LD + d) * PITCH + t] = f < NPR ? P[f * S + c] : Jc[D * S + c];
+    }
+    __syncthreads();
+    auto at = [&](int f, int d) -> float { return sm[(f * LD + d) * PITCH + lane]; };
+
+    // this warp's faces fs .. fe-1 (the last warp takes the rest of the block)
+    const int fs = f0 + w * FW;
+    const int fe = w == 3 ? f_end : min(fs + FW, f_end);
+    if (t0 + lane >= nT || fs >= fe) return;
+    const float gfac = K.gfacf;
+    // upper states of the cell below the first face, then the walk
+    float up[NF];
+    {
+        const int d = fs - 1 - (f0 - 3);
+#pragma unroll
+        for (int f = 0; f < NF; f++) {
+            if (f == NPR && !useJ) { up[f] = 0.f; continue; }
+            const float st[3] = {at(f, d - 1), at(f, d), at(f, d + 1)};
+            float um;
+            recon_cell<float, RC>(st, um, up[f]);
+        }
+    }
+#pragma unroll 1
+    for (int fi = fs; fi < fe; fi++) {
+        const int dR = fi - (f0 - 3);          // the cell above the face
+        float pL[NPR], pR[NPR], upn[NF];
+        float JL = up[NPR], JR = 0.f;
+#pragma unroll
+        for (int f = 0; f < NF; f++) {
+            if (f == NPR && !useJ) { upn[f] = 0.f; continue; }
+            const float st[3] = {at(f, dR - 1), at(f, dR), at(f, dR + 1)};
+            float um;
+            recon_cell<float, RC>(st, um, upn[f]);
+            if (f < NPR) { pL[f] = up[f]; pR[f] = um; }
+            else JR = um;
+        }
+        const long long cR = cell(lane, dR), cL = cR - s;
+        Met<float> m;
+        if (FLAT) {
+            m.alpha = 1.f;
+            m.beta[0] = m.beta[1] = m.beta[2] = 0.f;
+            m.g[0] = m.g[3] = m.g[5] = 1.f;
+            m.g[1] = m.g[2] = m.g[4] = 0.f;
+            m.gi[0] = m.gi[3] = m.gi[5] = 1.f;
+            m.gi[1] = m.gi[2] = m.gi[4] = 0.f;
+            m.sg = m.isg = 1.f;
+        } else {
+            m.alpha = (float)(0.5 * (met[M_ALPHA * S + cL] + met[M_ALPHA * S + cR]));
+            for (int a = 0; a < 3; a++)
+                m.beta[a] = (float)(0.5 * (met[(M_BETA + a) * S + cL] + met[(M_BETA + a) * S + cR]));
+            for (int a = 0; a < 6; a++)
+                m.g[a] = (float)(0.5 * (met[(M_GAMMA + a) * S + cL] + met[(M_GAMMA + a) * S + cR]));
+            met_complete(m);
+        }
+        // a face state with rho <= 0, p <= 0 or v^2 >= 1 falls back to its
+        // cell's values (all fields)
+#pragma unroll
+        for (int sd = 0; sd < 2; sd++) {
+            float *q = sd == 0 ? pL : pR;
+            float v[3] = {q[PR_VX], q[PR_VY], q[PR_VZ]}, vl[3];
+            lower<float, FLAT>(m, v, vl);
+            if (!(q[PR_RHO] > 0.f) || !(q[PR_P] > 0.f) || !(dot3(v, vl) < 1.f)) {
+                const int d = sd == 0 ? dR - 1 : dR;
+#pragma unroll
+                for (int f = 0; f < NPR; f++) q[f] = at(f, d);
+                if (useJ) {
+                    if (sd == 0) JL = at(NPR, d);
+                    else JR = at(NPR, d);
+                }
+            }
+        }
+        float sigma = K.sigma0f;
+        if (K.sigma_model == 1) {
+            sigma = (float)(K.sigma0 * 0.5 * (sig[cL] + sig[cR]));
+        } else if (K.sigma_model >= 2) {
+            double sgm = 0.0;
+            for (int sd = 0; sd < 2; sd++) {
+                const long long cc = sd == 0 ? cL : cR;
+                Met<double> mc;
+                load_metric<FLAT>(met, S, cc, mc);
+                double v[3] = {(double)P[PR_VX * S + cc], (double)P[PR_VY * S + cc],
+                               (double)P[PR_VZ * S + cc]}, vl[3];
+                lower<double, FLAT>(mc, v, vl);
+                double Dc = mc.sg * (double)P[PR_RHO * S + cc] / sqrt(1.0 - dot3(v, vl));
+                sgm += 0.5 * sigma_cell(K, sig, cc, Dc);
+            }
+            sigma = (float)sgm;
+        }
+        float cFL, cFR, cUU;
+        if (FLAT) {
+            cFL = 0.5f; cFR = 0.5f; cUU = -0.5f;
+        } else {
+            const float sq = sqrt(m.gi[sym(D, D)]);
+            const float bs = m.beta[D] / m.alpha;
+            float ap = sq - bs, am = -sq - bs;
+            ap = ap > 0.f ? ap : 0.f;
+            am = am < 0.f ? am : 0.f;
+            const float inv = 1.f / (ap - am);
+            cFL = ap * inv; cFR = -am * inv; cUU = ap * am * inv;
+        }
+        float acc[NCO];
+#pragma unroll
+        for (int f = 0; f < NCO; f++) acc[f] = 0.f;
+        ArrAcc<float> aa{acc};
+        flux_accumulate<float, FLAT, D>(pL, m, sigma, gfac, useJ, JL, cFL, -cUU, aa);
+        flux_accumulate<float, FLAT, D>(pR, m, sigma, gfac, useJ, JR, cFR, cUU, aa);
+#pragma unroll
+        for (int f = 0; f < NCO; f++) F[f * S + cR] = acc[f];
+#pragma unroll
+        for (int f = 0; f < NF; f++) up[f] = upn[f];
+    }
+}
+
 // Reconstruction of cell c along D: its state at the face below (m) and
 // above (p) for the 14 primitives and, when J != nullptr, the current J^D.
 template <class T, int RC>

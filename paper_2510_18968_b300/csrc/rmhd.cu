@@ -315,7 +315,10 @@ template <class T> static void launch_ghosts(rmhd_t h, T *buf, int nf)
     k_ghosts<T><<<grid, TPB, 0, h->st>>>(h->K, buf, nf, 0);
 }
 
-// FP32 face fluxes through shared-memory tiles (k_flux_tile)
+// FP32 face fluxes through shared-memory tiles: x faces by rows of 128
+// (k_flux_tile); y and z faces by walking runs (k_flux_walk, blocks of 32
+// x-lines x FB faces) for the TVD reconstructions, whose cell slopes the
+// two faces of a cell share, by 32 x 16 tiles (k_flux_tile) for WENO5
 template <bool FLAT, int RC>
 static void launch_flux_tile(rmhd_t h, const float *P, const float *J, float **Fd)
 {
@@ -325,20 +328,29 @@ static void launch_flux_tile(rmhd_t h, const float *P, const float *J, float **F
     if (G.g[0])
         k_flux_tile<FLAT, RC, 0><<<dim3((n0 + 127) / 128, n1, n2), TPB, 0, h->st>>>(
             h->K, P, J, b.met, b.sig, Fd[0]);
-    if (G.g[1])
-        k_flux_tile<FLAT, RC, 1><<<dim3((n0 + 31) / 32, (n1 + 15) / 16, n2), TPB, 0, h->st>>>(
-            h->K, P, J, b.met, b.sig, Fd[1]);
-    if (G.g[2])
-        k_flux_tile<FLAT, RC, 2><<<dim3((n0 + 31) / 32, n1, (n2 + 15) / 16), TPB, 0, h->st>>>(
-            h->K, P, J, b.met, b.sig, Fd[2]);
+    if constexpr (RC == RC_WENO5) {
+        if (G.g[1])
+            k_flux_tile<FLAT, RC, 1><<<dim3((n0 + 31) / 32, (n1 + 15) / 16, n2), TPB, 0, h->st>>>(
+                h->K, P, J, b.met, b.sig, Fd[1]);
+        if (G.g[2])
+            k_flux_tile<FLAT, RC, 2><<<dim3((n0 + 31) / 32, n1, (n2 + 15) / 16), TPB, 0, h->st>>>(
+                h->K, P, J, b.met, b.sig, Fd[2]);
+    } else {
+        if (G.g[1])
+            k_flux_walk<FLAT, RC, 1><<<dim3((n0 + 31) / 32, (n1 + FB - 1) / FB, n2), TPB, 0,
+                                       h->st>>>(h->K, P, J, b.met, b.sig, Fd[1]);
+        if (G.g[2])
+            k_flux_walk<FLAT, RC, 2><<<dim3((n0 + 31) / 32, n1, (n2 + FB - 1) / FB), TPB, 0,
+                                       h->st>>>(h->K, P, J, b.met, b.sig, Fd[2]);
+    }
 }
 
 // faces per thread of the run flux kernel (FP64 path)
 const int FLUX_RUN = 8;
 
 // FP64: the run kernel reconstructs each cell once (ALU-bound path); FP32:
-// shared-memory tiles (k_flux_tile; one thread per face, k_flux, beyond
-// the tiles' grid-dimension limits)
+// shared-memory tiles (k_flux_tile, k_flux_walk; one thread per face,
+// k_flux, beyond the tiles' grid-dimension limits)
 template <class T, bool FLAT, int RC>
 static void launch_flux_rc(rmhd_t h, const T *P, const T *J)
 {
