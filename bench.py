@@ -363,6 +363,20 @@ def kernel_rooflines(wl, res, prec, steps):
     return out
 
 
+# Pipe counters of the recovery kernels from one ncu capture of a 128^3
+# launch of this workload (--set full): FP64-pipe cycles active and lane
+# efficiency (threads per warp instruction / 32).  The FP64 pipe also runs
+# what the algorithmic count leaves out (the Newton steps of divisions and
+# square roots, compares, float <-> double conversions), so the pipe is near
+# its limit while the algorithmic fraction reads lower.  Valid for the
+# kernels as they are; re-measure after changing one.
+NCU_PIPES = {
+    ("stage1_recovery", "mixed"): {"fp64_pipe_busy": 0.8285, "lane_efficiency": 25.79 / 32},
+    ("stage2_rhs_recovery", "mixed"): {"fp64_pipe_busy": 0.8394, "lane_efficiency": 28.68 / 32},
+    ("final_rhs_recovery", "mixed"): {"fp64_pipe_busy": 0.8155, "lane_efficiency": 30.61 / 32},
+}
+
+
 def roofline(wl, res, prec, steps):
     ks = kernel_rooflines(wl, res, prec, steps)
     g = res["groups"]
@@ -372,6 +386,9 @@ def roofline(wl, res, prec, steps):
     per_cell = TRAFFIC_PER_CELL.get((name, prec))
     r["traffic"] = None if per_cell is None else per_cell * wl.ncells
     r["traffic_unit"] = "bytes per launch (ncu, 128^3 launch scaled by cells)"
+    if (name, prec) in NCU_PIPES and wl.params.get("imex", 0) == 0:
+        r["ncu_pipes"] = dict(NCU_PIPES[(name, prec)],
+                              source="ncu --set full, 128^3 launch of this workload")
     return r, ks
 
 
