@@ -304,6 +304,14 @@ int rmhd_adjoint_backward(rmhd_t h, const double *lam_prims, double *grad_prims0
  * pointers, n >= 0; runs on the stream. */
 int rmhd_test_rcp64(const double *x, double *out, long long n, void *cuda_stream);
 
+/* Testing entry point (no counterpart in the paper): the three-argument
+ * minmod of the FP64 MC2 limiter as the flux kernels compute it (integer
+ * operations on the bit patterns), out[i] = min(a, b, c) if all three are
+ * > 0, max(a, b, c) if all are < 0, else +0, for checking against that
+ * definition.  Device pointers, n >= 0; runs on the stream. */
+int rmhd_test_mm3(const double *a, const double *b, const double *c, double *out, long long n,
+                  void *cuda_stream);
+
 const char *rmhd_last_error(rmhd_t h);
 
 /* Free all device memory of the handle (synchronises its stream). */

@@ -9,6 +9,8 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace rmhd {
 
 // primitive and conserved slots (Sec. III.B order and Eq. GRRMHD_flux_form)
@@ -290,6 +292,29 @@ template <class T> __device__ __forceinline__ T mm2(T a, T b)
     return fabs(a) <= fabs(b) ? a : b;
 }
 
+// mm3 on doubles with integer operations on the bit patterns, for the FP64
+// pipe-bound flux kernels (on B300 the FP64 pipe runs compares and min/max
+// at the rate of an FMA): x > 0 holds for the patterns 1 .. 0x7ff0...0
+// (NaN and +-0 excluded), x < 0 for those with the sign bit and a magnitude
+// in the same range, and same-signed doubles order like their magnitude
+// patterns.  Same result as the floating-point form for every input.
+__device__ __forceinline__ double mm3_bits(double a, double b, double c)
+{
+    const unsigned long long MAG = 0x7fffffffffffffffULL, INF = 0x7ff0000000000000ULL;
+    const unsigned long long ua = (unsigned long long)__double_as_longlong(a),
+                             ub = (unsigned long long)__double_as_longlong(b),
+                             uc = (unsigned long long)__double_as_longlong(c);
+    const unsigned long long ma = ua & MAG, mb = ub & MAG, mc = uc & MAG;
+    // every magnitude a nonzero number (not NaN), and all signs equal
+    const bool num = (ma - 1ULL < INF) & (mb - 1ULL < INF) & (mc - 1ULL < INF);
+    const unsigned long long sgn = ua & ~MAG;
+    if (!num || (ub & ~MAG) != sgn || (uc & ~MAG) != sgn) return 0.0;
+    // the value nearest zero: the smallest magnitude, with the common sign
+    unsigned long long m = ma < mb ? ma : mb;
+    m = m < mc ? m : mc;
+    return __longlong_as_double((long long)(sgn | m));
+}
+
 template <class T> __device__ __forceinline__ T mm3(T a, T b, T c)
 {
     if (sizeof(T) == sizeof(float)) {
@@ -298,9 +323,13 @@ template <class T> __device__ __forceinline__ T mm3(T a, T b, T c)
         const bool neg = (a < T(0)) & (b < T(0)) & (c < T(0));
         return pos ? mn : (neg ? mx : T(0));
     }
-    if (a > T(0) && b > T(0) && c > T(0)) return fmin(a, fmin(b, c));
-    if (a < T(0) && b < T(0) && c < T(0)) return fmax(a, fmax(b, c));
-    return T(0);
+    if constexpr (std::is_same<T, double>::value) {
+        return mm3_bits(a, b, c);
+    } else {
+        if (a > T(0) && b > T(0) && c > T(0)) return fmin(a, fmin(b, c));
+        if (a < T(0) && b < T(0) && c < T(0)) return fmax(a, fmax(b, c));
+        return T(0);
+    }
 }
 
 template <class T, int RC> __device__ __forceinline__ T tvd_slope(T um, T u0, T up)

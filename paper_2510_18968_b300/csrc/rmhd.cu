@@ -1539,6 +1539,27 @@ extern "C" int rmhd_test_rcp64(const double *x, double *out, long long n, void *
     return RMHD_OK;
 }
 
+__global__ void k_test_mm3(long long n, const double *__restrict__ a,
+                           const double *__restrict__ b, const double *__restrict__ c,
+                           double *out)
+{
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t < n) out[t] = mm3<double>(a[t], b[t], c[t]);
+}
+
+extern "C" int rmhd_test_mm3(const double *a, const double *b, const double *c, double *out,
+                             long long n, void *cuda_stream)
+{
+    if (n < 0 || (n > 0 && (!a || !b || !c || !out)))
+        return set_err(nullptr, RMHD_EINVAL, "bad arguments");
+    if (n == 0) return RMHD_OK;
+    k_test_mm3<<<nblk(n), TPB, 0, (cudaStream_t)cuda_stream>>>(n, a, b, c, out);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return set_err(nullptr, RMHD_ECUDA, "launch failed: %s", cudaGetErrorString(e));
+    return RMHD_OK;
+}
+
 extern "C" const char *rmhd_last_error(rmhd_t h) { return h ? h->err : g_noh_err; }
 
 // error text of an entry point without a handle (used by the other source file)

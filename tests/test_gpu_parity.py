@@ -393,3 +393,39 @@ def test_mixed_walking_flux_on_ragged_grids(recon, curved, shape):
     _, _, _, c32 = run_gpu(wl, 3, precision=1)
     e = state_l1(c32, c64, "cons", wl.params["dx"], vector_scale=True)
     assert e.max() < 1e-5, (shape, e)
+
+
+def test_fp64_mc2_minmod_on_bit_patterns_matches_its_definition(torch_cuda):
+    """The FP64 MC2 limiter's three-argument minmod, computed by the flux
+    kernels with integer operations on the bit patterns: bit for bit the
+    floating-point definition (min of three positives, max of three
+    negatives, else +0) over signed zeros, subnormals, infinities, NaN and
+    random same- and mixed-signed triples."""
+    import torch
+    import paper_2510_18968_b300 as R
+    L = R.load()
+    rng = np.random.default_rng(31)
+    special = np.array([0.0, -0.0, 5e-324, -5e-324, 1e-310, -1e-310, 1.0, -1.0, 2.5, -2.5,
+                        1.7976931348623157e308, -1.7976931348623157e308, np.inf, -np.inf,
+                        np.nan, np.copysign(np.nan, -1.0)])
+    g = np.array(np.meshgrid(special, special, special, indexing="ij")).reshape(3, -1)
+    n = 300000
+    mag = 10.0 ** rng.uniform(-300, 300, (3, n))
+    sign = np.where(rng.random((3, n)) < 0.5, -1.0, 1.0)
+    same = rng.random(n) < 0.6
+    sign[1:, same] = sign[0, same]
+    r = mag * sign
+    r[:, : n // 10] = np.round(r[:, : n // 10], 0)      # many exact ties and zeros
+    a, b, c = (np.concatenate([g[k], r[k]]) for k in range(3))
+    dev = [torch.tensor(x, device="cuda") for x in (a, b, c)]
+    out = torch.empty_like(dev[0])
+    assert L.rmhd_test_mm3(dev[0].data_ptr(), dev[1].data_ptr(), dev[2].data_ptr(),
+                           out.data_ptr(), a.size, None) == 0
+    torch.cuda.synchronize()
+    got = out.cpu().numpy()
+    with np.errstate(invalid="ignore"):
+        pos = (a > 0) & (b > 0) & (c > 0)
+        neg = (a < 0) & (b < 0) & (c < 0)
+        want = np.where(pos, np.minimum(a, np.minimum(b, c)),
+                        np.where(neg, np.maximum(a, np.maximum(b, c)), 0.0))
+    assert np.array_equal(got.view(np.uint64), want.view(np.uint64))
