@@ -186,7 +186,6 @@ def fp64_flops(name, prec, iters, imex=0):
 # ~65 with its four divisions), two one-side flux states (~180 each: W,
 # enthalpy, EM energy, E x B, stress rows, EM rows, the HLLE accumulation)
 FLUX_FLOPS_PER_FACE_BY_RECON = {0: 30 * 10 + 360, 1: 30 * 12 + 360, 2: 30 * 65 + 360}
-FLUX_FLOPS_PER_FACE = FLUX_FLOPS_PER_FACE_BY_RECON[1]     # the MC2 blast
 FLUX_FIELDS = 15 + 14
 
 # DRAM bytes per cell of one launch (dram__bytes_read.sum +
@@ -198,7 +197,9 @@ TRAFFIC_PER_CELL = {
     # k_flux_tile (x) and k_flux_walk (y, z), mean of the three launches
     ("flux_stage2", "mixed"): ((140.820480e6 + 148.672768e6 + 148.647680e6) +
                                (76.327424e6 + 83.490048e6 + 83.136256e6)) / 3 / 128 ** 3,
-    ("flux_stage2", "fp64"): (981.657088e6 + 511.811328e6) / 128 ** 3,
+    # k_flux_run, mean of the x, y, z launches
+    ("flux_stage2", "fp64"): ((978.207488e6 + 371.160320e6 + 304.045056e6) +
+                              (513.766912e6 + 203.702784e6 + 202.905088e6)) / 3 / 128 ** 3,
 }
 
 
@@ -343,13 +344,22 @@ def kernel_rooflines(wl, res, prec, steps):
         if name.startswith("flux"):
             per_launch_ms = ms / steps / per_step[name]   # one direction per launch
             faces = N                                 # ~one face per cell per direction
-            esz = 4 if prec == "mixed" else 8
-            alg = FLUX_FIELDS * esz * faces
+            if prec == "fp64":
+                # the FP64 face kernel is bound by the FP64 pipe, not by HBM
+                fl = FLUX_FLOPS_PER_FACE_BY_RECON[wl.params["recon"]] * faces
+                ach = fl / (per_launch_ms * 1e-3) / 1e12
+                out[name] = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
+                             "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
+                             "peak_kind": "derived (148 SM x 2 DFMA/clk x 2.032 GHz)",
+                             "launch_ms": per_launch_ms, "alg_fp64_flops_per_launch": fl,
+                             "alg_bytes_per_launch": FLUX_FIELDS * 8 * faces}
+                continue
+            alg = FLUX_FIELDS * 4 * faces
             ach = alg / (per_launch_ms * 1e-3) / 1e9
             out[name] = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
                          "frac": ach / hbm, "peak_kind": kind, "launch_ms": per_launch_ms,
                          "alg_bytes_per_launch": alg,
-                         "alg_flops_per_face": FLUX_FLOPS_PER_FACE}
+                         "alg_flops_per_face": FLUX_FLOPS_PER_FACE_BY_RECON[wl.params["recon"]]}
         else:
             per_launch_ms = ms / steps / per_step.get(name, 1)
             f = fp64_flops(name, prec, res["iters"], imex) * N
