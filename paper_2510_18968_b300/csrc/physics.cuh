@@ -355,10 +355,23 @@ template <class T> __device__ __forceinline__ T weno5(T a, T b, T c, T d, T e)
     t1 = c - T(2) * d + e;
     t2 = T(3) * c - T(4) * d + e;
     T b2 = k13 * t1 * t1 + T(0.25) * t2 * t2;
-    T w0 = T(0.1) / ((eps + b0) * (eps + b0));
-    T w1 = T(0.6) / ((eps + b1) * (eps + b1));
-    T w2 = T(0.3) / ((eps + b2) * (eps + b2));
-    return (w0 * q0 + w1 * q1 + w2 * q2) / (w0 + w1 + w2);
+    if constexpr (std::is_same<T, double>::value) {
+        // the normalised weights d_k/s_k / sum_j d_j/s_j, s_k = (eps + b_k)^2,
+        // over the common denominator s_0 s_1 s_2: one division instead of
+        // four (FP64 divisions are a sequence of FP64-pipe instructions on
+        // B300).  The products stay finite while every b_k < 1e77, i.e. for
+        // jumps below ~1e38 in a primitive; FP32 keeps the four divisions,
+        // whose products would overflow much sooner.
+        const T s0 = (eps + b0) * (eps + b0), s1 = (eps + b1) * (eps + b1),
+                s2 = (eps + b2) * (eps + b2);
+        const T n0 = T(0.1) * (s1 * s2), n1 = T(0.6) * (s0 * s2), n2 = T(0.3) * (s0 * s1);
+        return (n0 * q0 + n1 * q1 + n2 * q2) / (n0 + n1 + n2);
+    } else {
+        T w0 = T(0.1) / ((eps + b0) * (eps + b0));
+        T w1 = T(0.6) / ((eps + b1) * (eps + b1));
+        T w2 = T(0.3) / ((eps + b2) * (eps + b2));
+        return (w0 * q0 + w1 * q1 + w2 * q2) / (w0 + w1 + w2);
+    }
 }
 
 template <class T, int RC>
