@@ -166,7 +166,11 @@ __device__ __forceinline__ void flux_accumulate(const T pr[NPR], const Met<T> &m
     lower<T, FLAT>(m, B, Bl);
     const T rho = pr[PR_RHO], p = pr[PR_P];
     const T v2 = dot3(v, vl);
-    const T W = T(1) / sqrt(T(1) - v2);
+    // Lorentz factor; in FP64 one reciprocal square root instead of a
+    // square root and a division (both FP64-pipe sequences on B300)
+    T W;
+    if constexpr (std::is_same<T, double>::value) W = rsqrt(1.0 - v2);
+    else W = T(1) / sqrt(T(1) - v2);
     const T h = rho + gfac * p;
     const T hW2 = h * W * W;
     const T em = T(0.5) * (dot3(E, El) + dot3(B, Bl));
