@@ -437,7 +437,7 @@ __device__ __forceinline__ void side_vjp(const double pr[NPR + 1], const Met<dou
     lower<double, FLAT>(m, B, Bl);
     const double rho = pr[PR_RHO];
     const double v2 = dot3(v, vl);
-    const double W = 1.0 / sqrt(1.0 - v2);
+    const double W = rsqrt(1.0 - v2);   // as the FP64 forward forms it
     const double h = rho + gfac * pr[PR_P];
     const double hW2 = h * W * W;
     const double Dc = sg * rho * W;
