@@ -198,8 +198,8 @@ TRAFFIC_PER_CELL = {
     ("flux_stage2", "mixed"): ((140.820480e6 + 148.672768e6 + 148.647680e6) +
                                (76.327424e6 + 83.490048e6 + 83.136256e6)) / 3 / 128 ** 3,
     # k_flux_run, mean of the x, y, z launches
-    ("flux_stage2", "fp64"): ((978.207488e6 + 371.160320e6 + 304.045056e6) +
-                              (513.766912e6 + 203.702784e6 + 202.905088e6)) / 3 / 128 ** 3,
+    ("flux_stage2", "fp64"): ((989.442560e6 + 372.153600e6 + 303.645184e6) +
+                              (514.565888e6 + 203.661056e6 + 202.688768e6)) / 3 / 128 ** 3,
 }
 
 
