@@ -378,15 +378,18 @@ def test_fp64_reciprocal_of_the_recovery_matches_division(torch_cuda):
 
 @pytest.mark.parametrize("recon", ["minmod", "mc2"])
 @pytest.mark.parametrize("curved", [False, True])
-@pytest.mark.parametrize("shape", [(5, 13, 11), (33, 9, 17), (3, 3, 3), (7, 1, 10), (9, 17, 1)])
-def test_mixed_walking_flux_on_ragged_grids(recon, curved, shape):
+@pytest.mark.parametrize("shape,qflux", [((5, 13, 11), 0), ((33, 9, 17), 0), ((3, 3, 3), 0),
+                                         ((7, 1, 10), 0), ((9, 17, 1), 0), ((6, 11, 19), 1)])
+def test_mixed_walking_flux_on_ragged_grids(recon, curved, shape, qflux):
     """The mixed path's y and z fluxes for TVD reconstructions walk runs of
     faces (blocks of 8 faces, the last block one more): extents that 8 does
     not divide, extents below one block, inactive directions, flat and
-    curved.  Against the FP64 path after 3 steps, relative L1 per field
+    curved, and the charge flux from Ohm's law at the faces (no staged
+    current).  Against the FP64 path after 3 steps, relative L1 per field
     within 1e-5."""
     from tests.helpers import state_l1
     wl = _smooth(0, recon, curved, shape=shape, seed=13)
+    wl.params["qflux_mode"] = qflux
     wl.params["bc"] = (0, 1, 0)
     wl.dt = 0.2 * min(h for h, n in zip(wl.params["dx"], shape) if n > 1)
     _, _, _, c64 = run_gpu(wl, 3)
