@@ -56,14 +56,22 @@ template <class T> __device__ __forceinline__ void met_complete(Met<T> &m)
 // the ~22 bits of the FP32 hardware reciprocal to well past the 53 of a
 // double in two steps (the result is within an ulp or two of 1/x).  About
 // four FP64 FMAs instead of the FP64 division sequence, which on B300 costs
-// ~11 FMAs of the FP64 pipe.  Arguments outside the FP32 exponent range
+// ~11 FMAs of the FP64 pipe.  The seed's float <-> double conversions are
+// done by moving the exponent and mantissa fields on the integer pipe (on
+// B300 the FP64 pipe runs conversions at the rate of an FMA): x is
+// truncated to 23 mantissa bits, which a seed tolerates, and the float
+// reciprocal widens exactly.  Arguments with |x| outside [2^-120, 2^120)
 // (and 0, inf, NaN) take the plain division.
 __device__ __forceinline__ double rcp64(double x)
 {
-    const float xf = (float)x;
-    const float ax = fabsf(xf);
-    if (!(ax > 1e-36f && ax < 1e36f)) return 1.0 / x;
-    double r = (double)__fdividef(1.0f, xf);
+    const unsigned long long bx = (unsigned long long)__double_as_longlong(x);
+    const unsigned hi = (unsigned)(bx >> 32), ex = (hi >> 20) & 0x7ffu;
+    if (ex < 903u || ex >= 1143u) return 1.0 / x;
+    const unsigned fx = (hi & 0x80000000u) | ((ex - 896u) << 23) | ((unsigned)(bx >> 29) & 0x7fffffu);
+    const unsigned rb = __float_as_uint(__fdividef(1.0f, __uint_as_float(fx)));
+    double r = __hiloint2double((int)((rb & 0x80000000u) | ((((rb >> 23) & 0xffu) + 896u) << 20) |
+                                      ((rb & 0x7fffffu) >> 3)),
+                                (int)(rb << 29));
     double e = fma(-x, r, 1.0);
     r = fma(r, e, r);
     e = fma(-x, r, 1.0);
