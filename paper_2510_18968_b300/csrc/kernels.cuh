@@ -49,6 +49,7 @@ struct StepConst {
     int qflux;            // 0 stage current, 1 Ohm's law at faces, 2 Gauss's law
     RecOpts ro;
     float sigma0f, gfacf; // FP32 copies for the FP32 stencil (no FP64 conversions)
+    float kappaf, idxf[3];
 };
 
 // a constant of StepConst in the stencil's type
@@ -1142,7 +1143,7 @@ __device__ __forceinline__ void sources(const StepConst &K, const T pr_in[NPR],
                                         const double *__restrict__ met, long long c,
                                         T Sv_out[NCO])
 {
-    const T kapT = (T)K.kappa;
+    const T kapT = kc<T>(K.kappa, K.kappaf);
     if (FLAT) {
         // only -Q v^i (E), -kappa Phi, Q - kappa Psi survive in flat space
         const T *pr = pr_in;
@@ -1156,9 +1157,9 @@ __device__ __forceinline__ void sources(const StepConst &K, const T pr_in[NPR],
     } else {
         // curved metric: evaluated in FP64 from the stage primitives
         double pr[NPR], Sv[NCO];
-        for (int f = 0; f < NPR; f++) pr[f] = (double)pr_in[f];
+        for (int f = 0; f < NPR; f++) pr[f] = to_double<T>(pr_in[f]);
         sources_curved<double>(K, pr, met, c, Sv);
-        for (int f = 0; f < NCO; f++) Sv_out[f] = (T)Sv[f];
+        for (int f = 0; f < NCO; f++) Sv_out[f] = from_double<T>(Sv[f]);
     }
 }
 
@@ -1176,7 +1177,7 @@ __device__ __forceinline__ void rhs_cell(const StepConst &K, const T pr[NPR],
     for (int d = 0; d < 3; d++) {
         if (G.g[d] == 0) continue;
         const long long s = dstride(G, d);
-        const T ih = (T)G.idx[d];
+        const T ih = kc<T>(G.idx[d], K.idxf[d]);
         const T *F = Fd[d];
 #pragma unroll
         for (int f = 0; f < NCO; f++) r[f] -= (F[f * G.S + c + s] - F[f * G.S + c]) * ih;
@@ -1244,7 +1245,7 @@ __device__ __forceinline__ void prim_write(const StepConst &K, long long c, cons
                                           T *P, double *Gs)
 {
     const long long S = K.G.S;
-    for (int f = 0; f < NPR; f++) P[f * S + c] = (T)pr[f];
+    for (int f = 0; f < NPR; f++) P[f * S + c] = from_double<T>(pr[f]);
     for (int f = 0; f < 4; f++) Gs[f * S + c] = pr[PR_P + f];
 }
 
@@ -1260,7 +1261,7 @@ __device__ __forceinline__ void stage1_write(const StepConst &K, long long c, co
     for (int a = 0; a < 3; a++) {
         const double r = (E[a] - u[CO_EX + a]) * ig;
         dR1[a * S + c] = r;
-        J1[a * S + c] = (T)(u[CO_Q] * pr[PR_VX + a] - r * iad);   // J = Q v - Dt R/(alpha Dt)
+        J1[a * S + c] = from_double<T>(u[CO_Q] * pr[PR_VX + a] - r * iad);   // J = Q v - Dt R/(alpha Dt)
     }
 }
 
@@ -1277,7 +1278,7 @@ __device__ __forceinline__ void stage2_write(const StepConst &K, long long c, co
     for (int a = 0; a < 3; a++) {
         const double r2 = (E[a] - us[CO_EX + a]) * ig;
         V[(CO_EX + a) * S + c] += 0.5 * (dR1[a * S + c] + r2);
-        J2[a * S + c] = (T)(us[CO_Q] * p2[PR_VX + a] - r2 * iad);
+        J2[a * S + c] = from_double<T>(us[CO_Q] * p2[PR_VX + a] - r2 * iad);
     }
 }
 
@@ -1384,7 +1385,7 @@ k_stage2(const StepConst K, const double *__restrict__ U, const T *__restrict__ 
         rhs_cell<FLAT, T>(K, pr, met, Fx, Fy, Fz, c, r);
         const double dt = K.dt, hdt = 0.5 * dt;
         for (int f = 0; f < NCO; f++) {
-            const double uu = U[f * S + c], rf = (double)r[f];
+            const double uu = U[f * S + c], rf = to_double<T>(r[f]);
             us[f] = uu + dt * rf;
             V[f * S + c] = uu + hdt * rf;
         }
@@ -1447,7 +1448,7 @@ k_final(const StepConst K, const double *__restrict__ Vb, const T *__restrict__ 
         const double hdt = 0.5 * K.dt;
         bool finite = true;
         for (int f = 0; f < NCO; f++) {
-            un[f] = Vb[f * S + c] + hdt * (double)r[f];
+            un[f] = Vb[f * S + c] + hdt * to_double<T>(r[f]);
             finite = finite && isfinite(un[f]);
             U[f * S + c] = un[f];
         }
@@ -1511,7 +1512,7 @@ __device__ __forceinline__ void row_combine(const StepConst &K, const ImexRow &r
         double *Fn = Fst + (long long)row.jnew * NCO * S + c;
 #pragma unroll
         for (int f = 0; f < NCO; f++) {
-            const double rf = (double)r[f];
+            const double rf = to_double<T>(r[f]);
             if (row.store) Fn[f * S] = rf;
             acc[f] = row.anew * rf;
         }

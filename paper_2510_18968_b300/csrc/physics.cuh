@@ -78,6 +78,52 @@ __device__ __forceinline__ double rcp64(double x)
     return fma(r, e, r);
 }
 
+// float <-> double for the mixed path's stored FP32 stencil values, by
+// moving the sign, exponent and mantissa fields on the integer pipe without
+// branches (on B300 the FP64 pipe runs conversions at the rate of an FMA,
+// and the recovery kernels that convert the FP32 right-hand side in and the
+// primitives out are FP64-pipe-bound).  Exact, with round to nearest even
+// for double -> float, for every value whose result is a normal number,
+// zero, infinity or NaN; magnitudes below the smallest normal float
+// (~1.2e-38) are flushed to a signed zero.
+__device__ __forceinline__ double f2d_ftz(float f)
+{
+    const unsigned u = __float_as_uint(f);
+    const unsigned sign = u & 0x80000000u, e = (u >> 23) & 0xffu, m = u & 0x7fffffu;
+    unsigned hi = sign | ((e + 896u) << 20) | (m >> 3);
+    hi = e == 0xffu ? (sign | 0x7ff00000u | (m >> 3)) : hi;
+    hi = e == 0u ? sign : hi;
+    const unsigned lo = e == 0u ? 0u : m << 29;
+    return __hiloint2double((int)hi, (int)lo);
+}
+
+__device__ __forceinline__ float d2f_ftz(double d)
+{
+    const unsigned long long u = (unsigned long long)__double_as_longlong(d);
+    const unsigned hi = (unsigned)(u >> 32), sign = hi & 0x80000000u;
+    const unsigned e = (hi >> 20) & 0x7ffu;
+    const unsigned mf = (unsigned)(u >> 29) & 0x7fffffu, rest = (unsigned)u & 0x1fffffffu;
+    unsigned bits = sign | ((e - 896u) << 23) | mf;
+    // nearest, ties to even; a carry out of the mantissa raises the exponent
+    bits += (rest > 0x10000000u) | ((rest == 0x10000000u) & mf);
+    const bool nan = e == 0x7ffu && (u << 12) != 0ULL;
+    bits = e > 1150u ? (sign | 0x7f800000u | (nan ? 0x400000u : 0u)) : bits;
+    bits = e < 897u ? sign : bits;
+    return __uint_as_float(bits);
+}
+
+// a double stored as T, and a T read as double
+template <class T> __device__ __forceinline__ T from_double(double x)
+{
+    if constexpr (std::is_same<T, float>::value) return d2f_ftz(x);
+    else return (T)x;
+}
+template <class T> __device__ __forceinline__ double to_double(T x)
+{
+    if constexpr (std::is_same<T, float>::value) return f2d_ftz(x);
+    else return (double)x;
+}
+
 // the same metric in another arithmetic type (constants for a dual number)
 template <class R> __device__ __forceinline__ Met<R> met_cast(const Met<double> &m)
 {

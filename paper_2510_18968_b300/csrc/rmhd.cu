@@ -691,6 +691,8 @@ extern "C" int rmhd_create(const rmhd_params *p, void *cuda_stream, rmhd_t *out)
     const Tableau tab = tableau(p->imex);
     K.gfac = p->gamma_eos / (p->gamma_eos - 1.0);
     K.gfacf = (float)K.gfac;
+    K.kappaf = (float)p->kappa;
+    for (int d = 0; d < 3; d++) K.idxf[d] = (float)G.idx[d];
     K.kappa = p->kappa;
     K.sigma_model = p->sigma_model;
     K.sigma0 = p->sigma0;
