@@ -193,7 +193,7 @@ FLUX_FIELDS = 15 + 14
 # by the cell count; traffic grows with the cells).  Valid for the kernels
 # as they are; re-measure after changing one.
 TRAFFIC_PER_CELL = {
-    ("stage2_rhs_recovery", "mixed"): (872.676864e6 + 479.636992e6) / 128 ** 3,
+    ("stage2_rhs_recovery", "mixed"): (866.735616e6 + 471.683072e6) / 128 ** 3,
     # k_flux_tile (x) and k_flux_walk (y, z), mean of the three launches
     ("flux_stage2", "mixed"): ((140.820480e6 + 148.672768e6 + 148.647680e6) +
                                (76.327424e6 + 83.490048e6 + 83.136256e6)) / 3 / 128 ** 3,
@@ -381,9 +381,9 @@ def kernel_rooflines(wl, res, prec, steps):
 # its limit while the algorithmic fraction reads lower.  Valid for the
 # kernels as they are; re-measure after changing one.
 NCU_PIPES = {
-    ("stage1_recovery", "mixed"): {"fp64_pipe_busy": 0.8285, "lane_efficiency": 25.79 / 32},
-    ("stage2_rhs_recovery", "mixed"): {"fp64_pipe_busy": 0.8394, "lane_efficiency": 28.68 / 32},
-    ("final_rhs_recovery", "mixed"): {"fp64_pipe_busy": 0.8155, "lane_efficiency": 30.61 / 32},
+    ("stage1_recovery", "mixed"): {"fp64_pipe_busy": 0.8179, "lane_efficiency": 26.80 / 32},
+    ("stage2_rhs_recovery", "mixed"): {"fp64_pipe_busy": 0.8198, "lane_efficiency": 29.17 / 32},
+    ("final_rhs_recovery", "mixed"): {"fp64_pipe_busy": 0.7368, "lane_efficiency": 30.86 / 32},
 }
 
 
