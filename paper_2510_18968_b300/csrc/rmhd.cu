@@ -398,10 +398,18 @@ static Defer defer_of(rmhd_t h, int which)
     return d;
 }
 
+// Deferred passes: 64-thread blocks, enough of them for every record of a
+// list of up to 148 * 96 * 64 (909 K) records to get its own thread, so that
+// no thread takes a second record after its first (a fallback record can
+// run for thousands of FP64 instructions); blocks past the list's count
+// return at once.  Small blocks free their slot as soon as their two warps
+// are done, which evens out the tail of the few long records.
+const int TPB_DEFER = 64;
 static unsigned deferred_blocks(rmhd_t h)
 {
-    long long want = nblk(h->b.dcap);
-    return (unsigned)(want < 148 * 8 ? (want > 0 ? want : 1) : 148 * 8);
+    long long want = (h->b.dcap + TPB_DEFER - 1) / TPB_DEFER;
+    const long long most = 148LL * 96;
+    return (unsigned)(want < most ? (want > 0 ? want : 1) : most);
 }
 
 // Gauss's-law charge of a stage (interior), then the ghosts of q
@@ -430,7 +438,7 @@ static void enqueue_stages12_t(rmhd_t h, cudaEvent_t *ev, double *Us)
     k_stage1<FLAT, T><<<nb, TPB, 0, h->st>>>(K, b.U, PA, b.GA, b.GA, b.dR1, J1, b.met, b.sig,
                                              defer_of(h, 0), b.stats);
     if (dfr)
-        k_deferred<FLAT, 1, T><<<nbd, TPB, 0, h->st>>>(K, defer_of(h, 0), b.met, b.sig, nullptr,
+        k_deferred<FLAT, 1, T><<<nbd, TPB_DEFER, 0, h->st>>>(K, defer_of(h, 0), b.met, b.sig, nullptr,
                                                        PA, b.GA, b.dR1, J1, nullptr, nullptr,
                                                        b.stats);
     mark(1);
@@ -443,7 +451,7 @@ static void enqueue_stages12_t(rmhd_t h, cudaEvent_t *ev, double *Us)
     k_stage2<FLAT, T><<<nb, TPB, 0, h->st>>>(K, b.U, PA, b.GA, F0, F1, F2, b.dR1, b.met, b.sig,
                                              PB, b.GB, b.V, J2, defer_of(h, 1), b.stats, Us);
     if (dfr)
-        k_deferred<FLAT, 2, T><<<nbd, TPB, 0, h->st>>>(K, defer_of(h, 1), b.met, b.sig, b.dR1,
+        k_deferred<FLAT, 2, T><<<nbd, TPB_DEFER, 0, h->st>>>(K, defer_of(h, 1), b.met, b.sig, b.dR1,
                                                        PB, b.GB, nullptr, J2, b.V, nullptr,
                                                        b.stats);
     mark(4);
@@ -468,7 +476,7 @@ template <bool FLAT, class T> static void enqueue_final_t(rmhd_t h, cudaEvent_t 
     k_final<FLAT, T><<<nb, TPB, 0, h->st>>>(K, b.V, PB, b.GB, F0, F1, F2, b.met, b.U, PA, b.GA,
                                             defer_of(h, 2), b.stats);
     if (dfr)
-        k_deferred<FLAT, 3, T><<<nbd, TPB, 0, h->st>>>(K, defer_of(h, 2), b.met, b.sig, nullptr,
+        k_deferred<FLAT, 3, T><<<nbd, TPB_DEFER, 0, h->st>>>(K, defer_of(h, 2), b.met, b.sig, nullptr,
                                                        PA, b.GA, nullptr, nullptr, nullptr, b.U,
                                                        b.stats);
     mark(7);
@@ -552,7 +560,7 @@ template <bool FLAT, class T> static void enqueue_general_t(rmhd_t h, ProfMarks 
                                                         Gb[cur], dRi, J, defer_of(h, i), b.stats);
         }
         if (dfr)
-            k_deferred<FLAT, 1, T><<<nbd, TPB, 0, h->st>>>(Ki, defer_of(h, i), b.met, b.sig,
+            k_deferred<FLAT, 1, T><<<nbd, TPB_DEFER, 0, h->st>>>(Ki, defer_of(h, i), b.met, b.sig,
                                                            nullptr, Pb[cur], Gb[cur], dRi, J,
                                                            nullptr, nullptr, b.stats);
         mark(i == 0 ? 0 : 3);
@@ -581,7 +589,7 @@ template <bool FLAT, class T> static void enqueue_general_t(rmhd_t h, ProfMarks 
                                                 b.dRs, b.met, b.U, Pb[0], Gb[0], defer_of(h, s),
                                                 b.stats);
     if (dfr)
-        k_deferred<FLAT, 3, T><<<nbd, TPB, 0, h->st>>>(K, defer_of(h, s), b.met, b.sig, nullptr,
+        k_deferred<FLAT, 3, T><<<nbd, TPB_DEFER, 0, h->st>>>(K, defer_of(h, s), b.met, b.sig, nullptr,
                                                        Pb[0], Gb[0], nullptr, nullptr, nullptr,
                                                        b.U, b.stats);
     mark(5);
