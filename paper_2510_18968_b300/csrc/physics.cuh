@@ -373,13 +373,23 @@ __device__ __forceinline__ double mm3_bits(double a, double b, double c)
     return __longlong_as_double((long long)(sgn | m));
 }
 
+// mm3 on floats for the issue-bound FP32 stencil: the smallest magnitude
+// by two min instructions on |a|, |b|, |c|, given a's sign; zero when the
+// signs differ, which (a ^ b) | (a ^ c) shows in its sign bit.  A zero
+// argument makes the magnitude zero.  Same value as the comparison form
+// for every non-NaN input (a zero result may carry a's sign).
+__device__ __forceinline__ float mm3_f32(float a, float b, float c)
+{
+    const float m = fminf(fabsf(a), fminf(fabsf(b), fabsf(c)));
+    const unsigned ua = __float_as_uint(a), ub = __float_as_uint(b), uc = __float_as_uint(c);
+    const unsigned differ = ((ua ^ ub) | (ua ^ uc)) & 0x80000000u;
+    return differ ? 0.0f : __uint_as_float(__float_as_uint(m) | (ua & 0x80000000u));
+}
+
 template <class T> __device__ __forceinline__ T mm3(T a, T b, T c)
 {
-    if (sizeof(T) == sizeof(float)) {
-        const T mn = fmin(a, fmin(b, c)), mx = fmax(a, fmax(b, c));
-        const bool pos = (a > T(0)) & (b > T(0)) & (c > T(0));
-        const bool neg = (a < T(0)) & (b < T(0)) & (c < T(0));
-        return pos ? mn : (neg ? mx : T(0));
+    if constexpr (std::is_same<T, float>::value) {
+        return mm3_f32(a, b, c);
     }
     if constexpr (std::is_same<T, double>::value) {
         return mm3_bits(a, b, c);
