@@ -195,8 +195,8 @@ FLUX_FIELDS = 15 + 14
 TRAFFIC_PER_CELL = {
     ("stage2_rhs_recovery", "mixed"): (866.735616e6 + 471.683072e6) / 128 ** 3,
     # k_flux_tile (x) and k_flux_walk (y, z), mean of the three launches
-    ("flux_stage2", "mixed"): ((140.807936e6 + 148.820224e6 + 148.728576e6) +
-                               (76.865024e6 + 82.869760e6 + 81.882880e6)) / 3 / 128 ** 3,
+    ("flux_stage2", "mixed"): ((140.807936e6 + 148.899840e6 + 148.886784e6) +
+                               (76.865024e6 + 86.961152e6 + 84.325120e6)) / 3 / 128 ** 3,
     # k_flux_run, mean of the x, y, z launches
     ("flux_stage2", "fp64"): ((989.442560e6 + 372.153600e6 + 303.645184e6) +
                               (514.565888e6 + 203.661056e6 + 202.688768e6)) / 3 / 128 ** 3,

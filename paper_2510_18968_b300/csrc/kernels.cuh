@@ -728,7 +728,7 @@ __device__ __forceinline__ void recon_cell(const T s[3], T &uM, T &uP)
 }
 
 template <bool FLAT, int RC, int D>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(128, 6)
 k_flux_walk(const StepConst K, const float *__restrict__ P, const float *__restrict__ Jc,
             const double *__restrict__ met, const double *__restrict__ sig, float *F)
 {
