@@ -312,6 +312,15 @@ int rmhd_test_rcp64(const double *x, double *out, long long n, void *cuda_stream
 int rmhd_test_mm3(const double *a, const double *b, const double *c, double *out, long long n,
                   void *cuda_stream);
 
+/* Testing entry point (no counterpart in the paper): the three-argument
+ * minmod of the FP32 MC2 limiter as the mixed path's flux kernels compute
+ * it (smallest magnitude by min instructions, signs compared on the bit
+ * patterns), for checking against the definition above on floats: the same
+ * value for every non-NaN input, a zero result possibly carrying a's sign.
+ * Device pointers, n >= 0; runs on the stream. */
+int rmhd_test_mm3f(const float *a, const float *b, const float *c, float *out, long long n,
+                   void *cuda_stream);
+
 const char *rmhd_last_error(rmhd_t h);
 
 /* Free all device memory of the handle (synchronises its stream). */

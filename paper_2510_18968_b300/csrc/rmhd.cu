@@ -1570,6 +1570,27 @@ extern "C" int rmhd_test_mm3(const double *a, const double *b, const double *c, 
     return RMHD_OK;
 }
 
+__global__ void k_test_mm3f(long long n, const float *__restrict__ a,
+                            const float *__restrict__ b, const float *__restrict__ c,
+                            float *out)
+{
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t < n) out[t] = mm3<float>(a[t], b[t], c[t]);
+}
+
+extern "C" int rmhd_test_mm3f(const float *a, const float *b, const float *c, float *out,
+                              long long n, void *cuda_stream)
+{
+    if (n < 0 || (n > 0 && (!a || !b || !c || !out)))
+        return set_err(nullptr, RMHD_EINVAL, "bad arguments");
+    if (n == 0) return RMHD_OK;
+    k_test_mm3f<<<nblk(n), TPB, 0, (cudaStream_t)cuda_stream>>>(n, a, b, c, out);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return set_err(nullptr, RMHD_ECUDA, "launch failed: %s", cudaGetErrorString(e));
+    return RMHD_OK;
+}
+
 extern "C" const char *rmhd_last_error(rmhd_t h) { return h ? h->err : g_noh_err; }
 
 // error text of an entry point without a handle (used by the other source file)

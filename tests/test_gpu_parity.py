@@ -432,3 +432,43 @@ def test_fp64_mc2_minmod_on_bit_patterns_matches_its_definition(torch_cuda):
         want = np.where(pos, np.minimum(a, np.minimum(b, c)),
                         np.where(neg, np.maximum(a, np.maximum(b, c)), 0.0))
     assert np.array_equal(got.view(np.uint64), want.view(np.uint64))
+
+
+def test_fp32_mc2_minmod_matches_its_definition(torch_cuda):
+    """The FP32 MC2 limiter's three-argument minmod as the mixed path's flux
+    kernels compute it (smallest magnitude by min instructions, signs
+    compared on the bit patterns): the value of the floating-point
+    definition (min of three positives, max of three negatives, else 0)
+    for every non-NaN triple, over signed zeros, subnormals, the largest
+    floats, infinities and random same- and mixed-signed triples; a
+    nonzero result is equal bit for bit, a zero one may carry a's sign."""
+    import torch
+    import paper_2510_18968_b300 as R
+    L = R.load()
+    rng = np.random.default_rng(37)
+    f32 = np.float32
+    special = np.array([0.0, -0.0, 1e-45, -1e-45, 1e-40, -1e-40, 1.0, -1.0, 2.5, -2.5,
+                        3.4028235e38, -3.4028235e38, np.inf, -np.inf], dtype=f32)
+    g = np.array(np.meshgrid(special, special, special, indexing="ij")).reshape(3, -1)
+    n = 300000
+    mag = (10.0 ** rng.uniform(-40, 38, (3, n))).astype(f32)
+    sign = np.where(rng.random((3, n)) < 0.5, -1.0, 1.0).astype(f32)
+    same = rng.random(n) < 0.6
+    sign[1:, same] = sign[0, same]
+    r = mag * sign
+    r[:, : n // 10] = np.round(r[:, : n // 10], 0)      # many exact ties and zeros
+    a, b, c = (np.concatenate([g[k], r[k]]).astype(f32) for k in range(3))
+    dev = [torch.tensor(x, device="cuda") for x in (a, b, c)]
+    out = torch.empty_like(dev[0])
+    assert L.rmhd_test_mm3f(dev[0].data_ptr(), dev[1].data_ptr(), dev[2].data_ptr(),
+                            out.data_ptr(), a.size, None) == 0
+    torch.cuda.synchronize()
+    got = out.cpu().numpy()
+    pos = (a > 0) & (b > 0) & (c > 0)
+    neg = (a < 0) & (b < 0) & (c < 0)
+    want = np.where(pos, np.minimum(a, np.minimum(b, c)),
+                    np.where(neg, np.maximum(a, np.maximum(b, c)), f32(0.0))).astype(f32)
+    assert np.array_equal(got, want)                   # values (0.0 == -0.0)
+    nz = want != 0
+    assert np.array_equal(got[nz].view(np.uint32), want[nz].view(np.uint32))
+    assert np.all((got[~nz] == 0) & ((got[~nz].view(np.uint32) & 0x7fffffff) == 0))
