@@ -74,6 +74,8 @@ def lib():
         L.orc_con2prim.argtypes = [P, _DP, i, d, d, d, _DP, _DP, _DP, _DP,
                                    ctypes.POINTER(i)]
         L.orc_con2prim.restype = i
+        L.orc_con2prim_batch.argtypes = [P, ctypes.c_long, _DP, i, d, _DP, _DP, _DP, _DP,
+                                         _DP, _DP, ctypes.c_void_p, ctypes.c_void_p]
         L.orc_rhs.argtypes = [P, _DP, _DP, _DP, _DP, _DP, _DP, _DP, _DP]
         L.orc_prim2con_grid.argtypes = [P, _DP, _DP, _DP, _DP, _DP]
         L.orc_step.argtypes = [P, _DP, _DP, _DP, _DP, _DP, _DP, _DP, d, i,
@@ -191,6 +193,22 @@ def con2prim(params, cons, implicit, c, sigma, guess, alpha=1.0,
                             float(sigma), float(alpha), _ptr(g6), _ptr(guess),
                             _ptr(prim), _ptr(cout), ctypes.byref(it))
     return prim, cout, it.value, st
+
+
+def con2prim_batch(params, cons, implicit, c, sigma, guess, alpha, g6):
+    """orc_con2prim on n points: cons, guess (n, 14), sigma, alpha (n,),
+    g6 (n, 6).  Returns (prim, cons_out, iterations, status)."""
+    P = params if isinstance(params, _Params) else make_params(**params)
+    cons, guess = _arr(cons), _arr(guess)
+    n = cons.shape[0]
+    sigma, alpha, g6 = _arr(sigma, n), _arr(alpha, n), _arr(g6, 6 * n)
+    assert cons.shape == (n, 14) and guess.shape == (n, 14)
+    prim, cout = np.zeros((n, 14)), np.zeros((n, 14))
+    it, st = np.zeros(n, np.int32), np.zeros(n, np.int32)
+    lib().orc_con2prim_batch(ctypes.byref(P), n, _ptr(cons), int(implicit), float(c),
+                             _ptr(sigma), _ptr(alpha), _ptr(g6), _ptr(guess), _ptr(prim),
+                             _ptr(cout), it.ctypes.data, st.ctypes.data)
+    return prim, cout, it, st
 
 
 # ------------------------------------------------------------ grid

@@ -27,12 +27,12 @@
  *  - Stiff term stored algebraically: Dt R(i) = (calE(i) - calE*)/gamma_imex.
  *  - Cell-centred conserved quantities inside the source terms are computed
  *    from the stage primitives.
- *  - Recovery: tolerance, iteration cap, divergence / slow-convergence
- *    stops, a damped 4D Newton fallback on (p, v_i), a second fallback that
- *    brackets the pressure root with the velocity solved at each pressure, a
- *    rerun of the paper iteration to its cap when it was stopped for being
- *    slow and both fallbacks failed, and an atmosphere reset are not given
- *    by the paper.
+ *  - Recovery: the tolerance, the iteration cap, what to do when the
+ *    paper's iteration does not converge and the atmosphere reset are not
+ *    given by the paper.  Here the paper's iteration runs to its cap; if it
+ *    does not converge, the one fallback brackets the pressure root (the
+ *    velocity equations solved at each trial pressure); if that fails, the
+ *    cell is reset to the atmosphere.
  */
 #include "rmhd_oracle.h"
 
@@ -589,24 +589,16 @@ static int p_converged(const c2p_in *in, double dp, double p)
 
 /* Steps (i)-(v): guess (p, v) from the previous stage; (ii) calE from the
  * implicit solve at the current v; (iii) fluid variables; (iv) Newton update
- * of p with f = p(rho,eps) - p, f' = v^2 c_s^2 - 1; (v) repeat.
- * Returns 1 on convergence. */
-/* Gives up (returns 0) when the iterate leaves the physical region, when the
- * change grows three times in a row above the rounding noise (divergence),
- * or, if allow_slow is 0, when after 6 iterations the observed contraction
- * rate predicts more than 24 further iterations (slow convergence: the
- * Newton fallback is cheaper).  *slow_stop tells which. */
+ * of p with f = p(rho,eps) - p, f' = v^2 c_s^2 - 1; (v) repeat until the
+ * changes of p and v are below the tolerance, at most c2p_maxit times.
+ * Returns 1 on convergence, 0 when the cap is reached or an iterate leaves
+ * the physical region (v^2 >= v2max, a non-positive denominator in step
+ * (iii), a non-finite value). */
 static int c2p_paper(const c2p_in *in, double *p_io, double v_io[3],
-                     double cE[3], double *rho_o, int *iters, int allow_slow,
-                     int *slow_stop)
+                     double cE[3], double *rho_o, int *iters)
 {
     double Gam = in->P->gamma_eos;
     double p = *p_io, v[3] = {v_io[0], v_io[1], v_io[2]};
-    double hist[3] = {0, 0, 0};
-    /* energy scale at the guess, for the change measure */
-    double sg0 = in->m->sg;
-    double scale0 = (in->tau + in->D + sg0 * p) / sg0;
-    *slow_stop = 0;
     for (int it = 1; it <= in->P->c2p_maxit; it++) {
         *iters = it;
         if (in->implicit) {
@@ -629,6 +621,7 @@ static int c2p_paper(const c2p_in *in, double *p_io, double v_io[3],
         for (int i = 0; i < 3; i++)
             if (fabs(vn[i] - v[i]) > dv) dv = fabs(vn[i] - v[i]);
         double dp = pn - p;
+        if (!isfinite(pn) || !isfinite(dv)) return 0;
         p = pn;
         for (int i = 0; i < 3; i++) v[i] = vn[i];
         *rho_o = rho;
@@ -637,135 +630,8 @@ static int c2p_paper(const c2p_in *in, double *p_io, double v_io[3],
             for (int i = 0; i < 3; i++) v_io[i] = v[i];
             return 1;
         }
-        /* divergence: three successive growing changes above the noise */
-        double meas = dv + fabs(dp) / scale0;
-        if (!isfinite(meas)) return 0;
-        if (it >= 3 && meas > hist[0] && hist[0] > hist[1] && hist[1] > hist[2]
-            && meas > 1e3 * in->P->c2p_tol)
-            return 0;
-        if (!allow_slow && it >= 6 && meas < hist[0] && hist[0] > 0.0) {
-            double rate = meas / hist[0];
-            if (rate > 0.0 && log(in->P->c2p_tol / meas) / log(rate) > 24.0) {
-                *slow_stop = 1;
-                return 0;
-            }
-        }
-        hist[2] = hist[1]; hist[1] = hist[0]; hist[0] = meas;
     }
     return 0;
-}
-
-/* Residual of the joint recovery system at x = (p, v_1, v_2, v_3):
- *   r_i = v_i (tau + D + sqrt(g) p - EM) - (S_i - eta_ijk calE^j calB^k)
- *   r_p = (Gamma-1) rho eps - p,
- * with calE from the implicit solve at v; both scaled by the energy scale. */
-static int c2p_resid(const c2p_in *in, const double x[4], double r[4],
-                     double cE[3], double *rho_o, double v_o[3])
-{
-    double Gam = in->P->gamma_eos;
-    double sg = in->m->sg;
-    double p = x[0];
-    double vl[3] = {x[1], x[2], x[3]}, v[3];
-    raise(in->m, vl, v);
-    double v2 = dot3(v, vl);
-    if (!(p > 0.0) || !(v2 < in->v2max)) return 0;
-    double W = 1.0 / sqrt(1.0 - v2);
-    if (in->implicit) {
-        for (int i = 0; i < 3; i++) cE[i] = in->cE0[i];
-        if (!implicit_E_nr(in->m, in->cE0, in->cB, v, W, in->sigma, in->c, cE))
-            return 0;
-    } else {
-        for (int i = 0; i < 3; i++) cE[i] = in->cE0[i];
-    }
-    double cEl[3], cBl[3];
-    lower(in->m, cE, cEl);
-    lower(in->m, in->cB, cBl);
-    double EM = (dot3(cE, cEl) + dot3(in->cB, cBl)) / (2.0 * sg);
-    double den = in->tau + in->D + sg * p - EM;
-    double scale = in->tau + in->D + sg * p;
-    for (int i = 0; i < 3; i++) {
-        double cross = 0.0;
-        for (int j = 0; j < 3; j++)
-            for (int k = 0; k < 3; k++)
-                cross += levi(i, j, k) * cE[j] * in->cB[k];
-        r[1 + i] = (vl[i] * den - (in->Sl[i] - cross)) / scale;
-    }
-    double rho = in->D / (sg * W);
-    double eps = (in->tau - in->D * (W - 1.0) - sg * p * (W * W - 1.0) - EM)
-                 / (in->D * W);
-    r[0] = ((Gam - 1.0) * rho * eps - p) * sg / scale;
-    *rho_o = rho;
-    for (int i = 0; i < 3; i++) v_o[i] = v[i];
-    return 1;
-}
-
-static double norm4(const double r[4])
-{
-    return sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2] + r[3] * r[3]);
-}
-
-/* Fallback: damped Newton on (p, v_i) with a forward-difference Jacobian. */
-static int c2p_newton4(const c2p_in *in, double *p_io, double v_io[3],
-                       double cE[3], double *rho_o, int *iters)
-{
-    double x[4], r[4], vdummy[3], rho;
-    double vl[3];
-    lower(in->m, v_io, vl);
-    x[0] = *p_io;
-    for (int i = 0; i < 3; i++) x[1 + i] = vl[i];
-    if (!c2p_resid(in, x, r, cE, &rho, vdummy)) {
-        x[1] = x[2] = x[3] = 0.0;
-        if (!(x[0] > 0.0)) x[0] = in->P->K_atmo * pow(in->P->rho_atmo, in->P->gamma_eos);
-        if (!c2p_resid(in, x, r, cE, &rho, vdummy)) return 0;
-    }
-    for (int it = 1; it <= 50; it++) {
-        *iters = it;
-        double J[16];
-        for (int col = 0; col < 4; col++) {
-            double xh[4] = {x[0], x[1], x[2], x[3]}, rh[4], ceh[3], rhoh, vh[3];
-            double h = col == 0 ? 1e-7 * x[0] : 1e-7;
-            xh[col] += h;
-            if (!c2p_resid(in, xh, rh, ceh, &rhoh, vh)) {
-                h = -h;
-                xh[col] = x[col] + h;
-                if (!c2p_resid(in, xh, rh, ceh, &rhoh, vh)) return 0;
-            }
-            for (int row = 0; row < 4; row++) J[row * 4 + col] = (rh[row] - r[row]) / h;
-        }
-        double rhs[4] = {-r[0], -r[1], -r[2], -r[3]}, dx[4];
-        if (!solve_dense(4, J, rhs, dx)) return 0;
-        double lam = 1.0, n0 = norm4(r);
-        double xt[4], rt[4], cet[3], rhot, vt[3];
-        int accepted = 0;
-        for (int ls = 0; ls < 40; ls++) {
-            for (int i = 0; i < 4; i++) xt[i] = x[i] + lam * dx[i];
-            if (c2p_resid(in, xt, rt, cet, &rhot, vt) && norm4(rt) < n0) {
-                accepted = 1;
-                break;
-            }
-            lam *= 0.5;
-        }
-        if (!accepted) {
-            /* no decrease possible: at the rounding floor if the step is tiny */
-            double sg = in->m->sg;
-            double dvm = fmax(fabs(dx[1]), fmax(fabs(dx[2]), fabs(dx[3])));
-            if (fabs(dx[0]) * sg <= in->P->c2p_tol * (in->tau + in->D + sg * x[0])
-                && dvm <= in->P->c2p_tol)
-                break;
-            return 0;
-        }
-        double stepp = lam * dx[0];
-        double stepv = fmax(fabs(lam * dx[1]), fmax(fabs(lam * dx[2]), fabs(lam * dx[3])));
-        for (int i = 0; i < 4; i++) { x[i] = xt[i]; r[i] = rt[i]; }
-        if (p_converged(in, stepp, x[0]) && stepv <= in->P->c2p_tol) break;
-        if (it == 50) return 0;
-    }
-    double v[3];
-    if (!c2p_resid(in, x, r, cE, &rho, v)) return 0;
-    *p_io = x[0];
-    for (int i = 0; i < 3; i++) v_io[i] = v[i];
-    *rho_o = rho;
-    return 1;
 }
 
 /* Residual of the velocity equations at fixed pressure p:
@@ -859,9 +725,9 @@ static int pressure_fn(const c2p_in *in, double p, double vl[3], double *f)
     return 1;
 }
 
-/* Second fallback: bracket the pressure root of f(p) (doubling or halving
- * from the guess), then the Illinois variant of regula falsi; each f(p)
- * solves the velocity equations at p. */
+/* Fallback, defined by the root itself: bracket the pressure root of f(p)
+ * (doubling or halving from the guess), then the Illinois variant of regula
+ * falsi; each f(p) solves the velocity equations at p. */
 static int c2p_bracket(const c2p_in *in, double *p_io, double v_io[3], double cE[3],
                        double *rho_o, int *iters)
 {
@@ -926,9 +792,11 @@ static int c2p_bracket(const c2p_in *in, double *p_io, double v_io[3], double cE
     return 0;
 }
 
-/* Returns status: 0 converged (paper iteration), 1 converged (Newton
- * fallback), 4 converged (pressure-bracket fallback), 2 failed ->
- * atmosphere, 3 converged but rho < rho_atmo -> atmosphere. */
+/* Returns status: 0 converged (paper iteration), 4 converged (pressure
+ * bracket), 2 failed -> atmosphere, 3 converged but rho < rho_atmo ->
+ * atmosphere.  (Status 1 is not produced here.)  The recovery is: the
+ * paper's iteration (steps i-v) to its cap; if it does not converge, the
+ * pressure bracket from the same guess; if that fails too, the atmosphere. */
 int orc_con2prim(const orc_params *P, const double cons_in[14], int implicit,
                  double c, double sigma, double alpha, const double g6[6],
                  const double guess[14], double prim[14], double cons_out[14],
@@ -954,13 +822,13 @@ int orc_con2prim(const orc_params *P, const double cons_in[14], int implicit,
     double p = guess[P_P], v[3] = {guess[P_VX], guess[P_VY], guess[P_VZ]};
     double cE[3] = {in.cE0[0], in.cE0[1], in.cE0[2]};
     double rho = 0.0;
-    int it1 = 0, it2 = 0, status, slow = 0;
+    int it1 = 0, it2 = 0, status;
     /* atmosphere without iterating: rho = D / (W sqrt(gamma)) <= D / sqrt(gamma)
      * for every velocity, so a density D / sqrt(gamma) below the floor puts
      * every root below it (reading of the atmosphere treatment, Sec. IV.E) */
     if (!(in.D / m.sg >= P->rho_atmo * (1.0 + P->atmo_tol))) {
         status = 3;
-    } else if (c2p_paper(&in, &p, v, cE, &rho, &it1, 0, &slow)) {
+    } else if (c2p_paper(&in, &p, v, cE, &rho, &it1)) {
         status = 0;
     } else {
         p = guess[P_P];
@@ -968,33 +836,11 @@ int orc_con2prim(const orc_params *P, const double cons_in[14], int implicit,
             v[i] = guess[P_VX + i];
             cE[i] = in.cE0[i];
         }
-        status = c2p_newton4(&in, &p, v, cE, &rho, &it2) ? 1 : 2;
-        if (status == 2) {
-            int it3 = 0;
-            p = guess[P_P];
-            for (int i = 0; i < 3; i++) {
-                v[i] = guess[P_VX + i];
-                cE[i] = in.cE0[i];
-            }
-            if (c2p_bracket(&in, &p, v, cE, &rho, &it3)) status = 4;
-            it2 += it3;
-        }
-        if (status == 2 && slow) {
-            /* both fallbacks failed on a state the paper iteration was
-             * converging on, slowly: let it run to its cap */
-            int it4 = 0, dummy;
-            p = guess[P_P];
-            for (int i = 0; i < 3; i++) {
-                v[i] = guess[P_VX + i];
-                cE[i] = in.cE0[i];
-            }
-            if (c2p_paper(&in, &p, v, cE, &rho, &it4, 1, &dummy)) status = 0;
-            it2 += it4;
-        }
+        status = c2p_bracket(&in, &p, v, cE, &rho, &it2) ? 4 : 2;
     }
     *iters = it1 + it2;
     /* atmosphere floor: rho below rho_atmo (1 + atmo_tol) is reset */
-    int ok = status == 0 || status == 1 || status == 4;
+    int ok = status == 0 || status == 4;
     if (ok && !(rho >= P->rho_atmo * (1.0 + P->atmo_tol))) status = 3;
     int reset = status == 2 || status == 3;
 
@@ -1028,6 +874,17 @@ int orc_con2prim(const orc_params *P, const double cons_in[14], int implicit,
         for (int i = 0; i < 3; i++) cons_out[C_SX + i] = full[C_SX + i];
     }
     return status;
+}
+
+void orc_con2prim_batch(const orc_params *P, long n, const double *cons, int implicit,
+                        double c, const double *sigma, const double *alpha,
+                        const double *g6, const double *guess, double *prim,
+                        double *cons_out, int *iters, int *status)
+{
+    for (long i = 0; i < n; i++)
+        status[i] = orc_con2prim(P, cons + 14 * i, implicit, c, sigma[i], alpha[i],
+                                 g6 + 6 * i, guess + 14 * i, prim + 14 * i,
+                                 cons_out + 14 * i, &iters[i]);
 }
 
 /* --------------------------- grid operations --------------------------- */

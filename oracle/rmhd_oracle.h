@@ -68,6 +68,12 @@ int  orc_con2prim(const orc_params *P, const double cons_in[14], int implicit,
                   double c, double sigma, double alpha, const double g6[6],
                   const double guess[14], double prim[14], double cons_out[14],
                   int *iters);
+/* orc_con2prim on n independent points (a plain loop), arrays point-major
+ * with stride 14 (cons, guess, prim, cons_out) or 6 (g6) per point */
+void orc_con2prim_batch(const orc_params *P, long n, const double *cons, int implicit,
+                        double c, const double *sigma, const double *alpha,
+                        const double *g6, const double *guess, double *prim,
+                        double *cons_out, int *iters, int *status);
 
 /* whole-grid operations */
 void orc_rhs(const orc_params *P, const double *alpha, const double *beta,

@@ -124,3 +124,70 @@ def random_flat_prim(rng, gamma_eos=2.0, vmax=0.8, scale=1.0):
     prim[8:11] = scale * rng.standard_normal(3)
     prim[11:14] = rng.standard_normal(3) * 0.3
     return prim
+
+
+# ------------------------------------------- many points at once (vectorised)
+
+def random_prims(rng, n, gamma_eos=2.0, vmax=0.8, scale=1.0):
+    """n random flat-space primitive states (rows), as random_flat_prim."""
+    prim = np.zeros((n, 14))
+    prim[:, 0] = rng.uniform(0.1, 2.0, n)
+    prim[:, 1] = rng.uniform(0.05, 2.0, n)
+    d = rng.standard_normal((n, 3))
+    prim[:, 2:5] = d / np.linalg.norm(d, axis=1)[:, None] * rng.uniform(0, vmax, n)[:, None]
+    prim[:, 5:8] = scale * rng.standard_normal((n, 3)) * 0.5
+    prim[:, 8:11] = scale * rng.standard_normal((n, 3))
+    prim[:, 11:14] = rng.standard_normal((n, 3)) * 0.3
+    return prim
+
+
+def textbook_cons_many(prim, gamma_eos):
+    """Flat-space conserved vectors of n states (rows): D = rho W,
+    S = (e + p) W^2 v + E x B, tau = (e + p) W^2 - p + (E^2 + B^2)/2 - D."""
+    rho, p = prim[:, 0], prim[:, 1]
+    v, E, B = prim[:, 2:5], prim[:, 5:8], prim[:, 8:11]
+    W = 1.0 / np.sqrt(1.0 - np.einsum("ni,ni->n", v, v))
+    w = (rho + p / (gamma_eos - 1.0) + p) * W * W
+    U = np.zeros_like(prim)
+    U[:, 0] = rho * W
+    U[:, 1:4] = w[:, None] * v + np.cross(E, B)
+    U[:, 4] = w - p + 0.5 * (np.einsum("ni,ni->n", E, E) + np.einsum("ni,ni->n", B, B)) - U[:, 0]
+    U[:, 5:8] = B
+    U[:, 8:11] = E
+    U[:, 11] = prim[:, 12]
+    U[:, 12] = prim[:, 11]
+    U[:, 13] = prim[:, 13]
+    return U
+
+
+def random_A_many(rng, n, strength=0.4):
+    A = np.eye(3) + strength * rng.uniform(-1, 1, (n, 3, 3))
+    bad = np.linalg.det(A) <= 0.3
+    while bad.any():
+        A[bad] = np.eye(3) + strength * rng.uniform(-1, 1, (int(bad.sum()), 3, 3))
+        bad = np.linalg.det(A) <= 0.3
+    return A
+
+
+def metric_of_many(A):
+    Ai = np.linalg.inv(A)
+    g = np.einsum("nki,nkj->nij", Ai, Ai)
+    g6 = np.stack([g[:, 0, 0], g[:, 0, 1], g[:, 0, 2], g[:, 1, 1], g[:, 1, 2], g[:, 2, 2]], 1)
+    return g6, 1.0 / np.linalg.det(A)
+
+
+def transform_prim_many(prim, A):
+    out = prim.copy()
+    for s in (slice(2, 5), slice(5, 8), slice(8, 11)):
+        out[:, s] = np.einsum("nij,nj->ni", A, prim[:, s])
+    return out
+
+
+def transform_cons_many(U, A):
+    J = np.linalg.det(A)
+    Ai = np.linalg.inv(A)
+    out = U / J[:, None]
+    out[:, 1:4] = np.einsum("nji,nj->ni", Ai, U[:, 1:4]) / J[:, None]
+    out[:, 5:8] = np.einsum("nij,nj->ni", A, U[:, 5:8]) / J[:, None]
+    out[:, 8:11] = np.einsum("nij,nj->ni", A, U[:, 8:11]) / J[:, None]
+    return out

@@ -1,7 +1,8 @@
 """Write tests/golden/recovery_hard_cases.npz: stage-1 recovery inputs on
-which the paper's iteration and the 4D Newton fallback both fail although a
-root exists (magnetised blast front of the 256^2 cylindrical explosion, step
-17, sigma = 1e3).  Calls only the oracle and the input generators."""
+which the paper's iteration fails although a root exists (magnetised blast
+front of the 256^2 cylindrical explosion, step 17, sigma = 1e3); the stored
+set was picked where a damped 4D Newton on (p, v_i) stalls too.  Calls only
+the oracle and the input generators."""
 import os
 import sys
 
@@ -26,7 +27,7 @@ def main():
     gam = 1.0 - 1.0 / np.sqrt(2.0)
     c_imp = gam * wl.dt
     # cells whose stage-1 recovery needs the pressure-bracket fallback
-    # (status 4): the paper iteration and the 4D Newton both fail there
+    # (status 4): the paper iteration fails there
     st = np.zeros(c.shape[1], int)
     its = np.zeros(c.shape[1], int)
     for i in range(c.shape[1]):

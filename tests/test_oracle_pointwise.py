@@ -284,49 +284,6 @@ def test_con2prim_round_trip_implicit(cs):
     assert fails == 0
 
 
-def test_con2prim_root_is_the_only_bracketed_root():
-    """Brute force: scan p over 6 decades around the answer, solve the (v,
-    calE) subsystem at each p with scipy, find every sign change of
-    f(p) = (Gamma-1) rho eps - p; exactly one root, equal to the recovery's."""
-    from scipy.optimize import brentq, fsolve
-    rng = np.random.default_rng(23)
-    gam_eos = 2.0
-    P = oracle.make_params(gamma_eos=gam_eos, rho_atmo=1e-14)
-    for trial in range(3):
-        cs = [0.5, 50.0, 5e3][trial]
-        prim, A, alpha, g6, Ux, Ustar = _manufactured(rng, gam_eos, cs, curved=False)
-        c = 0.25
-        sigma = cs / c
-        out, _, _, st = oracle.con2prim(P, Ustar, 1, c, sigma, prim, 1.0, g6)
-        assert st in (0, 1, 4)
-        D, S, tau, cB, E0 = Ustar[0], Ustar[1:4], Ustar[4], Ustar[5:8], Ustar[8:11]
-
-        def fluid(p, v):
-            E = oracle.implicit_E(E0, cB, v, sigma=sigma, c=c)
-            EM = 0.5 * (E @ E + cB @ cB)
-            return E, EM, tau + D + p - EM
-
-        def f_of_p(p):
-            def g(v):
-                if v @ v >= 1.0:
-                    return np.full(3, 1e3)
-                E, EM, den = fluid(p, v)
-                return v * den - (S - np.cross(E, cB))
-            v = fsolve(g, out[2:5], xtol=1e-14)
-            W = 1.0 / np.sqrt(1.0 - v @ v)
-            E, EM, den = fluid(p, v)
-            rho = D / W
-            eps = (tau - D * (W - 1) - p * (W * W - 1) - EM) / (D * W)
-            return (gam_eos - 1.0) * rho * eps - p
-
-        ps = out[1] * np.logspace(-3, 3, 120)   # grid avoids the root itself
-        fs_ = np.array([f_of_p(p) for p in ps])
-        sc = np.where(np.sign(fs_[:-1]) != np.sign(fs_[1:]))[0]
-        assert len(sc) == 1, (trial, sc)
-        root = brentq(f_of_p, ps[sc[0]], ps[sc[0] + 1], xtol=1e-15 * out[1], rtol=1e-15)
-        assert abs(root - out[1]) < 1e-9 * out[1]
-
-
 def test_con2prim_resets_unphysical_state_to_atmosphere():
     """A state with tau too small for its momentum has no root: the recovery
     reports failure and returns the atmosphere (rho_atmo, v = 0,
@@ -353,7 +310,7 @@ def _hard_cases():
 def test_pressure_bracket_recovers_states_where_newton_stalls():
     """Stage inputs from the magnetised blast front (tests/golden, written by
     make_recovery_cases.py from the oracle) on which the paper iteration and
-    the 4D Newton fail: the bracket finds a root, checked independently by
+    the kernel's 4D Newton fail: the bracket finds a root, checked independently by
     re-forming D, S_i, tau from the returned primitives and re-solving the
     implicit field (Eq. 3D_NR) at the returned velocity."""
     d = _hard_cases()
