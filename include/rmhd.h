@@ -177,6 +177,19 @@ int rmhd_step_profiled(rmhd_t h, double dt, int nsteps, double ms[RMHD_NPROF]);
 int rmhd_get_prims(rmhd_t h, double *prims, int on_device);
 int rmhd_get_cons(rmhd_t h, double *cons, int on_device);
 
+/* Checkpoint restore from the conserved variables alone (Sec. II.D: the
+ * evolved vector U = (D, S_i, tau, calB^i, calE^i, Phi, Psi, calQ), densitised,
+ * field order of rmhd_get_cons).  The primitives are recovered from them with
+ * the recovery of Sec. III.B at fixed calE (as after the last stage of a
+ * step); the guess (p, v^i) is the handle's current primitives when it has a
+ * state, otherwise v = 0 and p = (Gamma-1) max(tau/sqrt(gamma) - (E^2+B^2)/2, 0)
+ * (the energy density at rest; the atmosphere pressure when that is zero).
+ * A cell whose recovery fails is reset to the atmosphere as in a step (its
+ * D, S_i, tau replaced) and counted (rmhd_get_stats).  Synchronises.
+ * Errors: RMHD_EINVAL if a value is not finite or D <= 0 (state unchanged);
+ * RMHD_EC2P (soft) if some cells were reset. */
+int rmhd_set_cons(rmhd_t h, const double *cons, int on_device);
+
 /* Checkpoint restore: set conserved cons[14][N] together with the primitives
  * that were current with them (the recovery guess), bit-exact round trip with
  * rmhd_get_cons / rmhd_get_prims.  Errors: RMHD_EINVAL on non-finite values. */
@@ -207,7 +220,10 @@ int rmhd_rhs(rmhd_t h, const double *prims, const double *J, double *rhs,
  * reset), iters[npts], status[npts] (0 paper iteration, 1 Newton fallback,
  * 4 pressure-bracket fallback, 2 failed -> atmosphere, 3 floor ->
  * atmosphere).  p supplies gamma_eos,
- * rho_atmo, K_atmo, atmo_tol and the c2p_* options.  Runs on stream. */
+ * rho_atmo, K_atmo, atmo_tol and the c2p_* options.  Runs on stream.
+ * Errors: RMHD_EINVAL for npts < 0, a NULL array, or gamma_eos <= 1,
+ * c2p_tol <= 0, c2p_maxit < 1, c2p_wmax <= 1, rho_atmo <= 0, K_atmo < 0,
+ * atmo_tol < 0. */
 int rmhd_con2prim_points(const rmhd_params *p, int npts, const double *cons,
                          const double *guess, const double *alpha,
                          const double *gamma, const double *sigma, int implicit,
@@ -233,15 +249,15 @@ int rmhd_con2prim_points(const rmhd_params *p, int npts, const double *cons,
  * make that first call before any stream capture.  Calls share the one list
  * and it keeps the previous call's contents (the counter is cleared at the
  * start of each call): calls that overlap on the GPU race, so serialise
- * them.  Calls no cudaMalloc / cudaFree.  Errors: rmhd_last_error(NULL). */
+ * them.  Calls no cudaMalloc / cudaFree.  After a device reset the next call
+ * looks the array up again in the new context.  Parameter checks are those
+ * of rmhd_con2prim_points.  Errors: rmhd_last_error(NULL). */
 int rmhd_con2prim_points_noalloc(const rmhd_params *p, int npts, const double *cons,
                                  const double *guess, const double *alpha,
                                  const double *gamma, const double *sigma, int implicit,
                                  double c, double *prim, double *cons_out, int *iters,
                                  int *status, void *cuda_stream);
 
-/* Text of the last error on this handle (never NULL; "" if none).  With
- * h == NULL: the last error of a call that had no handle. */
 /* ---------------------------------------------------------------- adjoint
  * Discrete adjoint of the FP64 step (the paper has none; it differentiates
  * exactly the step rmhd_step takes: Table imex / Eq. IMEX3 for the stages,
@@ -321,6 +337,10 @@ int rmhd_test_mm3(const double *a, const double *b, const double *c, double *out
 int rmhd_test_mm3f(const float *a, const float *b, const float *c, float *out, long long n,
                    void *cuda_stream);
 
+/* Text of the last error on this handle (never NULL; "" if none).  With
+ * h == NULL: the last error, in the calling thread, of a call that had no
+ * handle (rmhd_create, rmhd_con2prim_points, rmhd_con2prim_points_noalloc,
+ * ...). */
 const char *rmhd_last_error(rmhd_t h);
 
 /* Free all device memory of the handle (synchronises its stream). */

@@ -1,8 +1,11 @@
 """Build the FP64 CPU oracle (test infrastructure) into oracle/_build/.
 
-The oracle is plain C compiled with -ffp-contract=off so that the compiler
-never fuses a multiply and an add: every rounding happens where the source
-says.  It is independent of the CUDA library and is only loaded by the tests,
+The oracle is plain C compiled with -O3 -ffp-contract=off so that the
+compiler never fuses a multiply and an add: every rounding happens where the
+source says.  No -march=native: the library is built on one machine and
+loaded on another (the GPU machine's host), whose CPU may lack instructions of
+the build machine's; -O3 alone changes no rounding (no reassociation without
+-ffast-math).  It is independent of the CUDA library and is only loaded by the tests,
 the smoke check and the benchmark's CPU-baseline leg.
 """
 import os
@@ -21,7 +24,7 @@ def build(force: bool = False) -> str:
             and os.path.getmtime(LIB) >= max(os.path.getmtime(SRC),
                                              os.path.getmtime(os.path.join(HERE, "rmhd_oracle.h")))):
         return LIB
-    cmd = ["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fno-fast-math",
+    cmd = ["gcc", "-O3", "-std=c99", "-ffp-contract=off", "-fno-fast-math",
            "-fPIC", "-shared", "-Wall", "-Wextra", "-o", LIB, SRC, "-lm"]
     subprocess.check_call(cmd)
     return LIB

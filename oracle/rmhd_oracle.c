@@ -704,13 +704,19 @@ static int solve_velocity(const c2p_in *in, double p, double vl[3])
         for (int i = 0; i < 3; i++) { vl[i] = vt[i]; g[i] = gt[i]; }
         if (step <= 1e-15) break;
     }
-    return 1;
+    /* solved only if the equations hold (scaled residual at rounding level) */
+    return norm3(g) < 1e-13;
 }
 
-/* f(p) = (Gamma-1) rho eps - p (scaled) with the velocity solved at p */
+/* f(p) = (Gamma-1) rho eps - p (scaled) with the velocity solved at p
+ * (Newton from vl; if that does not converge, from rest) */
 static int pressure_fn(const c2p_in *in, double p, double vl[3], double *f)
 {
-    if (!(p > 0.0) || !solve_velocity(in, p, vl)) return 0;
+    if (!(p > 0.0)) return 0;
+    if (!solve_velocity(in, p, vl)) {
+        vl[0] = vl[1] = vl[2] = 0.0;
+        if (!solve_velocity(in, p, vl)) return 0;
+    }
     double cE[3], v[3], g[3];
     vel_resid(in, p, vl, g, cE);
     raise(in->m, vl, v);
@@ -725,19 +731,30 @@ static int pressure_fn(const c2p_in *in, double p, double vl[3], double *f)
     return 1;
 }
 
-/* Fallback, defined by the root itself: bracket the pressure root of f(p)
- * (doubling or halving from the guess), then the Illinois variant of regula
- * falsi; each f(p) solves the velocity equations at p. */
+/* Fallback, defined by the root itself: the pressure root of f(p), the
+ * velocity equations solved at every trial pressure.  f is defined only
+ * above the lowest pressure at which those equations have a solution with
+ * v^2 < 1 (a lower pressure leaves too little enthalpy for the momentum),
+ * so a pressure where the solve fails lies below the root.  Search: from
+ * the guess, double the pressure while f is undefined or positive, halve
+ * it while f is negative; a halving that lands where f is undefined is
+ * replaced by geometric bisection between that pressure and the last one
+ * where f was defined.  Once f changes sign, the Illinois variant of regula
+ * falsi on the bracket. */
 static int c2p_bracket(const c2p_in *in, double *p_io, double v_io[3], double cE[3],
                        double *rho_o, int *iters)
 {
-    double vl[3], f0;
-    lower(in->m, v_io, vl);
+    double vl[3], v0[3], f0 = 0.0;
+    lower(in->m, v_io, v0);
+    for (int i = 0; i < 3; i++) vl[i] = v0[i];
     double p0 = *p_io > 0.0 ? *p_io : in->P->K_atmo * pow(in->P->rho_atmo, in->P->gamma_eos);
-    int n = 0;
-    if (!pressure_fn(in, p0, vl, &f0)) {
-        vl[0] = vl[1] = vl[2] = 0.0;
-        if (!pressure_fn(in, p0, vl, &f0)) return 0;
+    int n = 0, ok = pressure_fn(in, p0, vl, &f0);
+    /* f undefined at the guess: the root is above */
+    while (!ok) {
+        if (++n > 60) return 0;
+        p0 *= 2.0;
+        for (int i = 0; i < 3; i++) vl[i] = v0[i];
+        ok = pressure_fn(in, p0, vl, &f0);
     }
     double lo = p0, hi = p0, flo = f0, fhi = f0;
     double vlo[3] = {vl[0], vl[1], vl[2]}, vhi[3] = {vl[0], vl[1], vl[2]};
@@ -750,12 +767,24 @@ static int c2p_bracket(const c2p_in *in, double *p_io, double v_io[3], double cE
             if (!pressure_fn(in, hi, vhi, &fhi)) return 0;
         }
     } else {
+        /* hi: f < 0 and defined; und: a pressure below where f is undefined */
+        double und = 0.0;
         while (flo < 0.0) {
-            if (++n > 60) return 0;
-            hi = lo; fhi = flo;
-            for (int i = 0; i < 3; i++) vhi[i] = vlo[i];
-            lo = 0.5 * lo;
-            if (!pressure_fn(in, lo, vlo, &flo)) return 0;
+            if (++n > 120) return 0;
+            double pt = und > 0.0 ? sqrt(und * hi) : 0.5 * hi;
+            double vt[3] = {vhi[0], vhi[1], vhi[2]}, ft;
+            if (!pressure_fn(in, pt, vt, &ft)) {
+                und = pt;
+                if (und > hi * (1.0 - 1e-15)) return 0;
+                continue;
+            }
+            if (ft < 0.0) {
+                hi = pt; fhi = ft;
+                for (int i = 0; i < 3; i++) vhi[i] = vt[i];
+            } else {
+                lo = pt; flo = ft;
+                for (int i = 0; i < 3; i++) vlo[i] = vt[i];
+            }
         }
     }
     int side = 0;

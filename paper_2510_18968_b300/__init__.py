@@ -59,7 +59,7 @@ class Params(ctypes.Structure):
 
 EXPORTS = ("rmhd_default_params", "rmhd_create", "rmhd_set_metric", "rmhd_set_sigma",
            "rmhd_set_prims", "rmhd_step", "rmhd_get_prims", "rmhd_get_cons",
-           "rmhd_set_state", "rmhd_get_stats", "rmhd_step_profiled", "rmhd_rhs", "rmhd_con2prim_points",
+           "rmhd_set_state", "rmhd_set_cons", "rmhd_get_stats", "rmhd_step_profiled", "rmhd_rhs", "rmhd_con2prim_points",
            "rmhd_con2prim_points_noalloc", "rmhd_set_sigma0", "rmhd_adjoint_forward",
            "rmhd_adjoint_backward", "rmhd_test_rcp64", "rmhd_test_mm3", "rmhd_test_mm3f",
            "rmhd_last_error", "rmhd_destroy")
@@ -90,6 +90,7 @@ def load(build_if_missing=True):
     L.rmhd_get_prims.argtypes = [vp, vp, i]
     L.rmhd_get_cons.argtypes = [vp, vp, i]
     L.rmhd_set_state.argtypes = [vp, vp, vp, i]
+    L.rmhd_set_cons.argtypes = [vp, vp, i]
     L.rmhd_get_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
     L.rmhd_step_profiled.argtypes = [vp, d, i, ctypes.POINTER(ctypes.c_double)]
     L.rmhd_rhs.argtypes = [vp, vp, vp, vp, i]
@@ -225,6 +226,13 @@ class Solver:
     def set_prims(self, prim):
         p, d = _ptr(prim, 14 * self.N)
         return self._check(self.L.rmhd_set_prims(self.h, p, d))
+
+    def set_cons(self, cons):
+        """Restore from the conserved variables alone (primitives recovered
+        on the device); returns RMHD_EC2P (soft) when cells were reset to the
+        atmosphere."""
+        pc, d = _ptr(cons, 14 * self.N)
+        return self._check(self.L.rmhd_set_cons(self.h, pc, d), soft_ok=(RMHD_EC2P,))
 
     def set_state(self, cons, prim):
         pc, d = _ptr(cons, 14 * self.N)

@@ -233,7 +233,7 @@ __device__ double stage_adjoint(const StepConst &K, const Met<double> &m, const 
 // Fixed-order sum of the per-cell values v (padded layout) over the
 // interior, one block: each thread sums a strided subset in order, then a
 // shared-memory tree.  *out = the sum.
-__global__ void __launch_bounds__(1024)
+static __global__ void __launch_bounds__(1024)
 k_adj_sum(const StepConst K, const double *__restrict__ v, double *out)
 {
     __shared__ double part[1024];
@@ -759,7 +759,7 @@ k_adj_stage1(const StepConst K, const double *__restrict__ U, const double *__re
 
 // cells whose last recovery reset them to the atmosphere: U^{n+1} holds
 // fixed D, S_i, tau there, so no derivative flows back through those rows
-__global__ void __launch_bounds__(128)
+static __global__ void __launch_bounds__(128)
 k_adj_reset_mask(const StepConst K, const double *__restrict__ Pnext, double *lamU)
 {
     const Grid &G = K.G;

@@ -219,7 +219,7 @@ __global__ void k_scatter(const StepConst K, const double *__restrict__ src, T *
     for (int f = 0; f < nf; f++) dst[f * K.G.S + c] = (T)src[f * K.G.N + t];
 }
 
-__global__ void k_gather(const StepConst K, const double *__restrict__ src, double *dst, int nf)
+static __global__ void k_gather(const StepConst K, const double *__restrict__ src, double *dst, int nf)
 {
     long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (t >= K.G.N) return;
@@ -361,7 +361,7 @@ __global__ void k_prim2con(const StepConst K, const double *__restrict__ src,
 }
 
 // metric sanity: alpha > 0, gamma_ij positive definite (leading minors)
-__global__ void k_check_metric(const StepConst K, const double *__restrict__ met, int *bad)
+static __global__ void k_check_metric(const StepConst K, const double *__restrict__ met, int *bad)
 {
     long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (t >= K.G.N) return;
@@ -379,7 +379,7 @@ __global__ void k_check_metric(const StepConst K, const double *__restrict__ met
     if (!ok) atomicOr(bad, 1);
 }
 
-__global__ void k_check_finite(long long n, const double *__restrict__ a, int *bad)
+static __global__ void k_check_finite(long long n, const double *__restrict__ a, int *bad)
 {
     long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (t < n && !isfinite(a[t])) atomicOr(bad, 1);
@@ -1480,6 +1480,56 @@ k_final(const StepConst K, const double *__restrict__ Vb, const T *__restrict__ 
     record_stats(stats, active, status, deferred ? 0 : iters, !deferred);
 }
 
+// Primitives of a conserved state given alone (checkpoint restore): the
+// recovery with calE fixed (Sec. III.B) at every interior cell, the guess
+// (p, v^i) from Gin when given (the handle's current primitives), else
+// v = 0 and the pressure of the state's energy density at rest,
+// p = (Gamma-1) max(tau / sqrt(gamma) - (E^2 + B^2)/2, 0) (the atmosphere
+// pressure if that is zero).  A cell whose recovery fails is reset to the
+// atmosphere as in a step (its D, S_i, tau replaced).  One thread per cell,
+// the whole recovery inline.
+template <bool FLAT, class T>
+__global__ void __launch_bounds__(128)
+k_recover_cons(const StepConst K, double *U, const double *__restrict__ met,
+               const double *Gin, T *P, double *Gs, unsigned long long *stats)
+{
+    const Grid &G = K.G;
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const bool active = t < G.N;
+    int status = 0, iters = 0;
+    if (active) {
+        int i, j, k;
+        interior_coords(G, t, i, j, k);
+        const long long c = cell_at(G, i, j, k);
+        const long long S = G.S;
+        Met<double> m;
+        load_metric<FLAT>(met, S, c, m);
+        double u[NCO];
+        for (int f = 0; f < NCO; f++) u[f] = U[f * S + c];
+        RecIn in;
+        load_rec_in(u, in);
+        double gp, gv[3] = {0.0, 0.0, 0.0};
+        if (Gin) {
+            gp = Gin[c];
+            for (int a = 0; a < 3; a++) gv[a] = Gin[(1 + a) * S + c];
+        } else {
+            double El[3], Bl[3];
+            lower<double, FLAT>(m, in.cE0, El);
+            lower<double, FLAT>(m, in.cB, Bl);
+            const double isg = FLAT ? 1.0 : m.isg;
+            const double em = 0.5 * (dot3(in.cE0, El) + dot3(in.cB, Bl)) * isg * isg;
+            const double e = in.tau * isg - em;
+            gp = e > 0.0 ? (K.ro.Gam - 1.0) * e : K.ro.p_atmo;
+            if (!(gp > 0.0)) gp = K.ro.p_atmo > 0.0 ? K.ro.p_atmo : 1e-300;
+        }
+        double pn[NPR], E[3];
+        status = recover<FLAT>(in, m, K.ro, false, 0.0, gp, gv, u[CO_PHI], u[CO_PSI], u[CO_Q],
+                               pn, E, iters, REC_ALL);
+        final_write<FLAT>(K, c, pn, status, m, U, P, Gs);
+    }
+    record_stats(stats, active, status, iters);
+}
+
 // One row of the general IMEX-RK form (Sec. III.A) for the tableaux other
 // than Table imex, at one cell: u = U^n + dt sum_q aF_q F_q, and on calE
 // also + sum_q aR_q Dt R_q.  F_jnew (jnew >= 0, coefficient anew) is formed
@@ -1709,7 +1759,7 @@ __global__ void k_rhs(const StepConst K, const T *__restrict__ P, const T *__res
 }
 
 // pointwise recovery on independent points (testing entry point)
-__global__ void __launch_bounds__(128)
+static __global__ void __launch_bounds__(128)
 k_recover_points(const RecOpts ro, int npts, const double *__restrict__ cons,
                  const double *__restrict__ guess, const double *__restrict__ alpha,
                  const double *__restrict__ gam, const double *__restrict__ sigma, int implicit,

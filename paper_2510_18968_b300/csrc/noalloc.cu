@@ -19,7 +19,10 @@
 // that device current, on the first call made on that device; make that
 // first call before any stream capture.  All calls share the one list:
 // calls that overlap on the GPU (other streams, other host threads) race
-// and must be serialised by the caller.
+// and must be serialised by the caller.  A device reset (cudaDeviceReset)
+// destroys the context that held the array; the next call notices that the
+// address it kept no longer belongs to a live allocation and looks it up
+// again in the new context.
 #include <cuda_runtime.h>
 #include <mutex>
 #include <stdio.h>
@@ -44,12 +47,15 @@ static __device__ __align__(256) NoAllocScratch g_noalloc_scratch;
 const int MAX_DEVICES = 64;
 std::mutex g_mutex;
 NoAllocScratch *g_addr[MAX_DEVICES] = {nullptr};
-char g_err[256] = "";
+// error text of the calling thread's last failed call
+thread_local char g_err[256] = "";
 
 } // namespace
 
-// error text reported by rmhd_last_error(NULL) (defined with the C ABI)
+// error text reported by rmhd_last_error(NULL) and the parameter check
+// shared with rmhd_con2prim_points (both defined with the C ABI)
 void rmhd_internal_set_error(const char *msg);
+bool rmhd_internal_recovery_params_ok(const rmhd_params *p);
 
 namespace {
 
@@ -170,6 +176,16 @@ int scratch_address(NoAllocScratch **out)
         return fail(RMHD_EINVAL);
     }
     std::lock_guard<std::mutex> lock(g_mutex);
+    if (g_addr[dev]) {
+        // still an address of device memory in the current context?  (not
+        // after a device reset; the lookup below then runs again)
+        cudaPointerAttributes at;
+        if (cudaPointerGetAttributes(&at, g_addr[dev]) != cudaSuccess ||
+            at.type != cudaMemoryTypeDevice || at.device != dev) {
+            cudaGetLastError();   // clear the error of the stale query
+            g_addr[dev] = nullptr;
+        }
+    }
     if (!g_addr[dev]) {
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
@@ -209,8 +225,7 @@ extern "C" int rmhd_con2prim_points_noalloc(const rmhd_params *p, int npts, cons
         snprintf(g_err, sizeof g_err, "NULL array");
         return fail(RMHD_EINVAL);
     }
-    if (!(p->gamma_eos > 1.0) || !(p->c2p_tol > 0.0) || p->c2p_maxit < 1 ||
-        !(p->c2p_wmax > 1.0) || !(p->rho_atmo > 0.0)) {
+    if (!rmhd_internal_recovery_params_ok(p)) {
         snprintf(g_err, sizeof g_err, "recovery parameters out of range");
         return fail(RMHD_EINVAL);
     }

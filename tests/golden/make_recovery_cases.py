@@ -40,5 +40,30 @@ def main():
     print("cells", pick, "iterations", its[pick], "statuses", np.bincount(st))
 
 
-if __name__ == "__main__":
+if __name__ == "__main__" and len(sys.argv) == 1:
     main()
+
+
+def blast_step23():
+    """Write tests/golden/recovery_blast_step23.npz: the stage-1 recovery
+    inputs (U^n, guess P^n) of step 23 of the 256^2 cylindrical explosion
+    (sigma = 1e3) at the four blast-front cells where the Newton solve of the
+    velocity equations at the guess pressure does not converge from the
+    guess velocity, so that the pressure bracket must start its velocity
+    solves from rest."""
+    wl = W.cyl_blast(n=256, nz=1)
+    a, b, g, K = wl.metric_arrays()
+    m = oracle.Metric(a.ravel(), b.reshape(3, -1), g.reshape(6, -1), K.reshape(6, -1))
+    prim = np.ascontiguousarray(wl.prim.copy())
+    cons = oracle.prim2con_grid(wl.params, m, prim)
+    oracle.step(wl.params, m, cons, prim, wl.dt, 22)
+    c, p = cons.reshape(14, -1), prim.reshape(14, -1)
+    pick = np.array([26227, 26252, 39283, 39308])   # (x, y) = (115|140, 102|153)
+    np.savez(os.path.join(HERE, "recovery_blast_step23.npz"), cons=c[:, pick], guess=p[:, pick],
+             c=1.0 - 1.0 / np.sqrt(2.0), dt=wl.dt, sigma=wl.params["sigma0"],
+             gamma_eos=wl.params["gamma_eos"], cells=pick)
+    print("blast step 23 cells", pick)
+
+
+if __name__ == "__main__" and len(sys.argv) > 1 and sys.argv[1] == "blast23":
+    blast_step23()

@@ -292,6 +292,61 @@ def test_checkpoint_restore_is_bit_exact():
     s.close(); s2.close()
 
 
+def test_set_cons_recovers_the_oracle_state_and_steps_on():
+    """rmhd_set_cons (conserved vector of Sec. II.D alone) on a fresh handle:
+    the primitives it recovers (guess: the state at rest) are the oracle's
+    primitives of the same conserved state, the conserved vector is kept bit
+    for bit, and two more steps from there match the oracle's two more
+    steps (conformally curved metric, Gauss's-law charge)."""
+    import paper_2510_18968_b300 as R
+    wl = CASES["gauss_curved"]()
+    st, _, prim, cons = run_oracle(wl, 2)
+    s2 = R.Solver(dict(wl.params))
+    a, b, g, K = wl.metric_arrays()
+    s2.set_metric(np.ascontiguousarray(a), np.ascontiguousarray(b), np.ascontiguousarray(g),
+                  np.ascontiguousarray(K))
+    if wl.sigma_profile is not None:
+        s2.set_sigma(np.ascontiguousarray(wl.sigma_profile))
+    rc = s2.set_cons(np.ascontiguousarray(cons))
+    assert rc == R.RMHD_OK
+    assert np.array_equal(s2.get_cons(), cons)
+    err = rel_linf(s2.get_prims(), prim)
+    assert err.max() < 1e-12, err
+    s2.step(wl.dt, 2)
+    m = oracle_metric(wl)
+    c2, p2 = cons.copy(), prim.copy()
+    sf = None if wl.sigma_profile is None else wl.sigma_profile.ravel()
+    oracle.step(dict(wl.params), m, c2, p2, wl.dt, 2, sigma_field=sf)
+    err = rel_linf(s2.get_cons(), c2)
+    assert err.max() < 1e-12, err
+    s2.close()
+
+
+def test_set_cons_on_a_running_handle_and_bad_input():
+    """On a handle with a state the recovery starts from its primitives: a
+    restore of the handle's own conserved vector gives back its primitives;
+    D <= 0 or a non-finite value is rejected with the state unchanged."""
+    import paper_2510_18968_b300 as R
+    wl = W.cyl_blast(n=24, nz=3)
+    s = make_solver(wl)
+    s.step(wl.dt, 3)
+    cons, prim = s.get_cons(), s.get_prims()
+    assert s.set_cons(cons) == R.RMHD_OK
+    assert np.array_equal(s.get_cons(), cons)
+    assert rel_linf(s.get_prims(), prim).max() < 1e-13
+    for bad in ("D", "nan"):
+        c = cons.copy()
+        if bad == "D":
+            c[0, 1, 2, 3] = 0.0
+        else:
+            c[7, 0, 5, 5] = np.nan
+        with pytest.raises(R.RMHDError) as e:
+            s.set_cons(c)
+        assert e.value.code == R.RMHD_EINVAL
+        assert np.array_equal(s.get_cons(), cons)
+    s.close()
+
+
 def test_bad_inputs_are_rejected_and_leave_the_state():
     import paper_2510_18968_b300 as R
     wl = W.cyl_blast(n=16, nz=2)

@@ -261,3 +261,40 @@ def test_recovered_pressure_is_the_only_root_of_a_fine_scan(cs, curved):
         root = brentq(lambda p: f(p, vmid)[0], lo, hi, xtol=1e-16 * hi, rtol=1e-15)
         assert abs(root - p_rec) <= 1e-12 * p_rec, (root, p_rec)
         assert abs(root - prim[0, 1]) <= 1e-12 * prim[0, 1]
+
+
+def test_blast_front_states_whose_velocity_solve_needs_a_restart_have_their_root():
+    """Stage-1 inputs of the 256^2 cylindrical explosion at step 23
+    (tests/golden/recovery_blast_step23.npz, written from the oracle by
+    make_recovery_cases.py): the paper's iteration leaves the physical region,
+    and at the guess pressure Newton on the velocity equations does not
+    converge from the guess velocity.  A fine scan of f(p) (velocity solved
+    by continuation, as above) has exactly one root there; the recovery must
+    return it, and re-forming D, S_i, tau from its result must give the input
+    back."""
+    import os
+    from scipy.optimize import brentq
+    d = np.load(os.path.join(os.path.dirname(__file__), "golden", "recovery_blast_step23.npz"))
+    gam, sigma = float(d["gamma_eos"]), float(d["sigma"])
+    c = float(d["c"]) * float(d["dt"])
+    P = oracle.make_params(gamma_eos=gam, rho_atmo=1e-10, K_atmo=100.0)
+    for i in range(d["cons"].shape[1]):
+        U, G = d["cons"][:, i], d["guess"][:, i]
+        out, cout, it, st = oracle.con2prim(P, U, 1, c, sigma, G)
+        assert st == 4, st
+        f = _flat_stage_solver(U, U[8:11], c * sigma, gam)
+        ps = G[1] * np.logspace(-6, 4, 2000)
+        vals = np.empty(len(ps))
+        v = np.zeros(3)
+        for j in range(len(ps)):
+            vals[j], v = f(ps[j], v)
+        ok = np.isfinite(vals)
+        idx = np.where(ok[:-1] & ok[1:] & (np.sign(vals[:-1]) != np.sign(vals[1:])))[0]
+        assert len(idx) == 1, idx
+        vz = np.zeros(3)
+        root = brentq(lambda p: f(p, vz)[0], ps[idx[0]], ps[idx[0] + 1], xtol=1e-16 * ps[idx[0]],
+                      rtol=1e-15)
+        assert abs(out[1] - root) <= 1e-12 * root, (out[1], root)
+        Uf = fs.textbook_cons_many(out[None, :], gam)[0]
+        scale = U[4] + U[0] + out[1]
+        assert np.abs(Uf[:5] - U[:5]).max() <= 1e-12 * scale

@@ -38,17 +38,31 @@ def test_noalloc_recovery_matches_the_allocating_entry_point():
 
     P = dict(gamma_eos=4.0 / 3.0, rho_atmo=1e-14)
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+    def outputs(n):
+        return (torch.empty((14, n), dtype=torch.float64, device="cuda"),
+                torch.empty((14, n), dtype=torch.float64, device="cuda"),
+                torch.empty(n, dtype=torch.int32, device="cuda"),
+                torch.empty(n, dtype=torch.int32, device="cuda"))
+
+    # a first call loads the kernels' code onto the device (the driver may
+    # allocate for that); the device-memory check below starts after it
+    cin, guess, alpha, g6, sigma, c = _inputs(500, 64)
+    R.con2prim_points(P, dev(cin), dev(guess), dev(alpha), dev(g6), dev(sigma), 1, c,
+                      out=outputs(alpha.size), noalloc=True)
+    torch.cuda.synchronize()
     for call, seed in enumerate((501, 502)):
         cin, guess, alpha, g6, sigma, c = _inputs(seed, 4000)
         n = alpha.size
         args = (dev(cin), dev(guess), dev(alpha), dev(g6), dev(sigma), 1, c)
         ref = R.con2prim_points(P, *args)
-        out = (torch.empty((14, n), dtype=torch.float64, device="cuda"),
-               torch.empty((14, n), dtype=torch.float64, device="cuda"),
-               torch.empty(n, dtype=torch.int32, device="cuda"),
-               torch.empty(n, dtype=torch.int32, device="cuda"))
+        out = outputs(n)
+        torch.cuda.synchronize()
+        free_before = torch.cuda.mem_get_info()[0]
         got = R.con2prim_points(P, *args, out=out, noalloc=True)
         torch.cuda.synchronize()
+        # the call allocated no device memory (cudaMemGetInfo unchanged)
+        assert torch.cuda.mem_get_info()[0] == free_before, call
         rp, rc, ri, rs = [x.cpu().numpy() for x in ref]
         gp, gc, gi, gs = [x.cpu().numpy() for x in got]
         assert (rs == 1).sum() + (rs == 4).sum() > 0, "no point used the work list"
