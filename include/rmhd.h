@@ -196,6 +196,29 @@ int rmhd_set_cons(rmhd_t h, const double *cons, int on_device);
 int rmhd_set_state(rmhd_t h, const double *cons, const double *prims,
                    int on_device);
 
+/* ------------------------------------------------ z-slab decomposition
+ * A grid split into z-slabs, one handle per slab (Sec. III: boxes per
+ * process with ghost-zone synchronisation; the paper has no prescription
+ * for how).  Each handle covers its slab extended on every internal face by
+ * a halo of H layers, the reach of one step (stencil radius 3 per face-flux
+ * evaluation: H = 6 for RMHD_IMEX_SSP222, 9 for the three-flux schemes; +1
+ * per recovery with RMHD_QFLUX_GAUSS).  After every step the owned layers
+ * next to a face are copied into the neighbour's halo; a step then computes
+ * the owned cells exactly as one handle over the whole grid would, bit for
+ * bit, while the halo layers absorb the error of the handle's own boundary
+ * condition at the cut.  These two calls copy the state a step starts from
+ * (U, the primitives and, on the mixed path, the FP64 recovery guess) of
+ * interior z-layers [k0, k0 + nk) to or from a packed buffer, bit for bit:
+ * U's 14 fields, then the 14 primitives in the path's storage type, then
+ * (mixed) the 4 guess fields, each over the nk layers, x fastest.
+ * rmhd_state_layer_bytes gives the bytes per layer (-1 for a NULL handle).
+ * on_device as for rmhd_set_prims; host buffers go through the handle's
+ * staging buffer (RMHD_EINVAL if nk layers do not fit it: pass device
+ * memory).  Errors: RMHD_EINVAL for layers outside [0, nz) or no state. */
+long long rmhd_state_layer_bytes(rmhd_t h);
+int rmhd_get_state_layers(rmhd_t h, int k0, int nk, void *buf, int on_device);
+int rmhd_set_state_layers(rmhd_t h, int k0, int nk, const void *buf, int on_device);
+
 /* Counters since creation (synchronises):
  * [0] recovery calls, [1] recovery iterations (paper iteration + fallback),
  * [2] recoveries finished by the Newton fallback, [3] recoveries reset to the

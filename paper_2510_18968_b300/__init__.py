@@ -59,7 +59,8 @@ class Params(ctypes.Structure):
 
 EXPORTS = ("rmhd_default_params", "rmhd_create", "rmhd_set_metric", "rmhd_set_sigma",
            "rmhd_set_prims", "rmhd_step", "rmhd_get_prims", "rmhd_get_cons",
-           "rmhd_set_state", "rmhd_set_cons", "rmhd_get_stats", "rmhd_step_profiled", "rmhd_rhs", "rmhd_con2prim_points",
+           "rmhd_set_state", "rmhd_set_cons", "rmhd_state_layer_bytes", "rmhd_get_state_layers",
+           "rmhd_set_state_layers", "rmhd_get_stats", "rmhd_step_profiled", "rmhd_rhs", "rmhd_con2prim_points",
            "rmhd_con2prim_points_noalloc", "rmhd_set_sigma0", "rmhd_adjoint_forward",
            "rmhd_adjoint_backward", "rmhd_test_rcp64", "rmhd_test_mm3", "rmhd_test_mm3f",
            "rmhd_last_error", "rmhd_destroy")
@@ -91,6 +92,9 @@ def load(build_if_missing=True):
     L.rmhd_get_cons.argtypes = [vp, vp, i]
     L.rmhd_set_state.argtypes = [vp, vp, vp, i]
     L.rmhd_set_cons.argtypes = [vp, vp, i]
+    L.rmhd_state_layer_bytes.argtypes = [vp]
+    L.rmhd_get_state_layers.argtypes = [vp, i, i, vp, i]
+    L.rmhd_set_state_layers.argtypes = [vp, i, i, vp, i]
     L.rmhd_get_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
     L.rmhd_step_profiled.argtypes = [vp, d, i, ctypes.POINTER(ctypes.c_double)]
     L.rmhd_rhs.argtypes = [vp, vp, vp, vp, i]
@@ -110,6 +114,7 @@ def load(build_if_missing=True):
     for name in EXPORTS:
         if name not in ("rmhd_default_params", "rmhd_last_error"):
             getattr(L, name).restype = i
+    L.rmhd_state_layer_bytes.restype = ctypes.c_longlong
     _lib = L
     return L
 
@@ -159,6 +164,18 @@ def _ptr(a, nelem=None):
     if nelem is not None and a.size != nelem:
         raise ValueError(f"expected {nelem} elements, got {a.size}")
     return a.ctypes.data, 0
+
+
+def _raw_ptr(a, nbytes):
+    """(pointer, on_device) of a contiguous buffer of exactly nbytes bytes:
+    a CUDA torch tensor or a host numpy array of any dtype."""
+    if _is_torch(a):
+        if not a.is_contiguous() or a.numel() * a.element_size() != nbytes:
+            raise ValueError(f"need a contiguous buffer of {nbytes} bytes")
+        return ctypes.c_void_p(a.data_ptr()), int(a.is_cuda)
+    if not a.flags["C_CONTIGUOUS"] or a.nbytes != nbytes:
+        raise ValueError(f"need a contiguous buffer of {nbytes} bytes")
+    return a.ctypes.data_as(ctypes.c_void_p), 0
 
 
 def _stream_ptr(stream):
@@ -233,6 +250,21 @@ class Solver:
         atmosphere."""
         pc, d = _ptr(cons, 14 * self.N)
         return self._check(self.L.rmhd_set_cons(self.h, pc, d), soft_ok=(RMHD_EC2P,))
+
+    # ---- z-slab decomposition: raw state of a range of z-layers
+    def state_layer_bytes(self):
+        return int(self.L.rmhd_state_layer_bytes(self.h))
+
+    def get_state_layers(self, k0, nk, out):
+        """Pack the state of interior z-layers [k0, k0 + nk) into `out`
+        (a contiguous CUDA torch tensor or host numpy array of
+        nk * state_layer_bytes() bytes)."""
+        p, d = _raw_ptr(out, nk * self.state_layer_bytes())
+        return self._check(self.L.rmhd_get_state_layers(self.h, int(k0), int(nk), p, d))
+
+    def set_state_layers(self, k0, nk, buf):
+        p, d = _raw_ptr(buf, nk * self.state_layer_bytes())
+        return self._check(self.L.rmhd_set_state_layers(self.h, int(k0), int(nk), p, d))
 
     def set_state(self, cons, prim):
         pc, d = _ptr(cons, 14 * self.N)

@@ -3,6 +3,7 @@
 // with checkpoints, segment re-runs and the reverse sweep of the kernels in
 // adjoint.cuh.
 #include "host.cuh"
+#include "adjoint.cuh"
 
 // ------------------------------------------------------------------ adjoint
 

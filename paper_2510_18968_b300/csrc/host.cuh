@@ -12,7 +12,6 @@
 #include <string.h>
 
 #include "../../include/rmhd.h"
-#include "adjoint.cuh"
 #include "kernels.cuh"
 
 using namespace rmhd;

@@ -1758,50 +1758,5 @@ __global__ void k_rhs(const StepConst K, const T *__restrict__ P, const T *__res
     for (int f = 0; f < NCO; f++) out[f * K.G.N + t] = (double)r[f];
 }
 
-// pointwise recovery on independent points (testing entry point)
-static __global__ void __launch_bounds__(128)
-k_recover_points(const RecOpts ro, int npts, const double *__restrict__ cons,
-                 const double *__restrict__ guess, const double *__restrict__ alpha,
-                 const double *__restrict__ gam, const double *__restrict__ sigma, int implicit,
-                 double c, double gfac, double *prim, double *cons_out, int *iters, int *status)
-{
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= npts) return;
-    Met<double> m;
-    m.alpha = alpha[t];
-    m.beta[0] = m.beta[1] = m.beta[2] = 0.0;
-    for (int a = 0; a < 6; a++) m.g[a] = gam[a * npts + t];
-    met_complete(m);
-    RecIn in;
-    in.D = cons[CO_D * npts + t];
-    in.tau = cons[CO_TAU * npts + t];
-    for (int a = 0; a < 3; a++) {
-        in.S[a] = cons[(CO_SX + a) * npts + t];
-        in.cB[a] = cons[(CO_BX + a) * npts + t];
-        in.cE0[a] = cons[(CO_EX + a) * npts + t];
-    }
-    const double gv[3] = {guess[PR_VX * npts + t], guess[PR_VY * npts + t],
-                          guess[PR_VZ * npts + t]};
-    double pr[NPR], E[3];
-    int it = 0;
-    const double cc = implicit ? c * m.alpha * sigma[t] : 0.0;
-    int st = recover<false>(in, m, ro, implicit != 0, cc, guess[PR_P * npts + t], gv,
-                            cons[CO_PHI * npts + t], cons[CO_PSI * npts + t],
-                            cons[CO_Q * npts + t], pr, E, it);
-    double u[NCO];
-    for (int f = 0; f < NCO; f++) u[f] = cons[f * npts + t];
-    for (int a = 0; a < 3; a++) u[CO_EX + a] = E[a];
-    if (st == 2 || st == 3) {
-        double u2[NCO];
-        prim_to_cons<double, false>(pr, m, gfac, u2);
-        u[CO_D] = u2[CO_D];
-        u[CO_TAU] = u2[CO_TAU];
-        for (int a = 0; a < 3; a++) u[CO_SX + a] = u2[CO_SX + a];
-    }
-    for (int f = 0; f < NPR; f++) prim[f * npts + t] = pr[f];
-    for (int f = 0; f < NCO; f++) cons_out[f * npts + t] = u[f];
-    iters[t] = it;
-    status[t] = st;
-}
 
 } // namespace rmhd

@@ -241,6 +241,7 @@ extern "C" int rmhd_con2prim_points_noalloc(const rmhd_params *p, int npts, cons
     ro.atmo_floor = p->rho_atmo * (1.0 + p->atmo_tol);
     ro.maxit = p->c2p_maxit;
     ro.first_cap = p->c2p_maxit;
+    ro.kappa0 = 0.3;   // as rmhd_con2prim_points
     const double gfac = p->gamma_eos / (p->gamma_eos - 1.0);
     cudaStream_t st = (cudaStream_t)cuda_stream;
     // the list keeps the previous call's contents: clear the counter

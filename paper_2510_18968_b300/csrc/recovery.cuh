@@ -31,6 +31,8 @@ struct RecOpts {
     double rho_atmo, p_atmo, atmo_floor;  // atmo_floor = rho_atmo (1 + atmo_tol)
     int maxit;           // cap of the paper iteration
     int first_cap;       // paper iterations of the first pass (REC_FIRST)
+    double kappa0;       // stiff-coupling switch to Newton after one paper
+                         // iteration (0: never); see paper_run
 };
 
 struct RecIn {
@@ -93,7 +95,7 @@ __device__ __forceinline__ bool p_conv(const RecCtx<FLAT> &c, double dp, double 
 template <bool FLAT>
 __device__ __forceinline__ bool fluid_step(const RecCtx<FLAT> &c, const double E[3], double p,
                                            double vl[3], double v[3], double &v2, double &W,
-                                           double &Winv, double &num)
+                                           double &Winv, double &num, double *den_out = nullptr)
 {
     double El[3];
     lower<double, FLAT>(c.m, E, El);
@@ -101,6 +103,7 @@ __device__ __forceinline__ bool fluid_step(const RecCtx<FLAT> &c, const double E
     double P[3];
     cross3(E, c.in.cB, P);
     const double den = c.in.tau + c.in.D + sgv(c) * p - EM;
+    if (den_out) *den_out = den;
     const double iden = rcp64(den);
 #pragma unroll
     for (int i = 0; i < 3; i++) vl[i] = (c.in.S[i] - P[i]) * iden;
@@ -194,8 +197,9 @@ __device__ int paper_run(const RecCtx<FLAT> &c, PaperState &s, double p_guess, i
     while (s.it < last) {
         const int it = ++s.it;
         if (c.implicit) implicit_field<FLAT>(c, s.v, s.vl, s.v2, s.W, E);
-        double vn[3], Winv, num;
-        if (!fluid_step<FLAT>(c, E, s.p, s.vl, vn, s.v2, s.W, Winv, num)) return 0;
+        const double C1 = c.cc * s.W;   // coupling of this iteration's implicit solve
+        double vn[3], Winv, num, den;
+        if (!fluid_step<FLAT>(c, E, s.p, s.vl, vn, s.v2, s.W, Winv, num, &den)) return 0;
         const double omv = 1.0 - s.v2;
         const double f = g1 * num * omv * isgv(c) - s.p;
         double ratio;
@@ -215,6 +219,16 @@ __device__ int paper_run(const RecCtx<FLAT> &c, PaperState &s, double p_guess, i
         if (p_conv<FLAT>(c, dp, s.p) && dv <= c.o.tol) {
             rho_out = D * Winv * isgv(c);
             return 1;
+        }
+        // Stiff magnetised states: the velocity update of step (iii) through
+        // the implicit field contracts by about kappa = C/(1+C) B^2/den per
+        // iteration (C = cc W); a cell that has not converged in its first
+        // iteration while kappa > kappa0 would crawl or diverge, and is
+        // handed to the Newton fallback at once (same root)
+        if (it == 1 && c.implicit && c.o.kappa0 > 0.0 &&
+            C1 * c.B2 * isgv(c) > c.o.kappa0 * (1.0 + C1) * den) {
+            s.slow = 2;
+            return 0;
         }
         if (iscale0 == 0.0) iscale0 = sgv(c) * rcp64(c.in.tau + D + sgv(c) * p_guess);
         const double meas = dv + fabs(dp) * iscale0;
@@ -473,15 +487,21 @@ __device__ bool velocity_at(const RecCtx<FLAT> &c, double p, double vl[3])
         for (int i = 0; i < 3; i++) { vl[i] = vt[i]; g[i] = gt[i]; }
         if (step <= 1e-15) break;
     }
-    return true;
+    // solved only if the equations hold (scaled residual at rounding level)
+    return nrm3(g) < 1e-13;
 }
 
 // scaled f(p) = (Gamma-1) rho eps - p with the velocity solved at p
+// (Newton from vl; if that does not converge, from rest)
 template <bool FLAT>
 __device__ bool pressure_function(const RecCtx<FLAT> &c, double p, double vl[3], double &f,
                                   double E[3], double &rho)
 {
-    if (!(p > 0.0) || !velocity_at<FLAT>(c, p, vl)) return false;
+    if (!(p > 0.0)) return false;
+    if (!velocity_at<FLAT>(c, p, vl)) {
+        vl[0] = vl[1] = vl[2] = 0.0;
+        if (!velocity_at<FLAT>(c, p, vl)) return false;
+    }
     double g[3], v2;
     vel_residual<FLAT>(c, p, vl, g, E, v2);
     double El[3];
@@ -496,22 +516,32 @@ __device__ bool pressure_function(const RecCtx<FLAT> &c, double p, double vl[3],
     return true;
 }
 
-// Second fallback: bracket the pressure root (doubling or halving from the
-// guess), then Illinois regula falsi; every evaluation solves the velocity.
+// Second fallback: the pressure root with the velocity solved at every trial
+// pressure.  f is defined only above the lowest pressure at which the
+// velocity equations have a solution with v^2 < 1, so a pressure where the
+// solve fails lies below the root: from the guess, double the pressure
+// while f is undefined or positive, halve it while f is negative, replacing
+// a halving that lands where f is undefined by geometric bisection between
+// that pressure and the last one where f was defined; then Illinois regula
+// falsi on the bracket.
 template <bool FLAT>
 __device__ int bracket_fallback(const RecCtx<FLAT> &c, double &p, double v[3], double E[3],
                                 double &rho_out, int &iters)
 {
-    double vl[3], f0, rho;
-    lower<double, FLAT>(c.m, v, vl);
-    const double p0 = p > 0.0 ? p : c.o.p_atmo;
-    if (!pressure_function<FLAT>(c, p0, vl, f0, E, rho)) {
-        vl[0] = vl[1] = vl[2] = 0.0;
-        if (!pressure_function<FLAT>(c, p0, vl, f0, E, rho)) return 0;
+    double vl[3], v0[3], f0 = 0.0, rho;
+    lower<double, FLAT>(c.m, v, v0);
+    vl[0] = v0[0]; vl[1] = v0[1]; vl[2] = v0[2];
+    double p0 = p > 0.0 ? p : c.o.p_atmo;
+    int n = 0;
+    bool ok = pressure_function<FLAT>(c, p0, vl, f0, E, rho);
+    while (!ok) {   // f undefined at the guess: the root is above
+        if (++n > 60) return 0;
+        p0 *= 2.0;
+        vl[0] = v0[0]; vl[1] = v0[1]; vl[2] = v0[2];
+        ok = pressure_function<FLAT>(c, p0, vl, f0, E, rho);
     }
     double lo = p0, hi = p0, flo = f0, fhi = f0;
     double vlo[3] = {vl[0], vl[1], vl[2]}, vhi[3] = {vl[0], vl[1], vl[2]};
-    int n = 0;
     if (f0 > 0.0) {
         while (fhi > 0.0) {
             if (++n > 60) return 0;
@@ -521,12 +551,24 @@ __device__ int bracket_fallback(const RecCtx<FLAT> &c, double &p, double v[3], d
             if (!pressure_function<FLAT>(c, hi, vhi, fhi, E, rho)) return 0;
         }
     } else {
+        // hi: f < 0 and defined; und: a lower pressure where f is undefined
+        double und = 0.0;
         while (flo < 0.0) {
-            if (++n > 60) return 0;
-            hi = lo; fhi = flo;
-            for (int i = 0; i < 3; i++) vhi[i] = vlo[i];
-            lo = 0.5 * lo;
-            if (!pressure_function<FLAT>(c, lo, vlo, flo, E, rho)) return 0;
+            if (++n > 120) return 0;
+            const double pt = und > 0.0 ? sqrt(und * hi) : 0.5 * hi;
+            double vt[3] = {vhi[0], vhi[1], vhi[2]}, ft;
+            if (!pressure_function<FLAT>(c, pt, vt, ft, E, rho)) {
+                und = pt;
+                if (und > hi * (1.0 - 1e-15)) return 0;
+                continue;
+            }
+            if (ft < 0.0) {
+                hi = pt; fhi = ft;
+                for (int i = 0; i < 3; i++) vhi[i] = vt[i];
+            } else {
+                lo = pt; flo = ft;
+                for (int i = 0; i < 3; i++) vlo[i] = vt[i];
+            }
         }
     }
     int side = 0;
@@ -592,6 +634,7 @@ __device__ int recover(const RecIn &in, const Met<double> &m, const RecOpts &o,
     double rho = 0.0;
     int it1 = 0, it2 = 0, status;
     bool slow = false;
+    bool newton_inline = false;   // REC_FIRST: the stiff switch's Newton converged
     int first = -2;   // REC_FIRST / REC_RESUME outcome of the paper iteration
     // atmosphere without iterating: rho = D / (W sqrt(gamma)) <= D / sqrt(gamma)
     // for every velocity, so below the floor there every root is reset
@@ -610,9 +653,25 @@ __device__ int recover(const RecIn &in, const Met<double> &m, const RecOpts &o,
                 } else {
                     first = paper_run<FLAT>(c, s, guess_p, o.first_cap, E, rho, false, slow);
                 }
-                if (first != 1) {
+                if (first == 0 && s.slow == 2) {
+                    // stiff switch (paper_run): the Newton fallback here, from
+                    // the stage guess; deferred only if it fails
+                    c.iD = 1.0 / in.D;
+                    double pn = guess_p, vn[3] = {guess_v[0], guess_v[1], guess_v[2]};
+                    double En[3] = {in.cE0[0], in.cE0[1], in.cE0[2]}, rhon = 0.0;
+                    int itn = 0;
+                    if (newton_fallback<FLAT>(c, pn, vn, En, rhon, itn)) {
+                        newton_inline = true;
+                        it1 = s.it;
+                        it2 = itn;
+                        p = pn; rho = rhon;
+                        v[0] = vn[0]; v[1] = vn[1]; v[2] = vn[2];
+                        E[0] = En[0]; E[1] = En[1]; E[2] = En[2];
+                    }
+                }
+                if (first != 1 && !newton_inline) {
                     s.outcome = first;
-                    s.slow = slow ? 1 : 0;
+                    s.slow = slow || s.slow == 2 ? 1 : 0;
                     *ps = s;
                     iters = s.it;
                     return REC_DEFER;
@@ -626,19 +685,25 @@ __device__ int recover(const RecIn &in, const Met<double> &m, const RecOpts &o,
                     first = paper_run<FLAT>(c, s, guess_p, o.maxit, E, rho, false, slow);
                 }
             }
-            it1 = s.it;
-            p = s.p;
-            v[0] = s.v[0]; v[1] = s.v[1]; v[2] = s.v[2];
+            if (!newton_inline) {
+                it1 = s.it;
+                p = s.p;
+                v[0] = s.v[0]; v[1] = s.v[1]; v[2] = s.v[2];
+            }
         }
         // outcome of the paper iteration: 1 converged, 0 gave up
         int paper;
-        if (first != -2)
+        if (newton_inline)
+            paper = 2;
+        else if (first != -2)
             paper = first;
         else if (phase == REC_FALLBACK)
             paper = 0;
         else
             paper = paper_iteration<FLAT>(c, p, v, E, rho, it1, false, slow) ? 1 : 0;
-        if (paper == 1) {
+        if (paper == 2) {
+            status = 1;
+        } else if (paper == 1) {
             status = 0;
         } else if (phase == REC_PRIMARY) {
             iters = it1;

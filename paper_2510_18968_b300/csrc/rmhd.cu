@@ -83,6 +83,11 @@ static RecOpts rec_opts(const rmhd_params *p)
     o.atmo_floor = p->rho_atmo * (1.0 + p->atmo_tol);
     o.maxit = p->c2p_maxit;
     o.first_cap = p->c2p_first_pass > 0 ? p->c2p_first_pass : p->c2p_maxit;
+    // a cell whose first paper iteration did not converge goes to Newton at
+    // once when the iteration would contract by less than 0.3 per step
+    // (measured on the magnetised blast exterior: about 20 or more further
+    // paper iterations, more than a Newton solve costs)
+    o.kappa0 = 0.3;
     return o;
 }
 
@@ -444,6 +449,91 @@ extern "C" int rmhd_set_cons(rmhd_t h, const double *cons, int on_device)
     return RMHD_OK;
 }
 
+// ---------------------------------------------------- z-layers of the state
+// The state a step starts from is U (FP64), the primitives P (the path's
+// storage type) and, on the mixed path, the FP64 recovery guess G (p, v^i).
+// A packed z-range holds, for its nk interior layers (nx*ny cells each), the
+// 14 fields of U, then the 14 of P, then the 4 of G (mixed only), each field
+// x fastest, copied bit for bit.
+
+template <class T>
+__global__ void k_zlayers(const StepConst K, int k0, int nk, T *padded, T *packed, int nf,
+                          int unpack)
+{
+    const Grid &G = K.G;
+    const long long plane = (long long)G.n[0] * G.n[1];
+    const long long cells = plane * nk;
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= cells) return;
+    const int i = (int)(t % G.n[0]);
+    const int j = (int)((t / G.n[0]) % G.n[1]);
+    const int k = k0 + (int)(t / plane);
+    const long long c = cell_at(G, i, j, k);
+    for (int f = 0; f < nf; f++) {
+        if (unpack) padded[f * G.S + c] = packed[f * cells + t];
+        else packed[f * cells + t] = padded[f * G.S + c];
+    }
+}
+
+static long long layer_bytes(rmhd_t h)
+{
+    const bool mixed = h->p.precision == RMHD_PREC_MIXED;
+    const long long plane = (long long)h->K.G.n[0] * h->K.G.n[1];
+    return plane * (long long)(NCO * 8 + NPR * (mixed ? 4 : 8) + (mixed ? 4 * 8 : 0));
+}
+
+extern "C" long long rmhd_state_layer_bytes(rmhd_t h) { return h ? layer_bytes(h) : -1; }
+
+static int zlayers(rmhd_t h, int k0, int nk, void *buf, int on_device, int unpack)
+{
+    if (!h || !buf) return set_err(h, RMHD_EINVAL, "NULL argument");
+    const Grid &G = h->K.G;
+    if (k0 < 0 || nk < 1 || k0 + nk > G.n[2])
+        return set_err(h, RMHD_EINVAL, "z-layers [%d, %d) outside [0, %d)", k0, k0 + nk, G.n[2]);
+    if (!h->have_state) return set_err(h, RMHD_EINVAL, "no state: call rmhd_set_prims first");
+    const size_t bytes = (size_t)layer_bytes(h) * nk;
+    char *dev = (char *)buf;
+    if (!on_device) {
+        // through the staging buffer (14 N doubles)
+        if (bytes > sizeof(double) * NCO * (size_t)G.N)
+            return set_err(h, RMHD_EINVAL, "%d layers exceed the staging buffer; pass device "
+                                           "memory", nk);
+        dev = (char *)h->b.stage;
+        if (unpack) CK(cudaMemcpyAsync(dev, buf, bytes, cudaMemcpyHostToDevice, h->st));
+    }
+    const long long cells = (long long)G.n[0] * G.n[1] * nk;
+    const bool mixed = h->p.precision == RMHD_PREC_MIXED;
+    k_zlayers<double><<<nblk(cells), TPB, 0, h->st>>>(h->K, k0, nk, h->b.U, (double *)dev, NCO,
+                                                      unpack);
+    dev += sizeof(double) * NCO * cells;
+    if (mixed) {
+        k_zlayers<float><<<nblk(cells), TPB, 0, h->st>>>(h->K, k0, nk, (float *)h->b.PA,
+                                                         (float *)dev, NPR, unpack);
+        dev += sizeof(float) * NPR * cells;
+        k_zlayers<double><<<nblk(cells), TPB, 0, h->st>>>(h->K, k0, nk, h->b.GA, (double *)dev, 4,
+                                                          unpack);
+    } else {
+        k_zlayers<double><<<nblk(cells), TPB, 0, h->st>>>(h->K, k0, nk, (double *)h->b.PA,
+                                                          (double *)dev, NPR, unpack);
+    }
+    CK(cudaGetLastError());
+    if (!on_device) {
+        if (!unpack) CK(cudaMemcpyAsync(buf, h->b.stage, bytes, cudaMemcpyDeviceToHost, h->st));
+        CK(cudaStreamSynchronize(h->st));
+    }
+    return RMHD_OK;
+}
+
+extern "C" int rmhd_get_state_layers(rmhd_t h, int k0, int nk, void *buf, int on_device)
+{
+    return zlayers(h, k0, nk, buf, on_device, 0);
+}
+
+extern "C" int rmhd_set_state_layers(rmhd_t h, int k0, int nk, const void *buf, int on_device)
+{
+    return zlayers(h, k0, nk, (void *)buf, on_device, 1);
+}
+
 // The step as a CUDA graph: captured once on a private stream (a legacy
 // default stream cannot be captured), then launched on the handle's stream.
 // Re-captured when the step constants, the metric flag or the precision
@@ -647,6 +737,52 @@ extern "C" int rmhd_rhs(rmhd_t h, const double *prims, const double *J, double *
     if (rc) return rc;
     CK(cudaGetLastError());
     return stage_out(h, rhs, NCO, on_device);
+}
+
+// pointwise recovery on independent points (testing entry point)
+__global__ void __launch_bounds__(128)
+k_recover_points(const RecOpts ro, int npts, const double *__restrict__ cons,
+                 const double *__restrict__ guess, const double *__restrict__ alpha,
+                 const double *__restrict__ gam, const double *__restrict__ sigma, int implicit,
+                 double c, double gfac, double *prim, double *cons_out, int *iters, int *status)
+{
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= npts) return;
+    Met<double> m;
+    m.alpha = alpha[t];
+    m.beta[0] = m.beta[1] = m.beta[2] = 0.0;
+    for (int a = 0; a < 6; a++) m.g[a] = gam[a * npts + t];
+    met_complete(m);
+    RecIn in;
+    in.D = cons[CO_D * npts + t];
+    in.tau = cons[CO_TAU * npts + t];
+    for (int a = 0; a < 3; a++) {
+        in.S[a] = cons[(CO_SX + a) * npts + t];
+        in.cB[a] = cons[(CO_BX + a) * npts + t];
+        in.cE0[a] = cons[(CO_EX + a) * npts + t];
+    }
+    const double gv[3] = {guess[PR_VX * npts + t], guess[PR_VY * npts + t],
+                          guess[PR_VZ * npts + t]};
+    double pr[NPR], E[3];
+    int it = 0;
+    const double cc = implicit ? c * m.alpha * sigma[t] : 0.0;
+    int st = recover<false>(in, m, ro, implicit != 0, cc, guess[PR_P * npts + t], gv,
+                            cons[CO_PHI * npts + t], cons[CO_PSI * npts + t],
+                            cons[CO_Q * npts + t], pr, E, it);
+    double u[NCO];
+    for (int f = 0; f < NCO; f++) u[f] = cons[f * npts + t];
+    for (int a = 0; a < 3; a++) u[CO_EX + a] = E[a];
+    if (st == 2 || st == 3) {
+        double u2[NCO];
+        prim_to_cons<double, false>(pr, m, gfac, u2);
+        u[CO_D] = u2[CO_D];
+        u[CO_TAU] = u2[CO_TAU];
+        for (int a = 0; a < 3; a++) u[CO_SX + a] = u2[CO_SX + a];
+    }
+    for (int f = 0; f < NPR; f++) prim[f * npts + t] = pr[f];
+    for (int f = 0; f < NCO; f++) cons_out[f * npts + t] = u[f];
+    iters[t] = it;
+    status[t] = st;
 }
 
 // parameters the pointwise recovery entry points use (rmhd_con2prim_points

@@ -50,25 +50,25 @@ static void launch_flux_rc(rmhd_t h, const T *P, const T *J)
     const Buffers &b = h->b;
     T *Fd[3] = {(T *)b.F[0], (T *)b.F[1], (T *)b.F[2]};
     const int M = FLUX_RUN;
-    const bool run = sizeof(T) == sizeof(double);
+    constexpr bool run = sizeof(T) == sizeof(double);
     auto nthreads = [&](int d) {
         long long n = 1;
         for (int a = 0; a < 3; a++) n *= a == d ? (run ? (G.n[a] + 1 + M - 1) / M : G.n[a] + 1) : G.n[a];
         return n;
     };
-    if (run) {
+    if constexpr (run) {
         if (G.g[0]) k_flux_run<T, FLAT, RC, 0, M><<<nblk(nthreads(0)), TPB, 0, h->st>>>(h->K, P, J, b.met, b.sig, Fd[0]);
         if (G.g[1]) k_flux_run<T, FLAT, RC, 1, M><<<nblk(nthreads(1)), TPB, 0, h->st>>>(h->K, P, J, b.met, b.sig, Fd[1]);
         if (G.g[2]) k_flux_run<T, FLAT, RC, 2, M><<<nblk(nthreads(2)), TPB, 0, h->st>>>(h->K, P, J, b.met, b.sig, Fd[2]);
-        return;
+    } else {
+        if (G.n[1] <= 65535 && G.n[2] <= 65535) {   // grid-dimension limits of the tiles
+            launch_flux_tile<FLAT, RC>(h, P, J, Fd);
+            return;
+        }
+        if (G.g[0]) k_flux<T, FLAT, RC, 0><<<nblk(nthreads(0)), TPB, 0, h->st>>>(h->K, P, J, b.met, b.sig, Fd[0]);
+        if (G.g[1]) k_flux<T, FLAT, RC, 1><<<nblk(nthreads(1)), TPB, 0, h->st>>>(h->K, P, J, b.met, b.sig, Fd[1]);
+        if (G.g[2]) k_flux<T, FLAT, RC, 2><<<nblk(nthreads(2)), TPB, 0, h->st>>>(h->K, P, J, b.met, b.sig, Fd[2]);
     }
-    if (G.n[1] <= 65535 && G.n[2] <= 65535) {   // grid-dimension limits of the tiles
-        launch_flux_tile<FLAT, RC>(h, (const float *)P, (const float *)J, (float **)Fd);
-        return;
-    }
-    if (G.g[0]) k_flux<T, FLAT, RC, 0><<<nblk(nthreads(0)), TPB, 0, h->st>>>(h->K, P, J, b.met, b.sig, Fd[0]);
-    if (G.g[1]) k_flux<T, FLAT, RC, 1><<<nblk(nthreads(1)), TPB, 0, h->st>>>(h->K, P, J, b.met, b.sig, Fd[1]);
-    if (G.g[2]) k_flux<T, FLAT, RC, 2><<<nblk(nthreads(2)), TPB, 0, h->st>>>(h->K, P, J, b.met, b.sig, Fd[2]);
 }
 
 template <class T, bool FLAT> static void launch_flux(rmhd_t h, const T *P, const T *J)

@@ -175,7 +175,12 @@ def test_adjoint_matches_oracle_finite_differences(name, nsteps, every):
                                               target, dV)))
         adj.append(float(np.sum(grad * u)))
     adj, fd = np.array(adj), np.array(fd)
-    rel = np.abs(adj - fd) / np.maximum(np.abs(fd), 1e-3 * np.abs(fd).max())
+    # each direction relative to its own derivative, but at least to 1e-2 of
+    # the largest: the oracle's extrapolated differences carry an absolute
+    # error of ~1e-12 (its recovery stops at a tolerance of 1e-14 on the
+    # change of the iterate, divided by h = 1e-6), which is 1e-6 of a
+    # directional derivative a thousand times smaller than the largest one
+    rel = np.abs(adj - fd) / np.maximum(np.abs(fd), 1e-2 * np.abs(fd).max())
     print(name, "directional derivatives: adjoint vs oracle FD, max rel", rel.max())
     assert rel.max() < TOL, (name, adj, fd, rel)
 
@@ -256,7 +261,12 @@ def test_adjoint_of_the_resistive_alfven_inverse_problem():
         fd.append(_richardson(lambda h: L(wl.prim + h * u)))
         adj.append(float(np.sum(grad * u)))
     adj, fd = np.array(adj), np.array(fd)
-    rel = np.abs(adj - fd) / np.maximum(np.abs(fd), 1e-3 * np.abs(fd).max())
+    # each direction relative to its own derivative, but at least to 1e-2 of
+    # the largest: the oracle's extrapolated differences carry an absolute
+    # error of ~1e-12 (its recovery stops at a tolerance of 1e-14 on the
+    # change of the iterate, divided by h = 1e-6), which is 1e-6 of a
+    # directional derivative a thousand times smaller than the largest one
+    rel = np.abs(adj - fd) / np.maximum(np.abs(fd), 1e-2 * np.abs(fd).max())
     fds = _richardson(lambda h: L(wl.prim, 1e3 * np.exp(h)))
     print("32^3 Alfven, 60 steps: max rel over 32 directions", rel.max(),
           "dL/dlog sigma0", gls, fds)

@@ -6,7 +6,7 @@ import pytest
 
 import oracle
 import workloads as W
-from tests.helpers import make_solver, rel_linf, run_gpu, run_oracle, state_error
+from tests.helpers import make_solver, oracle_metric, rel_linf, run_gpu, run_oracle, state_error
 
 pytestmark = pytest.mark.gpu
 
@@ -274,6 +274,33 @@ def test_recovery_kernel_on_hard_states(torch_cuda):
                                         d["guess"][:, i])
         assert st == 4 and status[i] in (0, 1, 4), (st, status[i])
         assert np.allclose(prim[:, i], ref, rtol=1e-10, atol=1e-12 * np.abs(ref).max())
+
+
+def test_recovery_kernel_on_blast_states_that_need_a_velocity_restart(torch_cuda):
+    """Stage-1 inputs of the 256^2 blast at step 23 (tests/golden) on which
+    the velocity solve at the guess pressure fails from the guess velocity:
+    the kernel's fallbacks reach the oracle's root (no atmosphere reset)."""
+    import os
+    import paper_2510_18968_b300 as R
+    torch = torch_cuda
+    d = np.load(os.path.join(os.path.dirname(__file__), "golden", "recovery_blast_step23.npz"))
+    n = d["cons"].shape[1]
+    gam, sigma = float(d["gamma_eos"]), float(d["sigma"])
+    c = float(d["c"]) * float(d["dt"])
+    P = dict(gamma_eos=gam, rho_atmo=1e-10, K_atmo=100.0)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+    g6 = np.tile(np.array([[1.0], [0], [0], [1], [0], [1]]), (1, n))
+    prim, cout, iters, status = R.con2prim_points(
+        P, dev(d["cons"]), dev(d["guess"]), dev(np.ones(n)), dev(g6), dev(np.full(n, sigma)),
+        1, c)
+    torch.cuda.synchronize()
+    prim, status = prim.cpu().numpy(), status.cpu().numpy()
+    OP = oracle.make_params(**P)
+    for i in range(n):
+        ref, _, _, st = oracle.con2prim(OP, d["cons"][:, i], 1, c, sigma, d["guess"][:, i])
+        assert st == 4 and status[i] in (0, 1, 4), (st, status[i])
+        scale = np.abs(ref).max()
+        assert np.abs(prim[:, i] - ref).max() <= 1e-12 * scale, (i, prim[:, i] - ref)
 
 
 # ------------------------------------------------------------ API behaviour
