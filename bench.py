@@ -21,9 +21,10 @@ the per-kernel rooflines, and the configuration's whole 100-step run from
 the initial data is timed in ten blocks for both precisions ("run100",
 "fp64_run100"): the cost of a step grows as the blast evolves.
 
-One JSON line on stdout (rank 0).  With N > 1 (torchrun) every rank runs its
-own replica of the workload on its own GPU (the method has no data-path
-exchange between independent replicas; value = total zone-updates / max time).
+One JSON line on stdout (rank 0).  With N > 1 (torchrun) the grid is split
+into z-slabs, one per rank and GPU, with halos exchanged point to point after
+every step (paper_2510_18968_b300/slabs.py); value = the grid's
+zone-updates / the slowest rank's time (strong scaling).
 --impl reference times the FP64 CPU oracle on a bounded z-slab of the same
 workload on the host cores.
 """
@@ -386,6 +387,71 @@ def run_ours(args, rank, world, local):
     return wl, out
 
 
+def run_slabs(args, rank, world, local):
+    """N > 1: the 256^3 grid split into z-slabs over the ranks (one GPU
+    each), halos of H layers exchanged point to point (NCCL) after every
+    step (paper_2510_18968_b300.slabs).  Every rank times W warm-up and K
+    timed steps (step + exchange) between a barrier and a synchronize on
+    both sides; the job's time is the slowest rank's and the value counts
+    the grid's cells once (strong scaling: the total work is fixed).
+    End to end: each rank uploads its slab's primitives from pinned host
+    memory, steps once with the exchange, and reads its slab back."""
+    import torch
+    import torch.distributed as dist
+    import paper_2510_18968_b300 as R
+    from paper_2510_18968_b300 import slabs as S
+
+    torch.cuda.set_device(local)
+    dist.init_process_group("nccl")
+    wl = workload(args.n, args.imex)
+    nz = wl.params["n"][2]
+    H = S.halo_layers(wl.params)
+    periodic = wl.params["bc"][2] == 0
+    slab = S.make_slab(nz, world, rank, H, periodic)
+    out = {}
+    for prec in (["mixed", "fp64"] if args.precision == "both" else [args.precision]):
+        P = dict(wl.params, precision=1 if prec == "mixed" else 0)
+        s = S.slab_solver(R, P, wl.prim, None, None, slab)
+        st = S.SolverStepper(s)
+        ex = S.DistExchange(st, nz, H, periodic)
+        for _ in range(args.warmup):
+            st.step(wl.dt)
+            ex.exchange()
+        torch.cuda.synchronize()
+        dist.barrier()
+        sampler = ClockSampler(local)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with sampler:
+            torch.cuda.synchronize()
+            e0.record()
+            for _ in range(args.steps):
+                st.step(wl.dt)
+                ex.exchange()
+            e1.record()
+            torch.cuda.synchronize()
+        ms = reduce_max_ms(e0.elapsed_time(e1), world, "cuda")
+        # end to end through the public API, host buffers
+        prim_h = torch.empty((14,) + s.shape, dtype=torch.float64).pin_memory().numpy()
+        s.get_prims(prim_h)
+        dist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ke = max(1, min(args.steps, 3))
+        for _ in range(ke):
+            s.set_prims(prim_h)
+            st.step(wl.dt)
+            ex.exchange()
+            s.get_prims(prim_h)
+        torch.cuda.synchronize()
+        e2e_ms = reduce_max_ms(1e3 * (time.perf_counter() - t0), world, "cuda")
+        out[prec] = dict(ms=ms, clocks=sampler.summary(), e2e_ms=e2e_ms, e2e_steps=ke,
+                         slab_bytes=14 * 8 * int(np.prod(s.shape)),
+                         halo=H, local_layers=slab.nz_local, owned_layers=slab.z1 - slab.z0)
+        s.close()
+    dist.destroy_process_group()
+    return wl, out
+
+
 def kernel_rooflines(wl, res, prec, steps):
     """Roofline of every kernel group from its live CUDA-event time."""
     hbm, kind = _peaks()
@@ -726,6 +792,36 @@ def main():
                                  "per_core": per_core, "sample": sample},
                 "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    if world > 1:
+        wl, res = run_slabs(args, rank, world, local)
+        if rank != 0:
+            return
+        head = "mixed" if "mixed" in res else "fp64"
+        r = res[head]
+        N = wl.ncells
+        line = {"metric": METRIC, "value": N * args.steps / (r["ms"] * 1e-3), "unit": UNIT,
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": r["ms"] / args.steps, "higher_is_better": True,
+                "scaling": "strong", "vs_baseline": None,
+                "dtype": "f32+f64" if head == "mixed" else "f64", "data": "synthetic",
+                "config": dict(cfg, precision=head, parallelism=f"z-slabs x{world}",
+                               halo_layers=r["halo"], local_layers=r["local_layers"],
+                               owned_layers_rank0=r["owned_layers"],
+                               timed_call="rmhd_step (one step) + halo exchange (NCCL "
+                                          "point to point) per step")}
+        if "fp64" in res and head != "fp64":
+            line["fp64_value"] = N * args.steps / (res["fp64"]["ms"] * 1e-3)
+            line["fp64_ms_per_step"] = res["fp64"]["ms"] / args.steps
+        line["clocks"] = r["clocks"]
+        line["e2e"] = {"value": N * r["e2e_steps"] / (r["e2e_ms"] * 1e-3), "unit": UNIT,
+                       "h2d_bytes_per_step": r["slab_bytes"] * world,
+                       "d2h_bytes_per_step": r["slab_bytes"] * world,
+                       "pipeline": "per rank: rmhd_set_prims of its slab from pinned memory, "
+                                   "one step + exchange, rmhd_get_prims"}
+        line["gpu_launches"] = (launches_per_step(wl) + 6) * args.steps
         print(json.dumps(line))
         return
 
