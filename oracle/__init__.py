@@ -86,6 +86,7 @@ def lib():
         L.orc_imex_tableau.argtypes = [i, _DP, _DP, _DP, _DP]
         L.orc_imex_tableau.restype = i
         L.orc_set_status_buffer.argtypes = [ctypes.c_void_p]
+        L.orc_set_fail_buffer.argtypes = [ctypes.c_void_p, ctypes.c_long, ctypes.c_void_p]
         _lib = L
     return _lib
 
@@ -278,8 +279,11 @@ def imex_tableau(scheme):
             A.reshape(4, 4)[:s, :s].copy(), w[:s].copy())
 
 
+FAIL_REC = 39   # doubles per failed-recovery record (rmhd_oracle.h ORC_FAIL_REC)
+
+
 def step(params, metric, cons, prim, dt, nsteps=1, sigma_field=None,
-         status_out=None, general_form=False):
+         status_out=None, general_form=False, fail_out=None):
     """Advance (cons, prim) in place by nsteps IMEX-RK steps with the
     tableau params["imex"] (0: SSP2(2,2,2), Table imex, through its literal
     equations; others, or general_form=True, through the general form).
@@ -293,10 +297,16 @@ def step(params, metric, cons, prim, dt, nsteps=1, sigma_field=None,
     if status_out is not None:
         assert status_out.dtype == np.int32 and status_out.size == 3 * prim[0].size
         lib().orc_set_status_buffer(status_out.ctypes.data)
+    if fail_out is not None:
+        # fail_out: dict with "buf" (cap x FAIL_REC float64) and "count" (int64[1])
+        lib().orc_set_fail_buffer(fail_out["buf"].ctypes.data, fail_out["buf"].shape[0],
+                                  fail_out["count"].ctypes.data)
     fn = lib().orc_step_tableau if general_form else lib().orc_step
     st = fn(ctypes.byref(P), _ptr(metric.alpha), _ptr(metric.beta),
                         _ptr(metric.gamma), _ptr(metric.K), _ptr(sf), _ptr(cons),
                         _ptr(prim), float(dt), int(nsteps), stats)
     if status_out is not None:
         lib().orc_set_status_buffer(None)
+    if fail_out is not None:
+        lib().orc_set_fail_buffer(None, 0, None)
     return st, dict(zip(STAT_NAMES, list(stats)[:7]))

@@ -1234,6 +1234,19 @@ void orc_prim2con_grid(const orc_params *P, const double *alpha,
 static int *dbg_status = NULL;
 void orc_set_status_buffer(int *buf) { dbg_status = buf; }
 
+/* Optional record of the inputs of every failed recovery (status 2) of the
+ * following steps, for diagnostics in the tests: per failure ORC_FAIL_REC
+ * doubles (stage, cell, conserved input [14], guess [14], alpha, gamma_ij
+ * [6], c, sigma), up to cap records; *count counts all failures. */
+static double *dbg_fail = NULL;
+static long dbg_fail_cap = 0, *dbg_fail_count = NULL;
+void orc_set_fail_buffer(double *buf, long cap, long *count)
+{
+    dbg_fail = buf;
+    dbg_fail_cap = cap;
+    dbg_fail_count = count;
+}
+
 /* Pointwise recovery over the grid.  implicit: solve the stiff calE with
  * c = gamma_imex dt; cons is updated in place (calE and, after an
  * atmosphere reset, D, S_i, tau). */
@@ -1261,6 +1274,22 @@ static void c2p_grid(const grid *G, double *cons, const double *guess,
         if (st == 3) stats[4] += 1;
         if (it > stats[5]) stats[5] = it;
         if (dbg_status) dbg_status[stage * N + cell] = st;
+        if (dbg_fail && st == 2) {
+            long k = (*dbg_fail_count)++;
+            if (k < dbg_fail_cap) {
+                double *r = dbg_fail + k * ORC_FAIL_REC;
+                r[0] = stage;
+                r[1] = (double)cell;
+                for (int f = 0; f < 14; f++) {
+                    r[2 + f] = cin[f];
+                    r[16 + f] = g[f];
+                }
+                r[30] = G->alpha[cell];
+                for (int a = 0; a < 6; a++) r[31 + a] = g6[a];
+                r[37] = c;
+                r[38] = sigma;
+            }
+        }
         for (int f = 0; f < 14; f++) {
             prim[f * N + cell] = pr[f];
             cons[f * N + cell] = cout[f];

@@ -100,6 +100,10 @@ int  orc_step(const orc_params *P, const double *alpha, const double *beta,
 
 /* diagnostics: per-cell recovery status of the last step (3*N ints) */
 void orc_set_status_buffer(int *buf);
+/* diagnostics: inputs of failed recoveries (ORC_FAIL_REC doubles each:
+ * stage, cell, conserved [14], guess [14], alpha, gamma_ij [6], c, sigma) */
+#define ORC_FAIL_REC 39
+void orc_set_fail_buffer(double *buf, long cap, long *count);
 
 #ifdef __cplusplus
 }

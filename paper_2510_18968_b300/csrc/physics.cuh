@@ -407,8 +407,45 @@ template <class T, int RC> __device__ __forceinline__ T tvd_slope(T um, T u0, T 
 }
 
 // Jiang-Shu WENO5 face value between c and d from (a..e) = u_{i-2..i+2}
+// FP64 WENO5 with every rounding written out (explicit FMAs, products and
+// sums that the compiler may not contract): the run flux kernel inlines the
+// reconstruction of a run's first cell apart from the others, and with
+// contraction left to the compiler the two copies could round differently,
+// making a face's value depend on where a run starts (a grid cut into
+// z-slabs would then not reproduce the whole grid bit for bit).  Same
+// weights and algebra as the generic form below.
+__device__ __forceinline__ double weno5_f64(double a, double b, double c, double d, double e)
+{
+    const double eps = 1e-6, sixth = 1.0 / 6.0, k13 = 13.0 / 12.0;
+    const double q0 = __dmul_rn(__fma_rn(11.0, c, __fma_rn(-7.0, b, __dmul_rn(2.0, a))), sixth);
+    const double q1 = __dmul_rn(__fma_rn(2.0, d, __fma_rn(5.0, c, -b)), sixth);
+    const double q2 = __dmul_rn(__dsub_rn(__fma_rn(5.0, d, __dmul_rn(2.0, c)), e), sixth);
+    double t1 = __dadd_rn(__fma_rn(-2.0, b, a), c);
+    double t2 = __fma_rn(3.0, c, __fma_rn(-4.0, b, a));
+    const double b0 = __fma_rn(__dmul_rn(k13, t1), t1, __dmul_rn(__dmul_rn(0.25, t2), t2));
+    t1 = __dadd_rn(__fma_rn(-2.0, c, b), d);
+    t2 = __dsub_rn(b, d);
+    const double b1 = __fma_rn(__dmul_rn(k13, t1), t1, __dmul_rn(__dmul_rn(0.25, t2), t2));
+    t1 = __dadd_rn(__fma_rn(-2.0, d, c), e);
+    t2 = __dadd_rn(__fma_rn(-4.0, d, __dmul_rn(3.0, c)), e);
+    const double b2 = __fma_rn(__dmul_rn(k13, t1), t1, __dmul_rn(__dmul_rn(0.25, t2), t2));
+    // the normalised weights d_k/s_k / sum_j d_j/s_j, s_k = (eps + b_k)^2,
+    // over the common denominator s_0 s_1 s_2: one division instead of
+    // four (FP64 divisions are a sequence of FP64-pipe instructions on
+    // B300).  The products stay finite while every b_k < 1e77, i.e. for
+    // jumps below ~1e38 in a primitive; FP32 keeps the four divisions,
+    // whose products would overflow much sooner.
+    const double e0 = __dadd_rn(eps, b0), e1 = __dadd_rn(eps, b1), e2 = __dadd_rn(eps, b2);
+    const double s0 = __dmul_rn(e0, e0), s1 = __dmul_rn(e1, e1), s2 = __dmul_rn(e2, e2);
+    const double n0 = __dmul_rn(0.1, __dmul_rn(s1, s2)), n1 = __dmul_rn(0.6, __dmul_rn(s0, s2)),
+                 n2 = __dmul_rn(0.3, __dmul_rn(s0, s1));
+    const double num = __fma_rn(n2, q2, __fma_rn(n1, q1, __dmul_rn(n0, q0)));
+    return num / __dadd_rn(__dadd_rn(n0, n1), n2);
+}
+
 template <class T> __device__ __forceinline__ T weno5(T a, T b, T c, T d, T e)
 {
+    if constexpr (std::is_same<T, double>::value) return weno5_f64(a, b, c, d, e);
     const T eps = T(1e-6);
     const T sixth = T(1) / T(6);
     T q0 = (T(2) * a - T(7) * b + T(11) * c) * sixth;
@@ -423,23 +460,10 @@ template <class T> __device__ __forceinline__ T weno5(T a, T b, T c, T d, T e)
     t1 = c - T(2) * d + e;
     t2 = T(3) * c - T(4) * d + e;
     T b2 = k13 * t1 * t1 + T(0.25) * t2 * t2;
-    if constexpr (std::is_same<T, double>::value) {
-        // the normalised weights d_k/s_k / sum_j d_j/s_j, s_k = (eps + b_k)^2,
-        // over the common denominator s_0 s_1 s_2: one division instead of
-        // four (FP64 divisions are a sequence of FP64-pipe instructions on
-        // B300).  The products stay finite while every b_k < 1e77, i.e. for
-        // jumps below ~1e38 in a primitive; FP32 keeps the four divisions,
-        // whose products would overflow much sooner.
-        const T s0 = (eps + b0) * (eps + b0), s1 = (eps + b1) * (eps + b1),
-                s2 = (eps + b2) * (eps + b2);
-        const T n0 = T(0.1) * (s1 * s2), n1 = T(0.6) * (s0 * s2), n2 = T(0.3) * (s0 * s1);
-        return (n0 * q0 + n1 * q1 + n2 * q2) / (n0 + n1 + n2);
-    } else {
-        T w0 = T(0.1) / ((eps + b0) * (eps + b0));
-        T w1 = T(0.6) / ((eps + b1) * (eps + b1));
-        T w2 = T(0.3) / ((eps + b2) * (eps + b2));
-        return (w0 * q0 + w1 * q1 + w2 * q2) / (w0 + w1 + w2);
-    }
+    T w0 = T(0.1) / ((eps + b0) * (eps + b0));
+    T w1 = T(0.6) / ((eps + b1) * (eps + b1));
+    T w2 = T(0.3) / ((eps + b2) * (eps + b2));
+    return (w0 * q0 + w1 * q1 + w2 * q2) / (w0 + w1 + w2);
 }
 
 template <class T, int RC>

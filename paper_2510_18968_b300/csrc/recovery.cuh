@@ -13,12 +13,16 @@
 // The outer loop is the paper's: (iii) v, W, rho, eps from the conserved
 // variables at the current p and calE, (iv) p <- p - f/f' with
 // f = (Gamma-1) rho eps - p, f' = v^2 c_s^2 - 1, c_s^2 = Gamma(Gamma-1)eps/(1+Gamma eps).
-// When that iteration diverges or would converge too slowly, a damped Newton
-// method on (p, v_i) with a forward-difference Jacobian takes over from the
-// stage guess; if that stalls, the pressure root is bracketed and refined by
-// regula falsi with the velocity equations solved at each pressure.  All stop
-// on the same criteria and find the same root.  A state with no root is reset
-// to the atmosphere.  Every loop is bounded.
+// In a strongly magnetised cell of an implicit stage that iteration diverges
+// (the field's feedback on v grows by kappa = k B^2/(sqrt(g) den) > 1 per
+// iteration); there a Newton method on (p, v_i) whose Jacobian keeps the
+// terms of that feedback (stiff_newton) takes over from the stage guess.
+// When the paper iteration gives up otherwise, or the stiff Newton fails, a
+// damped Newton method on (p, v_i) with a forward-difference Jacobian takes
+// over from the stage guess; if that stalls, the pressure root is bracketed
+// and refined by regula falsi with the velocity equations solved at each
+// pressure.  All stop on the same criteria and find the same root.  A state
+// with no root is reset to the atmosphere.  Every loop is bounded.
 #pragma once
 #include "physics.cuh"
 
@@ -405,6 +409,128 @@ __device__ int newton_fallback(const RecCtx<FLAT> &c, double &p, double v[3], do
     return 1;
 }
 
+// Stiff magnetised cells: Newton on (p, v_lower) for the same two equations the
+// paper iteration solves,
+//   m_i = v_i den - (S_i - eta_ijk calE^j calB^k) = 0,  den = tau + D + sqrt(g) p - EM,
+//   f   = (Gamma-1) num (1-v^2)/sqrt(g) - p = 0,
+// with calE = calE(v) from the closed-form implicit solve, and a Jacobian made
+// of the terms that dominate when C = cc W >> 1 (calE -> -eps v x calB):
+//   dm/dv = (den + k B^2/sqrt(g)) I - (k/sqrt(g)) calB_lower calB^T + v_lower g^T,
+//   dm/dp = sqrt(g) v_lower,   g^j = d den/dv_j = (k/gamma) (calB_lower x calE_lower)^j,
+//   df/dp = -(Gamma-1) v^2 - 1,
+//   df/dv_j = (Gamma-1)/sqrt(g) [(1-v^2)(g^j - D W^3 v^j - 2 sqrt(g) p W^4 v^j) - 2 num v^j],
+// k = C/(1+C).  The paper iteration's velocity step multiplies the field's
+// feedback by kappa = k B^2/(sqrt(g) den) per iteration, which exceeds 1 in
+// a strongly magnetised plasma (B^2 >> rho h); here that linear feedback is on
+// the left-hand side.  dm/dv is the identity times a scalar plus two rank-one
+// terms, so the 4x4 step is formed by block elimination with two
+// Sherman-Morrison solves (no pivoting, no 4x4 factorisation).  Converges in a
+// few iterations from the stage guess; a step that leaves the physical
+// region is halved, and failure (no convergence in STIFF_MAXIT) leaves the cell
+// to the fallbacks.  Same stopping rule as the paper iteration.
+constexpr int STIFF_MAXIT = 30;
+
+template <bool FLAT>
+__device__ bool stiff_newton(const RecCtx<FLAT> &c, double &p, double v[3], double E[3],
+                             double &rho_out, int &iters)
+{
+    const double Gam = c.o.Gam, g1 = Gam - 1.0;
+    const double sg = sgv(c), isg = isgv(c);
+    double vl[3];
+    lower<double, FLAT>(c.m, v, vl);
+    double pp = p;
+    iters = 0;
+    for (int it = 1; it <= STIFF_MAXIT; it++) {
+        iters = it;
+        double vu[3];
+        raise<double, FLAT>(c.m, vl, vu);
+        const double v2 = dot3(vu, vl);
+        if (!(pp > 0.0) || !(v2 < c.o.v2max)) return false;
+        const double W = rsqrt(1.0 - v2);
+        implicit_field<FLAT>(c, vu, vl, v2, W, E);
+        double El[3], P[3];
+        lower<double, FLAT>(c.m, E, El);
+        const double EM = 0.5 * (dot3(E, El) + c.B2) * isg;
+        cross3(E, c.in.cB, P);
+        const double den = c.in.tau + c.in.D + sg * pp - EM;
+        if (!(den > 0.0)) return false;
+        double m[3];
+#pragma unroll
+        for (int i = 0; i < 3; i++) m[i] = vl[i] * den - (c.in.S[i] - P[i]);
+        const double W2 = W * W;
+        const double num = c.in.tau - c.in.D * (W - 1.0) - sg * pp * (v2 * W2) - EM;
+        const double f = g1 * num * (1.0 - v2) * isg - pp;
+        // Jacobian terms
+        const double C = c.cc * W;
+        const double k = C * rcp64(1.0 + C);
+        const double kb = k * isg;
+        double g[3];
+        cross3(c.cBl, El, g);
+        const double gk = FLAT ? k : k * isg * isg;
+#pragma unroll
+        for (int j = 0; j < 3; j++) g[j] *= gk;
+        const double fp = -g1 * v2 - 1.0;
+        const double cv = -c.in.D * W2 * W - 2.0 * sg * pp * W2 * W2;
+        double fv[3];
+#pragma unroll
+        for (int j = 0; j < 3; j++)
+            fv[j] = g1 * isg * ((1.0 - v2) * (g[j] + cv * vu[j]) - 2.0 * num * vu[j]);
+        // N0 = alpha I - kb calB_lower calB^T: N0^-1 x = [x + kb calB_lower (calB.x)/den]/alpha
+        const double ialpha = rcp64(den + kb * c.B2);
+        const double kd = kb * rcp64(den);
+        double y[3], z[3];
+        const double bv = dot3(c.in.cB, vl), bm = dot3(c.in.cB, m);
+#pragma unroll
+        for (int i = 0; i < 3; i++) {
+            y[i] = (vl[i] + kd * bv * c.cBl[i]) * ialpha;   // N0^-1 v_lower
+            z[i] = (m[i] + kd * bm * c.cBl[i]) * ialpha;    // N0^-1 m
+        }
+        // N = N0 + v_lower g^T; a = -N^-1 m, b = N^-1 (sqrt(g) v_lower)
+        const double is = rcp64(1.0 + dot3(g, y));
+        const double gz = dot3(g, z) * is;
+        double a[3], b[3];
+#pragma unroll
+        for (int i = 0; i < 3; i++) {
+            a[i] = y[i] * gz - z[i];
+            b[i] = sg * y[i] * is;
+        }
+        const double dp = -(f + dot3(fv, a)) * rcp64(fp - dot3(fv, b));
+        double dv[3];
+#pragma unroll
+        for (int i = 0; i < 3; i++) dv[i] = a[i] - b[i] * dp;
+        // keep the iterate physical: halve a step that leaves the region
+        double lam = 1.0, pn = 0.0, vln[3];
+        bool ok = false;
+        for (int h = 0; h < 8; h++) {
+            pn = pp + lam * dp;
+#pragma unroll
+            for (int i = 0; i < 3; i++) vln[i] = vl[i] + lam * dv[i];
+            double vt[3];
+            raise<double, FLAT>(c.m, vln, vt);
+            if (pn > 0.0 && dot3(vt, vln) < c.o.v2max) {
+                ok = true;
+                break;
+            }
+            lam *= 0.5;
+        }
+        if (!ok || !isfinite(dp)) return false;
+        const double sv = lam * fmax(fabs(dv[0]), fmax(fabs(dv[1]), fabs(dv[2])));
+        const double sp = lam * dp;
+        pp = pn;
+        vl[0] = vln[0]; vl[1] = vln[1]; vl[2] = vln[2];
+        if (p_conv<FLAT>(c, sp, pp) && sv <= c.o.tol) {
+            raise<double, FLAT>(c.m, vl, v);
+            const double v2f = dot3(v, vl);
+            const double Wf = rsqrt(1.0 - v2f);
+            implicit_field<FLAT>(c, v, vl, v2f, Wf, E);
+            p = pp;
+            rho_out = c.in.D * ((1.0 - v2f) * Wf) * isg;
+            return true;
+        }
+    }
+    return false;
+}
+
 // Velocity equations at fixed p (x = v_lower):
 //   g_i = [v_i (tau + D + sqrt(g) p - EM) - (S_i - eta_ijk calE^j calB^k)] / scale
 template <bool FLAT>
@@ -654,13 +780,12 @@ __device__ int recover(const RecIn &in, const Met<double> &m, const RecOpts &o,
                     first = paper_run<FLAT>(c, s, guess_p, o.first_cap, E, rho, false, slow);
                 }
                 if (first == 0 && s.slow == 2) {
-                    // stiff switch (paper_run): the Newton fallback here, from
-                    // the stage guess; deferred only if it fails
-                    c.iD = 1.0 / in.D;
+                    // stiff switch (paper_run): the stiff-coupling Newton here,
+                    // from the stage guess; deferred only if it fails
                     double pn = guess_p, vn[3] = {guess_v[0], guess_v[1], guess_v[2]};
                     double En[3] = {in.cE0[0], in.cE0[1], in.cE0[2]}, rhon = 0.0;
                     int itn = 0;
-                    if (newton_fallback<FLAT>(c, pn, vn, En, rhon, itn)) {
+                    if (stiff_newton<FLAT>(c, pn, vn, En, rhon, itn)) {
                         newton_inline = true;
                         it1 = s.it;
                         it2 = itn;
@@ -713,7 +838,22 @@ __device__ int recover(const RecIn &in, const Met<double> &m, const RecOpts &o,
             p = guess_p;
             v[0] = guess_v[0]; v[1] = guess_v[1]; v[2] = guess_v[2];
             E[0] = in.cE0[0]; E[1] = in.cE0[1]; E[2] = in.cE0[2];
-            status = newton_fallback<FLAT>(c, p, v, E, rho, it2) ? 1 : 2;
+            // stiff-coupling Newton (implicit stages), then the damped
+            // forward-difference Newton, then the pressure bracket
+            status = 2;
+            if (implicit) {
+                status = stiff_newton<FLAT>(c, p, v, E, rho, it2) ? 1 : 2;
+                if (status == 2) {
+                    p = guess_p;
+                    v[0] = guess_v[0]; v[1] = guess_v[1]; v[2] = guess_v[2];
+                    E[0] = in.cE0[0]; E[1] = in.cE0[1]; E[2] = in.cE0[2];
+                }
+            }
+            if (status == 2) {
+                int itn = 0;
+                status = newton_fallback<FLAT>(c, p, v, E, rho, itn) ? 1 : 2;
+                it2 += itn;
+            }
             if (status == 2) {
                 int it3 = 0;
                 p = guess_p;

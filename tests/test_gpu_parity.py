@@ -95,12 +95,43 @@ def test_recovery_kernel_matches_oracle(torch_cuda, curved, implicit):
     ok = ~failed(ref_st)
     assert ok.mean() > 0.95
     # pointwise comparison scaled per point by the state's magnitudes
+    err = np.zeros(n)
     for f in range(14):
-        scale = np.maximum(np.abs(ref[f, ok]), np.abs(ref[:, ok]).max(axis=0) * 1e-3)
-        err = np.abs(prim[f, ok] - ref[f, ok]) / scale
-        assert err.max() < 1e-10, (f, err.max())
-    assert np.allclose(cout[:, ok], ref_c[:, ok], rtol=1e-10,
-                       atol=1e-10 * np.abs(ref_c[:, ok]).max())
+        scale = np.maximum(np.abs(ref[f]), np.abs(ref).max(axis=0) * 1e-3)
+        err = np.maximum(err, np.abs(prim[f] - ref[f]) / scale)
+    differ = ok & (err >= 1e-10)
+    # A stiff stage system can have more than one root (the paper assumes
+    # one; reading of the recovery's uniqueness): where the two sides land on
+    # different roots, both must solve the stage equations, and such points
+    # must stay rare.
+    assert differ.mean() < 0.002, np.where(differ)[0]
+    for i in np.where(differ)[0]:
+        for sol in (prim[:, i], ref[:, i]):
+            rf, re = _stage_residual(sol, cin[:, i], d["alpha"][i], d["g6"][:, i],
+                                     d["sigma"][i] * d["alpha"][i] * d["c"] if implicit else 0.0)
+            assert rf < 1e-11 and re < 1e-11, (i, rf, re)
+    same = ok & ~differ
+    assert np.allclose(cout[:, same], ref_c[:, same], rtol=1e-10,
+                       atol=1e-10 * np.abs(ref_c[:, same]).max())
+
+
+def _stage_residual(prim, cin, alpha, g6, cs):
+    """Relative residuals of a recovered primitive state against the stage
+    input it came from: the conserved D, S_i, tau, calB from the primitives
+    (fluid rows), and calE* = calE + cs W (calE + eps v x B - (v.calE) v)
+    (the implicit field equation; cs = 0 with calE fixed)."""
+    cons = oracle.prim2con(prim, alpha, (0, 0, 0), g6, 4.0 / 3.0)
+    gm = np.array([[g6[0], g6[1], g6[2]], [g6[1], g6[3], g6[4]], [g6[2], g6[4], g6[5]]])
+    sg = np.sqrt(np.linalg.det(gm))
+    v, B = prim[2:5], prim[8:11]
+    vl = gm @ v
+    W_ = 1.0 / np.sqrt(1.0 - vl @ v)
+    eps_vB = np.cross(vl, gm @ (sg * B)) / sg
+    E = cons[8:11]
+    Estar = E + cs * W_ * (E + eps_vB - (vl @ E) * v)
+    rf = np.abs(cons[:8] - cin[:8]).max() / np.abs(cin[:8]).max()
+    re = np.abs(Estar - cin[8:11]).max() / max(np.abs(cin[8:11]).max(), 1e-300)
+    return rf, re
 
 
 # ------------------------------------------------------------ explicit RHS
@@ -167,6 +198,8 @@ CASES = {
     "cyl_blast": lambda: W.cyl_blast(n=40, nz=4),
     # the 256^3 blast's resolution (dx = 0.047) on a smaller box
     "cyl_blast_hr": lambda: W.cyl_blast(n=64, nz=1, L=1.5),
+    # the 256^3 blast's resolution on a box the front does not leave in 100 steps
+    "cyl_blast_hr128": lambda: W.cyl_blast(n=128, nz=1, L=3.0),
     "lane_emden": lambda: W.lane_emden_star(n=20),
     "current_sheet": lambda: W.current_sheet(n=120),
     # density-dependent conductivity (Eqs. sigma_evol, dynamo_sigma)
@@ -204,12 +237,15 @@ def test_one_step_matches_oracle(name):
     assert ep.max() < TOL1, ("prim", ep)
 
 
-# Multi-step parity on runs whose recoveries all succeed (an atmosphere reset
-# is a discontinuous decision): the blast at the 256^3 resolution recovers
-# everywhere for its first 20 steps on this machine, the star for 10.
+# Multi-step parity.  An atmosphere reset is a discrete decision; the resets
+# of these runs are recoveries of states that have no root (a brute-force scan
+# of f(p) finds no sign change), which both sides reset alike.  The blast at
+# the 256^3 resolution on the [-1.5, 1.5]^2 box meets its outflow faces after
+# ~35 steps (20 here); on the [-3, 3]^2 box it recovers every cell for 100.
 @pytest.mark.parametrize("name,nsteps", [("brio_wu", 100), ("alfven_s1e6", 100),
                                          ("current_sheet", 100), ("cyl_blast_hr", 20),
-                                         ("lane_emden", 10), ("cyl_blast_sigma_powD", 10),
+                                         ("cyl_blast_hr128", 100),
+                                         ("lane_emden", 100), ("cyl_blast_sigma_powD", 10),
                                          ("lane_emden_sigma_atmo", 10), ("gauss_curved", 20),
                                          ("shocktube_sigma_D12", 640), ("shocktube_sigma_D6", 640),
                                          ("lane_emden_gauss", 10)])
@@ -221,6 +257,30 @@ def test_many_steps_match_oracle(name, nsteps):
     ec, ep = state_error(cons_g, cons_o, "cons", dx), state_error(prim_g, prim_o, "prim", dx)
     assert ec.max() < TOL100, ("cons", ec, so, sg)
     assert ep.max() < TOL100, ("prim", ep)
+
+
+def test_blast_at_64_cubed_matches_oracle_for_100_steps():
+    """The cylindrical explosion with the 256^3 configuration's parameters
+    (box [-6, 6]^3, MC2, sigma = 1e3, dt = dx/4) on a 64^3 grid, 100 steps
+    (the configuration's run length), z active on the GPU.  The initial data
+    do not depend on z and the boundary is outflow, so every z-layer of the
+    exact 3D run equals the oracle's 64 x 64 x 1 run (pinned bit for bit on
+    the CPU by test_z_uniform_blast_equals_its_plane); the oracle result is
+    that run broadcast along z.  Its recovery failures (~4700 over the 100
+    steps, states without a root) are reset alike on both sides."""
+    wl2 = W.cyl_blast(n=64, nz=1)
+    st_o, so, prim_o, cons_o = run_oracle(wl2, 100)
+    wl3 = W.cyl_blast(n=64)
+    fails, sg, prim_g, cons_g = run_gpu(wl3, 100)
+    assert so["c2p_failures"] > 0 and (fails > 0) == (st_o == -4)
+    dx = wl3.params["dx"]
+    for k in (0, 31, 63):
+        ec = state_error(cons_g[:, k:k + 1], cons_o, "cons", dx)
+        ep = state_error(prim_g[:, k:k + 1], prim_o, "prim", dx)
+        assert ec.max() < TOL100, ("cons", k, ec)
+        assert ep.max() < TOL100, ("prim", k, ep)
+    # every layer of the GPU run is the same (z-uniform to the bit)
+    assert all(np.array_equal(cons_g[:, k], cons_g[:, 0]) for k in range(64))
 
 
 @pytest.mark.parametrize("shape,bc", [((3, 1, 1), 0), ((1, 7, 1), 1), ((1, 1, 9), 0),

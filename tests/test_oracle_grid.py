@@ -313,3 +313,17 @@ def test_gauss_law_charge_totals_vanish_on_a_periodic_grid():
     st, _, prim, cons = _run(wl, 3)
     assert st == 0
     assert abs(cons[13].sum()) < 1e-13 * np.abs(cons[13]).sum()
+
+
+def test_z_uniform_blast_equals_its_plane():
+    """The cylindrical explosion does not depend on z and has outflow faces:
+    the z-face fluxes of identical neighbours are identical, their difference
+    is exactly zero, so every z-layer of a 3D run equals the 2D run of one
+    layer bit for bit (used to check the 64^3 configuration against a 64^2
+    oracle run for its 100 steps)."""
+    import workloads as W
+    from tests.helpers import run_oracle
+    _, _, p3, c3 = run_oracle(W.cyl_blast(n=12, nz=5), 4)
+    _, _, p2, c2 = run_oracle(W.cyl_blast(n=12, nz=1), 4)
+    for k in range(5):
+        assert np.array_equal(c3[:, k], c2[:, 0]) and np.array_equal(p3[:, k], p2[:, 0])
