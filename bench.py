@@ -12,14 +12,18 @@ the 128^3 Alfven cube (rmhd_adjoint_forward + rmhd_adjoint_backward); the
 "configs" object the Brio-Wu shocktube's latency per step, the 128^3
 Alfven cube and the 192^3 curved star (--no-adjoint, --no-configs skip them).
 
-Timing: W warm-up steps from the initial data, then K steps through
+Timing: untimed steps from the initial data (the W warm-up steps, then on
+to the middle of the configuration's 100-step run), then K steps through
 rmhd_step (one step captured as a CUDA graph and replayed: the product
 call), CUDA events on the launching stream with a synchronize on both
-sides; `value` is that window.  The same K steps are then re-run from the
-same state through rmhd_step_profiled (events between the kernel groups) for
-the per-kernel rooflines, and the configuration's whole 100-step run from
-the initial data is timed in ten blocks for both precisions ("run100",
-"fp64_run100"): the cost of a step grows as the blast evolves.
+sides; `value` is that window (steps 41-60 for K = 20).  The cost of a step
+grows as the blast evolves, and a window in the middle of the run costs
+about its mean.  The same K steps are then re-run from the same state
+through rmhd_step_profiled (events between the kernel groups) for the
+per-kernel rooflines, and the configuration's whole 100-step run from the
+initial data is timed in ten blocks for both precisions ("run100",
+"fp64_run100"), then run again with events between the kernel groups (ms per
+step of each group by block of ten steps).
 
 One JSON line on stdout (rank 0).  With N > 1 (torchrun) the grid is split
 into z-slabs, one per rank and GPU, with halos exchanged point to point after
@@ -308,6 +312,14 @@ def timed_steps(s, dt, k, torch, blocks=1):
 RUN_STEPS = 100   # the cylindrical-blast configuration's run length
 
 
+def window_start(args):
+    """Steps before the timed window.  The cost of a step grows as the blast
+    evolves, so the K timed steps sit in the middle of the configuration's
+    100-step run (steps 41-60 for K = 20), where the step costs about the
+    run's mean; at least the W warm-up steps precede them."""
+    return max(args.warmup, (RUN_STEPS - args.steps) // 2)
+
+
 def run_ours(args, rank, world, local):
     import torch
     import paper_2510_18968_b300 as R
@@ -323,7 +335,9 @@ def run_ours(args, rank, world, local):
     for prec in (["mixed", "fp64"] if args.precision == "both" else [args.precision]):
         s = R.Solver(dict(wl.params, precision=1 if prec == "mixed" else 0))
         s.set_prims(prim0)
-        s.step(wl.dt, args.warmup)          # W warm-up steps (and the graph capture)
+        # untimed steps up to the window: the W warm-up steps (and the graph
+        # capture), then on to the window's start in the middle of the run
+        s.step(wl.dt, window_start(args))
         torch.cuda.synchronize()
         # state at the start of the timed window (for the per-kernel leg)
         cons_w, prim_w = s.get_cons(), s.get_prims()
@@ -359,6 +373,20 @@ def run_ours(args, rank, world, local):
                    max(1, str1["c2p_calls"] - str0["c2p_calls"]),
                "atmosphere_resets": (str1["c2p_failures"] - str0["c2p_failures"]) +
                                     (str1["atmo_floor_resets"] - str0["atmo_floor_resets"])}
+        # the same run again with events between the kernel groups
+        # (rmhd_step_profiled): ms per step of each group, by block of ten steps
+        s.set_prims(prim0)
+        by_block = []
+        for b in range(10):
+            sb0 = s.stats()
+            g = s.step_profiled(wl.dt, RUN_STEPS // 10)
+            sb1 = s.stats()
+            calls = max(1, sb1["c2p_calls"] - sb0["c2p_calls"])
+            row = {k: v / (RUN_STEPS // 10) for k, v in g.items()}
+            row["iterations_per_recovery"] = (sb1["c2p_iterations"] - sb0["c2p_iterations"]) / calls
+            row["fallbacks_per_recovery"] = (sb1["c2p_fallbacks"] - sb0["c2p_fallbacks"]) / calls
+            by_block.append(row)
+        run["groups_ms_per_step_by_block"] = by_block
         # end-to-end through the public API with host buffers: every job
         # uploads the primitives of the evolved state from pinned host
         # memory (rmhd_set_prims), steps once and reads the primitives back
@@ -839,8 +867,11 @@ def main():
             "dtype": "f32+f64" if head == "mixed" else "f64", "data": "synthetic",
             "config": dict(cfg, precision=head, parallelism=f"replicas x{world}",
                            timed_call="rmhd_step (CUDA-graph replay)",
-                           window=f"steps {args.warmup + 1}-{args.warmup + args.steps} of the "
-                                  f"run from the initial data")}
+                           window=f"steps {window_start(args) + 1}-"
+                                  f"{window_start(args) + args.steps} of the {RUN_STEPS}-step "
+                                  f"run from the initial data (untimed before it: "
+                                  f"{window_start(args)} steps, the {args.warmup} warm-up "
+                                  f"steps among them)")}
     # the configuration's whole RUN_STEPS-step run from the initial data,
     # both precisions (the cost per step grows as the blast evolves, so a
     # short early window overstates the run's mean rate)

@@ -310,3 +310,67 @@ def step(params, metric, cons, prim, dt, nsteps=1, sigma_field=None,
     if fail_out is not None:
         lib().orc_set_fail_buffer(None, 0, None)
     return st, dict(zip(STAT_NAMES, list(stats)[:7]))
+
+
+# ------------------------------------------------------- tangent-linear model
+
+_tlib = None
+
+
+class _TL(ctypes.Structure):
+    """One tangent number passed by value (value, derivative)."""
+    _fields_ = [("v", ctypes.c_double), ("d", ctypes.c_double)]
+
+
+def tangent_lib():
+    """The tangent-linear build of the oracle (the same C source on tangent
+    numbers: value and directional derivative, oracle/tangent.h)."""
+    global _tlib
+    if _tlib is None:
+        L = ctypes.CDLL(_build.build_tangent())
+        P = ctypes.POINTER(_Params)
+        v = ctypes.c_void_p
+        L.orc_prim2con_grid.argtypes = [P, v, v, v, v, v]
+        L.orc_step.argtypes = [P, v, v, v, v, v, v, v, _TL, ctypes.c_int,
+                               ctypes.POINTER(ctypes.c_longlong)]
+        L.orc_step.restype = ctypes.c_int
+        L.orc_set_tangent_log_sigma0.argtypes = [ctypes.c_double]
+        _tlib = L
+    return _tlib
+
+
+def _tl(value, deriv=None):
+    """A tangent array: (..., 2) float64, value and derivative interleaved."""
+    value = np.asarray(value, dtype=np.float64)
+    out = np.zeros(value.shape + (2,))
+    out[..., 0] = value
+    if deriv is not None:
+        out[..., 1] = deriv
+    return out
+
+
+def tangent_step(params, metric, prim, dprim, dt, nsteps, sigma_field=None, dlog_sigma0=0.0):
+    """Tangent-linear model of nsteps IMEX-SSP2(2,2,2) steps (forward-mode
+    differentiation of the oracle's step, branches as the values take them):
+    from the primitives prim and a direction dprim of them (and dlog_sigma0
+    of log sigma0), returns (status, stats, prim^N, dprim^N), dprim^N the
+    derivative of the final primitives along that direction.  The initial
+    conserved state is formed from prim (and its derivative from dprim)."""
+    L = tangent_lib()
+    prim = _arr(prim)
+    P = _grid_params(params, prim.shape[1:])
+    tp = np.ascontiguousarray(_tl(prim, dprim))
+    tc = np.zeros_like(tp)
+    ta, tb = _tl(metric.alpha), _tl(metric.beta)
+    tg, tk = _tl(metric.gamma), _tl(metric.K)
+    tsf = None if sigma_field is None else _tl(sigma_field)
+    p = lambda a: None if a is None else a.ctypes.data
+    L.orc_prim2con_grid(ctypes.byref(P), p(ta), p(tb), p(tg), p(tp), p(tc))
+    stats = (ctypes.c_longlong * 8)()
+    L.orc_set_tangent_log_sigma0(float(dlog_sigma0))
+    try:
+        st = L.orc_step(ctypes.byref(P), p(ta), p(tb), p(tg), p(tk), p(tsf), p(tc), p(tp),
+                        _TL(float(dt), 0.0), int(nsteps), stats)
+    finally:
+        L.orc_set_tangent_log_sigma0(0.0)
+    return st, dict(zip(STAT_NAMES, list(stats)[:7])), tp[..., 0].copy(), tp[..., 1].copy()

@@ -34,11 +34,21 @@
  *    velocity equations solved at each trial pressure); if that fails, the
  *    cell is reset to the atmosphere.
  */
+#ifdef ORC_TANGENT
+#include "tangent.h"
+typedef tl orc_real;
+#define VAL(x) ((x).v)
+#else
+#define VAL(x) (x)
+#endif
 #include "rmhd_oracle.h"
 
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+
+/* the arithmetic type (double; a tangent number in the tangent-linear build) */
+typedef orc_real real;
 
 enum { P_RHO, P_P, P_VX, P_VY, P_VZ, P_EX, P_EY, P_EZ, P_BX, P_BY, P_BZ,
        P_PSI, P_PHI, P_Q };
@@ -46,7 +56,7 @@ enum { C_D, C_SX, C_SY, C_SZ, C_TAU, C_BX, C_BY, C_BZ, C_EX, C_EY, C_EZ,
        C_PHI, C_PSI, C_Q };
 
 /* gamma of the IMEX-SSP2(2,2,2) tableau (Table imex): 1 - 1/sqrt(2) */
-static double imex_gamma(void) { return 1.0 - 1.0 / sqrt(2.0); }
+static real imex_gamma(void) { return 1.0 - 1.0 / sqrt(2.0); }
 
 /* Double Butcher tableaux (Sec. III.A): explicit At (strictly lower
  * triangular) with weights wt, implicit A (lower triangular, DIRK) with
@@ -67,13 +77,13 @@ static double imex_gamma(void) { return 1.0 - 1.0 / sqrt(2.0); }
  * Returns the number of stages, 0 for an unknown scheme. */
 typedef struct {
     int s;
-    double At[4][4], wt[4], A[4][4], w[4];
+    real At[4][4], wt[4], A[4][4], w[4];
 } imex_tab;
 
 static int imex_tableau(int scheme, imex_tab *T)
 {
     memset(T, 0, sizeof(*T));
-    double g = imex_gamma();
+    real g = imex_gamma();
     switch (scheme) {
     case 0:
         T->s = 2;
@@ -109,7 +119,7 @@ static int imex_tableau(int scheme, imex_tab *T)
         for (int i = 0; i < 3; i++) T->w[i] = T->wt[i];
         break;
     case 3: {
-        const double a = 0.24169426078821, b = 0.06042356519705, e = 0.12915286960590;
+        const real a = 0.24169426078821, b = 0.06042356519705, e = 0.12915286960590;
         T->s = 4;
         T->At[2][1] = 1.0;
         T->At[3][1] = 0.25;
@@ -134,7 +144,7 @@ static int imex_tableau(int scheme, imex_tab *T)
     return T->s;
 }
 
-int orc_imex_tableau(int scheme, double At[16], double wt[4], double A[16], double w[4])
+int orc_imex_tableau(int scheme, real At[16], real wt[4], real A[16], real w[4])
 {
     imex_tab T;
     int s = imex_tableau(scheme, &T);
@@ -150,13 +160,13 @@ int orc_imex_tableau(int scheme, double At[16], double wt[4], double A[16], doub
 }
 
 /* Levi-Civita symbol eta_{ijk} (= eta^{ijk}), indices 0..2 */
-static double levi(int i, int j, int k)
+static real levi(int i, int j, int k)
 {
-    return (double)((i - j) * (j - k) * (k - i) / 2);
+    return (real)((i - j) * (j - k) * (k - i) / 2);
 }
 
 /* symmetric 3x3 from (xx,xy,xz,yy,yz,zz) */
-static void unpack6(const double g6[6], double g[3][3])
+static void unpack6(const real g6[6], real g[3][3])
 {
     g[0][0] = g6[0]; g[0][1] = g6[1]; g[0][2] = g6[2];
     g[1][0] = g6[1]; g[1][1] = g6[3]; g[1][2] = g6[4];
@@ -164,22 +174,22 @@ static void unpack6(const double g6[6], double g[3][3])
 }
 
 typedef struct {
-    double alpha, beta[3];
-    double g[3][3], gi[3][3];
-    double sg; /* sqrt(det gamma_ij) */
+    real alpha, beta[3];
+    real g[3][3], gi[3][3];
+    real sg; /* sqrt(det gamma_ij) */
 } metric_pt;
 
 /* Sec. II.A: gamma^{ij} is the algebraic inverse of gamma_ij; sqrt(gamma). */
-static void make_metric(double alpha, const double beta[3], const double g6[6],
+static void make_metric(real alpha, const real beta[3], const real g6[6],
                         metric_pt *m)
 {
-    double g[3][3];
+    real g[3][3];
     unpack6(g6, g);
-    double c00 = g[1][1] * g[2][2] - g[1][2] * g[2][1];
-    double c01 = g[1][2] * g[2][0] - g[1][0] * g[2][2];
-    double c02 = g[1][0] * g[2][1] - g[1][1] * g[2][0];
-    double det = g[0][0] * c00 + g[0][1] * c01 + g[0][2] * c02;
-    double cof[3][3];
+    real c00 = g[1][1] * g[2][2] - g[1][2] * g[2][1];
+    real c01 = g[1][2] * g[2][0] - g[1][0] * g[2][2];
+    real c02 = g[1][0] * g[2][1] - g[1][1] * g[2][0];
+    real det = g[0][0] * c00 + g[0][1] * c01 + g[0][2] * c02;
+    real cof[3][3];
     cof[0][0] = c00; cof[0][1] = c01; cof[0][2] = c02;
     cof[1][0] = g[0][2] * g[2][1] - g[0][1] * g[2][2];
     cof[1][1] = g[0][0] * g[2][2] - g[0][2] * g[2][0];
@@ -197,9 +207,9 @@ static void make_metric(double alpha, const double beta[3], const double g6[6],
     for (int i = 0; i < 3; i++) m->beta[i] = beta ? beta[i] : 0.0;
 }
 
-void orc_metric_inverse(const double g6[6], double ginv6[6], double *sqrtg)
+void orc_metric_inverse(const real g6[6], real ginv6[6], real *sqrtg)
 {
-    static const double zero3[3] = {0, 0, 0};
+    static const real zero3[3] = {0, 0, 0};
     metric_pt m;
     make_metric(1.0, zero3, g6, &m);
     ginv6[0] = m.gi[0][0]; ginv6[1] = m.gi[0][1]; ginv6[2] = m.gi[0][2];
@@ -207,7 +217,7 @@ void orc_metric_inverse(const double g6[6], double ginv6[6], double *sqrtg)
     *sqrtg = m.sg;
 }
 
-static void lower(const metric_pt *m, const double u[3], double ul[3])
+static void lower(const metric_pt *m, const real u[3], real ul[3])
 {
     for (int i = 0; i < 3; i++) {
         ul[i] = 0.0;
@@ -215,7 +225,7 @@ static void lower(const metric_pt *m, const double u[3], double ul[3])
     }
 }
 
-static void raise(const metric_pt *m, const double ul[3], double u[3])
+static void raise(const metric_pt *m, const real ul[3], real u[3])
 {
     for (int i = 0; i < 3; i++) {
         u[i] = 0.0;
@@ -223,19 +233,19 @@ static void raise(const metric_pt *m, const double ul[3], double u[3])
     }
 }
 
-static double dot3(const double a[3], const double b[3])
+static real dot3(const real a[3], const real b[3])
 {
     return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
 }
 
 /* Primitive quantities derived at one point (Sec. II.A, II.C). */
 typedef struct {
-    double rho, p, eps, h, W, v2;
-    double v[3], vl[3], E[3], El[3], B[3], Bl[3];
-    double E2, B2;
+    real rho, p, eps, h, W, v2;
+    real v[3], vl[3], E[3], El[3], B[3], Bl[3];
+    real E2, B2;
 } prim_pt;
 
-static void derive_prim(const double *pr, const metric_pt *m, double Gam,
+static void derive_prim(const real *pr, const metric_pt *m, real Gam,
                         prim_pt *q)
 {
     q->rho = pr[P_RHO];
@@ -259,16 +269,16 @@ static void derive_prim(const double *pr, const metric_pt *m, double Gam,
 /* Eqs. conserved_dens, conserved_tau, conserved_S and the densitised
  * electromagnetic variables calE = sqrt(g) E, calB = sqrt(g) B,
  * Psi = sqrt(g) psi, Phi = sqrt(g) phi, Q = sqrt(g) q (Sec. II.D). */
-static void prim_to_cons(const double *pr, const metric_pt *m, double Gam,
-                         const prim_pt *q, double *c)
+static void prim_to_cons(const real *pr, const metric_pt *m, real Gam,
+                         const prim_pt *q, real *c)
 {
-    double sg = m->sg;
-    double hW2 = q->h * q->W * q->W;
+    real sg = m->sg;
+    real hW2 = q->h * q->W * q->W;
     c[C_D] = sg * q->rho * q->W;
     c[C_TAU] = sg * (hW2 - q->p + 0.5 * (q->E2 + q->B2)) - c[C_D];
     for (int i = 0; i < 3; i++) {
         /* epsilon_{ijk} E^j B^k with epsilon_{ijk} = sqrt(g) eta_{ijk} */
-        double cross = 0.0;
+        real cross = 0.0;
         for (int j = 0; j < 3; j++)
             for (int k = 0; k < 3; k++)
                 cross += sg * levi(i, j, k) * q->E[j] * q->B[k];
@@ -282,8 +292,8 @@ static void prim_to_cons(const double *pr, const metric_pt *m, double Gam,
     (void)Gam;
 }
 
-void orc_prim2con(const double prim[14], double alpha, const double beta[3],
-                  const double g6[6], double gamma_eos, double cons[14])
+void orc_prim2con(const real prim[14], real alpha, const real beta[3],
+                  const real g6[6], real gamma_eos, real cons[14])
 {
     metric_pt m;
     prim_pt q;
@@ -295,30 +305,30 @@ void orc_prim2con(const double prim[14], double alpha, const double beta[3],
 /* Flux vector F^d of Eq. GRRMHD_flux_form in direction d.  The current in
  * the charge flux is Ohm's law (Eq. Ohm_law) at this state, or the given
  * value *Jd when Jd is not NULL.  Returns also the conserved vector. */
-static void flux_point(int d, const double *pr, const metric_pt *m,
-                       double sigma, double Gam, const double *Jd, double *F,
-                       double *c)
+static void flux_point(int d, const real *pr, const metric_pt *m,
+                       real sigma, real Gam, const real *Jd, real *F,
+                       real *c)
 {
     prim_pt q;
     derive_prim(pr, m, Gam, &q);
     prim_to_cons(pr, m, Gam, &q, c);
-    double a = m->alpha, bd = m->beta[d], sg = m->sg;
-    double hW2 = q.h * q.W * q.W;
+    real a = m->alpha, bd = m->beta[d], sg = m->sg;
+    real hW2 = q.h * q.W * q.W;
 
     F[C_D] = (a * q.v[d] - bd) * c[C_D];
     for (int i = 0; i < 3; i++) {
         /* undensitised mixed stress S^d_i (Eq. conserved_Sij, see header) */
-        double delta = (i == d) ? 1.0 : 0.0;
-        double Sdi = hW2 * q.v[d] * q.vl[i] + delta * q.p
+        real delta = (i == d) ? 1.0 : 0.0;
+        real Sdi = hW2 * q.v[d] * q.vl[i] + delta * q.p
                      - q.E[d] * q.El[i] - q.B[d] * q.Bl[i]
                      + 0.5 * delta * (q.E2 + q.B2);
         F[C_SX + i] = a * sg * Sdi - bd * c[C_SX + i];
     }
-    double Sup_d = 0.0;
+    real Sup_d = 0.0;
     for (int j = 0; j < 3; j++) Sup_d += m->gi[d][j] * c[C_SX + j];
     F[C_TAU] = a * (Sup_d - q.v[d] * c[C_D]) - bd * c[C_TAU];
 
-    double cE[3], cB[3], cEl[3], cBl[3];
+    real cE[3], cB[3], cEl[3], cBl[3];
     for (int i = 0; i < 3; i++) {
         cE[i] = c[C_EX + i];
         cB[i] = c[C_BX + i];
@@ -326,7 +336,7 @@ static void flux_point(int d, const double *pr, const metric_pt *m,
     lower(m, cE, cEl);
     lower(m, cB, cBl);
     for (int i = 0; i < 3; i++) {
-        double curlE = 0.0, curlB = 0.0; /* epsilon^{i d j} X_j */
+        real curlE = 0.0, curlB = 0.0; /* epsilon^{i d j} X_j */
         for (int j = 0; j < 3; j++) {
             curlE += levi(i, d, j) / sg * cEl[j];
             curlB += levi(i, d, j) / sg * cBl[j];
@@ -339,19 +349,19 @@ static void flux_point(int d, const double *pr, const metric_pt *m,
 
     /* Ohm's law: J^d = Q v^d + W sigma [calE^d + eps^{djk} v_j calB_k
      *                                    - (v_k calE^k) v^d]              */
-    double vxB = 0.0;
+    real vxB = 0.0;
     for (int j = 0; j < 3; j++)
         for (int k = 0; k < 3; k++)
             vxB += levi(d, j, k) / sg * q.vl[j] * cBl[k];
-    double vE = dot3(q.vl, cE);
-    double J = c[C_Q] * q.v[d] + q.W * sigma * (cE[d] + vxB - vE * q.v[d]);
+    real vE = dot3(q.vl, cE);
+    real J = c[C_Q] * q.v[d] + q.W * sigma * (cE[d] + vxB - vE * q.v[d]);
     if (Jd) J = *Jd;
     F[C_Q] = a * J - bd * c[C_Q];
 }
 
-void orc_flux(int d, const double prim[14], double alpha, const double beta[3],
-              const double g6[6], double sigma, double gamma_eos,
-              double flux[14], double cons[14])
+void orc_flux(int d, const real prim[14], real alpha, const real beta[3],
+              const real g6[6], real sigma, real gamma_eos,
+              real flux[14], real cons[14])
 {
     metric_pt m;
     make_metric(alpha, beta, g6, &m);
@@ -360,24 +370,24 @@ void orc_flux(int d, const double prim[14], double alpha, const double beta[3],
 
 /* HLLE flux with the light-speed characteristic speeds of Sec. III:
  * lambda_+- = +-sqrt(gamma^dd) - beta^d/alpha. */
-static void hlle_point(int d, const double *pL, const double *pR,
-                       const metric_pt *m, double sigma, double Gam,
-                       const double *JL, const double *JR, double *F)
+static void hlle_point(int d, const real *pL, const real *pR,
+                       const metric_pt *m, real sigma, real Gam,
+                       const real *JL, const real *JR, real *F)
 {
-    double FL[14], FR[14], UL[14], UR[14];
+    real FL[14], FR[14], UL[14], UR[14];
     flux_point(d, pL, m, sigma, Gam, JL, FL, UL);
     flux_point(d, pR, m, sigma, Gam, JR, FR, UR);
-    double lp = sqrt(m->gi[d][d]) - m->beta[d] / m->alpha;
-    double lm = -sqrt(m->gi[d][d]) - m->beta[d] / m->alpha;
-    double ap = lp > 0.0 ? lp : 0.0;
-    double am = lm < 0.0 ? lm : 0.0;
+    real lp = sqrt(m->gi[d][d]) - m->beta[d] / m->alpha;
+    real lm = -sqrt(m->gi[d][d]) - m->beta[d] / m->alpha;
+    real ap = lp > 0.0 ? lp : 0.0;
+    real am = lm < 0.0 ? lm : 0.0;
     for (int f = 0; f < 14; f++)
         F[f] = (ap * FL[f] - am * FR[f] + ap * am * (UR[f] - UL[f])) / (ap - am);
 }
 
-void orc_hlle(int d, const double primL[14], const double primR[14],
-              double alpha, const double beta[3], const double g6[6],
-              double sigma, double gamma_eos, double flux[14])
+void orc_hlle(int d, const real primL[14], const real primR[14],
+              real alpha, const real beta[3], const real g6[6],
+              real sigma, real gamma_eos, real flux[14])
 {
     metric_pt m;
     make_metric(alpha, beta, g6, &m);
@@ -386,13 +396,13 @@ void orc_hlle(int d, const double primL[14], const double primR[14],
 
 /* ---------------- reconstruction (Sec. III: TVD and WENO) ---------------- */
 
-static double minmod2(double a, double b)
+static real minmod2(real a, real b)
 {
     if (a * b <= 0.0) return 0.0;
     return fabs(a) <= fabs(b) ? a : b;
 }
 
-static double minmod3(double a, double b, double c)
+static real minmod3(real a, real b, real c)
 {
     if (a > 0.0 && b > 0.0 && c > 0.0) return fmin(a, fmin(b, c));
     if (a < 0.0 && b < 0.0 && c < 0.0) return fmax(a, fmax(b, c));
@@ -400,7 +410,7 @@ static double minmod3(double a, double b, double c)
 }
 
 /* limited slope of the middle value um|u0|up */
-static double tvd_slope(int method, double um, double u0, double up)
+static real tvd_slope(int method, real um, real u0, real up)
 {
     if (method == 0) return minmod2(u0 - um, up - u0);           /* minmod */
     return minmod3(2.0 * (u0 - um), 0.5 * (up - um), 2.0 * (up - u0)); /* MC2 */
@@ -409,29 +419,29 @@ static double tvd_slope(int method, double um, double u0, double up)
 /* Jiang-Shu WENO5 value at the face between c and d, from the stencil
  * (a,b,c,d,e) = u_{i-2..i+2}; linear weights 1/10, 6/10, 3/10, eps 1e-6,
  * power 2. */
-static double weno5_face(double a, double b, double c, double d, double e)
+static real weno5_face(real a, real b, real c, real d, real e)
 {
-    const double eps = 1e-6;
-    double q0 = (2.0 * a - 7.0 * b + 11.0 * c) / 6.0;
-    double q1 = (-b + 5.0 * c + 2.0 * d) / 6.0;
-    double q2 = (2.0 * c + 5.0 * d - e) / 6.0;
-    double t;
-    double b0, b1, b2;
+    const real eps = 1e-6;
+    real q0 = (2.0 * a - 7.0 * b + 11.0 * c) / 6.0;
+    real q1 = (-b + 5.0 * c + 2.0 * d) / 6.0;
+    real q2 = (2.0 * c + 5.0 * d - e) / 6.0;
+    real t;
+    real b0, b1, b2;
     t = a - 2.0 * b + c;       b0 = 13.0 / 12.0 * t * t;
     t = a - 4.0 * b + 3.0 * c; b0 += 0.25 * t * t;
     t = b - 2.0 * c + d;       b1 = 13.0 / 12.0 * t * t;
     t = b - d;                 b1 += 0.25 * t * t;
     t = c - 2.0 * d + e;       b2 = 13.0 / 12.0 * t * t;
     t = 3.0 * c - 4.0 * d + e; b2 += 0.25 * t * t;
-    double w0 = 0.1 / ((eps + b0) * (eps + b0));
-    double w1 = 0.6 / ((eps + b1) * (eps + b1));
-    double w2 = 0.3 / ((eps + b2) * (eps + b2));
+    real w0 = 0.1 / ((eps + b0) * (eps + b0));
+    real w1 = 0.6 / ((eps + b1) * (eps + b1));
+    real w2 = 0.3 / ((eps + b2) * (eps + b2));
     return (w0 * q0 + w1 * q1 + w2 * q2) / (w0 + w1 + w2);
 }
 
 /* Left and right states at the face between s[2] and s[3] of the six-point
  * stencil s[0..5] = u_{i-2..i+3}. */
-static void recon_face(int method, const double s[6], double *uL, double *uR)
+static void recon_face(int method, const real s[6], real *uL, real *uR)
 {
     if (method == 2) {
         *uL = weno5_face(s[0], s[1], s[2], s[3], s[4]);
@@ -442,13 +452,13 @@ static void recon_face(int method, const double s[6], double *uL, double *uR)
     }
 }
 
-void orc_recon_line(int method, int n, const double *u, double *uL, double *uR)
+void orc_recon_line(int method, int n, const real *u, real *uL, real *uR)
 {
     for (int i = 0; i < n; i++) {
         uL[i] = NAN;
         uR[i] = NAN;
         if (i - 2 < 0 || i + 3 > n - 1) continue;
-        double s[6];
+        real s[6];
         for (int o = 0; o < 6; o++) s[o] = u[i - 2 + o];
         recon_face(method, s, &uL[i], &uR[i]);
     }
@@ -458,7 +468,7 @@ void orc_recon_line(int method, int n, const double *u, double *uL, double *uR)
 
 /* Solve the 3x3 system A x = b by Gaussian elimination with partial pivoting;
  * returns 0 if singular. */
-static int solve_dense(int n, double *A, double *b, double *x)
+static int solve_dense(int n, real *A, real *b, real *x)
 {
     for (int col = 0; col < n; col++) {
         int piv = col;
@@ -467,20 +477,20 @@ static int solve_dense(int n, double *A, double *b, double *x)
         if (A[piv * n + col] == 0.0) return 0;
         if (piv != col) {
             for (int c = 0; c < n; c++) {
-                double t = A[col * n + c];
+                real t = A[col * n + c];
                 A[col * n + c] = A[piv * n + c];
                 A[piv * n + c] = t;
             }
-            double t = b[col]; b[col] = b[piv]; b[piv] = t;
+            real t = b[col]; b[col] = b[piv]; b[piv] = t;
         }
         for (int r = col + 1; r < n; r++) {
-            double f = A[r * n + col] / A[col * n + col];
+            real f = A[r * n + col] / A[col * n + col];
             for (int c = col; c < n; c++) A[r * n + c] -= f * A[col * n + c];
             b[r] -= f * b[col];
         }
     }
     for (int r = n - 1; r >= 0; r--) {
-        double s = b[r];
+        real s = b[r];
         for (int c = r + 1; c < n; c++) s -= A[r * n + c] * x[c];
         x[r] = s / A[r * n + r];
     }
@@ -491,15 +501,15 @@ static int solve_dense(int n, double *A, double *b, double *x)
  *   + cc * (calE + eps^{ijk} v_j calB_k - (v_k calE^k) v^i),  cc = c alpha W sigma
  * (Eq. 3D_NR with c = a_ii Dt).  Starting from E (in/out).  Being linear in
  * calE, one step lands on the root; further steps only polish rounding. */
-static int implicit_E_nr(const metric_pt *m, const double Estar[3],
-                         const double cB[3], const double v[3], double W,
-                         double sigma, double c, double E[3])
+static int implicit_E_nr(const metric_pt *m, const real Estar[3],
+                         const real cB[3], const real v[3], real W,
+                         real sigma, real c, real E[3])
 {
-    double vl[3], cBl[3];
+    real vl[3], cBl[3];
     lower(m, v, vl);
     lower(m, cB, cBl);
-    double cc = c * m->alpha * W * sigma;
-    double vxB[3];
+    real cc = c * m->alpha * W * sigma;
+    real vxB[3];
     for (int i = 0; i < 3; i++) {
         vxB[i] = 0.0;
         for (int j = 0; j < 3; j++)
@@ -507,15 +517,15 @@ static int implicit_E_nr(const metric_pt *m, const double Estar[3],
                 vxB[i] += levi(i, j, k) / m->sg * vl[j] * cBl[k];
     }
     for (int it = 0; it < 4; it++) {
-        double vE = dot3(vl, E);
-        double f[3], J[9], dE[3];
+        real vE = dot3(vl, E);
+        real f[3], J[9], dE[3];
         for (int i = 0; i < 3; i++) {
             f[i] = E[i] - Estar[i] + cc * (E[i] + vxB[i] - vE * v[i]);
             for (int j = 0; j < 3; j++)
                 J[i * 3 + j] = (i == j ? 1.0 + cc : 0.0) - cc * v[i] * vl[j];
         }
         if (!solve_dense(3, J, f, dE)) return 0;
-        double dmax = 0.0, emax = 0.0;
+        real dmax = 0.0, emax = 0.0;
         for (int i = 0; i < 3; i++) {
             E[i] -= dE[i];
             if (fabs(dE[i]) > dmax) dmax = fabs(dE[i]);
@@ -526,15 +536,15 @@ static int implicit_E_nr(const metric_pt *m, const double Estar[3],
     return 1;
 }
 
-int orc_implicit_E(const double Estar[3], const double Bcons[3],
-                   const double v[3], double alpha, const double g6[6],
-                   double sigma, double c, double Eout[3])
+int orc_implicit_E(const real Estar[3], const real Bcons[3],
+                   const real v[3], real alpha, const real g6[6],
+                   real sigma, real c, real Eout[3])
 {
     metric_pt m;
     make_metric(alpha, NULL, g6, &m);
-    double vl[3];
+    real vl[3];
     lower(&m, v, vl);
-    double W = 1.0 / sqrt(1.0 - dot3(v, vl));
+    real W = 1.0 / sqrt(1.0 - dot3(v, vl));
     for (int i = 0; i < 3; i++) Eout[i] = Estar[i];
     return implicit_E_nr(&m, Estar, Bcons, v, W, sigma, c, Eout);
 }
@@ -544,27 +554,27 @@ int orc_implicit_E(const double Estar[3], const double Bcons[3],
 typedef struct {
     const orc_params *P;
     const metric_pt *m;
-    double D, Sl[3], tau, cB[3], cE0[3];
+    real D, Sl[3], tau, cB[3], cE0[3];
     int implicit;
-    double c, sigma, v2max;
+    real c, sigma, v2max;
 } c2p_in;
 
 /* Step (iii): velocity, W, rho, eps from the conserved variables, the current
  * electric field and pressure p.  Returns 0 when v^2 >= v2max or the
  * denominator is not positive. */
-static int recover_fluid(const c2p_in *in, const double cE[3], double p,
-                         double vl[3], double v[3], double *v2, double *W,
-                         double *rho, double *eps)
+static int recover_fluid(const c2p_in *in, const real cE[3], real p,
+                         real vl[3], real v[3], real *v2, real *W,
+                         real *rho, real *eps)
 {
     const metric_pt *m = in->m;
-    double sg = m->sg;
-    double cEl[3], cBl[3];
+    real sg = m->sg;
+    real cEl[3], cBl[3];
     lower(m, cE, cEl);
     lower(m, in->cB, cBl);
-    double EM = (dot3(cE, cEl) + dot3(in->cB, cBl)) / (2.0 * sg);
-    double den = in->tau + in->D + sg * p - EM;
+    real EM = (dot3(cE, cEl) + dot3(in->cB, cBl)) / (2.0 * sg);
+    real den = in->tau + in->D + sg * p - EM;
     for (int i = 0; i < 3; i++) {
-        double cross = 0.0; /* eta_{ijk} calE^j calB^k */
+        real cross = 0.0; /* eta_{ijk} calE^j calB^k */
         for (int j = 0; j < 3; j++)
             for (int k = 0; k < 3; k++)
                 cross += levi(i, j, k) * cE[j] * in->cB[k];
@@ -581,9 +591,9 @@ static int recover_fluid(const c2p_in *in, const double cE[3], double p,
 }
 
 /* energy scale used in the pressure stopping test: tau + D + sqrt(g) p */
-static int p_converged(const c2p_in *in, double dp, double p)
+static int p_converged(const c2p_in *in, real dp, real p)
 {
-    double sg = in->m->sg;
+    real sg = in->m->sg;
     return fabs(dp) * sg <= in->P->c2p_tol * (in->tau + in->D + sg * p);
 }
 
@@ -594,33 +604,33 @@ static int p_converged(const c2p_in *in, double dp, double p)
  * Returns 1 on convergence, 0 when the cap is reached or an iterate leaves
  * the physical region (v^2 >= v2max, a non-positive denominator in step
  * (iii), a non-finite value). */
-static int c2p_paper(const c2p_in *in, double *p_io, double v_io[3],
-                     double cE[3], double *rho_o, int *iters)
+static int c2p_paper(const c2p_in *in, real *p_io, real v_io[3],
+                     real cE[3], real *rho_o, int *iters)
 {
-    double Gam = in->P->gamma_eos;
-    double p = *p_io, v[3] = {v_io[0], v_io[1], v_io[2]};
+    real Gam = in->P->gamma_eos;
+    real p = *p_io, v[3] = {v_io[0], v_io[1], v_io[2]};
     for (int it = 1; it <= in->P->c2p_maxit; it++) {
         *iters = it;
         if (in->implicit) {
-            double vl[3];
+            real vl[3];
             lower(in->m, v, vl);
-            double v2 = dot3(v, vl);
+            real v2 = dot3(v, vl);
             if (!(v2 < in->v2max)) return 0;
-            double W = 1.0 / sqrt(1.0 - v2);
+            real W = 1.0 / sqrt(1.0 - v2);
             if (!implicit_E_nr(in->m, in->cE0, in->cB, v, W, in->sigma, in->c, cE))
                 return 0;
         }
-        double vl[3], vn[3], v2, W, rho, eps;
+        real vl[3], vn[3], v2, W, rho, eps;
         if (!recover_fluid(in, cE, p, vl, vn, &v2, &W, &rho, &eps)) return 0;
-        double f = (Gam - 1.0) * rho * eps - p;
-        double cs2 = eps > 0.0 ? Gam * (Gam - 1.0) * eps / (1.0 + Gam * eps) : 0.0;
-        double fp = v2 * cs2 - 1.0;
-        double pn = p - f / fp;
+        real f = (Gam - 1.0) * rho * eps - p;
+        real cs2 = eps > 0.0 ? Gam * (Gam - 1.0) * eps / (1.0 + Gam * eps) : 0.0;
+        real fp = v2 * cs2 - 1.0;
+        real pn = p - f / fp;
         if (!(pn > 0.0)) pn = 0.1 * p;
-        double dv = 0.0;
+        real dv = 0.0;
         for (int i = 0; i < 3; i++)
             if (fabs(vn[i] - v[i]) > dv) dv = fabs(vn[i] - v[i]);
-        double dp = pn - p;
+        real dp = pn - p;
         if (!isfinite(pn) || !isfinite(dv)) return 0;
         p = pn;
         for (int i = 0; i < 3; i++) v[i] = vn[i];
@@ -637,26 +647,26 @@ static int c2p_paper(const c2p_in *in, double *p_io, double v_io[3],
 /* Residual of the velocity equations at fixed pressure p:
  *   g_i = [v_i (tau + D + sqrt(g) p - EM) - (S_i - eta_ijk calE^j calB^k)] / scale
  * with calE from the implicit solve at v (or fixed); x = v_lower. */
-static int vel_resid(const c2p_in *in, double p, const double vl[3], double g[3],
-                     double cE[3])
+static int vel_resid(const c2p_in *in, real p, const real vl[3], real g[3],
+                     real cE[3])
 {
-    double v[3];
+    real v[3];
     raise(in->m, vl, v);
-    double v2 = dot3(v, vl);
+    real v2 = dot3(v, vl);
     if (!(v2 < in->v2max)) return 0;
-    double W = 1.0 / sqrt(1.0 - v2);
+    real W = 1.0 / sqrt(1.0 - v2);
     for (int i = 0; i < 3; i++) cE[i] = in->cE0[i];
     if (in->implicit &&
         !implicit_E_nr(in->m, in->cE0, in->cB, v, W, in->sigma, in->c, cE))
         return 0;
-    double sg = in->m->sg, cEl[3], cBl[3];
+    real sg = in->m->sg, cEl[3], cBl[3];
     lower(in->m, cE, cEl);
     lower(in->m, in->cB, cBl);
-    double EM = (dot3(cE, cEl) + dot3(in->cB, cBl)) / (2.0 * sg);
-    double scale = in->tau + in->D + sg * p;
-    double den = scale - EM;
+    real EM = (dot3(cE, cEl) + dot3(in->cB, cBl)) / (2.0 * sg);
+    real scale = in->tau + in->D + sg * p;
+    real den = scale - EM;
     for (int i = 0; i < 3; i++) {
-        double cross = 0.0;
+        real cross = 0.0;
         for (int j = 0; j < 3; j++)
             for (int k = 0; k < 3; k++)
                 cross += levi(i, j, k) * cE[j] * in->cB[k];
@@ -665,20 +675,20 @@ static int vel_resid(const c2p_in *in, double p, const double vl[3], double g[3]
     return 1;
 }
 
-static double norm3(const double g[3])
+static real norm3(const real g[3])
 {
     return sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
 }
 
 /* Velocity at fixed p: damped Newton on vel_resid from vl (in/out). */
-static int solve_velocity(const c2p_in *in, double p, double vl[3])
+static int solve_velocity(const c2p_in *in, real p, real vl[3])
 {
-    double g[3], cE[3];
+    real g[3], cE[3];
     if (!vel_resid(in, p, vl, g, cE)) return 0;
     for (int it = 0; it < 30; it++) {
-        double J[9], rhs[3], dv[3];
+        real J[9], rhs[3], dv[3];
         for (int col = 0; col < 3; col++) {
-            double vh[3] = {vl[0], vl[1], vl[2]}, gh[3], h = 1e-7;
+            real vh[3] = {vl[0], vl[1], vl[2]}, gh[3], h = 1e-7;
             vh[col] += h;
             if (!vel_resid(in, p, vh, gh, cE)) {
                 h = -h;
@@ -689,7 +699,7 @@ static int solve_velocity(const c2p_in *in, double p, double vl[3])
         }
         for (int i = 0; i < 3; i++) rhs[i] = -g[i];
         if (!solve_dense(3, J, rhs, dv)) return 0;
-        double lam = 1.0, vt[3], gt[3];
+        real lam = 1.0, vt[3], gt[3];
         int ok = 0;
         for (int ls = 0; ls < 40; ls++) {
             for (int i = 0; i < 3; i++) vt[i] = vl[i] + lam * dv[i];
@@ -700,7 +710,7 @@ static int solve_velocity(const c2p_in *in, double p, double vl[3])
             lam *= 0.5;
         }
         if (!ok) return norm3(g) < 1e-13;
-        double step = fmax(fabs(lam * dv[0]), fmax(fabs(lam * dv[1]), fabs(lam * dv[2])));
+        real step = fmax(fabs(lam * dv[0]), fmax(fabs(lam * dv[1]), fabs(lam * dv[2])));
         for (int i = 0; i < 3; i++) { vl[i] = vt[i]; g[i] = gt[i]; }
         if (step <= 1e-15) break;
     }
@@ -710,23 +720,23 @@ static int solve_velocity(const c2p_in *in, double p, double vl[3])
 
 /* f(p) = (Gamma-1) rho eps - p (scaled) with the velocity solved at p
  * (Newton from vl; if that does not converge, from rest) */
-static int pressure_fn(const c2p_in *in, double p, double vl[3], double *f)
+static int pressure_fn(const c2p_in *in, real p, real vl[3], real *f)
 {
     if (!(p > 0.0)) return 0;
     if (!solve_velocity(in, p, vl)) {
         vl[0] = vl[1] = vl[2] = 0.0;
         if (!solve_velocity(in, p, vl)) return 0;
     }
-    double cE[3], v[3], g[3];
+    real cE[3], v[3], g[3];
     vel_resid(in, p, vl, g, cE);
     raise(in->m, vl, v);
-    double v2 = dot3(v, vl), W = 1.0 / sqrt(1.0 - v2), sg = in->m->sg;
-    double cEl[3], cBl[3];
+    real v2 = dot3(v, vl), W = 1.0 / sqrt(1.0 - v2), sg = in->m->sg;
+    real cEl[3], cBl[3];
     lower(in->m, cE, cEl);
     lower(in->m, in->cB, cBl);
-    double EM = (dot3(cE, cEl) + dot3(in->cB, cBl)) / (2.0 * sg);
-    double rho = in->D / (sg * W);
-    double eps = (in->tau - in->D * (W - 1.0) - sg * p * (W * W - 1.0) - EM) / (in->D * W);
+    real EM = (dot3(cE, cEl) + dot3(in->cB, cBl)) / (2.0 * sg);
+    real rho = in->D / (sg * W);
+    real eps = (in->tau - in->D * (W - 1.0) - sg * p * (W * W - 1.0) - EM) / (in->D * W);
     *f = ((in->P->gamma_eos - 1.0) * rho * eps - p) * sg / (in->tau + in->D + sg * p);
     return 1;
 }
@@ -736,18 +746,18 @@ static int pressure_fn(const c2p_in *in, double p, double vl[3], double *f)
  * above the lowest pressure at which those equations have a solution with
  * v^2 < 1 (a lower pressure leaves too little enthalpy for the momentum),
  * so a pressure where the solve fails lies below the root.  Search: from
- * the guess, double the pressure while f is undefined or positive, halve
+ * the guess, real the pressure while f is undefined or positive, halve
  * it while f is negative; a halving that lands where f is undefined is
  * replaced by geometric bisection between that pressure and the last one
  * where f was defined.  Once f changes sign, the Illinois variant of regula
  * falsi on the bracket. */
-static int c2p_bracket(const c2p_in *in, double *p_io, double v_io[3], double cE[3],
-                       double *rho_o, int *iters)
+static int c2p_bracket(const c2p_in *in, real *p_io, real v_io[3], real cE[3],
+                       real *rho_o, int *iters)
 {
-    double vl[3], v0[3], f0 = 0.0;
+    real vl[3], v0[3], f0 = 0.0;
     lower(in->m, v_io, v0);
     for (int i = 0; i < 3; i++) vl[i] = v0[i];
-    double p0 = *p_io > 0.0 ? *p_io : in->P->K_atmo * pow(in->P->rho_atmo, in->P->gamma_eos);
+    real p0 = *p_io > 0.0 ? *p_io : in->P->K_atmo * pow(in->P->rho_atmo, in->P->gamma_eos);
     int n = 0, ok = pressure_fn(in, p0, vl, &f0);
     /* f undefined at the guess: the root is above */
     while (!ok) {
@@ -756,8 +766,8 @@ static int c2p_bracket(const c2p_in *in, double *p_io, double v_io[3], double cE
         for (int i = 0; i < 3; i++) vl[i] = v0[i];
         ok = pressure_fn(in, p0, vl, &f0);
     }
-    double lo = p0, hi = p0, flo = f0, fhi = f0;
-    double vlo[3] = {vl[0], vl[1], vl[2]}, vhi[3] = {vl[0], vl[1], vl[2]};
+    real lo = p0, hi = p0, flo = f0, fhi = f0;
+    real vlo[3] = {vl[0], vl[1], vl[2]}, vhi[3] = {vl[0], vl[1], vl[2]};
     if (f0 > 0.0) {
         while (fhi > 0.0) {
             if (++n > 60) return 0;
@@ -768,11 +778,11 @@ static int c2p_bracket(const c2p_in *in, double *p_io, double v_io[3], double cE
         }
     } else {
         /* hi: f < 0 and defined; und: a pressure below where f is undefined */
-        double und = 0.0;
+        real und = 0.0;
         while (flo < 0.0) {
             if (++n > 120) return 0;
-            double pt = und > 0.0 ? sqrt(und * hi) : 0.5 * hi;
-            double vt[3] = {vhi[0], vhi[1], vhi[2]}, ft;
+            real pt = und > 0.0 ? sqrt(und * hi) : 0.5 * hi;
+            real vt[3] = {vhi[0], vhi[1], vhi[2]}, ft;
             if (!pressure_fn(in, pt, vt, &ft)) {
                 und = pt;
                 if (und > hi * (1.0 - 1e-15)) return 0;
@@ -788,12 +798,12 @@ static int c2p_bracket(const c2p_in *in, double *p_io, double v_io[3], double cE
         }
     }
     int side = 0;
-    double sg = in->m->sg;
+    real sg = in->m->sg;
     for (int it = 0; it < 100; it++) {
         *iters = n + it + 1;
-        double pm = (lo * fhi - hi * flo) / (fhi - flo);
+        real pm = (lo * fhi - hi * flo) / (fhi - flo);
         if (!(pm > lo && pm < hi)) pm = 0.5 * (lo + hi);
-        double vm[3] = {vlo[0], vlo[1], vlo[2]}, fm;
+        real vm[3] = {vlo[0], vlo[1], vlo[2]}, fm;
         if (!pressure_fn(in, pm, vm, &fm)) return 0;
         if (fm > 0.0) {
             lo = pm; flo = fm;
@@ -807,12 +817,12 @@ static int c2p_bracket(const c2p_in *in, double *p_io, double v_io[3], double cE
             side = -1;
         }
         if ((hi - lo) * sg <= in->P->c2p_tol * (in->tau + in->D + sg * hi) || fm == 0.0) {
-            double g[3], v[3];
+            real g[3], v[3];
             *p_io = pm;
             for (int i = 0; i < 3; i++) vl[i] = vm[i];
             vel_resid(in, pm, vl, g, cE);
             raise(in->m, vl, v);
-            double W = 1.0 / sqrt(1.0 - dot3(v, vl));
+            real W = 1.0 / sqrt(1.0 - dot3(v, vl));
             for (int i = 0; i < 3; i++) v_io[i] = v[i];
             *rho_o = in->D / (sg * W);
             return 1;
@@ -821,14 +831,92 @@ static int c2p_bracket(const c2p_in *in, double *p_io, double v_io[3], double cE
     return 0;
 }
 
+#ifdef ORC_TANGENT
+/* Tangent-linear build only.  The recovery's root x = (p, v_i) solves
+ * R(x; inputs) = 0, R = (the velocity equations of vel_resid, the EOS
+ * residual (Gamma-1) rho eps - p of step (iii)-(iv)).  The iterations that
+ * found it carry derivatives that need not have converged when the values
+ * have (the stage guess often sits at the root, so the iteration stops after
+ * one or two steps while the guess's derivative is that of another state):
+ * the derivative of the root is therefore taken from the implicit-function
+ * theorem, dx = -R_x^-1 (dR/d inputs), at the converged values; then calE
+ * and rho are re-formed at the root for their derivatives.  Values are left
+ * as the recovery returned them. */
+static int eos_resid(const c2p_in *in, real p, const real vl[3], real R[4], real cE[3])
+{
+    if (!vel_resid(in, p, vl, R, cE)) return 0;
+    const metric_pt *m = in->m;
+    real v[3], cEl[3], cBl[3];
+    raise(m, vl, v);
+    real v2 = dot3(v, vl);
+    real W = 1.0 / sqrt(1.0 - v2);
+    lower(m, cE, cEl);
+    lower(m, in->cB, cBl);
+    real EM = (dot3(cE, cEl) + dot3(in->cB, cBl)) / (2.0 * m->sg);
+    real rho = in->D / (m->sg * W);
+    real eps = (in->tau - in->D * (W - 1.0) - m->sg * p * (W * W - 1.0) - EM) / (in->D * W);
+    R[3] = ((in->P->gamma_eos - 1.0) * rho * eps - p) / (in->tau + in->D + m->sg * p);
+    return 1;
+}
+
+static real strip(real x) { return tl(x.v, 0.0); }
+
+static void recovery_tangent(const c2p_in *in, real *p, real v[3], real cE[3], real *rho)
+{
+    const metric_pt *m = in->m;
+    real vl[3], x[4], R[4], Eh[3];
+    lower(m, v, vl);
+    x[0] = strip(*p);
+    for (int i = 0; i < 3; i++) x[1 + i] = strip(vl[i]);
+    /* inputs without derivatives, for the Jacobian R_x */
+    c2p_in in0 = *in;
+    in0.D = strip(in->D);
+    in0.tau = strip(in->tau);
+    in0.c = strip(in->c);
+    in0.sigma = strip(in->sigma);
+    for (int i = 0; i < 3; i++) {
+        in0.Sl[i] = strip(in->Sl[i]);
+        in0.cB[i] = strip(in->cB[i]);
+        in0.cE0[i] = strip(in->cE0[i]);
+    }
+    /* dR/d inputs along the direction: x without derivative */
+    if (!eos_resid(in, x[0], &x[1], R, Eh)) return;
+    real J[16], b[4], dx[4];
+    for (int r = 0; r < 4; r++) b[r] = tl(-R[r].d, 0.0);
+    for (int col = 0; col < 4; col++) {
+        real xs[4] = {x[0], x[1], x[2], x[3]}, Rc[4];
+        xs[col].d = 1.0;
+        if (!eos_resid(&in0, xs[0], &xs[1], Rc, Eh)) return;
+        for (int r = 0; r < 4; r++) J[r * 4 + col] = tl(Rc[r].d, 0.0);
+    }
+    if (!solve_dense(4, J, b, dx)) return;
+    /* the root with its derivative; calE and rho re-formed there */
+    real xt[4];
+    for (int k = 0; k < 4; k++) xt[k] = tl(x[k].v, dx[k].v);
+    real vu[3];
+    raise(m, &xt[1], vu);
+    real v2 = dot3(vu, &xt[1]);
+    real W = 1.0 / sqrt(1.0 - v2);
+    real Et[3] = {in->cE0[0], in->cE0[1], in->cE0[2]};
+    if (in->implicit && !implicit_E_nr(m, in->cE0, in->cB, vu, W, in->sigma, in->c, Et))
+        return;
+    p->d = xt[0].d;
+    for (int i = 0; i < 3; i++) {
+        v[i].d = vu[i].d;
+        cE[i].d = Et[i].d;
+    }
+    rho->d = (in->D / (m->sg * W)).d;
+}
+#endif
+
 /* Returns status: 0 converged (paper iteration), 4 converged (pressure
  * bracket), 2 failed -> atmosphere, 3 converged but rho < rho_atmo ->
  * atmosphere.  (Status 1 is not produced here.)  The recovery is: the
  * paper's iteration (steps i-v) to its cap; if it does not converge, the
  * pressure bracket from the same guess; if that fails too, the atmosphere. */
-int orc_con2prim(const orc_params *P, const double cons_in[14], int implicit,
-                 double c, double sigma, double alpha, const double g6[6],
-                 const double guess[14], double prim[14], double cons_out[14],
+int orc_con2prim(const orc_params *P, const real cons_in[14], int implicit,
+                 real c, real sigma, real alpha, const real g6[6],
+                 const real guess[14], real prim[14], real cons_out[14],
                  int *iters)
 {
     metric_pt m;
@@ -848,9 +936,9 @@ int orc_con2prim(const orc_params *P, const double cons_in[14], int implicit,
     in.sigma = sigma;
     in.v2max = 1.0 - 1.0 / (P->c2p_wmax * P->c2p_wmax);
 
-    double p = guess[P_P], v[3] = {guess[P_VX], guess[P_VY], guess[P_VZ]};
-    double cE[3] = {in.cE0[0], in.cE0[1], in.cE0[2]};
-    double rho = 0.0;
+    real p = guess[P_P], v[3] = {guess[P_VX], guess[P_VY], guess[P_VZ]};
+    real cE[3] = {in.cE0[0], in.cE0[1], in.cE0[2]};
+    real rho = 0.0;
     int it1 = 0, it2 = 0, status;
     /* atmosphere without iterating: rho = D / (W sqrt(gamma)) <= D / sqrt(gamma)
      * for every velocity, so a density D / sqrt(gamma) below the floor puts
@@ -868,6 +956,9 @@ int orc_con2prim(const orc_params *P, const double cons_in[14], int implicit,
         status = c2p_bracket(&in, &p, v, cE, &rho, &it2) ? 4 : 2;
     }
     *iters = it1 + it2;
+#ifdef ORC_TANGENT
+    if (status == 0 || status == 4) recovery_tangent(&in, &p, v, cE, &rho);
+#endif
     /* atmosphere floor: rho below rho_atmo (1 + atmo_tol) is reset */
     int ok = status == 0 || status == 4;
     if (ok && !(rho >= P->rho_atmo * (1.0 + P->atmo_tol))) status = 3;
@@ -883,7 +974,7 @@ int orc_con2prim(const orc_params *P, const double cons_in[14], int implicit,
         for (int i = 0; i < 3; i++)
             cE[i] = implicit ? in.cE0[i] / (1.0 + c * alpha * sigma) : in.cE0[i];
     }
-    double sg = m.sg;
+    real sg = m.sg;
     prim[P_RHO] = rho;
     prim[P_P] = p;
     for (int i = 0; i < 3; i++) {
@@ -896,7 +987,7 @@ int orc_con2prim(const orc_params *P, const double cons_in[14], int implicit,
     prim[P_PHI] = cons_in[C_PHI] / sg;
     prim[P_Q] = cons_in[C_Q] / sg;
     if (reset) {
-        double full[14];
+        real full[14];
         orc_prim2con(prim, alpha, NULL, g6, P->gamma_eos, full);
         cons_out[C_D] = full[C_D];
         cons_out[C_TAU] = full[C_TAU];
@@ -905,10 +996,10 @@ int orc_con2prim(const orc_params *P, const double cons_in[14], int implicit,
     return status;
 }
 
-void orc_con2prim_batch(const orc_params *P, long n, const double *cons, int implicit,
-                        double c, const double *sigma, const double *alpha,
-                        const double *g6, const double *guess, double *prim,
-                        double *cons_out, int *iters, int *status)
+void orc_con2prim_batch(const orc_params *P, long n, const real *cons, int implicit,
+                        real c, const real *sigma, const real *alpha,
+                        const real *g6, const real *guess, real *prim,
+                        real *cons_out, int *iters, int *status)
 {
     for (long i = 0; i < n; i++)
         status[i] = orc_con2prim(P, cons + 14 * i, implicit, c, sigma[i], alpha[i],
@@ -920,7 +1011,7 @@ void orc_con2prim_batch(const orc_params *P, long n, const double *cons, int imp
 
 typedef struct {
     const orc_params *P;
-    const double *alpha, *beta, *gam, *K, *sigma_field;
+    const real *alpha, *beta, *gam, *K, *sigma_field;
     int nx, ny, nz;
     long N;
 } grid;
@@ -943,32 +1034,42 @@ static long cidx(const grid *G, int i, int j, int k)
 
 static void cell_metric(const grid *G, long c, metric_pt *m)
 {
-    double beta[3], g6[6];
+    real beta[3], g6[6];
     for (int i = 0; i < 3; i++) beta[i] = G->beta[i * G->N + c];
     for (int i = 0; i < 6; i++) g6[i] = G->gam[i * G->N + c];
     make_metric(G->alpha[c], beta, g6, m);
 }
 
+/* sigma0; in the tangent-linear build it carries the derivative seeded for
+ * log sigma0 (orc_set_tangent_log_sigma0), d sigma0 = sigma0 d log sigma0 */
+#ifdef ORC_TANGENT
+static double tl_dlog_sigma0 = 0.0;
+void orc_set_tangent_log_sigma0(double d) { tl_dlog_sigma0 = d; }
+static real sigma0_of(const orc_params *P) { return tl(P->sigma0, P->sigma0 * tl_dlog_sigma0); }
+#else
+static real sigma0_of(const orc_params *P) { return P->sigma0; }
+#endif
+
 /* Conductivity models: uniform, tabulated profile, sigma0 D^gamma_sigma
  * (Eq. sigma_evol) and sigma0 max(1 - D_atmo/D, 0)^2 (Eq. dynamo_sigma). */
-static double sigma_of(const orc_params *P, const double *field, long c, double D)
+static real sigma_of(const orc_params *P, const real *field, long c, real D)
 {
     switch (P->sigma_model) {
-    case 1: return P->sigma0 * field[c];
-    case 2: return P->sigma0 * pow(D, P->sigma_exp);
+    case 1: return sigma0_of(P) * field[c];
+    case 2: return sigma0_of(P) * pow(D, P->sigma_exp);
     case 3: {
-        double t = 1.0 - P->D_atmo / D;
+        real t = 1.0 - P->D_atmo / D;
         if (!(t > 0.0)) t = 0.0;
-        return P->sigma0 * t * t;
+        return sigma0_of(P) * t * t;
     }
-    default: return P->sigma0;
+    default: return sigma0_of(P);
     }
 }
 
-static double sigma_cell_from_prim(const grid *G, const double *prim, long c)
+static real sigma_cell_from_prim(const grid *G, const real *prim, long c)
 {
     if (G->P->sigma_model < 2) return sigma_of(G->P, G->sigma_field, c, 0.0);
-    double pr[14], cons[14];
+    real pr[14], cons[14];
     metric_pt m;
     prim_pt q;
     for (int f = 0; f < 14; f++) pr[f] = prim[f * G->N + c];
@@ -982,16 +1083,16 @@ static double sigma_cell_from_prim(const grid *G, const double *prim, long c)
  * Jcell (3 x N, the cell-centred current of the stage) the charge-flux
  * current J^d is reconstructed from it like a primitive; without it Ohm's
  * law is evaluated at the reconstructed face states. */
-static void face_flux(const grid *G, const double *prim, const double *Jcell,
-                      int d, int i, int j, int k, double F[14])
+static void face_flux(const grid *G, const real *prim, const real *Jcell,
+                      int d, int i, int j, int k, real F[14])
 {
     const orc_params *P = G->P;
     int o[3] = {0, 0, 0};
-    double sL[15], sR[15];
+    real sL[15], sR[15];
     long cL = cidx(G, i, j, k);
     long cR = cidx(G, i + (d == 0), j + (d == 1), k + (d == 2));
     for (int f = 0; f < 14; f++) {
-        double s[6];
+        real s[6];
         for (int t = -2; t <= 3; t++) {
             o[d] = t;
             s[t + 2] = prim[f * G->N + cidx(G, i + o[0], j + o[1], k + o[2])];
@@ -999,7 +1100,7 @@ static void face_flux(const grid *G, const double *prim, const double *Jcell,
         recon_face(P->recon, s, &sL[f], &sR[f]);
     }
     if (Jcell) {
-        double s[6];
+        real s[6];
         for (int t = -2; t <= 3; t++) {
             o[d] = t;
             s[t + 2] = Jcell[d * G->N + cidx(G, i + o[0], j + o[1], k + o[2])];
@@ -1007,8 +1108,8 @@ static void face_flux(const grid *G, const double *prim, const double *Jcell,
         recon_face(P->recon, s, &sL[14], &sR[14]);
     }
     /* face metric: mean of the two cells */
-    double alpha = 0.5 * (G->alpha[cL] + G->alpha[cR]);
-    double beta[3], g6[6];
+    real alpha = 0.5 * (G->alpha[cL] + G->alpha[cR]);
+    real beta[3], g6[6];
     for (int a = 0; a < 3; a++)
         beta[a] = 0.5 * (G->beta[a * G->N + cL] + G->beta[a * G->N + cR]);
     for (int a = 0; a < 6; a++)
@@ -1016,18 +1117,18 @@ static void face_flux(const grid *G, const double *prim, const double *Jcell,
     metric_pt m;
     make_metric(alpha, beta, g6, &m);
     /* unphysical reconstructed states fall back to the cell values */
-    double *side[2] = {sL, sR};
+    real *side[2] = {sL, sR};
     long cell[2] = {cL, cR};
     for (int s = 0; s < 2; s++) {
-        double v[3] = {side[s][P_VX], side[s][P_VY], side[s][P_VZ]}, vl[3];
+        real v[3] = {side[s][P_VX], side[s][P_VY], side[s][P_VZ]}, vl[3];
         lower(&m, v, vl);
-        double v2 = dot3(v, vl);
+        real v2 = dot3(v, vl);
         if (!(side[s][P_RHO] > 0.0) || !(side[s][P_P] > 0.0) || !(v2 < 1.0)) {
             for (int f = 0; f < 14; f++) side[s][f] = prim[f * G->N + cell[s]];
             if (Jcell) side[s][14] = Jcell[d * G->N + cell[s]];
         }
     }
-    double sigma = 0.5 * (sigma_cell_from_prim(G, prim, cL)
+    real sigma = 0.5 * (sigma_cell_from_prim(G, prim, cL)
                           + sigma_cell_from_prim(G, prim, cR));
     if (Jcell)
         hlle_point(d, sL, sR, &m, sigma, P->gamma_eos, &sL[14], &sR[14], F);
@@ -1036,7 +1137,7 @@ static void face_flux(const grid *G, const double *prim, const double *Jcell,
 }
 
 /* d(field)/dx_d at cell (i,j,k) by 2nd-order central differences */
-static double dcell(const grid *G, const double *fld, int d, int i, int j, int k)
+static real dcell(const grid *G, const real *fld, int d, int i, int j, int k)
 {
     int n[3] = {G->nx, G->ny, G->nz};
     if (n[d] == 1) return 0.0;
@@ -1047,59 +1148,59 @@ static double dcell(const grid *G, const double *fld, int d, int i, int j, int k
 
 /* Source vector S of Eq. GRRMHD_flux_form without the stiff part of -alpha J
  * (i.e. with -alpha Q v^i only, Sec. III.A split F_E / R_E). */
-static void sources(const grid *G, const double *prim, int i, int j, int k,
-                    double S[14])
+static void sources(const grid *G, const real *prim, int i, int j, int k,
+                    real S[14])
 {
     const orc_params *P = G->P;
     long c = cidx(G, i, j, k);
     metric_pt m;
     cell_metric(G, c, &m);
-    double pr[14], cons[14];
+    real pr[14], cons[14];
     for (int f = 0; f < 14; f++) pr[f] = prim[f * G->N + c];
     prim_pt q;
     derive_prim(pr, &m, P->gamma_eos, &q);
     prim_to_cons(pr, &m, P->gamma_eos, &q, cons);
 
-    double da[3], db[3][3], dg[3][3][3], Kij[3][3];
-    double k6[6];
+    real da[3], db[3][3], dg[3][3][3], Kij[3][3];
+    real k6[6];
     for (int a = 0; a < 6; a++) k6[a] = G->K[a * G->N + c];
     unpack6(k6, Kij);
     for (int d = 0; d < 3; d++) {
         da[d] = dcell(G, G->alpha, d, i, j, k);
         for (int a = 0; a < 3; a++) db[d][a] = dcell(G, G->beta + a * G->N, d, i, j, k);
-        double d6[6];
+        real d6[6];
         for (int a = 0; a < 6; a++) d6[a] = dcell(G, G->gam + a * G->N, d, i, j, k);
         unpack6(d6, dg[d]); /* dg[d][a][b] = d_d gamma_ab */
     }
     /* Christoffel symbols Gamma^a_bc = 1/2 g^{al}(d_b g_lc + d_c g_lb - d_l g_bc) */
-    double Chr[3][3][3];
+    real Chr[3][3][3];
     for (int a = 0; a < 3; a++)
         for (int b = 0; b < 3; b++)
             for (int cc = 0; cc < 3; cc++) {
-                double s = 0.0;
+                real s = 0.0;
                 for (int l = 0; l < 3; l++)
                     s += m.gi[a][l] * (dg[b][l][cc] + dg[cc][l][b] - dg[l][b][cc]);
                 Chr[a][b][cc] = 0.5 * s;
             }
-    double Ktr = 0.0;
+    real Ktr = 0.0;
     for (int a = 0; a < 3; a++)
         for (int b = 0; b < 3; b++) Ktr += m.gi[a][b] * Kij[a][b];
 
     /* undensitised stress with both indices up */
-    double hW2 = q.h * q.W * q.W;
-    double Sup[3][3];
+    real hW2 = q.h * q.W * q.W;
+    real Sup[3][3];
     for (int a = 0; a < 3; a++)
         for (int b = 0; b < 3; b++)
             Sup[a][b] = hW2 * q.v[a] * q.v[b] + m.gi[a][b] * q.p
                         - q.E[a] * q.E[b] - q.B[a] * q.B[b]
                         + 0.5 * m.gi[a][b] * (q.E2 + q.B2);
-    double Sl[3] = {cons[C_SX], cons[C_SY], cons[C_SZ]}, Su[3];
+    real Sl[3] = {cons[C_SX], cons[C_SY], cons[C_SZ]}, Su[3];
     raise(&m, Sl, Su);
-    double al = m.alpha, sg = m.sg;
+    real al = m.alpha, sg = m.sg;
 
     for (int f = 0; f < 14; f++) S[f] = 0.0;
     for (int a = 0; a < 3; a++) {
-        double s = 0.0;
+        real s = 0.0;
         for (int b = 0; b < 3; b++)
             for (int cc = 0; cc < 3; cc++) s += Sup[b][cc] * dg[a][b][cc];
         s *= 0.5 * al * sg;
@@ -1108,7 +1209,7 @@ static void sources(const grid *G, const double *prim, int i, int j, int k,
         S[C_SX + a] = s;
     }
     {
-        double s = 0.0;
+        real s = 0.0;
         for (int a = 0; a < 3; a++)
             for (int b = 0; b < 3; b++) s += Sup[a][b] * Kij[a][b];
         s *= al * sg;
@@ -1117,13 +1218,13 @@ static void sources(const grid *G, const double *prim, int i, int j, int k,
     }
     for (int a = 0; a < 3; a++) {
         /* gamma^{ab} d_b alpha - alpha gamma^{bc} Gamma^a_bc */
-        double G1 = 0.0;
+        real G1 = 0.0;
         for (int b = 0; b < 3; b++) G1 += m.gi[a][b] * da[b];
-        double G2 = 0.0;
+        real G2 = 0.0;
         for (int b = 0; b < 3; b++)
             for (int cc = 0; cc < 3; cc++) G2 += m.gi[b][cc] * Chr[a][b][cc];
-        double geo = G1 - al * G2;
-        double sB = 0.0, sE = 0.0;
+        real geo = G1 - al * G2;
+        real sB = 0.0, sE = 0.0;
         for (int b = 0; b < 3; b++) {
             sB -= cons[C_BX + b] * db[b][a];
             sE -= cons[C_EX + b] * db[b][a];
@@ -1131,7 +1232,7 @@ static void sources(const grid *G, const double *prim, int i, int j, int k,
         S[C_BX + a] = sB + cons[C_PHI] * geo;
         S[C_EX + a] = sE + cons[C_PSI] * geo - al * cons[C_Q] * q.v[a];
     }
-    double Bda = 0.0, Eda = 0.0;
+    real Bda = 0.0, Eda = 0.0;
     for (int b = 0; b < 3; b++) {
         Bda += cons[C_BX + b] * da[b];
         Eda += cons[C_EX + b] * da[b];
@@ -1141,8 +1242,8 @@ static void sources(const grid *G, const double *prim, int i, int j, int k,
 }
 
 /* Non-stiff right-hand side F(U) = -d_k F^k + S (Sec. II.D / III.A) */
-static void rhs_grid(const grid *G, const double *prim, const double *Jcell,
-                     double *rhs)
+static void rhs_grid(const grid *G, const real *prim, const real *Jcell,
+                     real *rhs)
 {
     const orc_params *P = G->P;
     int n[3] = {G->nx, G->ny, G->nz};
@@ -1154,11 +1255,11 @@ static void rhs_grid(const grid *G, const double *prim, const double *Jcell,
         int m[3] = {n[0], n[1], n[2]};
         m[d] += 1;
         long Mf = (long)m[0] * m[1] * m[2];
-        double *Ff = (double *)malloc(sizeof(double) * 14 * Mf);
+        real *Ff = (real *)malloc(sizeof(real) * 14 * Mf);
         for (int k = 0; k < m[2]; k++)
             for (int j = 0; j < m[1]; j++)
                 for (int i = 0; i < m[0]; i++) {
-                    double F[14];
+                    real F[14];
                     face_flux(G, prim, Jcell, d, i - (d == 0), j - (d == 1),
                               k - (d == 2), F);
                     long fidx = ((long)k * m[1] + j) * m[0] + i;
@@ -1180,15 +1281,15 @@ static void rhs_grid(const grid *G, const double *prim, const double *Jcell,
         for (int j = 0; j < n[1]; j++)
             for (int i = 0; i < n[0]; i++) {
                 long c = ((long)k * n[1] + j) * n[0] + i;
-                double S[14];
+                real S[14];
                 sources(G, prim, i, j, k, S);
                 for (int f = 0; f < 14; f++) rhs[f * N + c] += S[f];
             }
 }
 
-static void make_grid(grid *G, const orc_params *P, const double *alpha,
-                      const double *beta, const double *gam, const double *K,
-                      const double *sigma_field)
+static void make_grid(grid *G, const orc_params *P, const real *alpha,
+                      const real *beta, const real *gam, const real *K,
+                      const real *sigma_field)
 {
     G->P = P;
     G->alpha = alpha;
@@ -1202,25 +1303,25 @@ static void make_grid(grid *G, const orc_params *P, const double *alpha,
     G->N = (long)G->nx * G->ny * G->nz;
 }
 
-void orc_rhs(const orc_params *P, const double *alpha, const double *beta,
-             const double *gam, const double *K, const double *sigma_field,
-             const double *prim, const double *Jcell, double *rhs)
+void orc_rhs(const orc_params *P, const real *alpha, const real *beta,
+             const real *gam, const real *K, const real *sigma_field,
+             const real *prim, const real *Jcell, real *rhs)
 {
     grid G;
     make_grid(&G, P, alpha, beta, gam, K, sigma_field);
     rhs_grid(&G, prim, Jcell, rhs);
 }
 
-void orc_prim2con_grid(const orc_params *P, const double *alpha,
-                       const double *beta, const double *gam,
-                       const double *prim, double *cons)
+void orc_prim2con_grid(const orc_params *P, const real *alpha,
+                       const real *beta, const real *gam,
+                       const real *prim, real *cons)
 {
     grid G;
     make_grid(&G, P, alpha, beta, gam, NULL, NULL);
     for (long c = 0; c < G.N; c++) {
         metric_pt m;
         cell_metric(&G, c, &m);
-        double pr[14], cn[14];
+        real pr[14], cn[14];
         for (int f = 0; f < 14; f++) pr[f] = prim[f * G.N + c];
         prim_pt q;
         derive_prim(pr, &m, P->gamma_eos, &q);
@@ -1250,20 +1351,20 @@ void orc_set_fail_buffer(double *buf, long cap, long *count)
 /* Pointwise recovery over the grid.  implicit: solve the stiff calE with
  * c = gamma_imex dt; cons is updated in place (calE and, after an
  * atmosphere reset, D, S_i, tau). */
-static void c2p_grid(const grid *G, double *cons, const double *guess,
-                     double *prim, int implicit, double c, long long stats[8],
+static void c2p_grid(const grid *G, real *cons, const real *guess,
+                     real *prim, int implicit, real c, long long stats[8],
                      int stage)
 {
     const orc_params *P = G->P;
     long N = G->N;
     for (long cell = 0; cell < N; cell++) {
-        double cin[14], g[14], pr[14], cout[14], g6[6];
+        real cin[14], g[14], pr[14], cout[14], g6[6];
         for (int f = 0; f < 14; f++) {
             cin[f] = cons[f * N + cell];
             g[f] = guess[f * N + cell];
         }
         for (int a = 0; a < 6; a++) g6[a] = G->gam[a * N + cell];
-        double sigma = implicit ? sigma_of(P, G->sigma_field, cell, cin[C_D]) : 0.0;
+        real sigma = implicit ? sigma_of(P, G->sigma_field, cell, cin[C_D]) : 0.0;
         int it = 0;
         int st = orc_con2prim(P, cin, implicit, c, sigma, G->alpha[cell], g6, g,
                               pr, cout, &it);
@@ -1281,13 +1382,13 @@ static void c2p_grid(const grid *G, double *cons, const double *guess,
                 r[0] = stage;
                 r[1] = (double)cell;
                 for (int f = 0; f < 14; f++) {
-                    r[2 + f] = cin[f];
-                    r[16 + f] = g[f];
+                    r[2 + f] = VAL(cin[f]);
+                    r[16 + f] = VAL(g[f]);
                 }
-                r[30] = G->alpha[cell];
-                for (int a = 0; a < 6; a++) r[31 + a] = g6[a];
-                r[37] = c;
-                r[38] = sigma;
+                r[30] = VAL(G->alpha[cell]);
+                for (int a = 0; a < 6; a++) r[31 + a] = VAL(g6[a]);
+                r[37] = VAL(c);
+                r[38] = VAL(sigma);
             }
         }
         for (int f = 0; f < 14; f++) {
@@ -1301,8 +1402,8 @@ static void c2p_grid(const grid *G, double *cons, const double *guess,
  * J = Q v + W sigma [...] and the stiff source is R_E = -alpha W sigma [...],
  * so at the stage's root J^i = Q v^i - (Dt R_E^i) / (alpha Dt), with Dt R_E
  * the stored stiff increment: bounded for any sigma. */
-static void stage_current(const grid *G, const double *U, const double *prim,
-                          const double *dR, double dt, double *J)
+static void stage_current(const grid *G, const real *U, const real *prim,
+                          const real *dR, real dt, real *J)
 {
     long N = G->N;
     for (int a = 0; a < 3; a++)
@@ -1315,14 +1416,14 @@ static void stage_current(const grid *G, const double *U, const double *prim,
  * the paper tests for the magnetised star, Sec. IV.E): Q = sqrt(gamma) q =
  * d_i calE^i, by 2nd-order central differences of the densitised field with
  * the grid's boundary condition; q = Q / sqrt(gamma). */
-static void gauss_charge(const grid *G, double *cons, double *prim)
+static void gauss_charge(const grid *G, real *cons, real *prim)
 {
     long N = G->N;
     for (int k = 0; k < G->nz; k++)
         for (int j = 0; j < G->ny; j++)
             for (int i = 0; i < G->nx; i++) {
                 long c = cidx(G, i, j, k);
-                double Q = 0.0;
+                real Q = 0.0;
                 for (int d = 0; d < 3; d++)
                     Q += dcell(G, &cons[(C_EX + d) * N], d, i, j, k);
                 metric_pt m;
@@ -1338,34 +1439,34 @@ static void gauss_charge(const grid *G, double *cons, double *prim)
  *   U^{n+1} = U^n + dt/2 (F[U1] + F[U2]) + dt/2 (R[U1] + R[U2])
  * R acts on calE only (Sec. III.A); each implicit stage is solved jointly
  * with the recovery (Sec. III.B); U^{n+1} is then recovered with calE fixed. */
-static int step_ssp222(const orc_params *P, const double *alpha, const double *beta,
-                       const double *gam, const double *K, const double *sigma_field,
-                       double *cons, double *prim, double dt, int nsteps,
+static int step_ssp222(const orc_params *P, const real *alpha, const real *beta,
+                       const real *gam, const real *K, const real *sigma_field,
+                       real *cons, real *prim, real dt, int nsteps,
                        long long stats[8])
 {
     grid G;
     make_grid(&G, P, alpha, beta, gam, K, sigma_field);
     long N = G.N;
-    double g = imex_gamma();
-    double *U1 = (double *)malloc(sizeof(double) * 14 * N);
-    double *U2 = (double *)malloc(sizeof(double) * 14 * N);
-    double *W1 = (double *)malloc(sizeof(double) * 14 * N);
-    double *W2 = (double *)malloc(sizeof(double) * 14 * N);
-    double *F1 = (double *)malloc(sizeof(double) * 14 * N);
-    double *F2 = (double *)malloc(sizeof(double) * 14 * N);
-    double *dR1 = (double *)malloc(sizeof(double) * 3 * N);
-    double *dR2 = (double *)malloc(sizeof(double) * 3 * N);
-    double *Jc = (double *)malloc(sizeof(double) * 3 * N);
-    double *Es2 = (double *)malloc(sizeof(double) * 3 * N);
+    real g = imex_gamma();
+    real *U1 = (real *)malloc(sizeof(real) * 14 * N);
+    real *U2 = (real *)malloc(sizeof(real) * 14 * N);
+    real *W1 = (real *)malloc(sizeof(real) * 14 * N);
+    real *W2 = (real *)malloc(sizeof(real) * 14 * N);
+    real *F1 = (real *)malloc(sizeof(real) * 14 * N);
+    real *F2 = (real *)malloc(sizeof(real) * 14 * N);
+    real *dR1 = (real *)malloc(sizeof(real) * 3 * N);
+    real *dR2 = (real *)malloc(sizeof(real) * 3 * N);
+    real *Jc = (real *)malloc(sizeof(real) * 3 * N);
+    real *Es2 = (real *)malloc(sizeof(real) * 3 * N);
     /* mode 2 (Gauss's law) overwrites Q after every recovery, so its charge
      * flux row is irrelevant; it is formed as in mode 0 */
-    const double *Jarg = P->qflux_mode != 1 ? Jc : NULL;
+    const real *Jarg = P->qflux_mode != 1 ? Jc : NULL;
     const int gauss = P->qflux_mode == 2;
     int status = 0;
     for (int s = 0; s < 8; s++) stats[s] = 0;
     for (int step = 0; step < nsteps; step++) {
         /* stage 1: purely implicit */
-        memcpy(U1, cons, sizeof(double) * 14 * N);
+        memcpy(U1, cons, sizeof(real) * 14 * N);
         c2p_grid(&G, U1, prim, W1, 1, g * dt, stats, 0);
         if (gauss) gauss_charge(&G, U1, W1);
         for (int a = 0; a < 3; a++)
@@ -1416,9 +1517,9 @@ static int step_ssp222(const orc_params *P, const double *alpha, const double *b
  * Terms with a zero coefficient are skipped, and F[U^(i)] is formed only
  * when a later row or wt uses it.  U^{n+1} is then recovered with calE
  * fixed (guess: the last stage's primitives). */
-int orc_step_tableau(const orc_params *P, const double *alpha, const double *beta,
-                     const double *gam, const double *K, const double *sigma_field,
-                     double *cons, double *prim, double dt, int nsteps,
+int orc_step_tableau(const orc_params *P, const real *alpha, const real *beta,
+                     const real *gam, const real *K, const real *sigma_field,
+                     real *cons, real *prim, real dt, int nsteps,
                      long long stats[8])
 {
     imex_tab T;
@@ -1427,26 +1528,26 @@ int orc_step_tableau(const orc_params *P, const double *alpha, const double *bet
     grid G;
     make_grid(&G, P, alpha, beta, gam, K, sigma_field);
     long N = G.N;
-    double *Ui = (double *)malloc(sizeof(double) * 14 * N);
-    double *Es = (double *)malloc(sizeof(double) * 3 * N);
-    double *Jc = (double *)malloc(sizeof(double) * 3 * N);
-    double *W[4], *F[4], *dR[4];
+    real *Ui = (real *)malloc(sizeof(real) * 14 * N);
+    real *Es = (real *)malloc(sizeof(real) * 3 * N);
+    real *Jc = (real *)malloc(sizeof(real) * 3 * N);
+    real *W[4], *F[4], *dR[4];
     int needF[4];
     for (int i = 0; i < s; i++) {
-        W[i] = (double *)malloc(sizeof(double) * 14 * N);
-        F[i] = (double *)malloc(sizeof(double) * 14 * N);
-        dR[i] = (double *)malloc(sizeof(double) * 3 * N);
+        W[i] = (real *)malloc(sizeof(real) * 14 * N);
+        F[i] = (real *)malloc(sizeof(real) * 14 * N);
+        dR[i] = (real *)malloc(sizeof(real) * 3 * N);
         needF[i] = T.wt[i] != 0.0;
         for (int k = i + 1; k < s; k++) needF[i] |= T.At[k][i] != 0.0;
     }
-    const double *Jarg = P->qflux_mode != 1 ? Jc : NULL;
+    const real *Jarg = P->qflux_mode != 1 ? Jc : NULL;
     const int gauss = P->qflux_mode == 2;
     int status = 0;
     for (int a = 0; a < 8; a++) stats[a] = 0;
     for (int step = 0; step < nsteps; step++) {
         for (int i = 0; i < s; i++) {
             /* explicit part of the stage */
-            memcpy(Ui, cons, sizeof(double) * 14 * N);
+            memcpy(Ui, cons, sizeof(real) * 14 * N);
             for (int j = 0; j < i; j++)
                 if (T.At[i][j] != 0.0)
                     for (long a = 0; a < 14 * N; a++) Ui[a] += dt * T.At[i][j] * F[j][a];
@@ -1496,9 +1597,9 @@ int orc_step_tableau(const orc_params *P, const double *alpha, const double *bet
 
 /* Steps with the scheme of P->imex: Table imex through its literal
  * equations, the other tableaux through the general form. */
-int orc_step(const orc_params *P, const double *alpha, const double *beta,
-             const double *gam, const double *K, const double *sigma_field,
-             double *cons, double *prim, double dt, int nsteps,
+int orc_step(const orc_params *P, const real *alpha, const real *beta,
+             const real *gam, const real *K, const real *sigma_field,
+             real *cons, real *prim, real dt, int nsteps,
              long long stats[8])
 {
     if (P->imex == 0)

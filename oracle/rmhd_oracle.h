@@ -27,6 +27,14 @@
 extern "C" {
 #endif
 
+/* The arithmetic type: double.  The tangent-linear build (rmhd_oracle.c
+ * compiled as C++ with ORC_TANGENT) defines orc_real as a tangent number
+ * (value and directional derivative, oracle/tangent.h) before including
+ * this header; every array below then holds such pairs. */
+#ifndef ORC_TANGENT
+typedef double orc_real;
+#endif
+
 typedef struct {
     int    n[3];          /* interior cells per direction, n=1: inactive     */
     double dx[3];         /* spacing                                          */
@@ -51,51 +59,51 @@ typedef struct {
 } orc_params;
 
 /* pointwise pieces (exported for the pin tests) */
-void orc_metric_inverse(const double g6[6], double ginv6[6], double *sqrtg);
-void orc_prim2con(const double prim[14], double alpha, const double beta[3],
-                  const double g6[6], double gamma_eos, double cons[14]);
-void orc_flux(int d, const double prim[14], double alpha, const double beta[3],
-              const double g6[6], double sigma, double gamma_eos,
-              double flux[14], double cons[14]);
-void orc_hlle(int d, const double primL[14], const double primR[14],
-              double alpha, const double beta[3], const double g6[6],
-              double sigma, double gamma_eos, double flux[14]);
-void orc_recon_line(int method, int n, const double *u, double *uL, double *uR);
-int  orc_implicit_E(const double Estar[3], const double Bcons[3],
-                    const double v[3], double alpha, const double g6[6],
-                    double sigma, double c, double Eout[3]);
-int  orc_con2prim(const orc_params *P, const double cons_in[14], int implicit,
-                  double c, double sigma, double alpha, const double g6[6],
-                  const double guess[14], double prim[14], double cons_out[14],
+void orc_metric_inverse(const orc_real g6[6], orc_real ginv6[6], orc_real *sqrtg);
+void orc_prim2con(const orc_real prim[14], orc_real alpha, const orc_real beta[3],
+                  const orc_real g6[6], orc_real gamma_eos, orc_real cons[14]);
+void orc_flux(int d, const orc_real prim[14], orc_real alpha, const orc_real beta[3],
+              const orc_real g6[6], orc_real sigma, orc_real gamma_eos,
+              orc_real flux[14], orc_real cons[14]);
+void orc_hlle(int d, const orc_real primL[14], const orc_real primR[14],
+              orc_real alpha, const orc_real beta[3], const orc_real g6[6],
+              orc_real sigma, orc_real gamma_eos, orc_real flux[14]);
+void orc_recon_line(int method, int n, const orc_real *u, orc_real *uL, orc_real *uR);
+int  orc_implicit_E(const orc_real Estar[3], const orc_real Bcons[3],
+                    const orc_real v[3], orc_real alpha, const orc_real g6[6],
+                    orc_real sigma, orc_real c, orc_real Eout[3]);
+int  orc_con2prim(const orc_params *P, const orc_real cons_in[14], int implicit,
+                  orc_real c, orc_real sigma, orc_real alpha, const orc_real g6[6],
+                  const orc_real guess[14], orc_real prim[14], orc_real cons_out[14],
                   int *iters);
 /* orc_con2prim on n independent points (a plain loop), arrays point-major
  * with stride 14 (cons, guess, prim, cons_out) or 6 (g6) per point */
-void orc_con2prim_batch(const orc_params *P, long n, const double *cons, int implicit,
-                        double c, const double *sigma, const double *alpha,
-                        const double *g6, const double *guess, double *prim,
-                        double *cons_out, int *iters, int *status);
+void orc_con2prim_batch(const orc_params *P, long n, const orc_real *cons, int implicit,
+                        orc_real c, const orc_real *sigma, const orc_real *alpha,
+                        const orc_real *g6, const orc_real *guess, orc_real *prim,
+                        orc_real *cons_out, int *iters, int *status);
 
 /* whole-grid operations */
-void orc_rhs(const orc_params *P, const double *alpha, const double *beta,
-             const double *gam, const double *K, const double *sigma_field,
-             const double *prim, const double *Jcell, double *rhs);
-void orc_prim2con_grid(const orc_params *P, const double *alpha,
-                       const double *beta, const double *gam,
-                       const double *prim, double *cons);
+void orc_rhs(const orc_params *P, const orc_real *alpha, const orc_real *beta,
+             const orc_real *gam, const orc_real *K, const orc_real *sigma_field,
+             const orc_real *prim, const orc_real *Jcell, orc_real *rhs);
+void orc_prim2con_grid(const orc_params *P, const orc_real *alpha,
+                       const orc_real *beta, const orc_real *gam,
+                       const orc_real *prim, orc_real *cons);
 /* tableau of an IMEX scheme (row-major 4x4, zero-padded); returns the
  * number of stages, 0 for an unknown scheme */
-int  orc_imex_tableau(int scheme, double At[16], double wt[4], double A[16],
-                      double w[4]);
+int  orc_imex_tableau(int scheme, orc_real At[16], orc_real wt[4], orc_real A[16],
+                      orc_real w[4]);
 /* the general IMEX-RK form with P->imex's tableau (any scheme, 0 included;
  * orc_step runs scheme 0 through its literal equations instead).  Returns
  * -6 for an unknown scheme. */
-int  orc_step_tableau(const orc_params *P, const double *alpha, const double *beta,
-                      const double *gam, const double *K, const double *sigma_field,
-                      double *cons, double *prim, double dt, int nsteps,
+int  orc_step_tableau(const orc_params *P, const orc_real *alpha, const orc_real *beta,
+                      const orc_real *gam, const orc_real *K, const orc_real *sigma_field,
+                      orc_real *cons, orc_real *prim, orc_real dt, int nsteps,
                       long long stats[8]);
-int  orc_step(const orc_params *P, const double *alpha, const double *beta,
-              const double *gam, const double *K, const double *sigma_field,
-              double *cons, double *prim, double dt, int nsteps,
+int  orc_step(const orc_params *P, const orc_real *alpha, const orc_real *beta,
+              const orc_real *gam, const orc_real *K, const orc_real *sigma_field,
+              orc_real *cons, orc_real *prim, orc_real dt, int nsteps,
               long long stats[8]);
 
 /* diagnostics: per-cell recovery status of the last step (3*N ints) */
@@ -104,6 +112,10 @@ void orc_set_status_buffer(int *buf);
  * stage, cell, conserved [14], guess [14], alpha, gamma_ij [6], c, sigma) */
 #define ORC_FAIL_REC 39
 void orc_set_fail_buffer(double *buf, long cap, long *count);
+#ifdef ORC_TANGENT
+/* tangent-linear build: derivative seed of log sigma0 for the next steps */
+void orc_set_tangent_log_sigma0(double d);
+#endif
 
 #ifdef __cplusplus
 }

@@ -1,5 +1,6 @@
 """The discrete adjoint (rmhd_adjoint_forward / rmhd_adjoint_backward)
-against central finite differences of the oracle's step.
+against central finite differences of the oracle's step and against the
+oracle's FP64 tangent-linear model (oracle.tangent_step).
 
 Loss L = sum_cells (B^y(t_N) - B^y_target)^2 dx^3 of the primitives after N
 steps; dL/dP^N = 2 (B^y - B^y_target) dx^3 in the B^y row.  The adjoint's
@@ -272,6 +273,46 @@ def test_adjoint_of_the_resistive_alfven_inverse_problem():
           "dL/dlog sigma0", gls, fds)
     assert rel.max() < TOL, (adj, fd, rel)
     assert abs(gls - fds) <= TOL * abs(fds)
+
+
+def test_adjoint_matches_the_oracle_tangent_linear():
+    """The adjoint inverse problem's setup (Alfven cube, WENO5, sigma = 1e3,
+    60 steps with checkpoints every 10, loss = sum (B^y - B^y_target)^2 dx^3,
+    target from the same initial data at sigma = 2e3) on a 16^3 grid, against
+    the oracle's own FP64 tangent-linear model (oracle.tangent_step: forward-
+    mode differentiation of the oracle's step): the adjoint's <dL/dP^0, u>
+    for six seeded smooth directions and dL/dlog sigma0 equal
+    <dL/dP^N, dP^N(u)> of the tangent-linear run, within 1e-6.  The target
+    and the loss's dL/dP^N are the oracle's own."""
+    wl = W.alfven_diag(n=16, sigma=1e3)
+    nsteps = 60
+    dx = wl.params["dx"]
+    dV = dx[0] * dx[1] * dx[2]
+    target = _oracle_final(wl, wl.prim, nsteps, sigma0=2e3)[9]
+    s = make_solver(wl)
+    s.adjoint_forward(wl.dt, nsteps, 10)
+    PN = s.get_prims()
+    lam = np.zeros_like(PN)
+    lam[9] = 2.0 * (PN[9] - target) * dV
+    grad, gls = s.adjoint_backward(lam)
+    s.close()
+    m = oracle_metric(wl)
+    rng = np.random.default_rng(2510)
+    adj, tlm = [], []
+    for u in _directions(wl.prim, rng, 6):
+        st, _, pN, dpN = oracle.tangent_step(wl.params, m, wl.prim, u, wl.dt, nsteps)
+        assert st == 0
+        tlm.append(float(np.sum(2.0 * (pN[9] - target) * dV * dpN[9])))
+        adj.append(float(np.sum(grad * u)))
+    adj, tlm = np.array(adj), np.array(tlm)
+    rel = np.abs(adj - tlm) / np.maximum(np.abs(tlm), 1e-2 * np.abs(tlm).max())
+    st, _, pN, ds = oracle.tangent_step(wl.params, m, wl.prim, np.zeros_like(wl.prim), wl.dt,
+                                        nsteps, dlog_sigma0=1.0)
+    tls = float(np.sum(2.0 * (pN[9] - target) * dV * ds[9]))
+    print("16^3 Alfven, 60 steps: adjoint vs oracle tangent-linear, max rel", rel.max(),
+          "dL/dlog sigma0", gls, tls)
+    assert rel.max() < TOL, (adj, tlm, rel)
+    assert abs(gls - tls) <= TOL * abs(tls), (gls, tls)
 
 
 def test_adjoint_leaves_the_state_and_rejects_unsupported_paths():
