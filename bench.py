@@ -317,6 +317,8 @@ def window_start(args):
     evolves, so the K timed steps sit in the middle of the configuration's
     100-step run (steps 41-60 for K = 20), where the step costs about the
     run's mean; at least the W warm-up steps precede them."""
+    if args.no_run100:      # short profiling runs: the window right after warm-up
+        return args.warmup
     return max(args.warmup, (RUN_STEPS - args.steps) // 2)
 
 
@@ -361,9 +363,10 @@ def run_ours(args, rank, world, local):
         # grows as the blast evolves)
         s.set_prims(prim0)
         str0 = s.stats()
-        ms_run, blk, per = timed_steps(s, wl.dt, RUN_STEPS, torch, blocks=10)
+        nrun = 10 if args.no_run100 else RUN_STEPS
+        ms_run, blk, per = timed_steps(s, wl.dt, nrun, torch, blocks=10)
         str1 = s.stats()
-        run = {"steps": RUN_STEPS, "ms": ms_run,
+        run = {"steps": nrun, "ms": ms_run,
                "ms_per_step_by_block": [b / k for b, k in zip(blk, per)],
                "paper_iterations_per_recovery":
                    (str1["c2p_iterations"] - str0["c2p_iterations"]) /
@@ -379,10 +382,10 @@ def run_ours(args, rank, world, local):
         by_block = []
         for b in range(10):
             sb0 = s.stats()
-            g = s.step_profiled(wl.dt, RUN_STEPS // 10)
+            g = s.step_profiled(wl.dt, nrun // 10)
             sb1 = s.stats()
             calls = max(1, sb1["c2p_calls"] - sb0["c2p_calls"])
-            row = {k: v / (RUN_STEPS // 10) for k, v in g.items()}
+            row = {k: v / (nrun // 10) for k, v in g.items()}
             row["iterations_per_recovery"] = (sb1["c2p_iterations"] - sb0["c2p_iterations"]) / calls
             row["fallbacks_per_recovery"] = (sb1["c2p_fallbacks"] - sb0["c2p_fallbacks"]) / calls
             by_block.append(row)
@@ -788,6 +791,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-configs", action="store_true")
+    ap.add_argument("--no-run100", action="store_true",
+                    help="skip the configuration's 100-step runs (short profiling runs)")
     ap.add_argument("--imex", type=int, default=0, choices=[0, 1, 2, 3],
                     help="IMEX scheme of the timed workload (0: SSP2(2,2,2), Table imex)")
     ap.add_argument("--adjoint-n", type=int, default=128)
@@ -894,7 +899,7 @@ def main():
     hbm, kind = _peaks()
     alg_b = ALG_BYTES_PER_ZONE[head]
     line["roofline"]["e2e_hbm_frac"] = alg_b * N * args.steps / (r["ms"] * 1e-3) / 1e9 / hbm
-    line["roofline"]["e2e_hbm_frac_run100"] = (alg_b * N * RUN_STEPS / (r["run"]["ms"] * 1e-3)
+    line["roofline"]["e2e_hbm_frac_run100"] = (alg_b * N * r["run"]["steps"] / (r["run"]["ms"] * 1e-3)
                                                / 1e9 / hbm)
     line["roofline"]["e2e_alg_bytes_per_zone"] = alg_b
     line["roofline"]["kernel_timing"] = ("rmhd_step_profiled over the same window from the "

@@ -360,6 +360,17 @@ int rmhd_test_mm3(const double *a, const double *b, const double *c, double *out
 int rmhd_test_mm3f(const float *a, const float *b, const float *c, float *out, long long n,
                    void *cuda_stream);
 
+/* Testing (no counterpart in the paper): the FP32 stencil kernels stage
+ * their tiles with tensor-map bulk copies (TMA) when enable != 0 (the
+ * default) and the grid allows it, with plain loads when enable == 0; the
+ * staged values, and so every result, are the same.  Applies to the flux
+ * launches enqueued afterwards in this process (a captured step graph keeps
+ * the choice it was captured with).  Returns the previous setting. */
+int rmhd_test_tile_copies(int enable);
+/* Testing: flux-kernel launches so far in this process that staged their
+ * tiles by tensor-map copies. */
+long long rmhd_test_tile_copy_launches(void);
+
 /* Text of the last error on this handle (never NULL; "" if none).  With
  * h == NULL: the last error, in the calling thread, of a call that had no
  * handle (rmhd_create, rmhd_con2prim_points, rmhd_con2prim_points_noalloc,

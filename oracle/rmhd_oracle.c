@@ -759,12 +759,29 @@ static int c2p_bracket(const c2p_in *in, real *p_io, real v_io[3], real cE[3],
     for (int i = 0; i < 3; i++) vl[i] = v0[i];
     real p0 = *p_io > 0.0 ? *p_io : in->P->K_atmo * pow(in->P->rho_atmo, in->P->gamma_eos);
     int n = 0, ok = pressure_fn(in, p0, vl, &f0);
-    /* f undefined at the guess: the root is above */
-    while (!ok) {
-        if (++n > 60) return 0;
-        p0 *= 2.0;
-        for (int i = 0; i < 3; i++) vl[i] = v0[i];
-        ok = pressure_fn(in, p0, vl, &f0);
+    /* f undefined at the guess: the root is above.  f is defined exactly
+     * above the lowest pressure p* at which the velocity equations have a
+     * solution, so the smallest defined pressure p0 2^k, k = 1 ... 60, each
+     * tried from the guess velocity, is found by bisection on k */
+    if (!ok) {
+        int klo = 0, khi = 60;
+        real vk[3] = {v0[0], v0[1], v0[2]}, fk;
+        if (!pressure_fn(in, p0 * ldexp(1.0, khi), vk, &fk)) return 0;
+        for (int i = 0; i < 3; i++) vl[i] = vk[i];
+        f0 = fk;
+        while (khi - klo > 1) {
+            const int km = (klo + khi) / 2;
+            for (int i = 0; i < 3; i++) vk[i] = v0[i];
+            if (pressure_fn(in, p0 * ldexp(1.0, km), vk, &fk)) {
+                khi = km;
+                f0 = fk;
+                for (int i = 0; i < 3; i++) vl[i] = vk[i];
+            } else {
+                klo = km;
+            }
+        }
+        n = khi;
+        p0 = p0 * ldexp(1.0, khi);
     }
     real lo = p0, hi = p0, flo = f0, fhi = f0;
     real vlo[3] = {vl[0], vl[1], vl[2]}, vhi[3] = {vl[0], vl[1], vl[2]};
@@ -785,7 +802,9 @@ static int c2p_bracket(const c2p_in *in, real *p_io, real v_io[3], real cE[3],
             real vt[3] = {vhi[0], vhi[1], vhi[2]}, ft;
             if (!pressure_fn(in, pt, vt, &ft)) {
                 und = pt;
-                if (und > hi * (1.0 - 1e-15)) return 0;
+                /* f < 0 down to within 1e-9 of the lowest defined pressure:
+                 * no root */
+                if (und > hi * (1.0 - 1e-9)) return 0;
                 continue;
             }
             if (ft < 0.0) {

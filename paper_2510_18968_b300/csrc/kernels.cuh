@@ -26,6 +26,7 @@
 #pragma once
 #include "physics.cuh"
 #include "recovery.cuh"
+#include "tma.cuh"
 
 namespace rmhd {
 
@@ -62,7 +63,8 @@ template <class T> __device__ __forceinline__ T kc(double d, float f)
 // metric fields: alpha, beta^x..z, gamma_xx..zz, K_xx..zz
 enum { M_ALPHA = 0, M_BETA = 1, M_GAMMA = 4, M_K = 10, NMET = 16 };
 
-enum { ST_ITERS = 0, ST_FALLBACK, ST_FAIL, ST_FLOOR, ST_MAXIT, ST_NAN, ST_CALLS, NSTAT };
+// ST_TILE: a stencil tile load did not complete within its wait bound
+enum { ST_ITERS = 0, ST_FALLBACK, ST_FAIL, ST_FLOOR, ST_MAXIT, ST_NAN, ST_CALLS, ST_TILE, NSTAT };
 
 __device__ __forceinline__ long long cell_at(const Grid &G, int i, int j, int k)
 {
@@ -526,17 +528,32 @@ __global__ void __launch_bounds__(128) k_flux(const StepConst K, const T *__rest
 // n) and stages 32 x 22 cells; every thread computes four or five faces
 // along D.  Coalesced loads all in flight at
 // once, then the stencil reads come from shared memory.
+// With tma != 0 the staged cells arrive by two bulk tensor copies (the 14
+// primitive fields, then J^D), completion on an mbarrier: D = 0 the row's
+// cells x0-3 .. x0+132 (boxes of 136 starting at the 4-aligned padded x0);
+// D > 0 boxes of 36 x 22 cells (x0-3 .. x0+32 by d0-3 .. d0+18).
 template <bool FLAT, int RC, int D>
 __global__ void __launch_bounds__(128)
 k_flux_tile(const StepConst K, const float *__restrict__ P, const float *__restrict__ Jc,
-            const double *__restrict__ met, const double *__restrict__ sig, float *F)
+            const double *__restrict__ met, const double *__restrict__ sig, float *F,
+            const __grid_constant__ CUtensorMap tmP, const __grid_constant__ CUtensorMap tmJ,
+            int tma, unsigned long long *stats)
 {
     constexpr int TX = D == 0 ? 128 : 32;   // faces (D = 0) or cells (D > 0) along x
     constexpr int TD = D == 0 ? 1 : 16;     // faces along D (D > 0)
-    constexpr int LX = D == 0 ? TX + 6 : TX;   // D = 0: the row's last block takes 129 faces
+    // D = 0: the row's last block takes 129 faces; rows of 136 (a multiple of
+    // 4 floats, as a tile copy needs)
+    // D > 0: rows of 36 floats starting 3 cells before x0 (a 4-aligned
+    // padded x), cell x0 + t at column t + 3
+    constexpr int LX = D == 0 ? TX + 8 : TX + 4;
+    constexpr int XO = D == 0 ? 0 : 3;
     constexpr int LD = D == 0 ? 1 : TD + 6;   // D > 0: the last block along D takes 17
     constexpr int NF = NPR + 1;
-    __shared__ float sm[NF][LD][LX];
+    constexpr int FSTRIDE = LD * LX;
+    constexpr int JOFF = (NPR * FSTRIDE + 31) / 32 * 32;   // J^D block, 128-byte aligned
+    __shared__ __align__(128) float sm[JOFF + FSTRIDE];
+    __shared__ __align__(8) uint64_t bar;
+    auto foff = [&](int f) -> int { return f < NPR ? f * FSTRIDE : JOFF; };
     const Grid &G = K.G;
     const long long S = G.S;
     const long long s = dstride(G, D);
@@ -559,8 +576,28 @@ k_flux_tile(const StepConst K, const float *__restrict__ P, const float *__restr
     // stage: cells x0-3 .. x0+TX+1 of the row (D = 0), or x0..x0+TX-1 by
     // d0-3 .. d0+TD+1 along D; only cells inside the padded grid
     const int nf_stage = useJ ? NF : NPR;
-    for (int idx = threadIdx.x; idx < LD * LX; idx += blockDim.x) {
-        const int dl = idx / LX, xl = idx - dl * LX;
+    if (tma) {
+        if (threadIdx.x == 0) mbar_init(&bar, 1);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            mbar_expect_tx(&bar, 4u * FSTRIDE * (NPR + (useJ ? 1 : 0)));
+            // padded coordinates: x of cell x0-3 is x0 (3 ghost cells); along
+            // D > 0 the first staged cell d0-3 is at d0
+            const int cy = D == 1 ? d0 : c1 + G.g[1];
+            const int cz = D == 2 ? d0 : c2 + G.g[2];
+            tma_load_4d(sm, &tmP, x0, cy, cz, 0, &bar);
+            if (useJ) tma_load_3d(sm + JOFF, &tmJ, x0, cy, cz, &bar);
+        }
+        // the block gives up together if any thread's bounded wait ran out
+        const bool arrived = mbar_wait(&bar, 0, TILE_WAIT_POLLS);
+        if (__syncthreads_or(!arrived)) {
+            if (threadIdx.x == 0) atomicOr(&stats[ST_TILE], 1ULL);
+            if (!arrived) mbar_wait(&bar, 0, TILE_WAIT_POLLS);   // let copies in flight land
+            return;
+        }
+    }
+    for (int idx = threadIdx.x; idx < (tma ? 0 : LD * (LX - XO)); idx += blockDim.x) {
+        const int dl = idx / (LX - XO), xl = idx - dl * (LX - XO);
         int ci, cj, ck;
         bool ok;
         if (D == 0) {
@@ -576,7 +613,7 @@ k_flux_tile(const StepConst K, const float *__restrict__ P, const float *__restr
         if (!ok) continue;
         const long long c = cell_at(G, ci, cj, ck);
         for (int f = 0; f < nf_stage; f++)
-            sm[f][dl][xl] = f < NPR ? P[f * S + c] : Jc[D * S + c];
+            sm[foff(f) + dl * LX + xl + XO] = f < NPR ? P[f * S + c] : Jc[D * S + c];
     }
     __syncthreads();
 
@@ -602,7 +639,7 @@ k_flux_tile(const StepConst K, const float *__restrict__ P, const float *__restr
         const long long cL = cR - s;
         // stencil o = 0..5: cells (face - 3 + o) along D
         auto at = [&](int f, int o) -> float {
-            return D == 0 ? sm[f][0][tx + o] : sm[f][dloc + o][tx];
+            return D == 0 ? sm[foff(f) + tx + o] : sm[foff(f) + (dloc + o) * LX + tx + XO];
         };
         float pL[NPR], pR[NPR];
 #pragma unroll
@@ -727,16 +764,29 @@ __device__ __forceinline__ void recon_cell(const T s[3], T &uM, T &uP)
     uM = s[1] - T(0.5) * sl;
 }
 
+// Staging by TMA (tma != 0): one bulk tensor copy of the 14 primitive fields
+// and one of J^D, boxes of 36 (x) by LD (along D) cells starting at the
+// 4-aligned x of the padded grid three cells before the block's first line,
+// so line t sits at column t + 3 of a 36-float row; completion on an
+// mbarrier.  Otherwise the threads stage the same rows with plain loads.
+constexpr int WALK_PITCH = 36;
+constexpr int WALK_LD = FB + 7;                                   // cells f0-3 .. f0+FB+3
+constexpr int WALK_JOFF = (NPR * WALK_LD * WALK_PITCH + 31) / 32 * 32;   // J rows, 128-byte aligned
+constexpr int WALK_SMEM = WALK_JOFF + WALK_LD * WALK_PITCH;
+
 template <bool FLAT, int RC, int D>
 __global__ void __launch_bounds__(128, 6)
 k_flux_walk(const StepConst K, const float *__restrict__ P, const float *__restrict__ Jc,
-            const double *__restrict__ met, const double *__restrict__ sig, float *F)
+            const double *__restrict__ met, const double *__restrict__ sig, float *F,
+            const __grid_constant__ CUtensorMap tmP, const __grid_constant__ CUtensorMap tmJ,
+            int tma, unsigned long long *stats)
 {
     static_assert(D > 0 && RC != RC_WENO5, "TVD faces along y and z only (else k_flux_tile)");
     constexpr int NF = NPR + 1;
-    constexpr int LD = FB + 7;     // cells f0-3 .. f0+FB+3 along D
-    constexpr int PITCH = 33;
-    __shared__ float sm[NF * LD * PITCH];
+    constexpr int LD = WALK_LD;
+    constexpr int PITCH = WALK_PITCH;
+    __shared__ __align__(128) float sm[WALK_SMEM];
+    __shared__ __align__(8) uint64_t bar;
     const Grid &G = K.G;
     const long long S = G.S;
     const long long s = dstride(G, D);
@@ -761,18 +811,44 @@ k_flux_walk(const StepConst K, const float *__restrict__ P, const float *__restr
         if (D == 1) return cell_at(G, b, a, c2);
         return cell_at(G, b, c2, a);
     };
-    // stage cells f0-3 .. f_end+1 along D of the block's lines (x fastest)
-    const int nd_stage = f_end + 2 - (f0 - 3);
-    const int nf_stage = useJ ? NF : NPR;
-    for (int idx = threadIdx.x; idx < 32 * nd_stage; idx += blockDim.x) {
-        const int d = idx >> 5, t = idx & 31;
-        if (t0 + t >= nT) continue;
-        const long long c = cell(t, d);
-        for (int f = 0; f < nf_stage; f++)
-            sm[(f * LD + d) * PITCH + t] = f < NPR ? P[f * S + c] : Jc[D * S + c];
+    // row of field f at position d (cell f0-3+d along D); line t at t + 3
+    auto row = [&](int f, int d) -> int {
+        return (f < NPR ? (f * LD + d) * PITCH : WALK_JOFF + d * PITCH) + 3;
+    };
+    if (tma) {
+        if (threadIdx.x == 0) mbar_init(&bar, 1);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const unsigned bytes = 4u * PITCH * LD * (NPR + (useJ ? 1 : 0));
+            mbar_expect_tx(&bar, bytes);
+            // padded coordinates: x of line -3 is t0 (3 ghost cells), the
+            // first cell along D (f0 - 3) is at f0, the fixed one at c2 + g
+            const int cy = D == 1 ? f0 : c2 + G.g[1];
+            const int cz = D == 1 ? c2 + G.g[2] : f0;
+            tma_load_4d(sm, &tmP, t0, cy, cz, 0, &bar);
+            if (useJ) tma_load_3d(sm + WALK_JOFF, &tmJ, t0, cy, cz, &bar);
+        }
+        // the block gives up together if any thread's bounded wait ran out
+        const bool arrived = mbar_wait(&bar, 0, TILE_WAIT_POLLS);
+        if (__syncthreads_or(!arrived)) {
+            if (threadIdx.x == 0) atomicOr(&stats[ST_TILE], 1ULL);
+            if (!arrived) mbar_wait(&bar, 0, TILE_WAIT_POLLS);   // let copies in flight land
+            return;
+        }
+    } else {
+        // stage cells f0-3 .. f_end+1 along D of the block's lines (x fastest)
+        const int nd_stage = f_end + 2 - (f0 - 3);
+        const int nf_stage = useJ ? NF : NPR;
+        for (int idx = threadIdx.x; idx < 32 * nd_stage; idx += blockDim.x) {
+            const int d = idx >> 5, t = idx & 31;
+            if (t0 + t >= nT) continue;
+            const long long c = cell(t, d);
+            for (int f = 0; f < nf_stage; f++)
+                sm[row(f, d) + t] = f < NPR ? P[f * S + c] : Jc[D * S + c];
+        }
+        __syncthreads();
     }
-    __syncthreads();
-    auto at = [&](int f, int d) -> float { return sm[(f * LD + d) * PITCH + lane]; };
+    auto at = [&](int f, int d) -> float { return sm[row(f, d) + lane]; };
 
     // this warp's faces fs .. fe-1 (the last warp takes the rest of the block)
     const int fs = f0 + w * FW;

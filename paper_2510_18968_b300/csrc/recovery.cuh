@@ -397,10 +397,11 @@ __device__ int newton_fallback(const RecCtx<FLAT> &c, double &p, double v[3], do
             if (p_conv<FLAT>(c, dx[0], x[0]) && dvm <= c.o.tol) break;
             return 0;
         }
-        const double sp = lam * dx[0];
-        const double sv = lam * fmax(fabs(dx[1]), fmax(fabs(dx[2]), fabs(dx[3])));
+        // converged when the full Newton step is below the tolerance (not
+        // the damped one, which a line search can make small anywhere)
+        const double sv = fmax(fabs(dx[1]), fmax(fabs(dx[2]), fabs(dx[3])));
         for (int k = 0; k < 4; k++) { x[k] = xt[k]; r[k] = rt[k]; }
-        if (p_conv<FLAT>(c, sp, x[0]) && sv <= c.o.tol) break;
+        if (p_conv<FLAT>(c, dx[0], x[0]) && sv <= c.o.tol) break;
         if (it == 50) return 0;
     }
     if (!joint_residual<FLAT>(c, x, r, E, rho, v)) return 0;
@@ -430,9 +431,11 @@ __device__ int newton_fallback(const RecCtx<FLAT> &c, double &p, double v[3], do
 // to the fallbacks.  Same stopping rule as the paper iteration.
 constexpr int STIFF_MAXIT = 30;
 
+// E_guess (optional): the implicit field already formed at the starting
+// point (the paper iteration's first implicit solve, at the same guess).
 template <bool FLAT>
 __device__ bool stiff_newton(const RecCtx<FLAT> &c, double &p, double v[3], double E[3],
-                             double &rho_out, int &iters)
+                             double &rho_out, int &iters, const double *E_guess = nullptr)
 {
     const double Gam = c.o.Gam, g1 = Gam - 1.0;
     const double sg = sgv(c), isg = isgv(c);
@@ -447,7 +450,13 @@ __device__ bool stiff_newton(const RecCtx<FLAT> &c, double &p, double v[3], doub
         const double v2 = dot3(vu, vl);
         if (!(pp > 0.0) || !(v2 < c.o.v2max)) return false;
         const double W = rsqrt(1.0 - v2);
-        implicit_field<FLAT>(c, vu, vl, v2, W, E);
+        if (!c.implicit) {
+            E[0] = c.in.cE0[0]; E[1] = c.in.cE0[1]; E[2] = c.in.cE0[2];
+        } else if (it == 1 && E_guess) {
+            E[0] = E_guess[0]; E[1] = E_guess[1]; E[2] = E_guess[2];
+        } else {
+            implicit_field<FLAT>(c, vu, vl, v2, W, E);
+        }
         double El[3], P[3];
         lower<double, FLAT>(c.m, E, El);
         const double EM = 0.5 * (dot3(E, El) + c.B2) * isg;
@@ -514,15 +523,17 @@ __device__ bool stiff_newton(const RecCtx<FLAT> &c, double &p, double v[3], doub
             lam *= 0.5;
         }
         if (!ok || !isfinite(dp)) return false;
-        const double sv = lam * fmax(fabs(dv[0]), fmax(fabs(dv[1]), fabs(dv[2])));
-        const double sp = lam * dp;
+        const double sv = fmax(fabs(dv[0]), fmax(fabs(dv[1]), fabs(dv[2])));
         pp = pn;
         vl[0] = vln[0]; vl[1] = vln[1]; vl[2] = vln[2];
-        if (p_conv<FLAT>(c, sp, pp) && sv <= c.o.tol) {
+        // converged when the full Newton step is below the tolerance (a
+        // halved step is small near the edge of the region without the
+        // equations being solved)
+        if (lam == 1.0 && p_conv<FLAT>(c, dp, pp) && sv <= c.o.tol) {
             raise<double, FLAT>(c.m, vl, v);
             const double v2f = dot3(v, vl);
             const double Wf = rsqrt(1.0 - v2f);
-            implicit_field<FLAT>(c, v, vl, v2f, Wf, E);
+            if (c.implicit) implicit_field<FLAT>(c, v, vl, v2f, Wf, E);
             p = pp;
             rho_out = c.in.D * ((1.0 - v2f) * Wf) * isg;
             return true;
@@ -645,11 +656,12 @@ __device__ bool pressure_function(const RecCtx<FLAT> &c, double p, double vl[3],
 // Second fallback: the pressure root with the velocity solved at every trial
 // pressure.  f is defined only above the lowest pressure at which the
 // velocity equations have a solution with v^2 < 1, so a pressure where the
-// solve fails lies below the root: from the guess, double the pressure
-// while f is undefined or positive, halve it while f is negative, replacing
-// a halving that lands where f is undefined by geometric bisection between
-// that pressure and the last one where f was defined; then Illinois regula
-// falsi on the bracket.
+// solve fails lies below the root: where f is undefined at the guess, the
+// smallest defined guess x 2^k (k <= 60) by bisection on k; from there,
+// double the pressure while f is positive, halve it while f is negative,
+// replacing a halving that lands where f is undefined by geometric bisection
+// between that pressure and the last one where f was defined (to 1e-9);
+// then Illinois regula falsi on the bracket.
 template <bool FLAT>
 __device__ int bracket_fallback(const RecCtx<FLAT> &c, double &p, double v[3], double E[3],
                                 double &rho_out, int &iters)
@@ -660,11 +672,29 @@ __device__ int bracket_fallback(const RecCtx<FLAT> &c, double &p, double v[3], d
     double p0 = p > 0.0 ? p : c.o.p_atmo;
     int n = 0;
     bool ok = pressure_function<FLAT>(c, p0, vl, f0, E, rho);
-    while (!ok) {   // f undefined at the guess: the root is above
-        if (++n > 60) return 0;
-        p0 *= 2.0;
-        vl[0] = v0[0]; vl[1] = v0[1]; vl[2] = v0[2];
-        ok = pressure_function<FLAT>(c, p0, vl, f0, E, rho);
+    if (!ok) {
+        // f undefined at the guess: the root is above.  f is defined exactly
+        // above the lowest pressure where the velocity equations have a
+        // solution, so the smallest defined p0 2^k, k = 1 ... 60 (each tried
+        // from the guess velocity), is found by bisection on k
+        int klo = 0, khi = 60;
+        double vk[3] = {v0[0], v0[1], v0[2]}, fk;
+        if (!pressure_function<FLAT>(c, p0 * ldexp(1.0, khi), vk, fk, E, rho)) return 0;
+        vl[0] = vk[0]; vl[1] = vk[1]; vl[2] = vk[2];
+        f0 = fk;
+        while (khi - klo > 1) {
+            const int km = (klo + khi) / 2;
+            vk[0] = v0[0]; vk[1] = v0[1]; vk[2] = v0[2];
+            if (pressure_function<FLAT>(c, p0 * ldexp(1.0, km), vk, fk, E, rho)) {
+                khi = km;
+                f0 = fk;
+                vl[0] = vk[0]; vl[1] = vk[1]; vl[2] = vk[2];
+            } else {
+                klo = km;
+            }
+        }
+        n = khi;
+        p0 = p0 * ldexp(1.0, khi);
     }
     double lo = p0, hi = p0, flo = f0, fhi = f0;
     double vlo[3] = {vl[0], vl[1], vl[2]}, vhi[3] = {vl[0], vl[1], vl[2]};
@@ -685,7 +715,9 @@ __device__ int bracket_fallback(const RecCtx<FLAT> &c, double &p, double v[3], d
             double vt[3] = {vhi[0], vhi[1], vhi[2]}, ft;
             if (!pressure_function<FLAT>(c, pt, vt, ft, E, rho)) {
                 und = pt;
-                if (und > hi * (1.0 - 1e-15)) return 0;
+                // f < 0 down to within 1e-9 of the lowest defined pressure:
+                // no root
+                if (und > hi * (1.0 - 1e-9)) return 0;
                 continue;
             }
             if (ft < 0.0) {
@@ -785,7 +817,7 @@ __device__ int recover(const RecIn &in, const Met<double> &m, const RecOpts &o,
                     double pn = guess_p, vn[3] = {guess_v[0], guess_v[1], guess_v[2]};
                     double En[3] = {in.cE0[0], in.cE0[1], in.cE0[2]}, rhon = 0.0;
                     int itn = 0;
-                    if (stiff_newton<FLAT>(c, pn, vn, En, rhon, itn)) {
+                    if (stiff_newton<FLAT>(c, pn, vn, En, rhon, itn, E)) {
                         newton_inline = true;
                         it1 = s.it;
                         it2 = itn;
@@ -838,16 +870,14 @@ __device__ int recover(const RecIn &in, const Met<double> &m, const RecOpts &o,
             p = guess_p;
             v[0] = guess_v[0]; v[1] = guess_v[1]; v[2] = guess_v[2];
             E[0] = in.cE0[0]; E[1] = in.cE0[1]; E[2] = in.cE0[2];
-            // stiff-coupling Newton (implicit stages), then the damped
-            // forward-difference Newton, then the pressure bracket
-            status = 2;
-            if (implicit) {
-                status = stiff_newton<FLAT>(c, p, v, E, rho, it2) ? 1 : 2;
-                if (status == 2) {
-                    p = guess_p;
-                    v[0] = guess_v[0]; v[1] = guess_v[1]; v[2] = guess_v[2];
-                    E[0] = in.cE0[0]; E[1] = in.cE0[1]; E[2] = in.cE0[2];
-                }
+            // the Newton method with the field-feedback Jacobian (exact with
+            // the field fixed), then the damped forward-difference Newton,
+            // then the pressure bracket
+            status = stiff_newton<FLAT>(c, p, v, E, rho, it2) ? 1 : 2;
+            if (status == 2) {
+                p = guess_p;
+                v[0] = guess_v[0]; v[1] = guess_v[1]; v[2] = guess_v[2];
+                E[0] = in.cE0[0]; E[1] = in.cE0[1]; E[2] = in.cE0[2];
             }
             if (status == 2) {
                 int itn = 0;

@@ -3,12 +3,66 @@
 // entry points (launches or a captured graph of the stage sequencing in
 // step_impl.cuh), and the testing entry points.  The adjoint entry points
 // are in adjoint_host.cu.
+#include <atomic>
+
 #include "host.cuh"
 
 namespace rmhd_host {
 // text of the calling thread's last error of a call without a handle
 thread_local char g_noh_err[512] = "";
 } // namespace rmhd_host
+
+namespace rmhd {
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// against the driver library), looked up once per process
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_tiled()
+{
+    static EncodeTiledFn fn = [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                             cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            p = nullptr;
+        return (EncodeTiledFn)p;
+    }();
+    return fn;
+}
+
+// tile copies enabled (rmhd_test_tile_copies), launches that used them
+static std::atomic<int> g_tile_copies{1};
+std::atomic<long long> g_tile_copy_launches{0};
+
+bool make_tile_map(CUtensorMap *map, const float *base, int px, int py, int pz,
+                   long long field_stride, int nf, int bx, int by, int bz)
+{
+    const EncodeTiledFn fn = encode_tiled();
+    if (!fn || !g_tile_copies.load()) return false;
+    // every stride a multiple of 16 bytes, the box's x extent too, the base
+    // 16-byte aligned: the conditions of a tile copy (the driver checks
+    // them again)
+    if ((px * 4) % 16 || (field_stride * 4) % 16 || (bx * 4) % 16 ||
+        ((uintptr_t)base) % 16)
+        return false;
+    const cuuint32_t rank = nf > 0 ? 4 : 3;
+    const cuuint64_t dims[4] = {(cuuint64_t)px, (cuuint64_t)py, (cuuint64_t)pz,
+                                (cuuint64_t)(nf > 0 ? nf : 1)};
+    const cuuint64_t strides[3] = {(cuuint64_t)px * 4, (cuuint64_t)px * py * 4,
+                                   (cuuint64_t)field_stride * 4};
+    const cuuint32_t box[4] = {(cuuint32_t)bx, (cuuint32_t)by, (cuuint32_t)bz,
+                               (cuuint32_t)(nf > 0 ? nf : 1)};
+    const cuuint32_t elem[4] = {1, 1, 1, 1};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, rank, (void *)base, dims, strides, box, elem,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+           CUDA_SUCCESS;
+}
+} // namespace rmhd
 
 extern "C" void rmhd_default_params(rmhd_params *p)
 {
@@ -141,7 +195,10 @@ extern "C" int rmhd_create(const rmhd_params *p, void *cuda_stream, rmhd_t *out)
         G.idx[d] = 1.0 / p->dx[d];
         G.bc[d] = p->bc[d];
     }
-    G.px = G.n[0] + 2 * G.g[0];
+    // x pitch rounded up to 4 cells when x is active: every row and every
+    // field then starts on a 16-byte boundary in both precisions, which the
+    // tensor-map (TMA) tile loads require; the pad cells are never read
+    G.px = G.g[0] ? (G.n[0] + 2 * G.g[0] + 3) / 4 * 4 : G.n[0];
     G.pxy = G.px * (G.n[1] + 2 * G.g[1]);
     G.S = (long long)G.pxy * (G.n[2] + 2 * G.g[2]);
     G.N = (long long)G.n[0] * G.n[1] * G.n[2];
@@ -610,6 +667,7 @@ extern "C" int rmhd_step(rmhd_t h, double dt, int nsteps, long long *fail_count)
     CK(cudaStreamSynchronize(h->st));
     *fail_count = (long long)(after[ST_FAIL] - before[ST_FAIL]);
     if (after[ST_NAN]) return set_err(h, RMHD_ENAN, "non-finite conserved values");
+    if (after[ST_TILE]) return set_err(h, RMHD_ECUDA, "a stencil tile load did not complete");
     if (*fail_count > 0)
         return set_err(h, RMHD_EC2P, "%lld recoveries reset to the atmosphere", *fail_count);
     return RMHD_OK;
@@ -863,6 +921,16 @@ __global__ void k_test_mm3f(long long n, const float *__restrict__ a,
 {
     const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (t < n) out[t] = mm3<float>(a[t], b[t], c[t]);
+}
+
+extern "C" int rmhd_test_tile_copies(int enable)
+{
+    return rmhd::g_tile_copies.exchange(enable != 0 ? 1 : 0);
+}
+
+extern "C" long long rmhd_test_tile_copy_launches(void)
+{
+    return rmhd::g_tile_copy_launches.load();
 }
 
 extern "C" int rmhd_test_mm3f(const float *a, const float *b, const float *c, float *out,

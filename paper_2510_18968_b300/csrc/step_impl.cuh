@@ -11,29 +11,61 @@
 // (k_flux_tile); y and z faces by walking runs (k_flux_walk, blocks of 32
 // x-lines x FB faces) for the TVD reconstructions, whose cell slopes the
 // two faces of a cell share, by 32 x 16 tiles (k_flux_tile) for WENO5
+// Tensor maps of the stage's primitives (14 fields) and of J^D for the tile
+// copies of one flux kernel, boxes {bx, by, bz}; false (plain staging) when
+// x is inactive or the driver refuses a map.
+static bool flux_maps(rmhd_t h, const float *P, const float *J, int D, int bx, int by, int bz,
+                      CUtensorMap *tmP, CUtensorMap *tmJ)
+{
+    const Grid &G = h->K.G;
+    memset(tmP, 0, sizeof(*tmP));
+    memset(tmJ, 0, sizeof(*tmJ));
+    if (G.g[0] != 3 || G.px % 4 != 0 || !P) return false;
+    const int py = G.n[1] + 2 * G.g[1], pz = G.n[2] + 2 * G.g[2];
+    if (!make_tile_map(tmP, P, G.px, py, pz, G.S, NPR, bx, by, bz)) return false;
+    if (h->K.qflux != 1 && J && !make_tile_map(tmJ, J + (size_t)D * G.S, G.px, py, pz, G.S, 0,
+                                               bx, by, bz))
+        return false;
+    g_tile_copy_launches.fetch_add(1);
+    return true;
+}
+
 template <bool FLAT, int RC>
 static void launch_flux_tile(rmhd_t h, const float *P, const float *J, float **Fd)
 {
     const Grid &G = h->K.G;
     const Buffers &b = h->b;
     const unsigned n0 = G.n[0], n1 = G.n[1], n2 = G.n[2];
-    if (G.g[0])
+    CUtensorMap tmP, tmJ;
+    if (G.g[0]) {
+        const int tma = flux_maps(h, P, J, 0, 136, 1, 1, &tmP, &tmJ);
         k_flux_tile<FLAT, RC, 0><<<dim3((n0 + 127) / 128, n1, n2), TPB, 0, h->st>>>(
-            h->K, P, J, b.met, b.sig, Fd[0]);
+            h->K, P, J, b.met, b.sig, Fd[0], tmP, tmJ, tma, b.stats);
+    }
     if constexpr (RC == RC_WENO5) {
-        if (G.g[1])
+        if (G.g[1]) {
+            const int tma = flux_maps(h, P, J, 1, 36, 22, 1, &tmP, &tmJ);
             k_flux_tile<FLAT, RC, 1><<<dim3((n0 + 31) / 32, (n1 + 15) / 16, n2), TPB, 0, h->st>>>(
-                h->K, P, J, b.met, b.sig, Fd[1]);
-        if (G.g[2])
+                h->K, P, J, b.met, b.sig, Fd[1], tmP, tmJ, tma, b.stats);
+        }
+        if (G.g[2]) {
+            const int tma = flux_maps(h, P, J, 2, 36, 1, 22, &tmP, &tmJ);
             k_flux_tile<FLAT, RC, 2><<<dim3((n0 + 31) / 32, n1, (n2 + 15) / 16), TPB, 0, h->st>>>(
-                h->K, P, J, b.met, b.sig, Fd[2]);
+                h->K, P, J, b.met, b.sig, Fd[2], tmP, tmJ, tma, b.stats);
+        }
     } else {
-        if (G.g[1])
+        if (G.g[1]) {
+            const int tma = flux_maps(h, P, J, 1, WALK_PITCH, WALK_LD, 1, &tmP, &tmJ);
             k_flux_walk<FLAT, RC, 1><<<dim3((n0 + 31) / 32, (n1 + FB - 1) / FB, n2), TPB, 0,
-                                       h->st>>>(h->K, P, J, b.met, b.sig, Fd[1]);
-        if (G.g[2])
+                                       h->st>>>(h->K, P, J, b.met, b.sig, Fd[1], tmP, tmJ, tma,
+                                                b.stats);
+        }
+        if (G.g[2]) {
+            const int tma = flux_maps(h, P, J, 2, WALK_PITCH, 1, WALK_LD, &tmP, &tmJ);
             k_flux_walk<FLAT, RC, 2><<<dim3((n0 + 31) / 32, n1, (n2 + FB - 1) / FB), TPB, 0,
-                                       h->st>>>(h->K, P, J, b.met, b.sig, Fd[2]);
+                                       h->st>>>(h->K, P, J, b.met, b.sig, Fd[2], tmP, tmJ, tma,
+                                                b.stats);
+        }
     }
 }
 

@@ -614,3 +614,40 @@ def test_fp32_mc2_minmod_matches_its_definition(torch_cuda):
     nz = want != 0
     assert np.array_equal(got[nz].view(np.uint32), want[nz].view(np.uint32))
     assert np.all((got[~nz] == 0) & ((got[~nz].view(np.uint32) & 0x7fffffff) == 0))
+
+
+@pytest.mark.parametrize("recon", ["minmod", "mc2", "weno5"])
+@pytest.mark.parametrize("curved", [False, True])
+@pytest.mark.parametrize("shape,qflux", [((37, 11, 6), 0), ((130, 19, 17), 0), ((64, 40, 1), 0),
+                                         ((5, 3, 9), 0), ((33, 1, 40), 0), ((70, 21, 9), 1)])
+def test_tile_copies_stage_what_plain_loads_stage(recon, curved, shape, qflux):
+    """The FP32 stencil kernels stage their tiles by tensor-map bulk copies
+    (TMA) or, with them switched off, by plain loads: two steps of the mixed
+    path must come out bit for bit the same (rows of 128 or 32 cells that
+    the extents do not divide, boxes running past the grid, extents below
+    one box, inactive directions, flat and curved, with and without the
+    staged current)."""
+    import paper_2510_18968_b300 as R
+    L = R.load()
+    wl = _smooth(0, recon, curved, shape=shape, seed=19)
+    wl.params["qflux_mode"] = qflux
+    wl.params["bc"] = (1, 0, 1)
+    wl.dt = 0.2 * min(h for h, n in zip(wl.params["dx"], shape) if n > 1)
+    out, used = [], []
+    prev = L.rmhd_test_tile_copies(1)
+    try:
+        for enable in (1, 0):
+            L.rmhd_test_tile_copies(enable)
+            n0 = L.rmhd_test_tile_copy_launches()
+            s = make_solver(wl, precision=1)
+            for _ in range(2):
+                s.step(wl.dt, 1)
+            out.append((s.get_cons(), s.get_prims()))
+            s.close()
+            used.append(L.rmhd_test_tile_copy_launches() - n0)
+    finally:
+        L.rmhd_test_tile_copies(prev)
+    # the copies ran where the grid holds a whole box across x (x extent of
+    # 33 cells or more) and, switched off, did not
+    assert used[1] == 0 and (used[0] > 0 or shape[0] < 33), used
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
