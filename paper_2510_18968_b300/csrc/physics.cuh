@@ -377,7 +377,12 @@ __device__ __forceinline__ double mm3_bits(double a, double b, double c)
 // by two min instructions on |a|, |b|, |c|, given a's sign; zero when the
 // signs differ, which (a ^ b) | (a ^ c) shows in its sign bit.  A zero
 // argument makes the magnitude zero.  Same value as the comparison form
-// for every non-NaN input (a zero result may carry a's sign).
+// for every non-NaN input (a zero result may carry a's sign).  NaN
+// arguments differ from the FP64 limiters: fminf ignores a NaN, so with
+// one NaN argument and the other two of a's sign the result is the smaller
+// of those two (the FP64 forms return 0); a NaN a gives a NaN slope.  The
+// mixed path's primitives are finite wherever the stencil reads them (a
+// non-finite conserved value stops the step with RMHD_ENAN first).
 __device__ __forceinline__ float mm3_f32(float a, float b, float c)
 {
     const float m = fminf(fabsf(a), fminf(fabsf(b), fabsf(c)));
