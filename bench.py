@@ -211,11 +211,11 @@ FLUX_FIELDS = 15 + 14
 # by the cell count; traffic grows with the cells).  Valid for the kernels
 # as they are; re-measure after changing one.
 TRAFFIC_PER_CELL = {
-    ("stage2_rhs_recovery", "mixed"): (891.962112e6 + 504.274176e6) / 128 ** 3,
+    ("stage2_rhs_recovery", "mixed"): (891.952896e6 + 503.537664e6) / 128 ** 3,
     # k_flux_tile (x) and k_flux_walk (y, z) with TMA tile loads, mean of the
     # three launches
-    ("flux_stage2", "mixed"): ((145.624832e6 + 152.813056e6 + 152.950784e6) +
-                               (79.967488e6 + 91.187712e6 + 89.742080e6)) / 3 / 128 ** 3,
+    ("flux_stage2", "mixed"): ((145.624832e6 + 152.910080e6 + 153.061120e6) +
+                               (79.967488e6 + 91.359488e6 + 89.982720e6)) / 3 / 128 ** 3,
     # k_flux_run, mean of the x, y, z launches
     ("flux_stage2", "fp64"): ((989.442560e6 + 372.153600e6 + 303.645184e6) +
                               (514.565888e6 + 203.661056e6 + 202.688768e6)) / 3 / 128 ** 3,
@@ -542,7 +542,7 @@ def kernel_rooflines(wl, res, prec, steps):
 # kernels as they are; re-measure after changing one.
 NCU_PIPES = {
     ("stage1_recovery", "mixed"): {"fp64_pipe_busy": 0.8179, "lane_efficiency": 26.80 / 32},
-    ("stage2_rhs_recovery", "mixed"): {"fp64_pipe_busy": 0.8021, "lane_efficiency": 27.71 / 32},
+    ("stage2_rhs_recovery", "mixed"): {"fp64_pipe_busy": 0.8080, "lane_efficiency": 27.71 / 32},
     ("final_rhs_recovery", "mixed"): {"fp64_pipe_busy": 0.7368, "lane_efficiency": 30.86 / 32},
 }
 

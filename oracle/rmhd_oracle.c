@@ -680,10 +680,12 @@ static real norm3(const real g[3])
     return sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
 }
 
-/* Velocity at fixed p: damped Newton on vel_resid from vl (in/out). */
+/* Velocity at fixed p: damped Newton on vel_resid from vl (in/out); gives
+ * up after eight damped steps in a row. */
 static int solve_velocity(const c2p_in *in, real p, real vl[3])
 {
     real g[3], cE[3];
+    int damped = 0;
     if (!vel_resid(in, p, vl, g, cE)) return 0;
     for (int it = 0; it < 30; it++) {
         real J[9], rhs[3], dv[3];
@@ -710,6 +712,10 @@ static int solve_velocity(const c2p_in *in, real p, real vl[3])
             lam *= 0.5;
         }
         if (!ok) return norm3(g) < 1e-13;
+        /* eight damped steps in a row: creeping toward a minimum of |g|
+         * that is not a solution; the pressure counts as undefined */
+        damped = lam < 1.0 ? damped + 1 : 0;
+        if (damped >= 8) return 0;
         real step = fmax(fabs(lam * dv[0]), fmax(fabs(lam * dv[1]), fabs(lam * dv[2])));
         for (int i = 0; i < 3; i++) { vl[i] = vt[i]; g[i] = gt[i]; }
         if (step <= 1e-15) break;

@@ -228,7 +228,7 @@ __device__ int paper_run(const RecCtx<FLAT> &c, PaperState &s, double p_guess, i
         // the implicit field contracts by about kappa = C/(1+C) B^2/den per
         // iteration (C = cc W); a cell that has not converged in its first
         // iteration while kappa > kappa0 would crawl or diverge, and is
-        // handed to the Newton fallback at once (same root)
+        // handed to the stiff-coupling Newton at once (same root)
         if (it == 1 && c.implicit && c.o.kappa0 > 0.0 &&
             C1 * c.B2 * isgv(c) > c.o.kappa0 * (1.0 + C1) * den) {
             s.slow = 2;
@@ -576,11 +576,13 @@ __device__ __forceinline__ double nrm3(const double g[3])
     return sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
 }
 
-// velocity at fixed p: damped Newton with a forward-difference Jacobian
+// velocity at fixed p: damped Newton with a forward-difference Jacobian;
+// gives up after eight damped steps in a row
 template <bool FLAT>
 __device__ bool velocity_at(const RecCtx<FLAT> &c, double p, double vl[3])
 {
     double g[3], E[3], v2;
+    int damped = 0;
     if (!vel_residual<FLAT>(c, p, vl, g, E, v2)) return false;
     for (int it = 0; it < 30; it++) {
         double J[9];
@@ -620,6 +622,10 @@ __device__ bool velocity_at(const RecCtx<FLAT> &c, double p, double vl[3])
             lam *= 0.5;
         }
         if (!ok) return n0 < 1e-13;
+        // eight damped steps in a row: creeping toward a minimum of |g| that
+        // is not a solution; the pressure counts as undefined
+        damped = lam < 1.0 ? damped + 1 : 0;
+        if (damped >= 8) return false;
         const double step = lam * fmax(fabs(dv[0]), fmax(fabs(dv[1]), fabs(dv[2])));
         for (int i = 0; i < 3; i++) { vl[i] = vt[i]; g[i] = gt[i]; }
         if (step <= 1e-15) break;
