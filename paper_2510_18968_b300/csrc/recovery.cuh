@@ -128,7 +128,7 @@ struct PaperState {
     int it;                   // iterations done
     double p, v[3], vl[3];    // current iterate
     double v2, W;             // of v
-    double prev0, prev1, prev2;  // change measures of the last iterations
+    float prev0, prev1, prev2;   // change measures of the last iterations
     int outcome;              // -1 undecided, 0 gave up (fallbacks next)
     int slow;                 // gave up for slow convergence
 };
@@ -137,7 +137,7 @@ __device__ __forceinline__ void pstate_save(const PaperState &s, double *dst, lo
 {
     const double vals[PSTATE] = {(double)s.it, s.p,     s.v[0],  s.v[1],  s.v[2],
                                  s.vl[0],      s.vl[1], s.vl[2], s.v2,    s.W,
-                                 s.prev0,      s.prev1, s.prev2, (double)s.outcome,
+                                 (double)s.prev0, (double)s.prev1, (double)s.prev2, (double)s.outcome,
                                  (double)s.slow};
     for (int k = 0; k < PSTATE; k++) dst[k * stride] = vals[k];
 }
@@ -152,9 +152,9 @@ __device__ __forceinline__ void pstate_load(PaperState &s, const double *src, lo
     }
     s.v2 = src[8 * stride];
     s.W = src[9 * stride];
-    s.prev0 = src[10 * stride];
-    s.prev1 = src[11 * stride];
-    s.prev2 = src[12 * stride];
+    s.prev0 = (float)src[10 * stride];
+    s.prev1 = (float)src[11 * stride];
+    s.prev2 = (float)src[12 * stride];
     s.outcome = (int)src[13 * stride];
     s.slow = (int)src[14 * stride];
 }
@@ -174,7 +174,7 @@ __device__ __forceinline__ bool paper_start(const RecCtx<FLAT> &c, double p, con
     // the first implicit solve needs W of the guess; with calE fixed the
     // first use of W is after fluid_step has set it
     s.W = c.implicit ? rsqrt(1.0 - s.v2) : 0.0;
-    s.prev0 = s.prev1 = s.prev2 = 0.0;
+    s.prev0 = s.prev1 = s.prev2 = 0.0f;
     s.outcome = -1;
     s.slow = 0;
     return true;
@@ -192,35 +192,43 @@ __device__ int paper_run(const RecCtx<FLAT> &c, PaperState &s, double p_guess, i
                          double E[3], double &rho_out, bool allow_slow, bool &slow_stop)
 {
     slow_stop = false;
-    const double Gam = c.o.Gam, g1 = Gam - 1.0, gg1 = Gam * (Gam - 1.0);
+    const double Gam = c.o.Gam, g1 = Gam - 1.0;
     const double D = c.in.D;
+    // FP32 copies for 1/f' and for the change measures and decisions (a
+    // derivative and magnitudes compared with the tolerance: their rounding
+    // moves neither the iteration's fixed point nor its FP64 iterate)
+    const float Gam_f = d2f_ftz(Gam), gg1_f = d2f_ftz(Gam * (Gam - 1.0)), D_f = d2f_ftz(D);
+    const float tol_f = d2f_ftz(c.o.tol), sg_f = FLAT ? 1.0f : d2f_ftz(c.sg);
+    const float tD_f = d2f_ftz(c.in.tau + D);   // energy scale: tau + D + sqrt(g) p
     // scale of the change measure (energy at the guess), needed only from
     // the second iteration on
-    double iscale0 = 0.0;
+    float iscale0 = 0.0f;
     const int last = limit < c.o.maxit ? limit : c.o.maxit;
     while (s.it < last) {
         const int it = ++s.it;
         if (c.implicit) implicit_field<FLAT>(c, s.v, s.vl, s.v2, s.W, E);
-        const double C1 = c.cc * s.W;   // coupling of this iteration's implicit solve
+        const double W1 = s.W;   // W of this iteration's implicit solve
         double vn[3], Winv, num, den;
         if (!fluid_step<FLAT>(c, E, s.p, s.vl, vn, s.v2, s.W, Winv, num, &den)) return 0;
         const double omv = 1.0 - s.v2;
         const double f = g1 * num * omv * isgv(c) - s.p;
         double ratio;
         if (num > 0.0) {
-            const double gn = Gam * num * Winv;
-            ratio = f * (D + gn) * rcp64(s.v2 * gg1 * num * Winv - D - gn);
+            const float num_f = d2f_ftz(num), Winv_f = d2f_ftz(Winv), v2_f = d2f_ftz(s.v2);
+            const float gn = Gam_f * num_f * Winv_f;
+            ratio = f * f2d_ftz(__fdividef(D_f + gn, v2_f * gg1_f * num_f * Winv_f - D_f - gn));
         } else {
             ratio = -f;
         }
         double pn = s.p - ratio;
         if (!(pn > 0.0)) pn = 0.1 * s.p;
-        const double dv =
-            fmax(fabs(vn[0] - s.v[0]), fmax(fabs(vn[1] - s.v[1]), fabs(vn[2] - s.v[2])));
-        const double dp = pn - s.p;
+        const float dv = fmaxf(fabsf(d2f_ftz(vn[0] - s.v[0])),
+                               fmaxf(fabsf(d2f_ftz(vn[1] - s.v[1])), fabsf(d2f_ftz(vn[2] - s.v[2]))));
+        const float dp = fabsf(d2f_ftz(pn - s.p));
         s.p = pn;
         s.v[0] = vn[0]; s.v[1] = vn[1]; s.v[2] = vn[2];
-        if (p_conv<FLAT>(c, dp, s.p) && dv <= c.o.tol) {
+        // step (v): |dp| sqrt(g) <= tol (tau + D + sqrt(g) p) and max|dv| <= tol
+        if (dp * sg_f <= tol_f * (tD_f + sg_f * d2f_ftz(pn)) && dv <= tol_f) {
             rho_out = D * Winv * isgv(c);
             return 1;
         }
@@ -229,22 +237,25 @@ __device__ int paper_run(const RecCtx<FLAT> &c, PaperState &s, double p_guess, i
         // iteration (C = cc W); a cell that has not converged in its first
         // iteration while kappa > kappa0 would crawl or diverge, and is
         // handed to the stiff-coupling Newton at once (same root)
-        if (it == 1 && c.implicit && c.o.kappa0 > 0.0 &&
-            C1 * c.B2 * isgv(c) > c.o.kappa0 * (1.0 + C1) * den) {
-            s.slow = 2;
-            return 0;
+        if (it == 1 && c.implicit && c.o.kappa0 > 0.0) {
+            const float C1_f = d2f_ftz(c.cc) * d2f_ftz(W1);   // coupling cc W
+            if (C1_f * d2f_ftz(c.B2) * (FLAT ? 1.0f : d2f_ftz(c.isg)) >
+                d2f_ftz(c.o.kappa0) * (1.0f + C1_f) * d2f_ftz(den)) {
+                s.slow = 2;
+                return 0;
+            }
         }
-        if (iscale0 == 0.0) iscale0 = sgv(c) * rcp64(c.in.tau + D + sgv(c) * p_guess);
-        const double meas = dv + fabs(dp) * iscale0;
+        if (iscale0 == 0.0f) iscale0 = __fdividef(sg_f, tD_f + sg_f * d2f_ftz(p_guess));
+        const float meas = dv + dp * iscale0;
         if (!isfinite(meas)) return 0;
         // diverging: three successive growing changes above the noise
         if (it >= 3 && meas > s.prev0 && s.prev0 > s.prev1 && s.prev1 > s.prev2 &&
-            meas > 1e3 * c.o.tol)
+            meas > 1e3f * tol_f)
             return 0;
         // converging too slowly: more than 24 further iterations predicted
-        if (!allow_slow && it >= 6 && meas < s.prev0 && s.prev0 > 0.0) {
-            const double rate = meas / s.prev0;
-            if (rate > 0.0 && log(c.o.tol / meas) / log(rate) > 24.0) {
+        if (!allow_slow && it >= 6 && meas < s.prev0 && s.prev0 > 0.0f) {
+            const float rate = meas / s.prev0;
+            if (rate > 0.0f && __logf(tol_f / meas) / __logf(rate) > 24.0f) {
                 slow_stop = true;
                 return 0;
             }
