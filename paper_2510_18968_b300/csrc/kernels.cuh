@@ -1325,6 +1325,17 @@ __device__ __forceinline__ void prim_write(const StepConst &K, long long c, cons
     for (int f = 0; f < 4; f++) Gs[f * S + c] = pr[PR_P + f];
 }
 
+// stage current J = Q v - Dt R/(alpha Dt) stored as T; the mixed path stores
+// it in FP32 and forms it in FP32 from the FP64 operands
+template <class T>
+__device__ __forceinline__ T stage_current(double Q, double v, double dR, double iad)
+{
+    if constexpr (std::is_same<T, float>::value)
+        return d2f_ftz(Q) * d2f_ftz(v) - d2f_ftz(dR) * d2f_ftz(iad);
+    else
+        return Q * v - dR * iad;
+}
+
 // outputs of stage 1 at a cell (primitives, Dt R1, stage current)
 template <class T>
 __device__ __forceinline__ void stage1_write(const StepConst &K, long long c, const double pr[NPR],
@@ -1337,7 +1348,7 @@ __device__ __forceinline__ void stage1_write(const StepConst &K, long long c, co
     for (int a = 0; a < 3; a++) {
         const double r = (E[a] - u[CO_EX + a]) * ig;
         dR1[a * S + c] = r;
-        J1[a * S + c] = from_double<T>(u[CO_Q] * pr[PR_VX + a] - r * iad);   // J = Q v - Dt R/(alpha Dt)
+        J1[a * S + c] = stage_current<T>(u[CO_Q], pr[PR_VX + a], r, iad);
     }
 }
 
@@ -1354,7 +1365,7 @@ __device__ __forceinline__ void stage2_write(const StepConst &K, long long c, co
     for (int a = 0; a < 3; a++) {
         const double r2 = (E[a] - us[CO_EX + a]) * ig;
         V[(CO_EX + a) * S + c] += 0.5 * (dR1[a * S + c] + r2);
-        J2[a * S + c] = from_double<T>(us[CO_Q] * p2[PR_VX + a] - r2 * iad);
+        J2[a * S + c] = stage_current<T>(us[CO_Q], p2[PR_VX + a], r2, iad);
     }
 }
 

@@ -460,6 +460,7 @@ __device__ bool stiff_newton(const RecCtx<FLAT> &c, double &p, double v[3], doub
     const float B2_ = d2f_ftz(c.B2), cc_ = d2f_ftz(c.cc), D_ = d2f_ftz(c.in.D);
     const float sg_ = FLAT ? 1.0f : d2f_ftz(sg), isg_ = FLAT ? 1.0f : d2f_ftz(isg);
     const float g1_ = d2f_ftz(g1);
+    const float tol_f = d2f_ftz(c.o.tol), tD_f = d2f_ftz(c.in.tau + c.in.D);
     double vl[3];
     lower<double, FLAT>(c.m, v, vl);
     double pp = p;
@@ -496,6 +497,7 @@ __device__ bool stiff_newton(const RecCtx<FLAT> &c, double &p, double v[3], doub
         // the blast's stiff cells, the iterations to reach it), which moves
         // about 60% of an iteration's arithmetic off the FP64 pipe.
         double dp, dv[3];
+        float dp_abs, sv;   // sizes of the step (stopping rule)
         {
             float vu_[3], vl_[3], El_[3], m_[3];
 #pragma unroll
@@ -543,8 +545,14 @@ __device__ bool stiff_newton(const RecCtx<FLAT> &c, double &p, double v[3], doub
             }
             const float dp_ = -__fdividef(f_ + dot3(fv, a), fp - dot3(fv, b));
             dp = f2d_ftz(dp_);
+            dp_abs = fabsf(dp_);
+            sv = 0.0f;
 #pragma unroll
-            for (int i = 0; i < 3; i++) dv[i] = f2d_ftz(a[i] - b[i] * dp_);
+            for (int i = 0; i < 3; i++) {
+                const float d = a[i] - b[i] * dp_;
+                dv[i] = f2d_ftz(d);
+                sv = fmaxf(sv, fabsf(d));
+            }
         }
         // keep the iterate physical: halve a step that leaves the region
         double lam = 1.0, pn = 0.0, vln[3];
@@ -562,13 +570,12 @@ __device__ bool stiff_newton(const RecCtx<FLAT> &c, double &p, double v[3], doub
             lam *= 0.5;
         }
         if (!ok || !isfinite(dp)) return false;
-        const double sv = fmax(fabs(dv[0]), fmax(fabs(dv[1]), fabs(dv[2])));
         pp = pn;
         vl[0] = vln[0]; vl[1] = vln[1]; vl[2] = vln[2];
         // converged when the full Newton step is below the tolerance (a
         // halved step is small near the edge of the region without the
         // equations being solved)
-        if (lam == 1.0 && p_conv<FLAT>(c, dp, pp) && sv <= c.o.tol) {
+        if (lam == 1.0 && dp_abs * sg_ <= tol_f * (tD_f + sg_ * d2f_ftz(pp)) && sv <= tol_f) {
             raise<double, FLAT>(c.m, vl, v);
             const double v2f = dot3(v, vl);
             const double Wf = rsqrt(1.0 - v2f);
