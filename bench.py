@@ -171,10 +171,12 @@ IMEX_ROWS = {
 # measured over the timed steps; the fallbacks count as overhead.
 # Flux kernels: per face, HBM bytes of a stencil read once (15 fields in,
 # 14 out) and flops of reconstruction + two flux states + HLLE.
-PAPER_ITER_FLOPS = {"implicit": 114, "fixed_E": 72}   # one paper iteration
+# FP64 only: the paper iteration's 1/f' and its change measures and stopping
+# decisions run in FP32, and so do the mixed path's stage currents.
+PAPER_ITER_FLOPS = {"implicit": 94, "fixed_E": 52}   # one paper iteration
 FP64_FIXED = {  # per cell, (mixed path, FP64 path)
-    "stage1_recovery": (28, 28),
-    "stage2_rhs_recovery": (97, 189),
+    "stage1_recovery": (19, 28),
+    "stage2_rhs_recovery": (88, 189),
     "final_rhs_recovery": (44, 136),
 }
 
@@ -223,8 +225,10 @@ TRAFFIC_PER_CELL = {
 
 
 def launches_per_step(wl):
-    """Kernels one step launches: a recovery kernel and its deferred pass per
-    stage and for the final recovery, the ghost fills (primitives, and the
+    """Kernels one step launches: a recovery kernel and its two deferred
+    passes (one thread per record, then one warp per record for those that
+    need the rest of the fallback chain) per stage and for the final
+    recovery, the ghost fills (primitives, and the
     stage currents when the charge flux uses them) of every stage whose F is
     formed and of the result, one flux kernel per active direction and
     formed F."""
@@ -232,7 +236,7 @@ def launches_per_step(wl):
     rows, _, nflux = IMEX_ROWS[wl.params.get("imex", 0)]
     stages = len(rows) + 1
     ghosts = nflux * (2 if wl.params["qflux_mode"] == 0 else 1) + 1
-    return 2 * (stages + 1) + ghosts + nflux * nd
+    return 3 * (stages + 1) + ghosts + nflux * nd
 
 
 def e2e_pipelined(R, torch, wl, prec, cons_h, prim_h, jobs_per_handle, handles=2):

@@ -37,7 +37,8 @@ struct Buffers {
     int *flag = nullptr;
     // deferred-recovery work lists (scratch): counters for the three
     // recoveries of a step, cell indices and records
-    int *dcount = nullptr, *didx = nullptr;
+    int *dcount = nullptr, *didx = nullptr;   // dcount: NDEFER list counters, then NDEFER
+    int *hidx = nullptr;                      // counters of the warp-per-record lists
     double *drec = nullptr;
     int dcap = 0;
     // general IMEX form (schemes other than Table imex): the F of earlier

@@ -1274,6 +1274,8 @@ struct Defer {
     int cap;             // 0: no deferral
     int *idx;            // interior linear index of the cell
     double *rec;         // DREC x cap, field-major
+    int *hcount;         // records handed on to the warp-per-record pass
+    int *hidx;           // their record slots
 };
 
 // warp-aggregated slot allocation; every lane of the warp must call it
@@ -1819,12 +1821,75 @@ k_deferred(const StepConst K, const Defer df, const double *__restrict__ met,
             const double cc =
                 implicit ? K.gimex * K.dt * m.alpha * sigma_cell(K, sig, c, in.D) : 0.0;
             status = recover<FLAT>(in, m, K.ro, implicit, cc, gp, gv, u[CO_PHI], u[CO_PSI],
-                                   u[CO_Q], pr, E, iters, REC_RESUME, &ps);
+                                   u[CO_Q], pr, E, iters, REC_RESUME_NEWTON, &ps);
+            if (status == REC_HARD) {
+                // the pressure bracket on a whole warp (next pass)
+                pstate_save(ps, df.rec + (NCO + 4) * cap + s, cap);
+            } else {
+                if (STAGE == 1) stage1_write(K, c, pr, E, u, m.alpha, P, Gs, dRo, J);
+                if (STAGE == 2) stage2_write(K, c, pr, E, u, m.alpha, dR1, P, Gs, V, J);
+                if (STAGE == 3) final_write<FLAT>(K, c, pr, status, m, U, P, Gs);
+            }
+        }
+        const bool hard = active && status == REC_HARD;
+        const unsigned mask = __ballot_sync(0xffffffffu, hard);
+        if (mask) {
+            const int lane = threadIdx.x & 31, leader = __ffs(mask) - 1;
+            int hb = 0;
+            if (lane == leader) hb = atomicAdd(df.hcount, __popc(mask));
+            hb = __shfl_sync(0xffffffffu, hb, leader);
+            if (hard) df.hidx[hb + __popc(mask & ((1u << lane) - 1u))] = s;
+        }
+        record_stats(stats, active && !hard, status, iters);
+    }
+}
+
+// The records whose paper iteration and both Newton methods failed: one warp
+// per record runs the pressure bracket (recover's warp-cooperative form,
+// every lane on the same record; lane 0 writes).  These are few (states
+// without a root, hard fronts) and each is long, so the warp's lanes
+// shorten the latency of the one record instead of running 32 records side
+// by side.
+template <bool FLAT, int STAGE, class T>
+__global__ void __launch_bounds__(128)
+k_deferred_hard(const StepConst K, const Defer df, const double *__restrict__ met,
+                const double *__restrict__ sig, const double *__restrict__ dR1, T *P,
+                double *Gs, double *dRo, T *J, double *V, double *U,
+                unsigned long long *stats)
+{
+    const Grid &G = K.G;
+    const int n = *df.hcount;
+    const long long cap = df.cap;
+    const int lane = threadIdx.x & 31;
+    const int warps = gridDim.x * (blockDim.x >> 5);
+    for (int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w < n; w += warps) {
+        const int s = df.hidx[w];
+        const long long t = df.idx[s];
+        int i, j, k;
+        interior_coords(G, t, i, j, k);
+        const long long c = cell_at(G, i, j, k);
+        double u[NCO], gv[3], pr[NPR], E[3];
+        for (int f = 0; f < NCO; f++) u[f] = df.rec[f * cap + s];
+        const double gp = df.rec[NCO * cap + s];
+        for (int a = 0; a < 3; a++) gv[a] = df.rec[(NCO + 1 + a) * cap + s];
+        PaperState ps;
+        pstate_load(ps, df.rec + (NCO + 4) * cap + s, cap);
+        Met<double> m;
+        load_metric<FLAT>(met, G.S, c, m);
+        RecIn in;
+        load_rec_in(u, in);
+        const bool implicit = STAGE != 3;
+        const double cc = implicit ? K.gimex * K.dt * m.alpha * sigma_cell(K, sig, c, in.D) : 0.0;
+        int iters = 0;
+        const int status = recover<FLAT, true>(in, m, K.ro, implicit, cc, gp, gv, u[CO_PHI],
+                                               u[CO_PSI], u[CO_Q], pr, E, iters,
+                                               REC_CHAIN_REST, &ps);
+        if (lane == 0) {
             if (STAGE == 1) stage1_write(K, c, pr, E, u, m.alpha, P, Gs, dRo, J);
             if (STAGE == 2) stage2_write(K, c, pr, E, u, m.alpha, dR1, P, Gs, V, J);
             if (STAGE == 3) final_write<FLAT>(K, c, pr, status, m, U, P, Gs);
         }
-        record_stats(stats, active, status, iters);
+        record_stats(stats, lane == 0, status, iters);
     }
 }
 

@@ -361,6 +361,44 @@ __device__ __forceinline__ bool solve4(double A[16], double b[4], double x[4])
     return true;
 }
 
+// Warp-cooperative form of the pressure bracket's velocity solves (WARP =
+// true): all 32 lanes of a warp hold the same record and take the same
+// branches; the independent evaluations of an iteration run side by side,
+// the forward-difference Jacobian's columns on lanes 0..2 and a line
+// search's candidate step lengths 2^-k, k = 0..39, on lane k mod 32.  The sequential search takes
+// the first k whose candidate is accepted; the warp takes the lowest
+// accepted k of each round of 32, which is the same k, with the same
+// arithmetic per candidate, so both forms make the same decisions.
+constexpr unsigned WARP_ALL = 0xffffffffu;
+constexpr int LS_MAX = 40;   // step halvings of a line search
+
+// 2^-k exactly (the sequential search's step length after k halvings)
+__device__ __forceinline__ double halvings(int k)
+{
+    return __hiloint2double((1023 - k) << 20, 0);
+}
+
+// lowest k in [0, LS_MAX) with eval(2^-k, payload) true, its payload
+// broadcast to every lane; -1 if none
+template <int NP, class F>
+__device__ __forceinline__ int warp_line_search(F eval, double out[NP])
+{
+    const int lane = threadIdx.x & 31;
+    for (int base = 0; base < LS_MAX; base += 32) {
+        const int k = base + lane;
+        double pay[NP];
+        const bool ok = k < LS_MAX && eval(halvings(k), pay);
+        const unsigned m = __ballot_sync(WARP_ALL, ok);
+        if (m) {
+            const int src = __ffs(m) - 1;
+#pragma unroll
+            for (int i = 0; i < NP; i++) out[i] = __shfl_sync(WARP_ALL, pay[i], src);
+            return base + src;
+        }
+    }
+    return -1;
+}
+
 // Fallback: damped Newton on (p, v_lower) with a forward-difference Jacobian.
 template <bool FLAT>
 __device__ int newton_fallback(const RecCtx<FLAT> &c, double &p, double v[3], double E[3],
@@ -395,7 +433,7 @@ __device__ int newton_fallback(const RecCtx<FLAT> &c, double &p, double v[3], do
         const double n0 = nrm4(r);
         double lam = 1.0, xt[4], rt[4], Et[3], rhot, vt[3];
         bool ok = false;
-        for (int ls = 0; ls < 40; ls++) {
+        for (int ls = 0; ls < LS_MAX; ls++) {
             for (int k = 0; k < 4; k++) xt[k] = x[k] + lam * dx[k];
             if (joint_residual<FLAT>(c, xt, rt, Et, rhot, vt) && nrm4(rt) < n0) {
                 ok = true;
@@ -624,7 +662,7 @@ __device__ __forceinline__ double nrm3(const double g[3])
 
 // velocity at fixed p: damped Newton with a forward-difference Jacobian;
 // gives up after eight damped steps in a row
-template <bool FLAT>
+template <bool FLAT, bool WARP = false>
 __device__ bool velocity_at(const RecCtx<FLAT> &c, double p, double vl[3])
 {
     double g[3], E[3], v2;
@@ -632,16 +670,49 @@ __device__ bool velocity_at(const RecCtx<FLAT> &c, double p, double vl[3])
     if (!vel_residual<FLAT>(c, p, vl, g, E, v2)) return false;
     for (int it = 0; it < 30; it++) {
         double J[9];
-        for (int col = 0; col < 3; col++) {
-            double vh[3] = {vl[0], vl[1], vl[2]}, gh[3], h = 1e-7;
-            vh[col] += h;
-            if (!vel_residual<FLAT>(c, p, vh, gh, E, v2)) {
-                h = -h;
-                vh[col] = vl[col] + h;
-                if (!vel_residual<FLAT>(c, p, vh, gh, E, v2)) return false;
+        if constexpr (WARP) {
+            // column `lane` on lanes 0..2, then every column on every lane
+            const int lane = threadIdx.x & 31;
+            double colv[3] = {0.0, 0.0, 0.0};
+            bool bad = false;
+            if (lane < 3) {
+                double vh[3], gh[3], Eh[3], v2h, h = 1e-7;
+                const double v0 = lane == 0 ? vl[0] : lane == 1 ? vl[1] : vl[2];
+                double vc = v0 + h;
+                vh[0] = lane == 0 ? vc : vl[0];
+                vh[1] = lane == 1 ? vc : vl[1];
+                vh[2] = lane == 2 ? vc : vl[2];
+                if (!vel_residual<FLAT>(c, p, vh, gh, Eh, v2h)) {
+                    h = -h;
+                    vc = v0 + h;
+                    vh[0] = lane == 0 ? vc : vl[0];
+                    vh[1] = lane == 1 ? vc : vl[1];
+                    vh[2] = lane == 2 ? vc : vl[2];
+                    bad = !vel_residual<FLAT>(c, p, vh, gh, Eh, v2h);
+                }
+                if (!bad) {
+                    const double ih = 1.0 / h;
+                    for (int row = 0; row < 3; row++) colv[row] = (gh[row] - g[row]) * ih;
+                }
             }
-            const double ih = 1.0 / h;
-            for (int row = 0; row < 3; row++) J[row * 3 + col] = (gh[row] - g[row]) * ih;
+            if (__any_sync(WARP_ALL, bad)) return false;
+#pragma unroll
+            for (int col = 0; col < 3; col++)
+#pragma unroll
+                for (int row = 0; row < 3; row++)
+                    J[row * 3 + col] = __shfl_sync(WARP_ALL, colv[row], col);
+        } else {
+            for (int col = 0; col < 3; col++) {
+                double vh[3] = {vl[0], vl[1], vl[2]}, gh[3], h = 1e-7;
+                vh[col] += h;
+                if (!vel_residual<FLAT>(c, p, vh, gh, E, v2)) {
+                    h = -h;
+                    vh[col] = vl[col] + h;
+                    if (!vel_residual<FLAT>(c, p, vh, gh, E, v2)) return false;
+                }
+                const double ih = 1.0 / h;
+                for (int row = 0; row < 3; row++) J[row * 3 + col] = (gh[row] - g[row]) * ih;
+            }
         }
         // 3x3 solve by Cramer's rule on -g
         const double det = J[0] * (J[4] * J[8] - J[5] * J[7]) - J[1] * (J[3] * J[8] - J[5] * J[6]) +
@@ -659,13 +730,31 @@ __device__ bool velocity_at(const RecCtx<FLAT> &c, double p, double vl[3])
         const double n0 = nrm3(g);
         double lam = 1.0, vt[3], gt[3];
         bool ok = false;
-        for (int ls = 0; ls < 40; ls++) {
-            for (int i = 0; i < 3; i++) vt[i] = vl[i] + lam * dv[i];
-            if (vel_residual<FLAT>(c, p, vt, gt, E, v2) && nrm3(gt) < n0) {
+        if constexpr (WARP) {
+            double pay[6];
+            const int k = warp_line_search<6>(
+                [&](double lm, double *q) {
+                    double vq[3], gq[3], Eq[3], v2q;
+                    for (int i = 0; i < 3; i++) vq[i] = vl[i] + lm * dv[i];
+                    const bool good = vel_residual<FLAT>(c, p, vq, gq, Eq, v2q) && nrm3(gq) < n0;
+                    for (int i = 0; i < 3; i++) { q[i] = vq[i]; q[3 + i] = gq[i]; }
+                    return good;
+                },
+                pay);
+            if (k >= 0) {
                 ok = true;
-                break;
+                lam = halvings(k);
+                for (int i = 0; i < 3; i++) { vt[i] = pay[i]; gt[i] = pay[3 + i]; }
             }
-            lam *= 0.5;
+        } else {
+            for (int ls = 0; ls < LS_MAX; ls++) {
+                for (int i = 0; i < 3; i++) vt[i] = vl[i] + lam * dv[i];
+                if (vel_residual<FLAT>(c, p, vt, gt, E, v2) && nrm3(gt) < n0) {
+                    ok = true;
+                    break;
+                }
+                lam *= 0.5;
+            }
         }
         if (!ok) return n0 < 1e-13;
         // eight damped steps in a row: creeping toward a minimum of |g| that
@@ -682,14 +771,14 @@ __device__ bool velocity_at(const RecCtx<FLAT> &c, double p, double vl[3])
 
 // scaled f(p) = (Gamma-1) rho eps - p with the velocity solved at p
 // (Newton from vl; if that does not converge, from rest)
-template <bool FLAT>
+template <bool FLAT, bool WARP = false>
 __device__ bool pressure_function(const RecCtx<FLAT> &c, double p, double vl[3], double &f,
                                   double E[3], double &rho)
 {
     if (!(p > 0.0)) return false;
-    if (!velocity_at<FLAT>(c, p, vl)) {
+    if (!velocity_at<FLAT, WARP>(c, p, vl)) {
         vl[0] = vl[1] = vl[2] = 0.0;
-        if (!velocity_at<FLAT>(c, p, vl)) return false;
+        if (!velocity_at<FLAT, WARP>(c, p, vl)) return false;
     }
     double g[3], v2;
     vel_residual<FLAT>(c, p, vl, g, E, v2);
@@ -714,7 +803,7 @@ __device__ bool pressure_function(const RecCtx<FLAT> &c, double p, double vl[3],
 // replacing a halving that lands where f is undefined by geometric bisection
 // between that pressure and the last one where f was defined (to 1e-9);
 // then Illinois regula falsi on the bracket.
-template <bool FLAT>
+template <bool FLAT, bool WARP = false>
 __device__ int bracket_fallback(const RecCtx<FLAT> &c, double &p, double v[3], double E[3],
                                 double &rho_out, int &iters)
 {
@@ -723,7 +812,7 @@ __device__ int bracket_fallback(const RecCtx<FLAT> &c, double &p, double v[3], d
     vl[0] = v0[0]; vl[1] = v0[1]; vl[2] = v0[2];
     double p0 = p > 0.0 ? p : c.o.p_atmo;
     int n = 0;
-    bool ok = pressure_function<FLAT>(c, p0, vl, f0, E, rho);
+    bool ok = pressure_function<FLAT, WARP>(c, p0, vl, f0, E, rho);
     if (!ok) {
         // f undefined at the guess: the root is above.  f is defined exactly
         // above the lowest pressure where the velocity equations have a
@@ -731,13 +820,13 @@ __device__ int bracket_fallback(const RecCtx<FLAT> &c, double &p, double v[3], d
         // from the guess velocity), is found by bisection on k
         int klo = 0, khi = 60;
         double vk[3] = {v0[0], v0[1], v0[2]}, fk;
-        if (!pressure_function<FLAT>(c, p0 * ldexp(1.0, khi), vk, fk, E, rho)) return 0;
+        if (!pressure_function<FLAT, WARP>(c, p0 * ldexp(1.0, khi), vk, fk, E, rho)) return 0;
         vl[0] = vk[0]; vl[1] = vk[1]; vl[2] = vk[2];
         f0 = fk;
         while (khi - klo > 1) {
             const int km = (klo + khi) / 2;
             vk[0] = v0[0]; vk[1] = v0[1]; vk[2] = v0[2];
-            if (pressure_function<FLAT>(c, p0 * ldexp(1.0, km), vk, fk, E, rho)) {
+            if (pressure_function<FLAT, WARP>(c, p0 * ldexp(1.0, km), vk, fk, E, rho)) {
                 khi = km;
                 f0 = fk;
                 vl[0] = vk[0]; vl[1] = vk[1]; vl[2] = vk[2];
@@ -756,7 +845,7 @@ __device__ int bracket_fallback(const RecCtx<FLAT> &c, double &p, double v[3], d
             lo = hi; flo = fhi;
             for (int i = 0; i < 3; i++) vlo[i] = vhi[i];
             hi = 2.0 * hi;
-            if (!pressure_function<FLAT>(c, hi, vhi, fhi, E, rho)) return 0;
+            if (!pressure_function<FLAT, WARP>(c, hi, vhi, fhi, E, rho)) return 0;
         }
     } else {
         // hi: f < 0 and defined; und: a lower pressure where f is undefined
@@ -765,7 +854,7 @@ __device__ int bracket_fallback(const RecCtx<FLAT> &c, double &p, double v[3], d
             if (++n > 120) return 0;
             const double pt = und > 0.0 ? sqrt(und * hi) : 0.5 * hi;
             double vt[3] = {vhi[0], vhi[1], vhi[2]}, ft;
-            if (!pressure_function<FLAT>(c, pt, vt, ft, E, rho)) {
+            if (!pressure_function<FLAT, WARP>(c, pt, vt, ft, E, rho)) {
                 und = pt;
                 // f < 0 down to within 1e-9 of the lowest defined pressure:
                 // no root
@@ -787,7 +876,7 @@ __device__ int bracket_fallback(const RecCtx<FLAT> &c, double &p, double v[3], d
         double pm = (lo * fhi - hi * flo) / (fhi - flo);
         if (!(pm > lo && pm < hi)) pm = 0.5 * (lo + hi);
         double vm[3] = {vlo[0], vlo[1], vlo[2]}, fm;
-        if (!pressure_function<FLAT>(c, pm, vm, fm, E, rho)) return 0;
+        if (!pressure_function<FLAT, WARP>(c, pm, vm, fm, E, rho)) return 0;
         if (fm > 0.0) {
             lo = pm; flo = fm;
             for (int i = 0; i < 3; i++) vlo[i] = vm[i];
@@ -816,15 +905,21 @@ __device__ int bracket_fallback(const RecCtx<FLAT> &c, double &p, double v[3], d
 // undecided then is handed back with its iterate in *ps, and a later pass
 // with REC_RESUME continues from exactly there (same arithmetic, same
 // decisions, same result as REC_ALL inline).
-enum { REC_ALL = 0, REC_PRIMARY = 1, REC_FALLBACK = 2, REC_FIRST = 3, REC_RESUME = 4 };
-enum { REC_DEFER = -1 };
+// REC_RESUME_NEWTON: as REC_RESUME, but a point whose paper iteration and
+// both Newton methods fail is handed back as REC_HARD (its iterate in *ps
+// marked given up) for the rest of the chain; REC_CHAIN_REST runs that rest
+// (the pressure bracket, the atmosphere), with WARP = true on a whole warp
+// per point.
+enum { REC_ALL = 0, REC_PRIMARY = 1, REC_FALLBACK = 2, REC_FIRST = 3, REC_RESUME = 4,
+       REC_RESUME_NEWTON = 5, REC_CHAIN_REST = 6 };
+enum { REC_DEFER = -1, REC_HARD = -2 };
 
 // Full pointwise recovery.  Writes the 14 primitives and the solved calE;
 // returns the status 0 (paper iteration), 1 (Newton fallback), 4 (pressure
 // bracket fallback), 2 (failed, atmosphere), 3 (rho below the floor,
 // atmosphere), or REC_DEFER (phase REC_PRIMARY only; nothing written).
 // guess_p, guess_v: previous stage.
-template <bool FLAT>
+template <bool FLAT, bool WARP = false>
 __device__ int recover(const RecIn &in, const Met<double> &m, const RecOpts &o,
                        bool implicit, double cc, double guess_p, const double guess_v[3],
                        double Phi, double Psi, double Q, double prim[NPR],
@@ -852,7 +947,9 @@ __device__ int recover(const RecIn &in, const Met<double> &m, const RecOpts &o,
     if (atmo) {
         status = 3;
     } else {
-        if (phase == REC_FIRST || phase == REC_RESUME) {
+        const bool resume =
+            phase == REC_RESUME || phase == REC_RESUME_NEWTON || phase == REC_CHAIN_REST;
+        if (phase == REC_FIRST || resume) {
             PaperState s;
             if (phase == REC_FIRST) {
                 // undecided or given up: both go to the second pass
@@ -925,23 +1022,31 @@ __device__ int recover(const RecIn &in, const Met<double> &m, const RecOpts &o,
             // the Newton method with the field-feedback Jacobian (exact with
             // the field fixed), then the damped forward-difference Newton,
             // then the pressure bracket
-            status = stiff_newton<FLAT>(c, p, v, E, rho, it2) ? 1 : 2;
+            // (REC_CHAIN_REST: both Newton methods failed in the pass before)
+            const bool rest = phase == REC_CHAIN_REST;
+            status = rest ? 2 : stiff_newton<FLAT>(c, p, v, E, rho, it2) ? 1 : 2;
             if (status == 2) {
                 p = guess_p;
                 v[0] = guess_v[0]; v[1] = guess_v[1]; v[2] = guess_v[2];
                 E[0] = in.cE0[0]; E[1] = in.cE0[1]; E[2] = in.cE0[2];
             }
-            if (status == 2) {
+            if (status == 2 && !rest) {
                 int itn = 0;
                 status = newton_fallback<FLAT>(c, p, v, E, rho, itn) ? 1 : 2;
                 it2 += itn;
+            }
+            if (status == 2 && phase == REC_RESUME_NEWTON) {
+                ps->outcome = 0;
+                ps->slow = slow ? 1 : 0;
+                iters = it1 + it2;
+                return REC_HARD;
             }
             if (status == 2) {
                 int it3 = 0;
                 p = guess_p;
                 v[0] = guess_v[0]; v[1] = guess_v[1]; v[2] = guess_v[2];
                 E[0] = in.cE0[0]; E[1] = in.cE0[1]; E[2] = in.cE0[2];
-                if (bracket_fallback<FLAT>(c, p, v, E, rho, it3)) status = 4;
+                if (bracket_fallback<FLAT, WARP>(c, p, v, E, rho, it3)) status = 4;
                 it2 += it3;
             }
             if (status == 2) {

@@ -164,10 +164,11 @@ static void free_all(Buffers &b)
     if (b.flag) cudaFree(b.flag);
     if (b.dcount) cudaFree(b.dcount);
     if (b.didx) cudaFree(b.didx);
+    if (b.hidx) cudaFree(b.hidx);
     if (b.drec) cudaFree(b.drec);
     b.stats = nullptr;
     b.flag = nullptr;
-    b.dcount = b.didx = nullptr;
+    b.dcount = b.didx = b.hidx = nullptr;
     b.drec = nullptr;
 }
 
@@ -266,8 +267,9 @@ extern "C" int rmhd_create(const rmhd_params *p, void *cuda_stream, rmhd_t *out)
         if (cap < 1024) cap = 1024;
         if (cap > (1LL << 30) / DREC) cap = (1LL << 30) / DREC;
         b.dcap = (int)cap;
-        if (cudaMalloc((void **)&b.dcount, NDEFER * sizeof(int)) != cudaSuccess ||
+        if (cudaMalloc((void **)&b.dcount, 2 * NDEFER * sizeof(int)) != cudaSuccess ||
             cudaMalloc((void **)&b.didx, sizeof(int) * (size_t)cap) != cudaSuccess ||
+            cudaMalloc((void **)&b.hidx, sizeof(int) * (size_t)cap) != cudaSuccess ||
             cudaMalloc((void **)&b.drec, sizeof(double) * DREC * (size_t)cap) != cudaSuccess) {
             free_all(b);
             set_err(nullptr, RMHD_ENOMEM, "cudaMalloc of the recovery work list failed");

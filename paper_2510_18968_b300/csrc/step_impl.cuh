@@ -119,6 +119,8 @@ static Defer defer_of(rmhd_t h, int which)
     d.cap = h->b.dcap;
     d.idx = h->b.didx;
     d.rec = h->b.drec;
+    d.hcount = h->b.dcount + NDEFER + which;
+    d.hidx = h->b.hidx;
     return d;
 }
 
@@ -129,6 +131,9 @@ static Defer defer_of(rmhd_t h, int which)
 // return at once.  Small blocks free their slot as soon as their two warps
 // are done, which evens out the tail of the few long records.
 const int TPB_DEFER = 64;
+// warp-per-record passes: four warps per block, four blocks per SM; blocks
+// past the list's count return at once
+const unsigned HARD_BLOCKS = 148 * 4;
 static unsigned deferred_blocks(rmhd_t h)
 {
     long long want = (h->b.dcap + TPB_DEFER - 1) / TPB_DEFER;
@@ -157,14 +162,18 @@ void enqueue_stages12_t(rmhd_t h, cudaEvent_t *ev, double *Us)
     const unsigned nbd = deferred_blocks(h);
     T *PA = (T *)b.PA, *PB = (T *)b.PB, *J1 = (T *)b.J1, *J2 = (T *)b.J2;
     T *F0 = (T *)b.F[0], *F1 = (T *)b.F[1], *F2 = (T *)b.F[2];
-    if (dfr) cudaMemsetAsync(b.dcount, 0, NDEFER * sizeof(int), h->st);
+    if (dfr) cudaMemsetAsync(b.dcount, 0, 2 * NDEFER * sizeof(int), h->st);
     mark(0);
     k_stage1<FLAT, T><<<nb, TPB, 0, h->st>>>(K, b.U, PA, b.GA, b.GA, b.dR1, J1, b.met, b.sig,
                                              defer_of(h, 0), b.stats);
-    if (dfr)
+    if (dfr) {
         k_deferred<FLAT, 1, T><<<nbd, TPB_DEFER, 0, h->st>>>(K, defer_of(h, 0), b.met, b.sig, nullptr,
                                                        PA, b.GA, b.dR1, J1, nullptr, nullptr,
                                                        b.stats);
+        k_deferred_hard<FLAT, 1, T><<<HARD_BLOCKS, 128, 0, h->st>>>(K, defer_of(h, 0), b.met, b.sig, nullptr,
+                                                       PA, b.GA, b.dR1, J1, nullptr, nullptr,
+                                                       b.stats);
+    }
     mark(1);
     launch_ghosts(h, PA, NPR);
     if (K.qflux == RMHD_QFLUX_GAUSS) gauss_charge<FLAT, T>(h, PA, nullptr);
@@ -174,10 +183,14 @@ void enqueue_stages12_t(rmhd_t h, cudaEvent_t *ev, double *Us)
     mark(3);
     k_stage2<FLAT, T><<<nb, TPB, 0, h->st>>>(K, b.U, PA, b.GA, F0, F1, F2, b.dR1, b.met, b.sig,
                                              PB, b.GB, b.V, J2, defer_of(h, 1), b.stats, Us);
-    if (dfr)
+    if (dfr) {
         k_deferred<FLAT, 2, T><<<nbd, TPB_DEFER, 0, h->st>>>(K, defer_of(h, 1), b.met, b.sig, b.dR1,
                                                        PB, b.GB, nullptr, J2, b.V, nullptr,
                                                        b.stats);
+        k_deferred_hard<FLAT, 2, T><<<HARD_BLOCKS, 128, 0, h->st>>>(K, defer_of(h, 1), b.met, b.sig, b.dR1,
+                                                       PB, b.GB, nullptr, J2, b.V, nullptr,
+                                                       b.stats);
+    }
     mark(4);
     launch_ghosts(h, PB, NPR);
     if (K.qflux == RMHD_QFLUX_GAUSS) gauss_charge<FLAT, T>(h, PB, nullptr);
@@ -199,10 +212,14 @@ template <bool FLAT, class T> void enqueue_final_t(rmhd_t h, cudaEvent_t *ev)
     mark(6);
     k_final<FLAT, T><<<nb, TPB, 0, h->st>>>(K, b.V, PB, b.GB, F0, F1, F2, b.met, b.U, PA, b.GA,
                                             defer_of(h, 2), b.stats);
-    if (dfr)
+    if (dfr) {
         k_deferred<FLAT, 3, T><<<nbd, TPB_DEFER, 0, h->st>>>(K, defer_of(h, 2), b.met, b.sig, nullptr,
                                                        PA, b.GA, nullptr, nullptr, nullptr, b.U,
                                                        b.stats);
+        k_deferred_hard<FLAT, 3, T><<<HARD_BLOCKS, 128, 0, h->st>>>(K, defer_of(h, 2), b.met, b.sig, nullptr,
+                                                       PA, b.GA, nullptr, nullptr, nullptr, b.U,
+                                                       b.stats);
+    }
     mark(7);
     launch_ghosts(h, PA, NPR);
     if (K.qflux == RMHD_QFLUX_GAUSS) gauss_charge<FLAT, T>(h, PA, b.U);
@@ -244,7 +261,7 @@ template <bool FLAT, class T> void enqueue_general_t(rmhd_t h, ProfMarks *pm)
     double *Gb[2] = {b.GA, b.GB};
     T *J = (T *)b.J1;
     T *F0 = (T *)b.F[0], *F1 = (T *)b.F[1], *F2 = (T *)b.F[2];
-    if (dfr) cudaMemsetAsync(b.dcount, 0, NDEFER * sizeof(int), h->st);
+    if (dfr) cudaMemsetAsync(b.dcount, 0, 2 * NDEFER * sizeof(int), h->st);
     mark(-1);
     int prev = 0;   // buffer of the previous stage's primitives (P^n: PA)
     for (int i = 0; i < s; i++) {
@@ -274,10 +291,14 @@ template <bool FLAT, class T> void enqueue_general_t(rmhd_t h, ProfMarks *pm)
                                                         F2, b.Fst, b.dRs, b.met, b.sig, Pb[cur],
                                                         Gb[cur], dRi, J, defer_of(h, i), b.stats);
         }
-        if (dfr)
+        if (dfr) {
             k_deferred<FLAT, 1, T><<<nbd, TPB_DEFER, 0, h->st>>>(Ki, defer_of(h, i), b.met, b.sig,
                                                            nullptr, Pb[cur], Gb[cur], dRi, J,
                                                            nullptr, nullptr, b.stats);
+            k_deferred_hard<FLAT, 1, T><<<HARD_BLOCKS, 128, 0, h->st>>>(Ki, defer_of(h, i), b.met, b.sig,
+                                                           nullptr, Pb[cur], Gb[cur], dRi, J,
+                                                           nullptr, nullptr, b.stats);
+        }
         mark(i == 0 ? 0 : 3);
         if (f_needed(tab, i)) {
             launch_ghosts(h, Pb[cur], NPR);
@@ -303,10 +324,14 @@ template <bool FLAT, class T> void enqueue_general_t(rmhd_t h, ProfMarks *pm)
     k_final_row<FLAT, T><<<nb, TPB, 0, h->st>>>(K, row, Pb[prev], Gb[prev], F0, F1, F2, b.Fst,
                                                 b.dRs, b.met, b.U, Pb[0], Gb[0], defer_of(h, s),
                                                 b.stats);
-    if (dfr)
+    if (dfr) {
         k_deferred<FLAT, 3, T><<<nbd, TPB_DEFER, 0, h->st>>>(K, defer_of(h, s), b.met, b.sig, nullptr,
                                                        Pb[0], Gb[0], nullptr, nullptr, nullptr,
                                                        b.U, b.stats);
+        k_deferred_hard<FLAT, 3, T><<<HARD_BLOCKS, 128, 0, h->st>>>(K, defer_of(h, s), b.met, b.sig, nullptr,
+                                                       Pb[0], Gb[0], nullptr, nullptr, nullptr,
+                                                       b.U, b.stats);
+    }
     mark(5);
     launch_ghosts(h, Pb[0], NPR);
     if (K.qflux == RMHD_QFLUX_GAUSS) gauss_charge<FLAT, T>(h, Pb[0], b.U);
