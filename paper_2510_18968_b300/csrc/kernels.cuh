@@ -958,6 +958,188 @@ k_flux_walk(const StepConst K, const float *__restrict__ P, const float *__restr
     }
 }
 
+// FP32 face fluxes along x for the TVD reconstructions, walking: each warp
+// takes a segment of 128 faces of one x row (the row's last segment also
+// its face n) in chunks of 32, lane L owning face and cell x0 + 32 ch + L.
+// Each cell is reconstructed once (one slope for its states at the face
+// below and above, the arithmetic of reconstruct()); a face takes the upper
+// state of the cell below from the lane below (a warp shuffle; lane 0 from
+// lane 31 of the chunk before, or, for the segment's first face, from the
+// cell x0 - 1 reconstructed by every lane) and the lower state of its own
+// cell, so that a warp stores 32 consecutive faces per field.  The block's
+// four warps take four consecutive rows, staged by one tensor-map copy of
+// 136 x 4 cells x 14 fields (cells x0-3 .. x0+132 of each row) and one of
+// J^x, completion on an mbarrier (tma != 0), or with plain loads.
+constexpr int XW_ROWS = 4;
+constexpr int XW_LX = 136;
+
+template <bool FLAT, int RC>
+__global__ void __launch_bounds__(128, 6)
+k_flux_xwalk(const StepConst K, const float *__restrict__ P, const float *__restrict__ Jc,
+             const double *__restrict__ met, const double *__restrict__ sig, float *F,
+             const __grid_constant__ CUtensorMap tmP, const __grid_constant__ CUtensorMap tmJ,
+             int tma, unsigned long long *stats)
+{
+    static_assert(RC != RC_WENO5, "TVD reconstructions only (else k_flux_tile)");
+    constexpr int D = 0;
+    constexpr int NF = NPR + 1;
+    constexpr int ROWSZ = XW_ROWS * XW_LX;   // floats per field
+    constexpr int JOFF = NPR * ROWSZ;        // J^x rows (a multiple of 32 floats)
+    static_assert(JOFF % 32 == 0, "128-byte aligned J rows");
+    __shared__ __align__(128) float sm[JOFF + ROWSZ];
+    __shared__ __align__(8) uint64_t bar;
+    const Grid &G = K.G;
+    const long long S = G.S;
+    const bool useJ = K.qflux != 1;   // mode 2: Q row overwritten later
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int x0 = blockIdx.x * 128;
+    const int j = blockIdx.y * XW_ROWS + w, k = blockIdx.z;
+    const int x_end = blockIdx.x + 1 == gridDim.x ? G.n[0] + 1 : x0 + 128;   // faces x0 .. x_end-1
+    if (tma) {
+        if (threadIdx.x == 0) mbar_init(&bar, 1);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            mbar_expect_tx(&bar, 4u * ROWSZ * (NPR + (useJ ? 1 : 0)));
+            // padded coordinates: x of cell x0-3 is x0 (3 ghost cells)
+            const int cy = blockIdx.y * XW_ROWS + G.g[1], cz = k + G.g[2];
+            tma_load_4d(sm, &tmP, x0, cy, cz, 0, &bar);
+            if (useJ) tma_load_3d(sm + JOFF, &tmJ, x0, cy, cz, &bar);
+        }
+        // the block gives up together if any thread's bounded wait ran out
+        const bool arrived = mbar_wait(&bar, 0, TILE_WAIT_POLLS);
+        if (__syncthreads_or(!arrived)) {
+            if (threadIdx.x == 0) atomicOr(&stats[ST_TILE], 1ULL);
+            if (!arrived) mbar_wait(&bar, 0, TILE_WAIT_POLLS);   // let copies in flight land
+            return;
+        }
+    } else {
+        // the same cells with plain loads (zeros past the row's ghost cells
+        // and for rows past the grid: read by no face that is stored)
+        const int nf_stage = useJ ? NF : NPR;
+        for (int idx = threadIdx.x; idx < ROWSZ; idx += blockDim.x) {
+            const int r = idx / XW_LX, xl = idx - r * XW_LX;
+            const int ci = x0 - 3 + xl, cj = blockIdx.y * XW_ROWS + r;
+            const bool ok = ci <= G.n[0] + 2 && cj < G.n[1];
+            const long long c = ok ? cell_at(G, ci, cj, k) : 0;
+            for (int f = 0; f < nf_stage; f++)
+                sm[(f < NPR ? f * ROWSZ : JOFF) + idx] =
+                    ok ? (f < NPR ? P[f * S + c] : Jc[D * S + c]) : 0.f;
+        }
+        __syncthreads();
+    }
+    if (j >= G.n[1]) return;   // the whole warp: rows past the grid
+    // field f of this warp's row at column xl (cell x0 - 3 + xl)
+    auto at = [&](int f, int xl) -> float {
+        return f < NPR ? sm[f * ROWSZ + w * XW_LX + xl] : sm[JOFF + w * XW_LX + xl];
+    };
+    const float gfac = K.gfacf;
+    const int nch = (x_end - x0 + 31) >> 5;   // 4, or 5 when the segment also takes face n
+    // upper states of the cell x0 - 1 (column 2): the left state of face x0
+    float carry[NF];
+#pragma unroll
+    for (int f = 0; f < NF; f++) {
+        if (f == NPR && !useJ) { carry[f] = 0.f; continue; }
+        const float st[3] = {at(f, 1), at(f, 2), at(f, 3)};
+        float um;
+        recon_cell<float, RC>(st, um, carry[f]);
+    }
+#pragma unroll 1
+    for (int ch = 0; ch < nch; ch++) {
+        const int fi = x0 + 32 * ch + lane;
+        const bool live = fi < x_end;
+        // column of cell fi; lanes past the segment's faces (which store
+        // nothing and feed only lanes past it) read a clamped column
+        const int xl = min(32 * ch + lane + 3, XW_LX - 2);
+        float pL[NPR], pR[NPR];
+        float JL = 0.f, JR = 0.f;
+#pragma unroll
+        for (int f = 0; f < NF; f++) {
+            if (f == NPR && !useJ) continue;
+            const float st[3] = {at(f, xl - 1), at(f, xl), at(f, xl + 1)};
+            float um, up;
+            recon_cell<float, RC>(st, um, up);
+            const float below = __shfl_up_sync(0xffffffffu, up, 1);
+            const float left = lane == 0 ? carry[f] : below;
+            carry[f] = __shfl_sync(0xffffffffu, up, 31);   // for the next chunk's lane 0
+            if (f < NPR) { pL[f] = left; pR[f] = um; }
+            else { JL = left; JR = um; }
+        }
+        if (!live) continue;
+        const long long cR = cell_at(G, fi, j, k), cL = cR - 1;
+        Met<float> m;
+        if (FLAT) {
+            m.alpha = 1.f;
+            m.beta[0] = m.beta[1] = m.beta[2] = 0.f;
+            m.g[0] = m.g[3] = m.g[5] = 1.f;
+            m.g[1] = m.g[2] = m.g[4] = 0.f;
+            m.gi[0] = m.gi[3] = m.gi[5] = 1.f;
+            m.gi[1] = m.gi[2] = m.gi[4] = 0.f;
+            m.sg = m.isg = 1.f;
+        } else {
+            m.alpha = (float)(0.5 * (met[M_ALPHA * S + cL] + met[M_ALPHA * S + cR]));
+            for (int a = 0; a < 3; a++)
+                m.beta[a] = (float)(0.5 * (met[(M_BETA + a) * S + cL] + met[(M_BETA + a) * S + cR]));
+            for (int a = 0; a < 6; a++)
+                m.g[a] = (float)(0.5 * (met[(M_GAMMA + a) * S + cL] + met[(M_GAMMA + a) * S + cR]));
+            met_complete(m);
+        }
+        // a face state with rho <= 0, p <= 0 or v^2 >= 1 falls back to its
+        // cell's values (all fields)
+#pragma unroll
+        for (int sd = 0; sd < 2; sd++) {
+            float *q = sd == 0 ? pL : pR;
+            float v[3] = {q[PR_VX], q[PR_VY], q[PR_VZ]}, vl[3];
+            lower<float, FLAT>(m, v, vl);
+            if (!(q[PR_RHO] > 0.f) || !(q[PR_P] > 0.f) || !(dot3(v, vl) < 1.f)) {
+                const int xc = sd == 0 ? xl - 1 : xl;
+#pragma unroll
+                for (int f = 0; f < NPR; f++) q[f] = at(f, xc);
+                if (useJ) {
+                    if (sd == 0) JL = at(NPR, xc);
+                    else JR = at(NPR, xc);
+                }
+            }
+        }
+        float sigma = K.sigma0f;
+        if (K.sigma_model == 1) {
+            sigma = (float)(K.sigma0 * 0.5 * (sig[cL] + sig[cR]));
+        } else if (K.sigma_model >= 2) {
+            double sgm = 0.0;
+            for (int sd = 0; sd < 2; sd++) {
+                const long long cc = sd == 0 ? cL : cR;
+                Met<double> mc;
+                load_metric<FLAT>(met, S, cc, mc);
+                double v[3] = {(double)P[PR_VX * S + cc], (double)P[PR_VY * S + cc],
+                               (double)P[PR_VZ * S + cc]}, vl[3];
+                lower<double, FLAT>(mc, v, vl);
+                double Dc = mc.sg * (double)P[PR_RHO * S + cc] / sqrt(1.0 - dot3(v, vl));
+                sgm += 0.5 * sigma_cell(K, sig, cc, Dc);
+            }
+            sigma = (float)sgm;
+        }
+        float cFL, cFR, cUU;
+        if (FLAT) {
+            cFL = 0.5f; cFR = 0.5f; cUU = -0.5f;
+        } else {
+            const float sq = sqrt(m.gi[sym(D, D)]);
+            const float bs = m.beta[D] / m.alpha;
+            float ap = sq - bs, am = -sq - bs;
+            ap = ap > 0.f ? ap : 0.f;
+            am = am < 0.f ? am : 0.f;
+            const float inv = 1.f / (ap - am);
+            cFL = ap * inv; cFR = -am * inv; cUU = ap * am * inv;
+        }
+        float acc[NCO];
+#pragma unroll
+        for (int f = 0; f < NCO; f++) acc[f] = 0.f;
+        ArrAcc<float> aa{acc};
+        flux_accumulate<float, FLAT, D>(pL, m, sigma, gfac, useJ, JL, cFL, -cUU, aa);
+        flux_accumulate<float, FLAT, D>(pR, m, sigma, gfac, useJ, JR, cFR, cUU, aa);
+#pragma unroll
+        for (int f = 0; f < NCO; f++) F[f * S + cR] = acc[f];
+    }
+}
+
 // Reconstruction of cell c along D: its state at the face below (m) and
 // above (p) for the 14 primitives and, when J != nullptr, the current J^D.
 template <class T, int RC>

@@ -7,10 +7,11 @@
 #pragma once
 #include "host.cuh"
 
-// FP32 face fluxes through shared-memory tiles: x faces by rows of 128
-// (k_flux_tile); y and z faces by walking runs (k_flux_walk, blocks of 32
-// x-lines x FB faces) for the TVD reconstructions, whose cell slopes the
-// two faces of a cell share, by 32 x 16 tiles (k_flux_tile) for WENO5
+// FP32 face fluxes through shared-memory tiles: for the TVD reconstructions,
+// whose cell slopes the two faces of a cell share, x faces by walking warps
+// (k_flux_xwalk, segments of 128 faces of four rows) and y and z faces by
+// walking runs (k_flux_walk, blocks of 32 x-lines x FB faces); for WENO5 x
+// faces by rows of 128 (k_flux_tile) and y, z faces by 32 x 16 tiles
 // Tensor maps of the stage's primitives (14 fields) and of J^D for the tile
 // copies of one flux kernel, boxes {bx, by, bz}; false (plain staging) when
 // x is inactive or the driver refuses a map.
@@ -38,9 +39,16 @@ static void launch_flux_tile(rmhd_t h, const float *P, const float *J, float **F
     const unsigned n0 = G.n[0], n1 = G.n[1], n2 = G.n[2];
     CUtensorMap tmP, tmJ;
     if (G.g[0]) {
-        const int tma = flux_maps(h, P, J, 0, 136, 1, 1, &tmP, &tmJ);
-        k_flux_tile<FLAT, RC, 0><<<dim3((n0 + 127) / 128, n1, n2), TPB, 0, h->st>>>(
-            h->K, P, J, b.met, b.sig, Fd[0], tmP, tmJ, tma, b.stats);
+        if constexpr (RC != RC_WENO5) {
+            const int tma = flux_maps(h, P, J, 0, XW_LX, XW_ROWS, 1, &tmP, &tmJ);
+            k_flux_xwalk<FLAT, RC><<<dim3((n0 + 127) / 128, (n1 + XW_ROWS - 1) / XW_ROWS, n2), TPB,
+                                     0, h->st>>>(h->K, P, J, b.met, b.sig, Fd[0], tmP, tmJ, tma,
+                                                 b.stats);
+        } else {
+            const int tma = flux_maps(h, P, J, 0, 136, 1, 1, &tmP, &tmJ);
+            k_flux_tile<FLAT, RC, 0><<<dim3((n0 + 127) / 128, n1, n2), TPB, 0, h->st>>>(
+                h->K, P, J, b.met, b.sig, Fd[0], tmP, tmJ, tma, b.stats);
+        }
     }
     if constexpr (RC == RC_WENO5) {
         if (G.g[1]) {
