@@ -751,7 +751,7 @@ k_flux_tile(const StepConst K, const float *__restrict__ P, const float *__restr
 // the cell below, carried in registers from the previous face, and the
 // lower state of the cell above.  The last block along D also takes face
 // n_D (its last warp walks one face more).
-constexpr int FW = 2;          // faces per warp run
+constexpr int FW = 3;          // faces per warp run
 constexpr int FB = 4 * FW;     // faces per block along D (the last block: one more)
 
 // TVD states of the cell s[1] (stencil s[0..2]) at its lower (uM) and
