@@ -216,8 +216,8 @@ TRAFFIC_PER_CELL = {
     ("stage2_rhs_recovery", "mixed"): (884.850944e6 + 493.886976e6) / 128 ** 3,
     # k_flux_xwalk (x) and k_flux_walk (y, z) with TMA tile loads, mean of
     # the three launches
-    ("flux_stage2", "mixed"): ((148.798208e6 + 152.910080e6 + 153.061120e6) +
-                               (79.073536e6 + 91.359488e6 + 89.982720e6)) / 3 / 128 ** 3,
+    ("flux_stage2", "mixed"): ((148.613376e6 + 152.915712e6 + 153.597952e6) +
+                               (77.392640e6 + 84.397824e6 + 85.279232e6)) / 3 / 128 ** 3,
     # k_flux_run, mean of the x, y, z launches
     ("flux_stage2", "fp64"): ((989.442560e6 + 372.153600e6 + 303.645184e6) +
                               (514.565888e6 + 203.661056e6 + 202.688768e6)) / 3 / 128 ** 3,
