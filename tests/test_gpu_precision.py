@@ -1,6 +1,6 @@
-"""Mixed precision at each configuration's own run length (the benchmark spec
-"Precision": FP32 reconstruction, fluxes and RK combination, FP64 recovery,
-implicit field and conserved accumulation): relative L1 per field of the
+"""Mixed precision at each configuration's own run length (the mixed path:
+FP32 reconstruction, fluxes and RK combination, FP64 recovery, implicit
+field and conserved accumulation): relative L1 per field of the
 mixed path against the FP64 path (itself checked against the oracle), with
 the scales of tests/helpers.state_l1 (vector components against their
 vector's scale, cleaning scalars and charge against their source fields).
