@@ -370,6 +370,19 @@ int rmhd_test_tile_copies(int enable);
 /* Testing: flux-kernel launches so far in this process that staged their
  * tiles by tensor-map copies. */
 long long rmhd_test_tile_copy_launches(void);
+/* Testing: the last part of the recovery's fallback chain (Sec. III.B has
+ * no fallback; the pressure bracket with the velocity solved at each trial
+ * pressure, then the atmosphere) on npts independent points of a flat
+ * metric, as the step's deferred passes run it: one thread per point
+ * (one_warp = 0) or one warp of 32 lanes per point (one_warp = 1).  Device
+ * pointers, layouts as rmhd_con2prim_points: cons[14][npts] (E slots hold
+ * calE*), guess[14][npts], sigma[npts]; outputs prim[14][npts],
+ * status[npts] (4 root found, 2 no root: atmosphere, 3 floor: atmosphere).
+ * Runs on stream.  Errors: RMHD_EINVAL as rmhd_con2prim_points. */
+int rmhd_test_bracket_points(const rmhd_params *p, int npts, const double *cons,
+                             const double *guess, const double *sigma, int implicit,
+                             double c, int one_warp, double *prim, int *status,
+                             void *cuda_stream);
 
 /* Text of the last error on this handle (never NULL; "" if none).  With
  * h == NULL: the last error, in the calling thread, of a call that had no

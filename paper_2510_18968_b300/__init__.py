@@ -63,7 +63,7 @@ EXPORTS = ("rmhd_default_params", "rmhd_create", "rmhd_set_metric", "rmhd_set_si
            "rmhd_set_state_layers", "rmhd_get_stats", "rmhd_step_profiled", "rmhd_rhs", "rmhd_con2prim_points",
            "rmhd_con2prim_points_noalloc", "rmhd_set_sigma0", "rmhd_adjoint_forward",
            "rmhd_adjoint_backward", "rmhd_test_rcp64", "rmhd_test_mm3", "rmhd_test_mm3f",
-           "rmhd_test_tile_copies", "rmhd_test_tile_copy_launches",
+           "rmhd_test_tile_copies", "rmhd_test_tile_copy_launches", "rmhd_test_bracket_points",
            "rmhd_last_error", "rmhd_destroy")
 
 _lib = None
@@ -113,6 +113,7 @@ def load(build_if_missing=True):
     L.rmhd_test_tile_copies.restype = ctypes.c_int
     L.rmhd_test_tile_copy_launches.argtypes = []
     L.rmhd_test_tile_copy_launches.restype = ctypes.c_longlong
+    L.rmhd_test_bracket_points.argtypes = [P, i, vp, vp, vp, i, d, i, vp, vp, vp]
     L.rmhd_last_error.argtypes = [vp]
     L.rmhd_last_error.restype = ctypes.c_char_p
     L.rmhd_destroy.argtypes = [vp]

@@ -365,10 +365,11 @@ __device__ __forceinline__ bool solve4(double A[16], double b[4], double x[4])
 // true): all 32 lanes of a warp hold the same record and take the same
 // branches; the independent evaluations of an iteration run side by side,
 // the forward-difference Jacobian's columns on lanes 0..2 and a line
-// search's candidate step lengths 2^-k, k = 0..39, on lane k mod 32.  The sequential search takes
-// the first k whose candidate is accepted; the warp takes the lowest
-// accepted k of each round of 32, which is the same k, with the same
-// arithmetic per candidate, so both forms make the same decisions.
+// search's candidate step lengths 2^-k, k = 0..39, on lane k mod 32.  The
+// sequential search takes the first k whose candidate is accepted; the warp
+// takes the lowest accepted k of each round of 32: the same k for the same
+// candidates.  The two compiled forms may round a candidate's residual
+// differently (fused multiply-adds), so their roots agree to rounding.
 constexpr unsigned WARP_ALL = 0xffffffffu;
 constexpr int LS_MAX = 40;   // step halvings of a line search
 

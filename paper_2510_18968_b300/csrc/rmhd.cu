@@ -845,6 +845,51 @@ k_recover_points(const RecOpts ro, int npts, const double *__restrict__ cons,
     status[t] = st;
 }
 
+// the pressure bracket and atmosphere of the fallback chain on independent
+// flat points (testing entry point): one thread per point, or (WARP) one
+// warp per point with lane 0 writing
+template <bool WARP>
+__global__ void __launch_bounds__(128)
+k_test_bracket_points(const RecOpts ro, int npts, const double *__restrict__ cons,
+                      const double *__restrict__ guess, const double *__restrict__ sigma,
+                      int implicit, double c, double *prim, int *status)
+{
+    const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+    const int t = WARP ? gt >> 5 : gt;
+    if (t >= npts) return;   // the whole warp when WARP
+    Met<double> m;
+    m.alpha = 1.0;
+    m.beta[0] = m.beta[1] = m.beta[2] = 0.0;
+    m.g[0] = m.g[3] = m.g[5] = 1.0;
+    m.g[1] = m.g[2] = m.g[4] = 0.0;
+    met_complete(m);
+    RecIn in;
+    in.D = cons[CO_D * npts + t];
+    in.tau = cons[CO_TAU * npts + t];
+    for (int a = 0; a < 3; a++) {
+        in.S[a] = cons[(CO_SX + a) * npts + t];
+        in.cB[a] = cons[(CO_BX + a) * npts + t];
+        in.cE0[a] = cons[(CO_EX + a) * npts + t];
+    }
+    const double gp = guess[PR_P * npts + t];
+    const double gv[3] = {guess[PR_VX * npts + t], guess[PR_VY * npts + t],
+                          guess[PR_VZ * npts + t]};
+    // a record whose paper iteration and both Newton methods gave up
+    PaperState ps = {};
+    ps.p = gp;
+    for (int a = 0; a < 3; a++) ps.v[a] = gv[a];
+    ps.outcome = 0;
+    double pr[NPR], E[3];
+    int it = 0;
+    const double cc = implicit ? c * sigma[t] : 0.0;
+    const int st = recover<true, WARP>(in, m, ro, implicit != 0, cc, gp, gv,
+                                       cons[CO_PHI * npts + t], cons[CO_PSI * npts + t],
+                                       cons[CO_Q * npts + t], pr, E, it, REC_CHAIN_REST, &ps);
+    if (WARP && (threadIdx.x & 31) != 0) return;
+    for (int f = 0; f < NPR; f++) prim[f * npts + t] = pr[f];
+    status[t] = st;
+}
+
 // parameters the pointwise recovery entry points use (rmhd_con2prim_points
 // and rmhd_con2prim_points_noalloc check the same set)
 __attribute__((visibility("hidden"))) bool rmhd_internal_recovery_params_ok(const rmhd_params *p)
@@ -923,6 +968,30 @@ __global__ void k_test_mm3f(long long n, const float *__restrict__ a,
 {
     const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (t < n) out[t] = mm3<float>(a[t], b[t], c[t]);
+}
+
+extern "C" int rmhd_test_bracket_points(const rmhd_params *p, int npts, const double *cons,
+                                        const double *guess, const double *sigma, int implicit,
+                                        double c, int one_warp, double *prim, int *status,
+                                        void *cuda_stream)
+{
+    rmhd_t h = nullptr;
+    if (!p) return set_err(h, RMHD_EINVAL, "params is NULL");
+    if (npts < 0) return set_err(h, RMHD_EINVAL, "npts < 0");
+    if (npts == 0) return RMHD_OK;
+    if (!cons || !guess || !prim || !status || (implicit && !sigma))
+        return set_err(h, RMHD_EINVAL, "NULL array");
+    if (!rmhd_internal_recovery_params_ok(p))
+        return set_err(h, RMHD_EINVAL, "recovery parameters out of range");
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    if (one_warp)
+        k_test_bracket_points<true><<<nblk(32LL * npts), TPB, 0, st>>>(
+            rec_opts(p), npts, cons, guess, sigma, implicit, c, prim, status);
+    else
+        k_test_bracket_points<false><<<nblk(npts), TPB, 0, st>>>(
+            rec_opts(p), npts, cons, guess, sigma, implicit, c, prim, status);
+    CK(cudaGetLastError());
+    return RMHD_OK;
 }
 
 extern "C" int rmhd_test_tile_copies(int enable)
